@@ -1,0 +1,197 @@
+/*
+ * idos.h - C ABI of the GB300 MLMC integrated-density-of-states library
+ * (libidos.so).
+ *
+ * The library computes, for honeycomb tight-binding sheets with random
+ * vacancies, the smoothed integrated density of states (IDoS) per unit area
+ * of eq. (4.1)-(4.2) of Plechac & von Schwerin, "Multi-level Monte Carlo
+ * acceleration of computations on multi-layer materials with random
+ * defects", sample by sample, and the multilevel Monte Carlo estimator of
+ * its expectation, eq. (2.6), with the control variates of Sec. 3.3.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an idos_status code: 0 = IDOS_OK, negative on
+ *    error.  No C++ exception crosses the ABI.  idos_status_string() gives a
+ *    static message; idos_last_error() gives the last detailed message of the
+ *    calling thread.
+ *  - All pointers named *_out / out and all input arrays are HOST pointers
+ *    owned by the caller, unless a parameter says otherwise.  The model owns
+ *    all device memory it allocates; nothing returned aliases it.
+ *  - A model runs every kernel on the CUDA stream given at creation (a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ *    that return host results synchronise that stream before returning.
+ *  - A model must not be used from two threads at once.
+ *  - Level index 0 is the paper's level l = 1 (the coarsest supercell).
+ *  - Units: eV, Angstrom; IDoS in states per Angstrom^2 (no spin factor).
+ *  - Site index inside an N x N supercell: m = 2(i + N j) + s, cell (i, j),
+ *    sublattice s (A = 0, B = 1); lattice a1 = a(1,0), a2 = a(1/2, sqrt3/2),
+ *    tau_B = (a1 + a2)/3.  k-points: K x K Monkhorst-Pack grid on the
+ *    supercell reciprocal cell, index i1 + K i2.
+ */
+#ifndef IDOS_H
+#define IDOS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IDOS_MAX_LEVELS 8
+
+enum idos_status {
+  IDOS_OK = 0,
+  IDOS_ERR_INVALID_ARG = -1,   /* bad pointer, size, level, or descriptor field */
+  IDOS_ERR_OUT_OF_MEMORY = -2, /* device or pinned allocation failed           */
+  IDOS_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed   */
+  IDOS_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up            */
+  IDOS_ERR_NOT_CONVERGED = -5, /* an iteration hit its limit                    */
+  IDOS_ERR_UNSUPPORTED = -6,   /* valid request this build does not implement   */
+  IDOS_ERR_NO_DEVICE = -7      /* no CUDA device of compute capability 10.3     */
+};
+
+enum idos_kind { IDOS_GRAPHENE = 0, IDOS_TMDC = 1 };
+
+/* Arithmetic of the per-k eigen-solve.
+ * IDOS_FP64: Householder reduction, Sturm bisection and smoothing in float64.
+ * IDOS_FP32_REFINE64: reduction and bisection in float32, then
+ *   refine64_iters float64 bisection steps on the float32 tridiagonal; the
+ *   smoothing argument and every sum are float64, erfc is evaluated in float32. */
+enum idos_precision { IDOS_FP64 = 0, IDOS_FP32_REFINE64 = 1 };
+
+/* Smoothed step g of eq. (4.2).
+ * IDOS_SMOOTH_GAUSS: g(x) = erfc(x / sqrt 2) / 2 (delta = standard deviation).
+ * IDOS_SMOOTH_POLY:  g(x) = 1/2 - 9x/8 + 5x^3/8 on [-1, 1], 1 below, 0 above
+ *                    (compact, both moment conditions of eq. (4.2)). */
+enum idos_smoothing { IDOS_SMOOTH_GAUSS = 0, IDOS_SMOOTH_POLY = 1 };
+
+/* Model description (Sec. 3.1-3.3, Sec. 4.2-4.3).  Plain data, copied by
+ * idos_create_model. */
+typedef struct idos_model_desc {
+  int32_t kind;        /* idos_kind                                         */
+  int32_t precision;   /* idos_precision                                    */
+  int32_t smoothing;   /* idos_smoothing                                    */
+  int32_t n_levels;    /* 1 .. IDOS_MAX_LEVELS                              */
+  int32_t N[IDOS_MAX_LEVELS];     /* supercell side per level; N[l] = 2 N[l-1]
+                                     when n_levels > 1 (Sec. 2.2, 3.3)       */
+  int32_t Kside[IDOS_MAX_LEVELS]; /* Monkhorst-Pack side per level (>= 1)    */
+  double t;            /* nearest-neighbour hopping, eq. (3.2b) (eV)        */
+  double eps_onsite;   /* on-site energy eps_2p, eq. (3.2a) (eV)            */
+  double a;            /* lattice constant (Angstrom)                       */
+  double p;            /* vacancy probability, Sec. 3.2, in [0, 1]          */
+  double sentinel;     /* diagonal of a removed site in idos_hamiltonian()  */
+  double e_min, e_max; /* energy grid eps_j = e_min + j (e_max-e_min)/(n_E-1) */
+  double delta;        /* smoothing width, eq. (4.2) (> 0)                  */
+  int32_t n_E;         /* number of energies, 2 .. 4096                     */
+  int32_t refine64_iters; /* float64 bisection steps in IDOS_FP32_REFINE64  */
+  uint64_t model_seed; /* parameter seed of the TMDC-shaped model           */
+  int64_t workspace_bytes; /* device workspace cap; 0 = library default      */
+} idos_model_desc;
+
+typedef struct idos_model idos_model;
+
+/* Create a model on the current CUDA device.  Validates d, allocates the
+ * level accumulators and a workspace.  *out receives the handle (NULL on
+ * error).  cuda_stream: cudaStream_t as void*, or NULL. */
+int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** out);
+
+/* Free every device buffer of the model (synchronises its stream). NULL ok. */
+void idos_destroy_model(idos_model* m);
+
+/* Static text for a status code. */
+const char* idos_status_string(int status);
+
+/* Detailed message of the last error on the calling thread ("" if none). */
+const char* idos_last_error(void);
+
+/* Draw n_samples outcomes of level `level` (sample indices first_sample ..
+ * first_sample + n_samples - 1, generator key `seed`), compute for each
+ *   Y = Q_l(omega) - (1/4) sum_r Q_{l-1}(omega; corner r)   (level >= 1)
+ *   Y = Q_0(omega)                                         (level == 0)
+ * (eq. (2.6) and the control variate of Sec. 3.3; corners use level l-1's
+ * Kside) and add sum Y, sum Y^2 (float64, fixed summation order) and the
+ * sample count to the model's level accumulators.
+ * per_sample_Y: NULL, or host float64[n_samples * n_E] receiving every Y.
+ * Errors: INVALID_ARG (level out of range, n_samples < 0), CUDA, OUT_OF_MEMORY. */
+int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed,
+                      int64_t first_sample, double* per_sample_Y);
+
+/* Same as idos_sample_level, but also returns the per-sample fine IDoS
+ * Q_l (host float64[n_samples * n_E], may be NULL) and the four corner IDoS
+ * (host float64[n_samples * 4 * n_E], corner r = ri + 2 rj, may be NULL;
+ * ignored on level 0).  Parity entry point. */
+int idos_sample_level_detail(idos_model* m, int level, int64_t n_samples, uint64_t seed,
+                             int64_t first_sample, double* per_sample_Y,
+                             double* Q_fine, double* Q_coarse);
+
+/* Read the accumulators of one level: *M samples, sum[n_E], sumsq[n_E]
+ * (host, may be NULL), *seconds of GPU time spent on the level (may be NULL). */
+int idos_get_level_stats(const idos_model* m, int level, int64_t* M, double* sum,
+                         double* sumsq, double* seconds);
+
+/* Zero the accumulators of one level, or of all levels when level == -1. */
+int idos_reset_level_stats(idos_model* m, int level);
+
+/* IDoS Q(eps_j) of eq. (4.1)-(4.2) for ONE supercell configuration: side N,
+ * Kside x Kside grid.  mask: host u8[2 N^2] (1 = site removed), or NULL to
+ * draw it from (seed, level, sample) exactly as idos_sample_level does.
+ * idos_out: host float64[n_E].  eigs_out: NULL or host float64[Kside^2 * 2N^2]:
+ * per k the ascending eigenvalues of the active block, then NaN padding to 2N^2. */
+int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_t seed,
+                   int level, int64_t sample, double* idos_out, double* eigs_out);
+
+/* Options of the adaptive estimator. */
+typedef struct idos_mlmc_opts {
+  double tol;            /* TOL of Sec. 2 (states / Angstrom^2)                  */
+  double theta;          /* statistical share of TOL (0 < theta < 1)             */
+  double c_alpha;        /* confidence quantile (1.96)                           */
+  int64_t pilot_samples; /* samples per level in the pilot round (>= 2)          */
+  int32_t work_model;    /* 0: W_l from the flop model sum n^3; 1: measured time */
+  int32_t max_rounds;    /* extra allocation rounds after the pilot (>= 1)       */
+  uint64_t seed;         /* generator key                                        */
+} idos_mlmc_opts;
+
+/* Result of the adaptive estimator; every array is caller-owned host memory. */
+typedef struct idos_estimate {
+  double* mean;    /* float64[n_E]: eq. (2.6)                               */
+  double* var;     /* float64[n_E]: sum_l V_l(eps)/M_l                       */
+  int64_t* M;      /* int64[n_levels]: samples used per level               */
+  double* V;       /* float64[n_levels]: max over eps of the level variance  */
+  double* W;       /* float64[n_levels]: work per sample used in eq. (2.7)   */
+  double seconds;  /* wall time of the call                                  */
+} idos_estimate;
+
+/* Adaptive MLMC (Sec. 2.2): pilot round of pilot_samples per level, V_l and
+ * W_l, M_l from eq. (2.7) with target variance (theta tol / c_alpha)^2, extra
+ * samples, combine by eq. (2.6).  Starts from zeroed accumulators.  Sample
+ * indices continue from 0 on every level. */
+int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* out);
+
+/* ---- parity / diagnostic entry points (same kernels as the hot path) ---- */
+
+/* Vacancy masks of samples first_sample .. first_sample + n_samples - 1 of
+ * `level` for an N x N cell: host u8[n_samples * 2 N^2] (1 = removed),
+ * computed on the device by the hot path's generator (Philox4x64-10, key
+ * (seed, 1), counter (site, sample, level, 0), vacant iff word0 < p 2^64). */
+int idos_vacancy_masks(idos_model* m, int N, int level, uint64_t seed, int64_t first_sample,
+                       int64_t n_samples, uint8_t* out);
+
+/* H(k) of eq. (3.2a)-(3.2b) for one configuration and one grid point, as the
+ * assembly kernel builds it, written as a full 2N^2 x 2N^2 complex128 matrix
+ * (row-major, interleaved re/im: host float64[2 * (2N^2)^2]) with removed
+ * sites' rows and columns zero and m->sentinel on their diagonal. */
+int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t* mask,
+                     double* out);
+
+/* All eigenvalues of `batch` dense Hermitian n x n matrices (host complex128,
+ * row-major, interleaved re/im, float64[batch * 2 n^2]) through the hot
+ * path's Householder reduction and Sturm bisection in `precision`; eigs_out:
+ * host float64[batch * n], ascending per matrix.  cuda_stream as above. */
+int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const double* H,
+                  double* eigs_out, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDOS_H */

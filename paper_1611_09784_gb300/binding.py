@@ -1,0 +1,246 @@
+"""ctypes binding of libidos.so: argument marshalling only.
+
+Every call goes straight to the C ABI declared in include/idos.h; outputs are
+numpy arrays allocated here and filled by the library.  CUDA streams are
+passed as integer handles (e.g. ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MAX_LEVELS = 8
+GRAPHENE, TMDC = 0, 1
+FP64, FP32_REFINE64 = 0, 1
+SMOOTH_GAUSS, SMOOTH_POLY = 0, 1
+_PRECISION = {"fp64": FP64, "fp32": FP32_REFINE64, FP64: FP64, FP32_REFINE64: FP32_REFINE64}
+_SMOOTHING = {"gauss": SMOOTH_GAUSS, "poly": SMOOTH_POLY, SMOOTH_GAUSS: SMOOTH_GAUSS, SMOOTH_POLY: SMOOTH_POLY}
+_KIND = {"graphene": GRAPHENE, "tmdc": TMDC, GRAPHENE: GRAPHENE, TMDC: TMDC}
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("precision", C.c_int32), ("smoothing", C.c_int32), ("n_levels", C.c_int32),
+        ("N", C.c_int32 * MAX_LEVELS), ("Kside", C.c_int32 * MAX_LEVELS),
+        ("t", C.c_double), ("eps_onsite", C.c_double), ("a", C.c_double), ("p", C.c_double),
+        ("sentinel", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double), ("delta", C.c_double),
+        ("n_E", C.c_int32), ("refine64_iters", C.c_int32), ("model_seed", C.c_uint64),
+        ("workspace_bytes", C.c_int64),
+    ]
+
+
+class MlmcOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("theta", C.c_double), ("c_alpha", C.c_double),
+                ("pilot_samples", C.c_int64), ("work_model", C.c_int32), ("max_rounds", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class Estimate(C.Structure):
+    _fields_ = [("mean", C.POINTER(C.c_double)), ("var", C.POINTER(C.c_double)),
+                ("M", C.POINTER(C.c_int64)), ("V", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
+                ("seconds", C.c_double)]
+
+
+class IdosError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {status_string(status)} ({status}): {detail}")
+        self.status = status
+
+
+_LIB = None
+_SYMBOLS = {
+    "idos_create_model": (C.c_int, [C.POINTER(ModelDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "idos_destroy_model": (None, [C.c_void_p]),
+    "idos_status_string": (C.c_char_p, [C.c_int]),
+    "idos_last_error": (C.c_char_p, []),
+    "idos_sample_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_int64, C.c_void_p]),
+    "idos_sample_level_detail": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_int64,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_get_level_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p,
+                                       C.POINTER(C.c_double)]),
+    "idos_reset_level_stats": (C.c_int, [C.c_void_p, C.c_int]),
+    "idos_eval_idos": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_uint64, C.c_int, C.c_int64,
+                                 C.c_void_p, C.c_void_p]),
+    "idos_mlmc_estimate": (C.c_int, [C.c_void_p, C.POINTER(MlmcOpts), C.POINTER(Estimate)]),
+    "idos_vacancy_masks": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int64, C.c_int64,
+                                     C.c_void_p]),
+    "idos_hamiltonian": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "libidos.so")
+
+
+def load_library():
+    """Load libidos.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(python -m paper_1611_09784_gb300.build)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SYMBOLS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load_library().idos_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        detail = load_library().idos_last_error().decode(errors="replace")
+        raise IdosError(status, where, detail)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def make_desc(cfg: dict) -> ModelDesc:
+    """ModelDesc from a plain dict (keys as in the C struct; levels as [(N, K), ...])."""
+    d = ModelDesc()
+    d.kind = _KIND[cfg.get("kind", "graphene")]
+    d.precision = _PRECISION[cfg.get("precision", "fp32")]
+    d.smoothing = _SMOOTHING[cfg.get("smoothing", "gauss")]
+    levels = cfg["levels"]
+    d.n_levels = len(levels)
+    for i, (N, K) in enumerate(levels):
+        d.N[i] = int(N)
+        d.Kside[i] = int(K)
+    d.t = float(cfg.get("t", -2.7))
+    d.eps_onsite = float(cfg.get("eps_onsite", 0.0))
+    d.a = float(cfg.get("a", 2.46))
+    d.p = float(cfg.get("p", 0.05))
+    d.sentinel = float(cfg.get("sentinel", 1.0e3))
+    d.e_min = float(cfg.get("e_min", -9.0))
+    d.e_max = float(cfg.get("e_max", 9.0))
+    d.delta = float(cfg.get("delta", 0.1))
+    d.n_E = int(cfg.get("n_E", 201))
+    d.refine64_iters = int(cfg.get("refine64_iters", 0))
+    d.model_seed = int(cfg.get("model_seed", 0))
+    d.workspace_bytes = int(cfg.get("workspace_bytes", 0))
+    return d
+
+
+class Model:
+    """Owner of one idos_model handle."""
+
+    def __init__(self, cfg: dict, stream: int | None = None):
+        lib = load_library()
+        self.cfg = dict(cfg)
+        self.desc = make_desc(cfg)
+        self.n_E = self.desc.n_E
+        self.n_levels = self.desc.n_levels
+        h = C.c_void_p()
+        _check(lib.idos_create_model(C.byref(self.desc), C.c_void_p(stream or 0), C.byref(h)),
+               "idos_create_model")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().idos_destroy_model(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sample_level(self, level: int, n_samples: int, seed: int, first_sample: int = 0,
+                     want_Y: bool = False):
+        Y = np.empty((n_samples, self.n_E)) if want_Y else None
+        _check(load_library().idos_sample_level(self._h, level, n_samples, seed, first_sample, _ptr(Y)),
+               "idos_sample_level")
+        return Y
+
+    def sample_level_detail(self, level: int, n_samples: int, seed: int, first_sample: int = 0):
+        Y = np.empty((n_samples, self.n_E))
+        Qf = np.empty((n_samples, self.n_E))
+        Qc = np.empty((n_samples, 4, self.n_E)) if level > 0 else None
+        _check(load_library().idos_sample_level_detail(self._h, level, n_samples, seed, first_sample,
+                                                       _ptr(Y), _ptr(Qf), _ptr(Qc)),
+               "idos_sample_level_detail")
+        return Y, Qf, Qc
+
+    def get_level_stats(self, level: int):
+        s1 = np.empty(self.n_E)
+        s2 = np.empty(self.n_E)
+        M = C.c_int64()
+        secs = C.c_double()
+        _check(load_library().idos_get_level_stats(self._h, level, C.byref(M), _ptr(s1), _ptr(s2),
+                                                   C.byref(secs)), "idos_get_level_stats")
+        return int(M.value), s1, s2, float(secs.value)
+
+    def reset_level_stats(self, level: int = -1):
+        _check(load_library().idos_reset_level_stats(self._h, level), "idos_reset_level_stats")
+
+    def eval_idos(self, N: int, K: int, mask=None, seed: int = 0, level: int = 0, sample: int = 0,
+                  want_eigs: bool = False):
+        Q = np.empty(self.n_E)
+        E = np.empty((K * K, 2 * N * N)) if want_eigs else None
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        _check(load_library().idos_eval_idos(self._h, N, K, _ptr(m), seed, level, sample, _ptr(Q), _ptr(E)),
+               "idos_eval_idos")
+        return (Q, E) if want_eigs else Q
+
+    def mlmc_estimate(self, tol: float, theta: float = 0.5, c_alpha: float = 1.96, pilot_samples: int = 16,
+                      work_model: int = 0, max_rounds: int = 3, seed: int = 0):
+        o = MlmcOpts(tol, theta, c_alpha, pilot_samples, work_model, max_rounds, seed)
+        mean = np.empty(self.n_E)
+        var = np.empty(self.n_E)
+        M = np.empty(self.n_levels, dtype=np.int64)
+        V = np.empty(self.n_levels)
+        W = np.empty(self.n_levels)
+        est = Estimate(mean.ctypes.data_as(C.POINTER(C.c_double)), var.ctypes.data_as(C.POINTER(C.c_double)),
+                       M.ctypes.data_as(C.POINTER(C.c_int64)), V.ctypes.data_as(C.POINTER(C.c_double)),
+                       W.ctypes.data_as(C.POINTER(C.c_double)), 0.0)
+        _check(load_library().idos_mlmc_estimate(self._h, C.byref(o), C.byref(est)), "idos_mlmc_estimate")
+        return {"mean": mean, "var": var, "M": M, "V": V, "W": W, "seconds": est.seconds}
+
+    def vacancy_masks(self, N: int, level: int, seed: int, first_sample: int, n_samples: int):
+        out = np.empty((n_samples, 2 * N * N), dtype=np.uint8)
+        _check(load_library().idos_vacancy_masks(self._h, N, level, seed, first_sample, n_samples, _ptr(out)),
+               "idos_vacancy_masks")
+        return out
+
+    def hamiltonian(self, N: int, K: int, k_index: int, mask):
+        n = 2 * N * N
+        out = np.empty((n, n), dtype=np.complex128)
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        _check(load_library().idos_hamiltonian(self._h, N, K, k_index, _ptr(m), _ptr(out)), "idos_hamiltonian")
+        return out
+
+
+def create_model(cfg: dict, stream: int | None = None) -> Model:
+    return Model(cfg, stream)
+
+
+def eigvalsh(H, precision="fp32", refine64_iters: int = 0, stream: int | None = None):
+    """Eigenvalues of a batch of Hermitian matrices through the GPU path."""
+    H = np.ascontiguousarray(H, dtype=np.complex128)
+    if H.ndim == 2:
+        H = H[None]
+    batch, n, _ = H.shape
+    out = np.empty((batch, n))
+    _check(load_library().idos_eigvalsh(_PRECISION[precision], refine64_iters, n, batch, _ptr(H), _ptr(out),
+                                        C.c_void_p(stream or 0)), "idos_eigvalsh")
+    return out

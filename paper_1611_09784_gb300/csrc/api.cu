@@ -1,0 +1,528 @@
+// api.cu - the C ABI of libidos: model lifetime, the per-level sampling
+// driver (eq. (2.6) with the control variates of Sec. 3.3), single
+// configuration evaluation, the adaptive MLMC estimator (Sec. 2.2,
+// eq. (2.7)) and the parity entry points.  Host code only; every arithmetic
+// step of the path runs in the kernels of k_*.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace idos {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* get_error() { return g_last_error.c_str(); }
+
+double cell_area(double a) { return 0.5 * std::sqrt(3.0) * a * a; }
+
+int Arena::reserve(size_t bytes, cudaStream_t s) {
+  if (bytes <= cap) return IDOS_OK;
+  IDOS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (base) IDOS_CUDA_TRY(cudaFree(base));
+  base = nullptr;
+  cap = 0;
+  const size_t want = std::max(bytes, size_t(64) << 20);
+  IDOS_CUDA_TRY(cudaMalloc(&base, want));
+  cap = want;
+  used = 0;
+  return IDOS_OK;
+}
+
+void Arena::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+  cap = used = 0;
+}
+
+namespace {
+
+constexpr size_t kDefaultWorkspace = size_t(3) << 30;   // 3 GiB
+constexpr size_t kSmallBudget = size_t(768) << 20;      // per-chunk small buffers
+
+int check_device(int& sm_count) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    return IDOS_ERR_NO_DEVICE;
+  }
+  cudaDeviceProp p;
+  IDOS_CUDA_TRY(cudaGetDeviceProperties(&p, dev));
+  if (p.major != 10 || p.minor != 3) {
+    set_error("libidos is built for sm_103a (GB300); device reports compute capability " +
+              std::to_string(p.major) + "." + std::to_string(p.minor));
+    return IDOS_ERR_NO_DEVICE;
+  }
+  sm_count = p.multiProcessorCount;
+  return IDOS_OK;
+}
+
+int validate(const idos_model_desc* d) {
+  auto bad = [](const char* m) { set_error(m); return IDOS_ERR_INVALID_ARG; };
+  if (!d) return bad("null descriptor");
+  if (d->kind != IDOS_GRAPHENE) {
+    set_error("only the graphene model is implemented in this build");
+    return IDOS_ERR_UNSUPPORTED;
+  }
+  if (d->precision != IDOS_FP64 && d->precision != IDOS_FP32_REFINE64) return bad("precision");
+  if (d->smoothing != IDOS_SMOOTH_GAUSS && d->smoothing != IDOS_SMOOTH_POLY) return bad("smoothing");
+  if (d->n_levels < 1 || d->n_levels > IDOS_MAX_LEVELS) return bad("n_levels out of range");
+  for (int l = 0; l < d->n_levels; ++l) {
+    if (d->N[l] < 1 || d->N[l] > 64) return bad("N[l] must lie in 1..64");
+    if (d->Kside[l] < 1 || d->Kside[l] > 64) return bad("Kside[l] must lie in 1..64");
+    if (l > 0 && d->N[l] != 2 * d->N[l - 1]) return bad("N[l] must equal 2 N[l-1]");
+  }
+  if (!(d->p >= 0.0 && d->p <= 1.0)) return bad("p must lie in [0, 1]");
+  if (!(d->delta > 0.0)) return bad("delta must be positive");
+  if (!(d->e_max > d->e_min)) return bad("e_max must exceed e_min");
+  if (d->n_E < 2 || d->n_E > 1024) return bad("n_E must lie in 2..1024");
+  if (d->refine64_iters < 0 || d->refine64_iters > 64) return bad("refine64_iters must lie in 0..64");
+  if (!(d->a > 0.0)) return bad("lattice constant must be positive");
+  return IDOS_OK;
+}
+
+size_t tsize(int precision) { return precision == IDOS_FP64 ? 8 : 4; }
+
+EnergyGrid grid_of(const idos_model_desc& d) {
+  return EnergyGrid{d.e_min, d.e_max, d.delta, d.n_E, d.smoothing, d.precision == IDOS_FP32_REFINE64 ? 1 : 0};
+}
+
+// Eigen-solve + IDoS of every cell of `cells` on a Kside grid: Q[count][n_E].
+// `eigs_keep` (optional) receives the device eigenvalue buffer pointer.
+int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double** eigs_keep) {
+  const int n_max = cells.n_sites;
+  const int K2 = Kside * Kside;
+  const int64_t n_mat = cells.count * (int64_t)K2;
+  const size_t ts = tsize(M->d.precision);
+  void* d = M->ws.take<char>(ts * n_mat * n_max);
+  void* e2 = M->ws.take<char>(ts * n_mat * n_max);
+  double* eigs = M->ws.take<double>((size_t)n_mat * n_max);
+  if (!d || !e2 || !eigs) {
+    set_error("workspace too small for the eigen-solve buffers");
+    return IDOS_ERR_OUT_OF_MEMORY;
+  }
+  SolveArgs a;
+  a.cells = &cells;
+  a.Kside = Kside;
+  a.n_max = n_max;
+  a.n_mat = n_mat;
+  a.t = M->d.t;
+  a.eps = M->d.eps_onsite;
+  a.d = d;
+  a.e2 = e2;
+  a.stream = M->stream;
+  a.ws = &M->ws;
+  if (small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
+  else IDOS_TRY(solve_large(M->d.precision, a));
+  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs,
+                         M->stream));
+  const double area = (double)cells.N * cells.N * cell_area(M->d.a);
+  IDOS_TRY(launch_idos(eigs, cells.n_act, K2, n_max, cells.count, area, grid_of(M->d), Q, M->stream));
+  if (eigs_keep) *eigs_keep = eigs;
+  return IDOS_OK;
+}
+
+bool take_cells(Arena& ws, CellSet& c, int N, int64_t count) {
+  c.N = N;
+  c.n_sites = 2 * N * N;
+  c.count = count;
+  c.mask = ws.take<uint8_t>((size_t)count * c.n_sites);
+  c.n_act = ws.take<int>((size_t)count);
+  c.act = ws.take<int>((size_t)count * c.n_sites);
+  c.inv = ws.take<int>((size_t)count * c.n_sites);
+  return c.mask && c.n_act && c.act && c.inv;
+}
+
+size_t cells_bytes(int N, int64_t count) {
+  const size_t ns = 2 * (size_t)N * N;
+  return count * (ns * 9 + 4) + 4 * 256;
+}
+
+size_t solve_bytes(int precision, int N, int Kside, int64_t count, int n_E) {
+  const size_t ns = 2 * (size_t)N * N;
+  const size_t nmat = (size_t)count * Kside * Kside;
+  return nmat * ns * (2 * tsize(precision) + 8) + count * (size_t)n_E * 8 + 3 * 256;
+}
+
+// Room the large-matrix path wants for its dense batch (0 if the small path runs).
+size_t large_room(const Model* M, int N, int Kside, int64_t count) {
+  const int n = 2 * N * N;
+  if (small_path_fits(M->d.precision, n)) return 0;
+  const size_t per = 2 * tsize(M->d.precision) * ((size_t)n * n + 80 * (size_t)n) + 4096;
+  const size_t cap = M->d.workspace_bytes > 0 ? (size_t)M->d.workspace_bytes : kDefaultWorkspace;
+  const size_t want = per * (size_t)count * Kside * Kside;
+  return std::max(per, std::min(want, cap));
+}
+
+int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh,
+              double* Qfh, double* Qch) {
+  const idos_model_desc& d = M->d;
+  const int Nf = d.N[level], Kf = d.Kside[level];
+  const bool coarse = level > 0;
+  const int Nc = coarse ? Nf / 2 : 0, Kc = coarse ? d.Kside[level - 1] : 0;
+  const int n_E = d.n_E;
+  const size_t per_sample = cells_bytes(Nf, 1) + solve_bytes(d.precision, Nf, Kf, 1, n_E) +
+                            (coarse ? cells_bytes(Nc, 4) + solve_bytes(d.precision, Nc, Kc, 4, n_E) : 0) +
+                            3 * n_E * sizeof(double);
+  int64_t chunk = std::max<int64_t>(1, (int64_t)(kSmallBudget / per_sample));
+  chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_samples, 1));
+  IDOS_CUDA_TRY(cudaEventRecord(M->ev0, M->stream));
+  for (int64_t s0 = 0; s0 < n_samples; s0 += chunk) {
+    const int64_t S = std::min(chunk, n_samples - s0);
+    const size_t need = S * per_sample + 64 * 1024 + ((S + 63) / 64) * 2 * n_E * 8 +
+                        std::max(large_room(M, Nf, Kf, S), coarse ? large_room(M, Nc, Kc, 4 * S) : 0);
+    IDOS_TRY(M->ws.reserve(need, M->stream));
+    M->ws.reset();
+    CellSet fine, crs;
+    if (!take_cells(M->ws, fine, Nf, S)) { set_error("workspace (fine cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
+    double* Qf = M->ws.take<double>((size_t)S * n_E);
+    double* Y = M->ws.take<double>((size_t)S * n_E);
+    double* Qc = nullptr;
+    if (coarse) {
+      if (!take_cells(M->ws, crs, Nc, 4 * S)) { set_error("workspace (corner cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
+      Qc = M->ws.take<double>((size_t)4 * S * n_E);
+    }
+    if (!Qf || !Y || (coarse && !Qc)) { set_error("workspace (IDoS buffers)"); return IDOS_ERR_OUT_OF_MEMORY; }
+    IDOS_TRY(launch_fine_masks(fine.mask, fine.n_sites, S, seed, level, first + s0, d.p, M->stream));
+    IDOS_TRY(launch_cell_maps(fine, M->stream));
+    if (coarse) {
+      IDOS_TRY(launch_corner_masks(fine.mask, Nf, S, crs.mask, M->stream));
+      IDOS_TRY(launch_cell_maps(crs, M->stream));
+    }
+    // the large path takes its dense batch from whatever is left, so the
+    // bigger solve goes last
+    const size_t mark = M->ws.used;
+    if (coarse) {
+      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr));
+      M->ws.used = mark;
+    }
+    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr));
+    M->ws.used = mark;
+    double* acc = M->acc + (size_t)level * 2 * n_E;
+    IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, M->ws, M->stream));
+    if (Yh) IDOS_CUDA_TRY(cudaMemcpyAsync(Yh + s0 * n_E, Y, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, M->stream));
+    if (Qfh) IDOS_CUDA_TRY(cudaMemcpyAsync(Qfh + s0 * n_E, Qf, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, M->stream));
+    if (Qch && coarse)
+      IDOS_CUDA_TRY(cudaMemcpyAsync(Qch + s0 * 4 * n_E, Qc, sizeof(double) * 4 * S * n_E, cudaMemcpyDeviceToHost, M->stream));
+    if (Yh || Qfh || Qch) IDOS_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  }
+  IDOS_CUDA_TRY(cudaEventRecord(M->ev1, M->stream));
+  IDOS_CUDA_TRY(cudaEventSynchronize(M->ev1));
+  float ms = 0.f;
+  IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, M->ev0, M->ev1));
+  M->M[level] += n_samples;
+  M->seconds[level] += ms * 1e-3;
+  return IDOS_OK;
+}
+
+double flop_model(const idos_model_desc& d, int level) {
+  // work per sample ~ sum over eigen-solves of n^3 (Sec. 4.4: cost per solve ~ N^6)
+  auto cube = [](double x) { return x * x * x; };
+  const double nf = 2.0 * d.N[level] * d.N[level];
+  double w = (double)d.Kside[level] * d.Kside[level] * cube(nf);
+  if (level > 0) {
+    const double nc = nf / 4.0;
+    w += 4.0 * d.Kside[level - 1] * d.Kside[level - 1] * cube(nc);
+  }
+  return w;
+}
+
+}  // namespace
+}  // namespace idos
+
+using namespace idos;
+
+struct idos_model : public idos::Model {};
+
+extern "C" {
+
+const char* idos_status_string(int status) {
+  switch (status) {
+    case IDOS_OK: return "ok";
+    case IDOS_ERR_INVALID_ARG: return "invalid argument";
+    case IDOS_ERR_OUT_OF_MEMORY: return "out of memory";
+    case IDOS_ERR_CUDA: return "CUDA error";
+    case IDOS_ERR_TIMEOUT: return "device wait timed out";
+    case IDOS_ERR_NOT_CONVERGED: return "not converged";
+    case IDOS_ERR_UNSUPPORTED: return "unsupported";
+    case IDOS_ERR_NO_DEVICE: return "no sm_103 device";
+    default: return "unknown status";
+  }
+}
+
+const char* idos_last_error(void) { return get_error(); }
+
+int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** out) {
+  if (!out) { set_error("null output handle"); return IDOS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  IDOS_TRY(validate(d));
+  int sms = 0;
+  IDOS_TRY(check_device(sms));
+  idos_model* m = new idos_model();
+  m->d = *d;
+  m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  m->sm_count = sms;
+  const size_t acc_bytes = sizeof(double) * 2 * d->n_E * d->n_levels;
+  cudaError_t e = cudaMalloc(&m->acc, acc_bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->acc, 0, acc_bytes, m->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    set_error(std::string("model allocation: ") + cudaGetErrorString(e));
+    idos_destroy_model(m);
+    return e == cudaErrorMemoryAllocation ? IDOS_ERR_OUT_OF_MEMORY : IDOS_ERR_CUDA;
+  }
+  *out = m;
+  return IDOS_OK;
+}
+
+void idos_destroy_model(idos_model* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  if (m->acc) cudaFree(m->acc);
+  if (m->ev0) cudaEventDestroy(m->ev0);
+  if (m->ev1) cudaEventDestroy(m->ev1);
+  m->ws.release();
+  delete m;
+}
+
+int idos_sample_level_detail(idos_model* m, int level, int64_t n_samples, uint64_t seed, int64_t first_sample,
+                             double* per_sample_Y, double* Q_fine, double* Q_coarse) {
+  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  if (level < 0 || level >= m->d.n_levels) { set_error("level out of range"); return IDOS_ERR_INVALID_ARG; }
+  if (n_samples < 0 || first_sample < 0) { set_error("negative sample count or index"); return IDOS_ERR_INVALID_ARG; }
+  if (n_samples == 0) return IDOS_OK;
+  return run_level(m, level, n_samples, seed, first_sample, per_sample_Y, Q_fine, Q_coarse);
+}
+
+int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed, int64_t first_sample,
+                      double* per_sample_Y) {
+  return idos_sample_level_detail(m, level, n_samples, seed, first_sample, per_sample_Y, nullptr, nullptr);
+}
+
+int idos_get_level_stats(const idos_model* m, int level, int64_t* M, double* sum, double* sumsq,
+                         double* seconds) {
+  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  if (level < 0 || level >= m->d.n_levels) { set_error("level out of range"); return IDOS_ERR_INVALID_ARG; }
+  const int n_E = m->d.n_E;
+  const double* acc = m->acc + (size_t)level * 2 * n_E;
+  if (sum) IDOS_CUDA_TRY(cudaMemcpyAsync(sum, acc, sizeof(double) * n_E, cudaMemcpyDeviceToHost, m->stream));
+  if (sumsq) IDOS_CUDA_TRY(cudaMemcpyAsync(sumsq, acc + n_E, sizeof(double) * n_E, cudaMemcpyDeviceToHost, m->stream));
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (M) *M = m->M[level];
+  if (seconds) *seconds = m->seconds[level];
+  return IDOS_OK;
+}
+
+int idos_reset_level_stats(idos_model* m, int level) {
+  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  if (level < -1 || level >= m->d.n_levels) { set_error("level out of range"); return IDOS_ERR_INVALID_ARG; }
+  const int n_E = m->d.n_E;
+  const int l0 = level < 0 ? 0 : level, l1 = level < 0 ? m->d.n_levels : level + 1;
+  for (int l = l0; l < l1; ++l) {
+    IDOS_CUDA_TRY(cudaMemsetAsync(m->acc + (size_t)l * 2 * n_E, 0, sizeof(double) * 2 * n_E, m->stream));
+    m->M[l] = 0;
+    m->seconds[l] = 0.0;
+  }
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return IDOS_OK;
+}
+
+int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_t seed, int level,
+                   int64_t sample, double* idos_out, double* eigs_out) {
+  if (!m || !idos_out) { set_error("null model or output"); return IDOS_ERR_INVALID_ARG; }
+  if (N < 1 || N > 64 || Kside < 1 || Kside > 64 || sample < 0) { set_error("N, Kside or sample out of range"); return IDOS_ERR_INVALID_ARG; }
+  const int n_E = m->d.n_E;
+  const size_t need = cells_bytes(N, 1) + solve_bytes(m->d.precision, N, Kside, 1, n_E) + 8 * n_E + 65536 +
+                      large_room(m, N, Kside, 1);
+  IDOS_TRY(m->ws.reserve(need, m->stream));
+  m->ws.reset();
+  CellSet c;
+  if (!take_cells(m->ws, c, N, 1)) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
+  double* Q = m->ws.take<double>(n_E);
+  if (!Q) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
+  if (mask) {
+    IDOS_CUDA_TRY(cudaMemcpyAsync(c.mask, mask, c.n_sites, cudaMemcpyHostToDevice, m->stream));
+  } else {
+    IDOS_TRY(launch_fine_masks(c.mask, c.n_sites, 1, seed, level, sample, m->d.p, m->stream));
+  }
+  IDOS_TRY(launch_cell_maps(c, m->stream));
+  double* eigs = nullptr;
+  IDOS_TRY(solve_and_idos(m, c, Kside, Q, &eigs));
+  IDOS_CUDA_TRY(cudaMemcpyAsync(idos_out, Q, sizeof(double) * n_E, cudaMemcpyDeviceToHost, m->stream));
+  if (eigs_out)
+    IDOS_CUDA_TRY(cudaMemcpyAsync(eigs_out, eigs, sizeof(double) * Kside * Kside * c.n_sites,
+                                  cudaMemcpyDeviceToHost, m->stream));
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return IDOS_OK;
+}
+
+int idos_vacancy_masks(idos_model* m, int N, int level, uint64_t seed, int64_t first_sample, int64_t n_samples,
+                       uint8_t* out) {
+  if (!m || !out) { set_error("null model or output"); return IDOS_ERR_INVALID_ARG; }
+  if (N < 1 || N > 64 || n_samples < 0 || first_sample < 0) { set_error("bad size"); return IDOS_ERR_INVALID_ARG; }
+  const size_t bytes = (size_t)n_samples * 2 * N * N;
+  IDOS_TRY(m->ws.reserve(bytes + 4096, m->stream));
+  m->ws.reset();
+  uint8_t* buf = m->ws.take<uint8_t>(bytes);
+  if (!buf) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
+  IDOS_TRY(launch_fine_masks(buf, 2 * N * N, n_samples, seed, level, first_sample, m->d.p, m->stream));
+  IDOS_CUDA_TRY(cudaMemcpyAsync(out, buf, bytes, cudaMemcpyDeviceToHost, m->stream));
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return IDOS_OK;
+}
+
+int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t* mask, double* out) {
+  if (!m || !mask || !out) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
+  if (N < 1 || N > 32 || Kside < 1 || k_index < 0 || k_index >= Kside * Kside) {
+    set_error("N (<= 32), Kside or k_index out of range");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  const int n = 2 * N * N;
+  IDOS_TRY(m->ws.reserve(cells_bytes(N, 1) + sizeof(double2) * (size_t)n * n + 8192, m->stream));
+  m->ws.reset();
+  CellSet c;
+  if (!take_cells(m->ws, c, N, 1)) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
+  double2* H = m->ws.take<double2>((size_t)n * n);
+  if (!H) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
+  IDOS_CUDA_TRY(cudaMemcpyAsync(c.mask, mask, n, cudaMemcpyHostToDevice, m->stream));
+  SolveArgs a;
+  a.cells = &c;
+  a.Kside = Kside;
+  a.t = m->d.t;
+  a.eps = m->d.eps_onsite;
+  a.stream = m->stream;
+  IDOS_TRY(launch_assemble_dense(a, k_index, H, m->d.sentinel));
+  IDOS_CUDA_TRY(cudaMemcpyAsync(out, H, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToHost, m->stream));
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return IDOS_OK;
+}
+
+int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const double* H, double* eigs_out,
+                  void* cuda_stream) {
+  if (!H || !eigs_out) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
+  if (precision != IDOS_FP64 && precision != IDOS_FP32_REFINE64) { set_error("precision"); return IDOS_ERR_INVALID_ARG; }
+  if (n < 1 || n > 8192 || batch < 0 || refine64_iters < 0 || refine64_iters > 64) {
+    set_error("n, batch or refine64_iters out of range");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  if (batch == 0) return IDOS_OK;
+  int sms = 0;
+  IDOS_TRY(check_device(sms));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  Arena ws;
+  const size_t nn = (size_t)n * n;
+  const size_t ts = tsize(precision);
+  const bool small = small_path_fits(precision, n);
+  const size_t large = small ? 0 : 2 * ts * (nn + 80 * (size_t)n) * (size_t)std::min<int64_t>(batch, 8) + 8192;
+  const size_t need = sizeof(double2) * nn * batch + batch * (size_t)n * (2 * ts + 8) + large + 65536;
+  int st = ws.reserve(need, s);
+  if (st != IDOS_OK) return st;
+  double2* Hd = ws.take<double2>(nn * batch);
+  void* d = ws.take<char>(ts * batch * n);
+  void* e2 = ws.take<char>(ts * batch * n);
+  double* eigs = ws.take<double>((size_t)batch * n);
+  int rc = IDOS_OK;
+  if (!Hd || !d || !e2 || !eigs) { set_error("workspace"); rc = IDOS_ERR_OUT_OF_MEMORY; }
+  if (rc == IDOS_OK) {
+    cudaError_t e = cudaMemcpyAsync(Hd, H, sizeof(double2) * nn * batch, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = IDOS_ERR_CUDA; }
+  }
+  if (rc == IDOS_OK) {
+    SolveArgs a;
+    a.Kside = 1;
+    a.n_max = n;
+    a.n_mat = batch;
+    a.H = Hd;
+    a.d = d;
+    a.e2 = e2;
+    a.stream = s;
+    a.ws = &ws;
+    rc = small ? solve_small(precision, a) : solve_large(precision, a);
+  }
+  if (rc == IDOS_OK) rc = launch_bisect(precision, refine64_iters, d, e2, nullptr, 1, n, batch, eigs, s);
+  if (rc == IDOS_OK) {
+    cudaError_t e = cudaMemcpyAsync(eigs_out, eigs, sizeof(double) * batch * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = IDOS_ERR_CUDA; }
+  }
+  cudaStreamSynchronize(s);
+  ws.release();
+  return rc;
+}
+
+int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* out) {
+  if (!m || !o || !out || !out->mean || !out->var) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
+  if (!(o->tol > 0) || !(o->theta > 0 && o->theta < 1) || !(o->c_alpha > 0) || o->pilot_samples < 2 ||
+      o->max_rounds < 1) {
+    set_error("tol, theta, c_alpha, pilot_samples (>= 2) or max_rounds (>= 1) out of range");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  const int L = m->d.n_levels, n_E = m->d.n_E;
+  IDOS_TRY(idos_reset_level_stats(m, -1));
+  std::vector<double> sum(n_E), sq(n_E);
+  std::vector<double> V(L), W(L);
+  std::vector<int64_t> target(L, o->pilot_samples);
+  for (int round = 0; round <= o->max_rounds; ++round) {
+    for (int l = 0; l < L; ++l) {
+      const int64_t extra = target[l] - m->M[l];
+      if (extra > 0) IDOS_TRY(idos_sample_level(m, l, extra, o->seed, m->M[l], nullptr));
+    }
+    if (round == o->max_rounds) break;
+    // V_l (max over the grid of the unbiased sample variance), W_l
+    for (int l = 0; l < L; ++l) {
+      int64_t M = 0;
+      double secs = 0;
+      IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
+      double vmax = 0.0;
+      for (int j = 0; j < n_E; ++j) {
+        const double mean = sum[j] / M;
+        const double v = std::max(0.0, (sq[j] - M * mean * mean) / (M - 1));
+        vmax = std::max(vmax, v);
+      }
+      V[l] = std::max(vmax, 1e-300);
+      W[l] = o->work_model == 1 ? std::max(secs / M, 1e-12) : flop_model(m->d, l);
+    }
+    // eq. (2.7)
+    double s = 0.0;
+    for (int l = 0; l < L; ++l) s += std::sqrt(W[l] * V[l]);
+    const double f = (o->c_alpha / (o->theta * o->tol)) * (o->c_alpha / (o->theta * o->tol));
+    bool more = false;
+    for (int l = 0; l < L; ++l) {
+      const int64_t Ml = std::max<int64_t>(2, (int64_t)std::ceil(f * std::sqrt(V[l] / W[l]) * s));
+      if (Ml > m->M[l]) more = true;
+      target[l] = std::max(target[l], Ml);
+    }
+    if (!more) break;
+  }
+  // combine, eq. (2.6)
+  std::fill(out->mean, out->mean + n_E, 0.0);
+  std::fill(out->var, out->var + n_E, 0.0);
+  for (int l = 0; l < L; ++l) {
+    int64_t M = 0;
+    double secs = 0;
+    IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
+    double vmax = 0.0;
+    for (int j = 0; j < n_E; ++j) {
+      const double mean = sum[j] / M;
+      const double v = std::max(0.0, (sq[j] - M * mean * mean) / (M - 1));
+      out->mean[j] += mean;
+      out->var[j] += v / M;
+      vmax = std::max(vmax, v);
+    }
+    if (out->M) out->M[l] = M;
+    if (out->V) out->V[l] = vmax;
+    if (out->W) out->W[l] = o->work_model == 1 ? secs / M : flop_model(m->d, l);
+  }
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return IDOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// internal.h - host-side declarations shared by the libidos translation units:
+// the model object behind the C ABI, the device workspace arena and the
+// kernel launchers of each stage of the path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/idos.h"
+#include "common.cuh"
+
+namespace idos {
+
+// Bump allocator over one device buffer.  reset() at the start of every API
+// call; grow() reallocates (after a stream sync) when a call needs more.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  size_t peak = 0;
+  int reserve(size_t bytes, cudaStream_t s);   // ensure capacity >= bytes
+  void reset() { used = 0; }
+  template <typename T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    size_t need = off + count * sizeof(T);
+    if (need > cap) return nullptr;
+    used = need;
+    if (used > peak) peak = used;
+    return reinterpret_cast<T*>(base + off);
+  }
+  void release();
+};
+
+// One set of supercell configurations of equal side N ("cells"): vacancy
+// masks and the compaction maps from site index to active row.
+struct CellSet {
+  int N = 0;
+  int n_sites = 0;   // 2 N^2
+  int64_t count = 0;
+  uint8_t* mask = nullptr;  // [count][n_sites], 1 = removed
+  int* n_act = nullptr;     // [count]
+  int* act = nullptr;       // [count][n_sites] active sites, ascending
+  int* inv = nullptr;       // [count][n_sites] site -> active row, or -1
+};
+
+// Inputs of one batched eigen-solve: every cell of a CellSet at every point
+// of a Kside x Kside grid (matrix index = cell * K^2 + k), or `count`
+// explicit Hermitian matrices (H != nullptr, Kside = 1, n_act = n_max).
+struct SolveArgs {
+  const CellSet* cells = nullptr;
+  int Kside = 1;
+  int n_max = 0;            // matrix dimension capacity = 2 N^2
+  int64_t n_mat = 0;
+  double t = 0, eps = 0;    // hopping and on-site energy
+  const double2* H = nullptr;
+  void* d = nullptr;        // T[n_mat][n_max] diagonal of the tridiagonal
+  void* e2 = nullptr;       // T[n_mat][n_max] squared off-diagonal (e2[i] couples i, i+1)
+  cudaStream_t stream = 0;
+  Arena* ws = nullptr;
+};
+
+struct Model {
+  idos_model_desc d{};
+  cudaStream_t stream = 0;
+  double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
+  int64_t M[IDOS_MAX_LEVELS] = {};
+  double seconds[IDOS_MAX_LEVELS] = {};
+  Arena ws;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int sm_count = 0;
+};
+
+// ---- stage launchers (return idos_status) ----
+int launch_fine_masks(uint8_t* out, int n_sites, int64_t count, uint64_t seed, int level,
+                      int64_t first_sample, double p, cudaStream_t s);
+int launch_corner_masks(const uint8_t* fine, int N, int64_t count, uint8_t* out, cudaStream_t s);
+int launch_cell_maps(CellSet& c, cudaStream_t s);
+int launch_assemble_dense(const SolveArgs& a, int k_index, double2* out, double sentinel);
+
+// Householder reduction to real symmetric tridiagonal (d, e^2).
+bool small_path_fits(int precision, int n_max);
+int solve_small(int precision, const SolveArgs& a);
+int solve_large(int precision, const SolveArgs& a);
+
+// Sturm-count bisection: eigs[mat][n_max] ascending, NaN beyond n_act.
+int launch_bisect(int precision, int refine64_iters, const void* d, const void* e2,
+                  const int* n_act_cell, int K2, int n_max, int64_t n_mat, double* eigs,
+                  cudaStream_t s);
+
+// Smoothed IDoS per cell (eq. (4.1)-(4.2)): Q[cell][n_E].
+struct EnergyGrid { double e_min, e_max, delta; int n_E; int smoothing; int fp32_erfc; };
+int launch_idos(const double* eigs, const int* n_act_cell, int K2, int n_max, int64_t n_cells,
+                double area, const EnergyGrid& g, double* Q, cudaStream_t s);
+
+// Level difference and float64 statistics: Y = Qf - (1/4) sum_r Qc[r] (or Qf),
+// acc[0][j] += sum_s Y, acc[1][j] += sum_s Y^2, optional Y export.
+int launch_level_stats(const double* Qf, const double* Qc, int64_t S, int n_E, double* Y,
+                       double* acc, Arena& ws, cudaStream_t s);
+
+double cell_area(double a);   // |a1 x a2| = sqrt(3)/2 a^2
+
+}  // namespace idos

@@ -1,0 +1,215 @@
+// k_small.cu - fused H(k) assembly + Householder tridiagonalisation of small
+// Hermitian matrices held entirely in shared memory (one thread group per
+// matrix, several groups per CTA).
+//
+// H(k) (eq. (3.2a)-(3.2b)) is built directly in shared memory on the kept
+// sites only (vacancies compacted out, Sec. 3.2), so it never touches HBM.
+// The reduction is the unblocked Householder method with a real scaling
+// factor: for column j, with x = A[j+1:, j], sigma = ||x||, phase ph = x_1/|x_1|,
+//   v = x + ph sigma e_1,  tau = 1 / (sigma (sigma + |x_1|)),  P = I - tau v v^H,
+// P x = -ph sigma e_1, so the Hermitian tridiagonal has |e_j| = sigma and
+// its eigenvalues are those of the real symmetric (d, |e|).  The two-sided
+// update uses p = tau A22 v, K = tau/2 Re(v^H p), w = p - K v,
+// A22 <- A22 - v w^H - w v^H, fused with the next step's product: each step
+// reads and writes the trailing block once.
+#include <cfloat>
+
+#include "graphene.cuh"
+#include "internal.h"
+
+namespace idos {
+
+namespace {
+
+template <typename T>
+struct SmallLayout {
+  // per group: A[n_max * n_max], v[2][n_max], w[2][n_max] (complex), scratch
+  __host__ __device__ static size_t bytes(int n_max) {
+    const size_t b = sizeof(c2<T>) * ((size_t)n_max * n_max + 4 * (size_t)n_max + 3) + sizeof(T) * 64;
+    return (b + 15) & ~size_t(15);
+  }
+};
+
+template <typename T, int NT, int MPB>
+__global__ void __launch_bounds__(NT* MPB)
+k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
+                const int* __restrict__ inv, int N, int K, int n_max, int64_t n_mat, double t_hop,
+                double eps, const double2* __restrict__ Hin, T* __restrict__ d_out,
+                T* __restrict__ e2_out) {
+  using C = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int gid = threadIdx.x / NT;
+  const int tid = threadIdx.x % NT;
+  const int64_t mat = (int64_t)blockIdx.x * MPB + gid;
+  if (mat >= n_mat) return;   // whole group leaves together
+
+  unsigned char* base = smem_raw + (size_t)gid * SmallLayout<T>::bytes(n_max);
+  C* A = reinterpret_cast<C*>(base);
+  C* vb0 = A + (size_t)n_max * n_max;
+  C* vb1 = vb0 + n_max;
+  C* wb0 = vb1 + n_max;
+  C* wb1 = wb0 + n_max;
+  C* ph = wb1 + n_max;
+  T* scratch = reinterpret_cast<T*>(ph + 3);
+
+  const int K2 = K * K;
+  const int64_t cell = mat / K2;
+  const int kidx = (int)(mat - cell * K2);
+  const int n = Hin ? n_max : n_act_cell[cell];
+  T* dO = d_out + mat * n_max;
+  T* eO = e2_out + mat * n_max;
+  if (n <= 0) return;
+
+  // ---------------------------------------------------------- assembly ---
+  if (Hin) {
+    const double2* src = Hin + mat * (int64_t)n * n;
+    for (int i = tid; i < n * n; i += NT) A[i] = mk<T>((T)src[i].x, (T)src[i].y);
+  } else {
+    const int n_sites = 2 * N * N;
+    if (tid < 3) {
+      const double2 p = graphene_phase(N, K, kidx, tid);
+      ph[tid] = mk<T>((T)(t_hop * p.x), (T)(t_hop * p.y));
+    }
+    for (int i = tid; i < n * n; i += NT) A[i] = mk<T>(T(0), T(0));
+    group_sync<NT, MPB>(gid);
+    const int* actc = act + cell * n_sites;
+    const int* invc = inv + cell * n_sites;
+    for (int a = tid; a < n; a += NT) {
+      int nb[3];
+      bool fromB;
+      graphene_neighbours(N, actc[a], nb, fromB);
+      C* row = A + (size_t)a * n;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int col = invc[nb[b]];
+        if (col < 0) continue;
+        const C hp = fromB ? conjg<T>(ph[b]) : ph[b];
+        row[col] = cadd<T>(row[col], hp);
+      }
+      row[a].x += (T)eps;
+    }
+  }
+  group_sync<NT, MPB>(gid);
+
+  // ------------------------------------------------------ tridiagonalise ---
+  C* v = vb0; C* w = wb0;       // pending update (v, w) of the previous step
+  C* nv = vb1; C* nw = wb1;     // this step's reflector and update vector
+  bool pend = false;
+  for (int j = 0; j < n - 1; ++j) {
+    // (a) bring row j up to date (columns c >= j): it is conj of column j.
+    if (pend) {
+      const C vj = v[j], wj = w[j];
+      for (int c = j + tid; c < n; c += NT) {
+        C a = A[(size_t)j * n + c];
+        a = csub<T>(a, cmulc<T>(vj, w[c]));
+        a = csub<T>(a, cmulc<T>(wj, v[c]));
+        A[(size_t)j * n + c] = a;
+      }
+    }
+    group_sync<NT, MPB>(gid);
+    // (b) x_c = conj(A[j][c]), c > j.  sigma^2 = |x_{j+1}|^2 + rest.
+    T rest = T(0);
+    for (int c = j + 2 + tid; c < n; c += NT) rest += cabs2<T>(A[(size_t)j * n + c]);
+    rest = group_sum<NT, MPB, T>(rest, scratch, gid);
+    const C alpha = conjg<T>(A[(size_t)j * n + j + 1]);
+    const T aa2 = cabs2<T>(alpha);
+    const T sigma2 = aa2 + rest;
+    if (tid == 0) {
+      dO[j] = A[(size_t)j * n + j].x;
+      eO[j] = sigma2;
+    }
+    // a column whose entries below the subdiagonal are (numerically) zero is
+    // already reduced; |e_j|^2 is recorded either way
+    const bool tr = rest > (sizeof(T) == 4 ? T(1e-30f) : T(1e-290));
+    T tau = T(0);
+    if (tr) {
+      const T sigma = sqrt(sigma2), aa = sqrt(aa2);
+      const C phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+      tau = T(1) / (sigma * (sigma + aa));
+      for (int c = j + 1 + tid; c < n; c += NT)
+        nv[c] = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * n + c]);
+    }
+    group_sync<NT, MPB>(gid);
+    // (c) fused pass: apply the pending update to the trailing block and
+    //     accumulate p = tau A22 v with the updated entries.
+    T kpart = T(0);
+    for (int c = j + 1 + tid; c < n; c += NT) {
+      C p = mk<T>(T(0), T(0));
+      const C wc = pend ? w[c] : mk<T>(T(0), T(0));
+      const C vc = pend ? v[c] : mk<T>(T(0), T(0));
+      for (int r = j + 1; r < n; ++r) {
+        C a = A[(size_t)r * n + c];
+        if (pend) {
+          a = csub<T>(a, cmulc<T>(v[r], wc));
+          a = csub<T>(a, cmulc<T>(w[r], vc));
+          A[(size_t)r * n + c] = a;
+        }
+        if (tr) p = cadd<T>(p, cjmul<T>(a, nv[r]));   // (A22 v)_c = sum_r conj(A[r][c]) v_r
+      }
+      if (tr) {
+        p = cscale<T>(p, tau);
+        nw[c] = p;
+        kpart += nv[c].x * p.x + nv[c].y * p.y;   // Re(conj(v_c) p_c)
+      }
+    }
+    if (tr) {
+      const T Kc = T(0.5) * tau * group_sum<NT, MPB, T>(kpart, scratch, gid);
+      for (int c = j + 1 + tid; c < n; c += NT) nw[c] = csub<T>(nw[c], cscale<T>(nv[c], Kc));
+    }
+    pend = tr;
+    C* tv = v; v = nv; nv = tv;
+    C* tw = w; w = nw; nw = tw;
+    group_sync<NT, MPB>(gid);
+  }
+  if (tid == 0) {
+    C a = A[(size_t)(n - 1) * n + (n - 1)];
+    if (pend) {
+      a = csub<T>(a, cmulc<T>(v[n - 1], w[n - 1]));
+      a = csub<T>(a, cmulc<T>(w[n - 1], v[n - 1]));
+    }
+    dO[n - 1] = a.x;
+  }
+}
+
+template <typename T, int NT, int MPB>
+int run_small(const SolveArgs& a) {
+  const size_t smem = SmallLayout<T>::bytes(a.n_max) * MPB;
+  auto kern = k_small_tridiag<T, NT, MPB>;
+  IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t blocks = (a.n_mat + MPB - 1) / MPB;
+  const CellSet* c = a.cells;
+  kern<<<(unsigned)blocks, NT * MPB, smem, a.stream>>>(
+      c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside,
+      a.n_max, a.n_mat, a.t, a.eps, a.H, reinterpret_cast<T*>(a.d), reinterpret_cast<T*>(a.e2));
+  IDOS_CHECK_LAUNCH();
+  return IDOS_OK;
+}
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+}  // namespace
+
+bool small_path_fits(int precision, int n_max) {
+  const size_t b = precision == IDOS_FP64 ? SmallLayout<double>::bytes(n_max)
+                                          : SmallLayout<float>::bytes(n_max);
+  return n_max <= 256 && b <= kSmemLimit;
+}
+
+template <typename T>
+static int solve_small_t(const SolveArgs& a) {
+  if (a.n_max <= 32) {
+    // up to 4 matrices per CTA while they fit
+    if (SmallLayout<T>::bytes(a.n_max) * 4 <= kSmemLimit) return run_small<T, 32, 4>(a);
+    return run_small<T, 32, 1>(a);
+  }
+  if (a.n_max <= 64) return run_small<T, 64, 1>(a);
+  if (a.n_max <= 128) return run_small<T, 128, 1>(a);
+  return run_small<T, 256, 1>(a);
+}
+
+int solve_small(int precision, const SolveArgs& a) {
+  if (a.n_mat == 0) return IDOS_OK;
+  return precision == IDOS_FP64 ? solve_small_t<double>(a) : solve_small_t<float>(a);
+}
+
+}  // namespace idos

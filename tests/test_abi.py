@@ -1,0 +1,64 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every
+function include/idos.h declares (no compute call: there may be no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "idos.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(idos_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_boundary():
+    names = declared_functions()
+    for must in ("idos_create_model", "idos_sample_level", "idos_eval_idos", "idos_mlmc_estimate",
+                 "idos_get_level_stats", "idos_destroy_model", "idos_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1611_09784_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_loads_and_status_strings():
+    import paper_1611_09784_gb300 as pkg
+    pkg.load_library()
+    assert pkg.status_string(0) == "ok"
+    assert pkg.status_string(-1) == "invalid argument"
+    assert pkg.status_string(-7) == "no sm_103 device"
+
+
+def test_create_model_rejects_bad_descriptors_without_gpu():
+    """Descriptor validation runs before any device call."""
+    import paper_1611_09784_gb300 as pkg
+    base = dict(levels=[(4, 6), (8, 3)], p=0.05)
+    for bad in (dict(levels=[(4, 6), (6, 3)]), dict(p=1.5), dict(n_E=1), dict(delta=0.0),
+                dict(e_min=1.0, e_max=0.0), dict(levels=[(65, 1)])):
+        cfg = dict(base)
+        cfg.update(bad)
+        with pytest.raises(pkg.IdosError) as ei:
+            pkg.create_model(cfg)
+        assert ei.value.status == -1
+    with pytest.raises(pkg.IdosError) as ei:
+        pkg.create_model(dict(base, kind="tmdc"))
+    assert ei.value.status in (-6, -7)
+
+
+def test_no_oracle_import_in_product():
+    """The product package never imports the oracle."""
+    pkgdir = os.path.join(ROOT, "paper_1611_09784_gb300")
+    for dp, _, fs in os.walk(pkgdir):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f

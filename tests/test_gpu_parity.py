@@ -1,0 +1,171 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle on the
+same seeded inputs: masks bit-exact, H(k) entries, eigenvalues within 1e-4 eV,
+per-sample IDoS and level differences within 1e-5 states/A^2."""
+import numpy as np
+import pytest
+
+from oracle import hamiltonian as oham
+from oracle import idos as oidos
+from oracle import lattice as olat
+from oracle import mlmc as omlmc
+from oracle import philox as ophilox
+from synthetic import BASE_SEED
+from synthetic import matrices as synth
+
+from gpu_common import EIG_TOL, IDOS_TOL, cfg_and_prm, graphene_prm, sorted_active
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_1611_09784_gb300")
+
+
+@pytest.fixture(scope="module", params=["fp64", "fp32"])
+def model(request):
+    w, cfg, prm = cfg_and_prm(precision=request.param)
+    m = pkg.create_model(cfg)
+    yield m, w, prm, request.param
+    m.close()
+
+
+@pytest.mark.parametrize("N,level,p", [(1, 0, 0.5), (2, 1, 0.3), (4, 0, 0.05), (8, 2, 0.05), (32, 3, 0.05),
+                                       (3, 0, 0.0), (2, 0, 1.0)])
+def test_masks_bit_exact(N, level, p):
+    w, cfg, prm = cfg_and_prm(precision="fp32", p=p)
+    with pkg.create_model(cfg) as m:
+        got = m.vacancy_masks(N, level, BASE_SEED, 5, 6)
+    for s in range(6):
+        ref = ophilox.vacancy_mask(BASE_SEED, level, 5 + s, 2 * N * N, p)
+        assert np.array_equal(got[s], ref)
+
+
+@pytest.mark.parametrize("N,K", [(1, 3), (2, 2), (3, 2), (4, 6), (8, 3)])
+def test_hamiltonian_entries(model, N, K):
+    m, w, prm, _ = model
+    mask = ophilox.vacancy_mask(7, 0, N, 2 * N * N, 0.2)
+    ks = olat.kpoints(N, K, prm["a"])
+    for kidx in (0, K * K - 1, (K * K) // 2):
+        got = m.hamiltonian(N, K, kidx, mask)
+        ref = oham.hamiltonian(N, ks[kidx], mask, prm["t"], prm["eps_onsite"], prm["a"], prm["sentinel"])
+        assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 32, 33, 64, 100, 128, 160, 200, 300, 512])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_eigvalsh_random_hermitian(n, precision):
+    batch = 3 if n <= 200 else 2
+    H = np.stack([synth.hermitian(n, 1000 * n + b, scale=3.0) for b in range(batch)])
+    got = pkg.eigvalsh(H, precision=precision, refine64_iters=4)
+    ref = np.linalg.eigvalsh(H)
+    tol = 1e-9 if precision == "fp64" else EIG_TOL
+    assert np.max(np.abs(np.sort(got, axis=1) - ref)) < tol
+
+
+def test_eigvalsh_degenerate_and_diagonal():
+    # a diagonal matrix with repeated entries and a block of zeros
+    d = np.array([0.0] * 10 + [1.5] * 6 + [-2.0] * 4 + list(np.linspace(-3, 3, 12)))
+    H = np.diag(d).astype(np.complex128)
+    for prec in ("fp64", "fp32"):
+        got = pkg.eigvalsh(H, precision=prec, refine64_iters=2)[0]
+        assert np.max(np.abs(np.sort(got) - np.sort(d))) < 1e-6
+
+
+@pytest.mark.parametrize("N,K", [(1, 6), (2, 4), (4, 6), (8, 3), (16, 2)])
+def test_eval_idos_seeded(model, N, K):
+    m, w, prm, prec = model
+    for sample in (0, 1):
+        Q, E = m.eval_idos(N, K, seed=w["seed"], level=1, sample=sample, want_eigs=True)
+        mask = ophilox.vacancy_mask(w["seed"], 1, sample, 2 * N * N, prm["p"])
+        Eo = oidos.band_energies(N, K, mask, prm)
+        Qo = oidos.sample_idos(N, K, mask, prm)
+        for g, r in zip(sorted_active(E), Eo):
+            assert g.shape == r.shape
+            assert np.max(np.abs(g - r)) < EIG_TOL
+        assert np.max(np.abs(Q - Qo)) < IDOS_TOL
+
+
+def test_eval_idos_full_size_n2048(model):
+    """Finest level of the MLMC workload (N = 32, n = 2048, one grid point)."""
+    m, w, prm, prec = model
+    Q, E = m.eval_idos(32, 1, seed=w["seed"], level=3, sample=0, want_eigs=True)
+    mask = ophilox.vacancy_mask(w["seed"], 3, 0, 2048, prm["p"])
+    Eo = oidos.band_energies(32, 1, mask, prm)
+    g = sorted_active(E)[0]
+    assert g.shape == Eo[0].shape
+    assert np.max(np.abs(g - Eo[0])) < EIG_TOL
+    assert np.max(np.abs(Q - oidos.idos_from_bands(Eo, olat.supercell_area(32, prm["a"]),
+                                                   oidos.energy_grid(-9, 9, 201), 0.1))) < IDOS_TOL
+
+
+def test_eval_idos_given_mask_edge_cases(model):
+    m, w, prm, prec = model
+    N, K = 4, 2
+    area = olat.supercell_area(N, prm["a"])
+    # pristine: saturation and particle-hole
+    Q = m.eval_idos(N, K, mask=np.zeros(32, np.uint8))
+    assert abs(Q[-1] - 32 / area) < 1e-9
+    assert np.max(np.abs(Q + Q[::-1] - 32 / area)) < IDOS_TOL
+    # all removed: Q = 0
+    Q = m.eval_idos(N, K, mask=np.ones(32, np.uint8))
+    assert np.all(Q == 0.0)
+    # one kept site: isolated orbital at eps_2p = 0
+    mk = np.ones(32, np.uint8)
+    mk[5] = 0
+    Q, E = m.eval_idos(N, K, mask=mk, want_eigs=True)
+    assert np.all(np.abs(E[:, 0]) < 1e-12)
+    assert np.max(np.abs(Q - oidos.sample_idos(N, K, mk, prm))) < IDOS_TOL
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_sample_level_matches_oracle(model, level):
+    m, w, prm, prec = model
+    levels = w["levels"]
+    n = 3
+    first = 11
+    m.reset_level_stats(level)
+    Y, Qf, Qc = m.sample_level_detail(level, n, w["seed"], first)
+    for s in range(n):
+        ref = omlmc.level_sample(prm, levels, level, first + s, w["seed"])
+        assert np.max(np.abs(Qf[s] - ref["Q_fine"])) < IDOS_TOL
+        assert np.max(np.abs(Y[s] - ref["Y"])) < IDOS_TOL
+        if level > 0:
+            for r in range(4):
+                assert np.max(np.abs(Qc[s, r] - ref["Q_coarse"][r])) < IDOS_TOL
+    M, s1, s2, secs = m.get_level_stats(level)
+    assert M == n
+    assert np.allclose(s1, Y.sum(0), rtol=0, atol=1e-12)
+    assert np.allclose(s2, (Y ** 2).sum(0), rtol=0, atol=1e-12)
+    assert secs > 0
+
+
+def test_sample_level_chunk_independent(model):
+    """Results do not depend on how samples are batched."""
+    m, w, prm, prec = model
+    Y1, _, _ = m.sample_level_detail(1, 40, w["seed"], 0)
+    Y2a, _, _ = m.sample_level_detail(1, 17, w["seed"], 0)
+    Y2b, _, _ = m.sample_level_detail(1, 23, w["seed"], 17)
+    assert np.array_equal(Y1, np.concatenate([Y2a, Y2b]))
+
+
+def test_level3_full_size_sampled(model):
+    """One sample of the finest MLMC level (fine n = 2048, corners n = 512)."""
+    m, w, prm, prec = model
+    Y, Qf, Qc = m.sample_level_detail(3, 1, w["seed"], 2)
+    ref = omlmc.level_sample(prm, w["levels"], 3, 2, w["seed"])
+    assert np.max(np.abs(Qf[0] - ref["Q_fine"])) < IDOS_TOL
+    assert np.max(np.abs(Y[0] - ref["Y"])) < IDOS_TOL
+
+
+def test_poly_smoothing():
+    w, cfg, prm = cfg_and_prm(precision="fp64", smoothing="poly")
+    with pkg.create_model(cfg) as m:
+        Q = m.eval_idos(4, 6, seed=w["seed"], level=0, sample=4)
+    mask = ophilox.vacancy_mask(w["seed"], 0, 4, 32, prm["p"])
+    assert np.max(np.abs(Q - oidos.sample_idos(4, 6, mask, prm))) < IDOS_TOL
+
+
+def test_invalid_arguments_on_gpu(model):
+    m = model[0]
+    with pytest.raises(pkg.IdosError):
+        m.sample_level(9, 1, 0)
+    with pytest.raises(pkg.IdosError):
+        m.eval_idos(0, 1)
