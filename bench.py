@@ -1,0 +1,513 @@
+"""Benchmark: MLMC estimate of the expected IDoS of graphene with vacancies
+(levels N = 4, 8, 16, 32; TOL = 1e-3 states/A^2) on GB300.
+
+One step = one pass of the whole path over the workload's fixed per-level
+sample allocation M_l (tests/golden/mlmc_allocation_graphene.json, written by
+an oracle-only script from eq. (2.7)): vacancy masks, corner slicing, H(k)
+assembly, Householder reduction, Sturm bisection, smoothed IDoS, level
+differences and float64 statistics on the device, then the eq. (2.6) combine
+on the host.  Metric: eigen-solves per second (higher is better).
+
+Also reported: `e2e` (the adaptive public call idos_mlmc_estimate(TOL) with
+host outputs, wall clock), time-to-TOL of MLMC vs plain MC at the finest level
+on the same GPU, per-kernel CUDA-event times, the roofline of the dominant
+kernel, the oracle timed on the host cores (`cpu_baseline`), and SM clocks
+sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU: replicas only (weak scaling), each rank draws disjoint samples.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALLOC_FILE = os.path.join(ROOT, "tests", "golden", "mlmc_allocation_graphene.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+WORKLOAD = "graphene_mlmc"
+METRIC = "eigsolves/s (MLMC IDoS estimate, TOL=1e-3)"
+UNIT = "eigsolves/s"
+REFINE64 = 1
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ------------------------------------------------------------------ helpers --
+def load_alloc():
+    with open(ALLOC_FILE) as f:
+        return json.load(f)
+
+
+def eigsolves_per_sample(levels, level):
+    N, K = levels[level]
+    n = K * K
+    if level > 0:
+        n += 4 * levels[level - 1][1] ** 2
+    return n
+
+
+def workload_config(alloc, w):
+    return {"workload": WORKLOAD, "model": "graphene pz NN tight-binding, t=-2.7 eV, a=2.46 A",
+            "p": w["p"], "levels_N_K": w["levels"], "samples_per_level": alloc["M"], "tol": w["tol"],
+            "n_E": w["n_E"], "delta": w["delta"], "precision": f"fp32 reduction + {REFINE64} fp64 bisection step",
+            "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash(name):
+    path = os.path.join(ROOT, "paper_1611_09784_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel, algorithmic_per_launch):
+    """DRAM bytes per launch of `kernel`: the committed ncu capture's DRAM bytes
+    per algorithmic byte times this run's algorithmic bytes per launch; None
+    when there is no capture or the kernel source changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            for ln in f:
+                if ln.startswith("#") or not ln.strip():
+                    continue
+                k, src, h, ratio = ln.split()[:4]
+                if k == kernel and kernel_source_hash(src) == h:
+                    return float(ratio) * algorithmic_per_launch
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------- algorithmic work --
+def n_act_of(masks, N):
+    """Kept-site counts of the fine cells and of their 4 corners (site index
+    m = 2(i + N j) + s, corner r = ri + 2 rj)."""
+    import numpy as np
+    S = masks.shape[0]
+    keep = 1 - masks.reshape(S, N, N, 2)
+    fine = keep.reshape(S, -1).sum(1)
+    h = N // 2
+    corners = []
+    for r in range(4):
+        ri, rj = r % 2, r // 2
+        corners.append(keep[:, rj * h:(rj + 1) * h, ri * h:(ri + 1) * h, :].reshape(S, -1).sum(1))
+    return fine, np.stack(corners, 1)
+
+
+def algorithmic_work(m, levels, M, seed, firsts, fp_bytes=8):
+    """Exact algorithmic work of one step from the samples' kept-site counts:
+    flops of the small-matrix Householder kernel (16/3 n^3 per matrix), bytes
+    of the large-matrix GEMV (trailing block read once per column), flops of
+    the rank-2k panel updates."""
+    import numpy as np
+    small_flops = 0.0
+    gemv_bytes = 0.0
+    her2k_flops = 0.0
+    nb = 32
+
+    def add(n_arr, K2, big):
+        nonlocal small_flops, gemv_bytes, her2k_flops
+        n = n_arr.astype(np.float64)
+        if not big:
+            small_flops += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
+        else:
+            # sum_{j=0}^{n-2} (n-j-1)^2 = (n-1) n (2n-1) / 6
+            gemv_bytes += K2 * fp_bytes * float(np.sum((n - 1) * n * (2 * n - 1) / 6.0))
+            for nn in n_arr:
+                for jn in range(nb, int(nn), nb):
+                    mm = nn - jn
+                    her2k_flops += K2 * 8.0 * 2 * nb * mm * mm
+    for l, (N, K) in enumerate(levels):
+        if not M[l]:
+            continue
+        masks = m.vacancy_masks(N, l, seed, firsts[l], M[l])
+        fine, corners = n_act_of(masks, N)
+        big = 2 * N * N > 160
+        add(fine, K * K, big)
+        if l > 0:
+            Kc = levels[l - 1][1]
+            bigc = 2 * (N // 2) ** 2 > 160
+            add(corners.reshape(-1), Kc * Kc, bigc)
+    return {"k_small_tridiag": small_flops, "k_lg_gemv": gemv_bytes, "k_lg_her2k": her2k_flops}
+
+
+def roofline(prof, work, steps, pk, pk_kind, clocks):
+    """Roofline object for the kernel with the largest event time."""
+    ranked = sorted(prof.items(), key=lambda kv: -kv[1][0])
+    models = {"k_lg_gemv": "hbm", "k_small_tridiag": "alu", "k_lg_her2k": "alu"}
+    for name, (ms, launches) in ranked:
+        if name not in models:
+            continue
+        per_launch_s = ms * 1e-3 / launches
+        units_per_launch = work[name] * steps / launches
+        bound = models[name]
+        if bound == "hbm":
+            achieved = units_per_launch / per_launch_s / 1e9
+            peak = pk["hbm_gbs"]
+            unit = "GB/s"
+        else:
+            achieved = units_per_launch / per_launch_s / 1e12
+            mhz = pk.get("sm_max_mhz", 2070.0)
+            peak = 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+            unit = "TFLOP/s"
+        tr = ncu_traffic(name, units_per_launch) if bound == "hbm" else None
+        return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": tr, "algorithmic_per_launch": units_per_launch,
+                "launches": launches, "avg_launch_ms": per_launch_s * 1e3,
+                "peak_source": f"{pk_kind}" + (" HBM copy" if bound == "hbm" else
+                                               " SM clock x 152 SMs x 128 FP32 lanes x 2"),
+                "dominant_by_event_time": ranked[0][0]}
+    return None
+
+
+# ------------------------------------------------------------- oracle (CPU) --
+def _oracle_job(args):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle import mlmc as omlmc
+    from synthetic import model_params, workload
+    level, sample, seed = args
+    w = workload(WORKLOAD)
+    prm = model_params(w)
+    t0 = time.perf_counter()
+    omlmc.level_sample(prm, w["levels"], level, sample, seed)
+    return level, time.perf_counter() - t0
+
+
+def oracle_pool():
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def oracle_measure(pool, cores, alloc, levels, frac=1.0 / 16, first=50_000_000, seed=161109784):
+    """Run a bounded, workload-shaped sample of level samples on all host cores
+    (one process per core, BLAS single-threaded) and extrapolate the oracle's
+    eigen-solves/s over the full allocation."""
+    M = alloc["M"]
+    counts = [max(1, int(math.ceil(Ml * frac))) for Ml in M]
+    jobs = [(l, first + s, seed) for l in range(len(M)) for s in range(counts[l])]
+    jobs.sort(key=lambda j: -j[0])
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    per = [[] for _ in M]
+    for l, t in res:
+        per[l].append(t)
+    mean = [sum(x) / len(x) for x in per]
+    core_seconds = sum(Ml * t for Ml, t in zip(M, mean))
+    full_wall = core_seconds / cores
+    eig = sum(Ml * eigsolves_per_sample(levels, l) for l, Ml in enumerate(M))
+    return {"value": eig / full_wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{counts} level samples (levels 0..3) of the allocation {M}, run on {cores} host "
+                       f"processes (1 BLAS thread each) in {wall:.1f} s; per-level mean seconds {[round(x, 4) for x in mean]} "
+                       f"extrapolated to the full allocation assuming all cores busy"),
+            "seconds_per_step_extrapolated": full_wall}
+
+
+# ------------------------------------------------------------------- GPU arm --
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = cores = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.skip_extras:
+        pool, cores = oracle_pool()     # spawn pool before the first GPU call
+    if world > 1:
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1611_09784_gb300 as pkg
+    from synthetic import workload
+
+    w = workload(WORKLOAD)
+    alloc = load_alloc()
+    levels = [tuple(x) for x in w["levels"]]
+    M = list(alloc["M"])
+    if args.levels is not None:
+        keep = {int(x) for x in args.levels.split(",")}
+        M = [Ml if l in keep else 0 for l, Ml in enumerate(M)]
+    stream = torch.cuda.Stream(device=dev)
+    cfg = dict(w["model"], p=w["p"], levels=levels, e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
+               delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64)
+    model = pkg.create_model(cfg, stream=stream.cuda_stream)
+    seed = w["seed"] + 1000 * rank
+    eig_step = sum(Ml * eigsolves_per_sample(levels, l) for l, Ml in enumerate(M))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(idx):
+        for l, Ml in enumerate(M):
+            if Ml:
+                model.sample_level(l, Ml, seed, first_sample=idx * Ml)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    model.reset_level_stats(-1)
+    model.reset_profile()
+    model.set_profiling(True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(args.warmup + k)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    model.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    prof = model.get_profile()
+    # combine (eq. (2.6)) on the host from the device accumulators: the estimate
+    mean = np.zeros(w["n_E"])
+    var = np.zeros(w["n_E"])
+    for l in range(len(M)):
+        if not M[l]:
+            continue
+        Ml, s1, s2, _ = model.get_level_stats(l)
+        mu = s1 / Ml
+        mean += mu
+        var += np.maximum(s2 - Ml * mu * mu, 0) / (Ml - 1) / Ml
+    t_max = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t_max.item())
+    value = world * args.steps * eig_step / (total_ms_max * 1e-3)
+
+    # algorithmic work of the timed steps (exact kept-site counts)
+    firsts_steps = [[(args.warmup + k) * Ml for Ml in M] for k in range(args.steps)]
+    work = {"k_small_tridiag": 0.0, "k_lg_gemv": 0.0, "k_lg_her2k": 0.0}
+    for firsts in firsts_steps:
+        wk = algorithmic_work(model, levels, M, seed, firsts)
+        for k2 in work:
+            work[k2] += wk[k2] / args.steps
+    pk, pk_kind = peaks()
+    roof = roofline(prof, work, args.steps, pk, pk_kind, clk)
+
+    if args.skip_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+                              "partial": "timed steps only (--skip-extras)", "samples_per_level": M,
+                              "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
+                              "roofline": roof, "clocks": clk}), flush=True)
+        model.close()
+        if pool is not None:
+            pool.close()
+        return
+
+    # ---- e2e: the public adaptive call, host outputs, wall clock ----
+    e2e_vals, e2e_s, h2d, d2h, est = [], [], 0, 0, None
+    for k in range(args.steps):
+        model2 = pkg.create_model(cfg, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        est = model2.mlmc_estimate(w["tol"], theta=w["theta"], c_alpha=w["c_alpha"], pilot_samples=32,
+                                   max_rounds=3, seed=seed + 17 + k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        nE = sum(int(est["M"][l]) * eigsolves_per_sample(levels, l) for l in range(len(levels)))
+        e2e_vals.append(nE / dt)
+        e2e_s.append(dt)
+        h2d, d2h = est["h2d_bytes"], est["d2h_bytes"]
+        model2.close()
+    e2e_value = world * statistics.median(e2e_vals)
+
+    # ---- time-to-TOL: plain MC at the finest level on the same GPU ----
+    Nf, Kf = levels[-1]
+    mc_cfg = dict(cfg, levels=[(Nf, Kf)])
+    mc = pkg.create_model(mc_cfg, stream=stream.cuda_stream)
+    pilot = 32
+    mc.sample_level(0, pilot, seed + 99, 0)
+    Mp, s1, s2, _ = mc.get_level_stats(0)
+    mu = s1 / Mp
+    v_mc = float(np.max(np.maximum(s2 - Mp * mu * mu, 0) / (Mp - 1)))
+    m_mc = int(math.ceil((w["c_alpha"] / (w["theta"] * w["tol"])) ** 2 * v_mc))
+    mc.reset_level_stats(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mc.sample_level(0, m_mc, seed + 99, pilot)
+    torch.cuda.synchronize()
+    mc_s = time.perf_counter() - t0
+    mc.close()
+
+    cpu = None
+    if pool is not None:
+        cpu = oracle_measure(pool, cores, alloc, levels)
+        pool.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (reduction, bisection) + f64 (refine, sums)",
+            "data": "synthetic (seeded Philox vacancy masks)",
+            "config": workload_config(alloc, w),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "call": "idos_mlmc_estimate(TOL=1e-3) adaptive, host outputs, wall clock",
+                    "seconds_per_call": statistics.median(e2e_s), "samples_per_level": [int(x) for x in est["M"]]},
+            "time_to_tol": {"mlmc_adaptive_s": statistics.median(e2e_s), "mlmc_fixed_alloc_s": total_ms_max / args.steps * 1e-3,
+                            "plain_mc_s": mc_s, "plain_mc_samples": m_mc, "plain_mc_level": [Nf, Kf],
+                            "speedup_mlmc_vs_mc": mc_s / statistics.median(e2e_s)},
+            "gpu_launches": int(sum(v[1] for v in prof.values()) // args.steps),
+            "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
+            "roofline": roof,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "estimate_check": {"Q_at_e_max": float(mean[-1]), "max_std": float(np.sqrt(np.max(var)))},
+        }
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------------- reference arm --
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synthetic import workload
+    w = workload(WORKLOAD)
+    alloc = load_alloc()
+    levels = [tuple(x) for x in w["levels"]]
+    pool, cores = oracle_pool()
+    vals, secs = [], []
+    for i in range(args.warmup + args.steps):
+        r = oracle_measure(pool, cores, alloc, levels, first=60_000_000 + 10_000 * i)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["seconds_per_step_extrapolated"])
+    pool.close()
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Philox vacancy masks)", "config": workload_config(alloc, w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--levels", default=None,
+                    help="comma list of level indices to run (profiling a part of the workload)")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="only the timed steps: no e2e / plain-MC / CPU-baseline measurements")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

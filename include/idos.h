@@ -82,7 +82,7 @@ typedef struct idos_model_desc {
   double sentinel;     /* diagonal of a removed site in idos_hamiltonian()  */
   double e_min, e_max; /* energy grid eps_j = e_min + j (e_max-e_min)/(n_E-1) */
   double delta;        /* smoothing width, eq. (4.2) (> 0)                  */
-  int32_t n_E;         /* number of energies, 2 .. 4096                     */
+  int32_t n_E;         /* number of energies, 2 .. 1024                     */
   int32_t refine64_iters; /* float64 bisection steps in IDOS_FP32_REFINE64  */
   uint64_t model_seed; /* parameter seed of the TMDC-shaped model           */
   int64_t workspace_bytes; /* device workspace cap; 0 = library default      */
@@ -159,6 +159,9 @@ typedef struct idos_estimate {
   double* V;       /* float64[n_levels]: max over eps of the level variance  */
   double* W;       /* float64[n_levels]: work per sample used in eq. (2.7)   */
   double seconds;  /* wall time of the call                                  */
+  int32_t rounds;  /* allocation rounds performed after the pilot            */
+  int64_t h2d_bytes; /* bytes copied host -> device during the call          */
+  int64_t d2h_bytes; /* bytes copied device -> host during the call          */
 } idos_estimate;
 
 /* Adaptive MLMC (Sec. 2.2): pilot round of pilot_samples per level, V_l and
@@ -166,6 +169,25 @@ typedef struct idos_estimate {
  * samples, combine by eq. (2.6).  Starts from zeroed accumulators.  Sample
  * indices continue from 0 on every level. */
 int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* out);
+
+/* ---- kernel timing (tracing) ----
+ * With profiling enabled every kernel launch of the model is bracketed by a
+ * pair of CUDA events on the model's stream; the pairs are resolved when the
+ * call that launched them synchronises, and accumulated per kernel family.
+ * The events add a few microseconds per launch. */
+
+/* enable != 0 turns timing on, 0 off.  Does not clear the totals. */
+int idos_set_profiling(idos_model* m, int enable);
+
+/* Number of kernel families (valid kid values are 0 .. count-1). */
+int idos_profile_count(void);
+
+/* Totals of kernel family kid since the last reset: *name (static string,
+ * may be NULL), *ms summed event time, *launches. */
+int idos_get_profile(const idos_model* m, int kid, const char** name, double* ms, int64_t* launches);
+
+/* Zero the totals. */
+int idos_reset_profile(idos_model* m);
 
 /* ---- parity / diagnostic entry points (same kernels as the hot path) ---- */
 

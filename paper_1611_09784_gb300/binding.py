@@ -41,7 +41,8 @@ class MlmcOpts(C.Structure):
 class Estimate(C.Structure):
     _fields_ = [("mean", C.POINTER(C.c_double)), ("var", C.POINTER(C.c_double)),
                 ("M", C.POINTER(C.c_int64)), ("V", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("rounds", C.c_int32), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64)]
 
 
 class IdosError(RuntimeError):
@@ -69,6 +70,11 @@ _SYMBOLS = {
                                      C.c_void_p]),
     "idos_hamiltonian": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "idos_profile_count": (C.c_int, []),
+    "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int64)]),
+    "idos_reset_profile": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -212,9 +218,30 @@ class Model:
         W = np.empty(self.n_levels)
         est = Estimate(mean.ctypes.data_as(C.POINTER(C.c_double)), var.ctypes.data_as(C.POINTER(C.c_double)),
                        M.ctypes.data_as(C.POINTER(C.c_int64)), V.ctypes.data_as(C.POINTER(C.c_double)),
-                       W.ctypes.data_as(C.POINTER(C.c_double)), 0.0)
+                       W.ctypes.data_as(C.POINTER(C.c_double)), 0.0, 0, 0, 0)
         _check(load_library().idos_mlmc_estimate(self._h, C.byref(o), C.byref(est)), "idos_mlmc_estimate")
-        return {"mean": mean, "var": var, "M": M, "V": V, "W": W, "seconds": est.seconds}
+        return {"mean": mean, "var": var, "M": M, "V": V, "W": W, "seconds": est.seconds,
+                "rounds": est.rounds, "h2d_bytes": est.h2d_bytes, "d2h_bytes": est.d2h_bytes}
+
+    def set_profiling(self, enable: bool = True):
+        _check(load_library().idos_set_profiling(self._h, 1 if enable else 0), "idos_set_profiling")
+
+    def reset_profile(self):
+        _check(load_library().idos_reset_profile(self._h), "idos_reset_profile")
+
+    def get_profile(self) -> dict:
+        """{kernel name: (total ms, launches)} for families that launched."""
+        lib = load_library()
+        out = {}
+        for kid in range(lib.idos_profile_count()):
+            name = C.c_char_p()
+            ms = C.c_double()
+            n = C.c_int64()
+            _check(lib.idos_get_profile(self._h, kid, C.byref(name), C.byref(ms), C.byref(n)),
+                   "idos_get_profile")
+            if n.value:
+                out[name.value.decode()] = (float(ms.value), int(n.value))
+        return out
 
     def vacancy_masks(self, N: int, level: int, seed: int, first_sample: int, n_samples: int):
         out = np.empty((n_samples, 2 * N * N), dtype=np.uint8)

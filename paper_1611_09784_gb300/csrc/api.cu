@@ -232,6 +232,20 @@ double flop_model(const idos_model_desc& d, int level) {
   return w;
 }
 
+// Makes the model's profiler the active one for the duration of an API call
+// and resolves its event pairs once the call has synchronised.
+struct ProfGuard {
+  Model* m;
+  explicit ProfGuard(Model* mm) : m(mm) { set_active_profiler(mm ? &mm->prof : nullptr); }
+  ~ProfGuard() {
+    if (m && m->prof.enabled) {
+      cudaStreamSynchronize(m->stream);
+      m->prof.resolve();
+    }
+    set_active_profiler(nullptr);
+  }
+};
+
 }  // namespace
 }  // namespace idos
 
@@ -298,6 +312,7 @@ int idos_sample_level_detail(idos_model* m, int level, int64_t n_samples, uint64
   if (level < 0 || level >= m->d.n_levels) { set_error("level out of range"); return IDOS_ERR_INVALID_ARG; }
   if (n_samples < 0 || first_sample < 0) { set_error("negative sample count or index"); return IDOS_ERR_INVALID_ARG; }
   if (n_samples == 0) return IDOS_OK;
+  ProfGuard pg(m);
   return run_level(m, level, n_samples, seed, first_sample, per_sample_Y, Q_fine, Q_coarse);
 }
 
@@ -339,6 +354,7 @@ int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_
   if (!m || !idos_out) { set_error("null model or output"); return IDOS_ERR_INVALID_ARG; }
   if (N < 1 || N > 64 || Kside < 1 || Kside > 64 || sample < 0) { set_error("N, Kside or sample out of range"); return IDOS_ERR_INVALID_ARG; }
   const int n_E = m->d.n_E;
+  ProfGuard pg(m);
   const size_t need = cells_bytes(N, 1) + solve_bytes(m->d.precision, N, Kside, 1, n_E) + 8 * n_E + 65536 +
                       large_room(m, N, Kside, 1);
   IDOS_TRY(m->ws.reserve(need, m->stream));
@@ -457,6 +473,28 @@ int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const
   return rc;
 }
 
+int idos_set_profiling(idos_model* m, int enable) {
+  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  m->prof.enabled = enable != 0;
+  return IDOS_OK;
+}
+
+int idos_profile_count(void) { return KID_COUNT; }
+
+int idos_get_profile(const idos_model* m, int kid, const char** name, double* ms, int64_t* launches) {
+  if (!m || kid < 0 || kid >= KID_COUNT) { set_error("null model or kid out of range"); return IDOS_ERR_INVALID_ARG; }
+  if (name) *name = kernel_name(kid);
+  if (ms) *ms = m->prof.ms[kid];
+  if (launches) *launches = m->prof.launches[kid];
+  return IDOS_OK;
+}
+
+int idos_reset_profile(idos_model* m) {
+  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  m->prof.clear();
+  return IDOS_OK;
+}
+
 int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* out) {
   if (!m || !o || !out || !out->mean || !out->var) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
   if (!(o->tol > 0) || !(o->theta > 0 && o->theta < 1) || !(o->c_alpha > 0) || o->pilot_samples < 2 ||
@@ -470,6 +508,8 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   std::vector<double> sum(n_E), sq(n_E);
   std::vector<double> V(L), W(L);
   std::vector<int64_t> target(L, o->pilot_samples);
+  int64_t d2h = 0;
+  int rounds = 0;
   for (int round = 0; round <= o->max_rounds; ++round) {
     for (int l = 0; l < L; ++l) {
       const int64_t extra = target[l] - m->M[l];
@@ -481,6 +521,7 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
       int64_t M = 0;
       double secs = 0;
       IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
+      d2h += 2 * (int64_t)sizeof(double) * n_E;
       double vmax = 0.0;
       for (int j = 0; j < n_E; ++j) {
         const double mean = sum[j] / M;
@@ -500,6 +541,7 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
       if (Ml > m->M[l]) more = true;
       target[l] = std::max(target[l], Ml);
     }
+    ++rounds;
     if (!more) break;
   }
   // combine, eq. (2.6)
@@ -509,6 +551,7 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
     int64_t M = 0;
     double secs = 0;
     IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
+    d2h += 2 * (int64_t)sizeof(double) * n_E;
     double vmax = 0.0;
     for (int j = 0; j < n_E; ++j) {
       const double mean = sum[j] / M;
@@ -522,6 +565,9 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
     if (out->W) out->W[l] = o->work_model == 1 ? secs / M : flop_model(m->d, l);
   }
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  out->rounds = rounds;
+  out->h2d_bytes = 0;   // every input (model, seeds, sizes) travels as kernel arguments
+  out->d2h_bytes = d2h;
   return IDOS_OK;
 }
 

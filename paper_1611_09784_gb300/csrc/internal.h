@@ -10,6 +10,7 @@
 
 #include "../../include/idos.h"
 #include "common.cuh"
+#include "profiler.h"
 
 namespace idos {
 
@@ -71,6 +72,7 @@ struct Model {
   Arena ws;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int sm_count = 0;
+  Profiler prof;
 };
 
 // ---- stage launchers (return idos_status) ----

@@ -135,6 +135,7 @@ int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int
   auto kern = k_bisect<S, G, MPB>;
   IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t blocks = (n_mat + MPB - 1) / MPB;
+  ProfScope ps(KID_BISECT, s);
   kern<<<(unsigned)blocks, G * MPB, smem, s>>>(reinterpret_cast<const S*>(d), reinterpret_cast<const S*>(e2),
                                                n_act_cell, K2, n_max, n_mat, refine, eigs);
   IDOS_CHECK_LAUNCH();

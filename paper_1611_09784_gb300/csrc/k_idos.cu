@@ -118,6 +118,7 @@ int launch_idos(const double* eigs, const int* n_act_cell, int K2, int n_max, in
   const double inv_norm = 1.0 / (area * K2);
   const size_t smem = sizeof(double) * (size_t)n_max;
   IDOS_CUDA_TRY(cudaFuncSetAttribute(k_idos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ProfScope ps(KID_IDOS, s);
   k_idos<<<(unsigned)n_cells, IDOS_THREADS, smem, s>>>(eigs, n_act_cell, K2, n_max, inv_norm, g.e_min, span,
                                                        g.delta, g.n_E, g.smoothing, g.fp32_erfc, Q);
   IDOS_CHECK_LAUNCH();
@@ -134,6 +135,7 @@ int launch_level_stats(const double* Qf, const double* Qc, int64_t S, int n_E, d
     return IDOS_ERR_OUT_OF_MEMORY;
   }
   const dim3 grid((n_E + 127) / 128, (unsigned)n_chunks);
+  ProfScope ps(KID_LEVEL_STATS, s);
   k_level_partial<<<grid, 128, 0, s>>>(Qf, Qc, S, n_E, Y, partial);
   IDOS_CHECK_LAUNCH();
   k_level_final<<<(n_E + 127) / 128, 128, 0, s>>>(partial, n_chunks, n_E, acc);

@@ -305,6 +305,7 @@ int solve_large_t(const SolveArgs& a) {
     {
       const int64_t total = nb_mat * (int64_t)nm;
       const int64_t blocks = std::min<int64_t>((total + 127) / 128, 152 * 16);
+      ProfScope ps(KID_LG_ASSEMBLE, a.stream);
       k_lg_assemble<T><<<(unsigned)blocks, 128, 0, a.stream>>>(
           s, cells ? cells->act : nullptr, cells ? cells->inv : nullptr, cells ? cells->N : 0,
           a.Kside, a.t, a.eps, a.H ? a.H + m0 * (int64_t)nm * nm : nullptr, A);
@@ -314,13 +315,23 @@ int solve_large_t(const SolveArgs& a) {
     for (int j0 = 0; j0 < nm; j0 += NB) {
       for (int i = 0; i < NB && j0 + i < nm; ++i) {
         const int j = j0 + i;
-        k_lg_start<T><<<(unsigned)nb_mat, 1024, 0, a.stream>>>(s, j0, i, A, V, W, tau, dB, eB);
-        k_lg_gemv<T><<<ggrid, GEMV_ROWS, 0, a.stream>>>(s, j, i, A, V, tau, part, n_slices);
-        k_lg_finish<T><<<(unsigned)nb_mat, 1024, 0, a.stream>>>(s, j0, i, V, W, tau, part, n_slices);
+        {
+          ProfScope ps(KID_LG_START, a.stream);
+          k_lg_start<T><<<(unsigned)nb_mat, 1024, 0, a.stream>>>(s, j0, i, A, V, W, tau, dB, eB);
+        }
+        {
+          ProfScope ps(KID_LG_GEMV, a.stream);
+          k_lg_gemv<T><<<ggrid, GEMV_ROWS, 0, a.stream>>>(s, j, i, A, V, tau, part, n_slices);
+        }
+        {
+          ProfScope ps(KID_LG_FINISH, a.stream);
+          k_lg_finish<T><<<(unsigned)nb_mat, 1024, 0, a.stream>>>(s, j0, i, V, W, tau, part, n_slices);
+        }
       }
       const int jn = j0 + NB;
       if (jn < nm) {
         const dim3 hgrid((nm - jn + 31) / 32, (nm - jn + 31) / 32, (unsigned)nb_mat);
+        ProfScope ps(KID_LG_HER2K, a.stream);
         k_lg_her2k<T><<<hgrid, dim3(32, 8), 0, a.stream>>>(s, jn, A, V, W);
       }
       IDOS_CHECK_LAUNCH();

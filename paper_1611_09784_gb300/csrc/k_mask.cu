@@ -30,6 +30,7 @@ int launch_fine_masks(uint8_t* out, int n_sites, int64_t count, uint64_t seed, i
   if (total == 0) return IDOS_OK;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
+  ProfScope ps(KID_MASKS, s);
   k_fine_masks<<<(unsigned)blocks, threads, 0, s>>>(out, n_sites, total, seed, level, first_sample,
                                                    thr, all_removed);
   IDOS_CHECK_LAUNCH();
@@ -59,6 +60,7 @@ int launch_corner_masks(const uint8_t* fine, int N, int64_t count, uint8_t* out,
   if (total == 0) return IDOS_OK;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
+  ProfScope ps(KID_CORNERS, s);
   k_corner_masks<<<(unsigned)blocks, threads, 0, s>>>(fine, N, total, out);
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
@@ -100,6 +102,7 @@ __global__ void k_cell_maps(const uint8_t* __restrict__ mask, int n_sites, int* 
 int launch_cell_maps(CellSet& c, cudaStream_t s) {
   if (c.count == 0) return IDOS_OK;
   const int threads = c.n_sites >= 1024 ? 1024 : (c.n_sites >= 256 ? 256 : 32);
+  ProfScope ps(KID_CELL_MAPS, s);
   k_cell_maps<<<(unsigned)c.count, threads, 0, s>>>(c.mask, c.n_sites, c.n_act, c.act, c.inv);
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;

@@ -178,6 +178,7 @@ int run_small(const SolveArgs& a) {
   IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t blocks = (a.n_mat + MPB - 1) / MPB;
   const CellSet* c = a.cells;
+  ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
   kern<<<(unsigned)blocks, NT * MPB, smem, a.stream>>>(
       c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside,
       a.n_max, a.n_mat, a.t, a.eps, a.H, reinterpret_cast<T*>(a.d), reinterpret_cast<T*>(a.e2));
