@@ -212,6 +212,43 @@ int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t
 int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const double* H,
                   double* eigs_out, void* cuda_stream);
 
+/* ---- allocation-free evaluation ----
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: code that owns all device memory through its
+ * own pool and forbids outside allocations, code that must not trigger the
+ * implicit device-wide synchronisation of cudaMalloc / cudaFree in a
+ * latency-critical loop, or code that cannot create a model (model creation
+ * allocates its accumulators and workspace).
+ *
+ * Computes exactly what idos_eval_idos computes for one configuration (same
+ * kernels, same results), without a model and without allocating: its
+ * scratch (kept-site maps, tridiagonals, eigenvalues when eigs_dev_out is
+ * NULL) lives in one file-scope static device array of 1 MiB that every GPU
+ * which loads libidos.so holds until the process exits.
+ *  - d: model description (only the single-configuration fields are used:
+ *    kind, precision, smoothing, t, eps_onsite, a, p, e_min, e_max, delta,
+ *    n_E, refine64_iters).
+ *  - N, Kside: supercell side and k-grid side.  Only matrices of the
+ *    shared-memory path are accepted (2N^2 <= 160 in float32, <= 112 in
+ *    float64), and the scratch must fit 1 MiB (about 2 K^2 2N^2 (2 s + 8)
+ *    bytes, s = 4 or 8); larger requests return IDOS_ERR_INVALID_ARG with the
+ *    byte count in idos_last_error().
+ *  - mask_dev: DEVICE u8[2N^2] (1 = removed), or NULL to draw the mask from
+ *    (seed, level, sample) as idos_sample_level does.
+ *  - idos_dev_out: DEVICE float64[n_E]; eigs_dev_out: NULL or DEVICE
+ *    float64[Kside^2 * 2N^2] (layout as in idos_eval_idos).  Caller-owned.
+ *  - cuda_stream: cudaStream_t as void* (NULL = legacy default stream).  The
+ *    call enqueues its kernels and returns without synchronising.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress, once per device); make that first call before any
+ * stream capture.  All calls share the array and every call overwrites all
+ * of the scratch it reads, so nothing needs clearing between calls; calls
+ * whose kernels overlap on the GPU (other streams, other host threads) race
+ * on the array and must be serialised by the caller. */
+int idos_eval_idos_noalloc(const idos_model_desc* d, int N, int Kside, const uint8_t* mask_dev,
+                           uint64_t seed, int level, int64_t sample, double* idos_dev_out,
+                           double* eigs_dev_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,8 @@ _SYMBOLS = {
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]),
     "idos_reset_profile": (C.c_int, [C.c_void_p]),
+    "idos_eval_idos_noalloc": (C.c_int, [C.POINTER(ModelDesc), C.c_int, C.c_int, C.c_void_p, C.c_uint64, C.c_int,
+                                         C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -271,3 +273,15 @@ def eigvalsh(H, precision="fp32", refine64_iters: int = 0, stream: int | None = 
     _check(load_library().idos_eigvalsh(_PRECISION[precision], refine64_iters, n, batch, _ptr(H), _ptr(out),
                                         C.c_void_p(stream or 0)), "idos_eigvalsh")
     return out
+
+
+def eval_idos_noalloc(cfg: dict, N: int, K: int, idos_dev_ptr: int, eigs_dev_ptr: int | None = None,
+                      mask_dev_ptr: int | None = None, seed: int = 0, level: int = 0, sample: int = 0,
+                      stream: int | None = None):
+    """Allocation-free single-configuration IDoS (no model): inputs and outputs
+    are caller-owned DEVICE pointers (integers, e.g. tensor.data_ptr()); the
+    call enqueues on `stream` and returns without synchronising."""
+    d = make_desc(cfg)
+    _check(load_library().idos_eval_idos_noalloc(C.byref(d), N, K, C.c_void_p(mask_dev_ptr or 0), seed, level,
+                                                 sample, C.c_void_p(idos_dev_ptr), C.c_void_p(eigs_dev_ptr or 0),
+                                                 C.c_void_p(stream or 0)), "idos_eval_idos_noalloc")
