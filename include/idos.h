@@ -53,10 +53,13 @@ enum idos_status {
 enum idos_kind { IDOS_GRAPHENE = 0, IDOS_TMDC = 1 };
 
 /* Arithmetic of the per-k eigen-solve.
- * IDOS_FP64: Householder reduction, Sturm bisection and smoothing in float64.
- * IDOS_FP32_REFINE64: reduction and bisection in float32, then
- *   refine64_iters float64 bisection steps on the float32 tridiagonal; the
- *   smoothing argument and every sum are float64, erfc is evaluated in float32. */
+ * IDOS_FP64: Householder reduction and smoothing in float64; eigenvalues by a
+ *   float32 Sturm bracket then safeguarded float64 Newton on the float64
+ *   tridiagonal's characteristic polynomial, to float64 resolution.
+ * IDOS_FP32_REFINE64: reduction and Sturm bisection in float32, then
+ *   refine64_iters float64 passes (Sturm count + Newton step each) on the
+ *   float32 tridiagonal; the smoothing argument and every sum are float64,
+ *   erfc is evaluated in float32. */
 enum idos_precision { IDOS_FP64 = 0, IDOS_FP32_REFINE64 = 1 };
 
 /* Smoothed step g of eq. (4.2).
@@ -83,7 +86,7 @@ typedef struct idos_model_desc {
   double e_min, e_max; /* energy grid eps_j = e_min + j (e_max-e_min)/(n_E-1) */
   double delta;        /* smoothing width, eq. (4.2) (> 0)                  */
   int32_t n_E;         /* number of energies, 2 .. 1024                     */
-  int32_t refine64_iters; /* float64 bisection steps in IDOS_FP32_REFINE64  */
+  int32_t refine64_iters; /* float64 Newton/Sturm passes (FP32_REFINE64)  */
   uint64_t model_seed; /* parameter seed of the TMDC-shaped model           */
   int64_t workspace_bytes; /* device workspace cap; 0 = library default      */
 } idos_model_desc;
@@ -145,7 +148,8 @@ typedef struct idos_mlmc_opts {
   double tol;            /* TOL of Sec. 2 (states / Angstrom^2)                  */
   double theta;          /* statistical share of TOL (0 < theta < 1)             */
   double c_alpha;        /* confidence quantile (1.96)                           */
-  int64_t pilot_samples; /* samples per level in the pilot round (>= 2)          */
+  int64_t pilot_samples; /* pilot samples on level 0 (>= 2); level l takes
+                            max(4, ceil(pilot_samples sqrt(W_0/W_l))), W = flop model */
   int32_t work_model;    /* 0: W_l from the flop model sum n^3; 1: measured time */
   int32_t max_rounds;    /* extra allocation rounds after the pilot (>= 1)       */
   uint64_t seed;         /* generator key                                        */
@@ -164,7 +168,7 @@ typedef struct idos_estimate {
   int64_t d2h_bytes; /* bytes copied device -> host during the call          */
 } idos_estimate;
 
-/* Adaptive MLMC (Sec. 2.2): pilot round of pilot_samples per level, V_l and
+/* Adaptive MLMC (Sec. 2.2): pilot round (see pilot_samples), V_l and
  * W_l, M_l from eq. (2.7) with target variance (theta tol / c_alpha)^2, extra
  * samples, combine by eq. (2.6).  Starts from zeroed accumulators.  Sample
  * indices continue from 0 on every level. */

@@ -153,10 +153,10 @@ size_t solve_bytes(int precision, int N, int Kside, int64_t count, int n_E) {
 size_t large_room(const Model* M, int N, int Kside, int64_t count) {
   const int n = 2 * N * N;
   if (small_path_fits(M->d.precision, n)) return 0;
-  const size_t per = 2 * tsize(M->d.precision) * ((size_t)n * n + 80 * (size_t)n) + 4096;
+  const size_t one = large_path_bytes(M->d.precision, n, 1);
   const size_t cap = M->d.workspace_bytes > 0 ? (size_t)M->d.workspace_bytes : kDefaultWorkspace;
-  const size_t want = per * (size_t)count * Kside * Kside;
-  return std::max(per, std::min(want, cap));
+  const size_t want = large_path_bytes(M->d.precision, n, count * (int64_t)Kside * Kside);
+  return std::max(one, std::min(want, cap));
 }
 
 int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh,
@@ -436,7 +436,7 @@ int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const
   const size_t nn = (size_t)n * n;
   const size_t ts = tsize(precision);
   const bool small = small_path_fits(precision, n);
-  const size_t large = small ? 0 : 2 * ts * (nn + 80 * (size_t)n) * (size_t)std::min<int64_t>(batch, 8) + 8192;
+  const size_t large = small ? 0 : large_path_bytes(precision, n, std::min<int64_t>(batch, 8));
   const size_t need = sizeof(double2) * nn * batch + batch * (size_t)n * (2 * ts + 8) + large + 65536;
   int st = ws.reserve(need, s);
   if (st != IDOS_OK) return st;
@@ -507,7 +507,11 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   IDOS_TRY(idos_reset_level_stats(m, -1));
   std::vector<double> sum(n_E), sq(n_E);
   std::vector<double> V(L), W(L);
-  std::vector<int64_t> target(L, o->pilot_samples);
+  // pilot: pilot_samples on level 0, fewer on costlier levels
+  std::vector<int64_t> target(L);
+  for (int l = 0; l < L; ++l)
+    target[l] = std::max<int64_t>(4, (int64_t)std::ceil(o->pilot_samples *
+                                                        std::sqrt(flop_model(m->d, 0) / flop_model(m->d, l))));
   int64_t d2h = 0;
   int rounds = 0;
   for (int round = 0; round <= o->max_rounds; ++round) {

@@ -86,6 +86,8 @@ int launch_assemble_dense(const SolveArgs& a, int k_index, double2* out, double 
 bool small_path_fits(int precision, int n_max);
 int solve_small(int precision, const SolveArgs& a);
 int solve_large(int precision, const SolveArgs& a);
+// Workspace the large-matrix path needs to hold n_mat matrices in one batch.
+size_t large_path_bytes(int precision, int n_max, int64_t n_mat);
 
 // Sturm-count bisection: eigs[mat][n_max] ascending, NaN beyond n_act.
 int launch_bisect(int precision, int refine64_iters, const void* d, const void* e2,

@@ -7,9 +7,20 @@
 // with a pivot of magnitude below pivmin replaced by -pivmin (a perturbation
 // of x by at most pivmin).  Eigenvalue k (0-based) is the smallest x with
 // count(x) >= k + 1; each thread bisects one index inside the Gershgorin
-// interval, all threads of a group reading the same (d, e^2) from shared
-// memory (broadcast).  IDOS_FP32_REFINE64 bisects in float32 to convergence
-// and then continues `refine` steps in float64 on the same tridiagonal.
+// interval in float32, all threads of a group reading the same (d, e^2)
+// from shared memory (broadcast).
+//
+// The float64 stage works on the characteristic polynomials of the leading
+// blocks, p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1}
+// (a pivot is p_{i+1}/p_i, so the count is the number of sign changes), and
+// their x-derivatives, rescaled by exact powers of two: no division.  One
+// pass gives the count at x and the Newton step -p_n/p_n', used inside the
+// current bracket (safeguarded Newton: bisect when the step leaves it).
+//   IDOS_FP32_REFINE64: float32 bisection to 2 ulp, then refine64_iters
+//     float64 passes starting at the bracket midpoint;
+//   IDOS_FP64: float32 bisection on the rounded tridiagonal gives a bracket,
+//     checked and widened in float64, then safeguarded Newton to float64
+//     resolution.
 #include <cfloat>
 
 #include "internal.h"
@@ -35,6 +46,53 @@ __device__ __forceinline__ int sturm_count(const S* __restrict__ d, const S* __r
   return cnt;
 }
 
+// One float64 pass: count of eigenvalues below x and the Newton step
+// -p_n(x)/p_n'(x) of the characteristic polynomial.
+template <typename S>
+__device__ __forceinline__ int sturm_newton64(const S* __restrict__ d, const S* __restrict__ e2, int n, double x,
+                                              double& step) {
+  double p0 = 1.0, p1 = (double)d[0] - x;       // p_{i-1}, p_i
+  double q0 = 0.0, q1 = -1.0;                   // derivatives
+  if (p1 == 0.0) p1 = -0x1p-1000;              // exact zero pivot counts as negative
+  int cnt = p1 < 0.0;
+  for (int i = 1; i < n; ++i) {
+    const double t = (double)d[i] - x, b = (double)e2[i - 1];
+    double p2 = t * p1 - b * p0;
+    const double q2 = t * q1 - b * q0 - p1;
+    if (p2 == 0.0) p2 = -copysign(fmax(fabs(p1) * 0x1p-52, 0x1p-1000), p1);   // zero pivot -> negative
+    cnt += (p2 < 0.0) != (p1 < 0.0);
+    p0 = p1; p1 = p2; q0 = q1; q1 = q2;
+    if ((i & 15) == 0) {                       // keep the sequence in range: exact 2^-e scaling
+      const double m = fmax(fmax(fabs(p0), fabs(p1)), fmax(fabs(q0), fabs(q1)));
+      if (m > 0x1p+400 || (m < 0x1p-400 && m > 0.0)) {
+        const int e = ilogb(m);
+        p0 = scalbn(p0, -e); p1 = scalbn(p1, -e); q0 = scalbn(q0, -e); q1 = scalbn(q1, -e);
+      }
+    }
+  }
+  step = (q1 != 0.0) ? -p1 / q1 : 0.0;
+  return cnt;
+}
+
+// Safeguarded Newton for eigenvalue k inside [lo, hi] (count(lo) <= k < count(hi)).
+template <typename S>
+__device__ __forceinline__ double newton_polish(const S* d, const S* e2, int n, int k, double lo, double hi,
+                                                int passes) {
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < passes; ++it) {
+    double step;
+    const int c = sturm_newton64<S>(d, e2, n, x, step);
+    if (c >= k + 1) hi = x; else lo = x;
+    const double xn = x + step;
+    const bool inside = xn > lo && xn < hi;
+    const double nx = inside ? xn : 0.5 * (lo + hi);
+    if (nx == x || hi - lo <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) { x = nx; break; }
+    if (inside && fabs(step) <= 2.0 * DBL_EPSILON * fabs(x)) { x = nx; break; }
+    x = nx;
+  }
+  return x;
+}
+
 template <typename T>
 __device__ __forceinline__ T ulp_of(T x) {
   if constexpr (sizeof(T) == 4) return fabsf(x) * FLT_EPSILON + FLT_MIN;
@@ -54,25 +112,30 @@ __device__ __forceinline__ void bisect_index(const S* d, const S* e2, int n, int
   }
 }
 
-// One group of G threads per matrix, MPB groups per CTA.  S = storage type of
-// (d, e^2); float64 bisection when S is double, float32 + refine otherwise.
+// One group of G threads per (matrix, chunk of `chunk` eigenvalue indices),
+// MPB groups per CTA; every group holds its matrix's whole (d, e^2) in shared
+// memory.  S = storage type of (d, e^2).
 template <typename S, int G, int MPB>
 __global__ void __launch_bounds__(G* MPB)
 k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __restrict__ n_act_cell,
-         int K2, int n_max, int64_t n_mat, int refine, double* __restrict__ eigs) {
+         int K2, int n_max, int64_t n_mat, int chunk, int refine, double* __restrict__ eigs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int gid = threadIdx.x / G, tid = threadIdx.x % G;
-  const int64_t mat = (int64_t)blockIdx.x * MPB + gid;
+  const int n_chunks = (n_max + chunk - 1) / chunk;
+  const int64_t gidx = (int64_t)blockIdx.x * MPB + gid;
+  const int64_t mat = gidx / n_chunks;
+  const int c_lo = (int)(gidx - mat * n_chunks) * chunk;
+  const int c_hi = min(n_max, c_lo + chunk);
   if (mat >= n_mat) return;
   S* d = reinterpret_cast<S*>(smem_raw) + (size_t)gid * 2 * n_max;
   S* e2 = d + n_max;
   __shared__ double red_lo[MPB][G / 32], red_hi[MPB][G / 32], red_e[MPB][G / 32];
   const int n = n_act_cell ? n_act_cell[mat / K2] : n_max;
   double* out = eigs + mat * n_max;
-  for (int i = tid; i < n_max; i += G) {
+  for (int i = c_lo + tid; i < c_hi; i += G) {
     if (i >= n) out[i] = __longlong_as_double(0x7ff8000000000000ll);   // NaN padding
   }
-  if (n <= 0) return;
+  if (n <= 0 || c_lo >= n) return;
   // Gershgorin bounds and the largest e^2, in double for safety
   double glo = 1e300, ghi = -1e300, emax = 0.0;
   for (int i = tid; i < n; i += G) {
@@ -106,38 +169,39 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   const double span = fmax(ghi - glo, 1e-30);
   glo -= 1e-6 * span + 1e-12;   // float rounding of the reduced bounds
   ghi += 1e-6 * span + 1e-12;
-  for (int k = tid; k < n; k += G) {
+  const float piv32 = 1e-30f * fmaxf(1.0f, (float)emax);
+  for (int k = c_lo + tid; k < min(n, c_hi); k += G) {
     if constexpr (sizeof(S) == 8) {
-      const double piv = 1e-290 * fmax(1.0, emax);
-      double lo = glo, hi = ghi;
-      bisect_index<double, S>(d, e2, n, k, piv, lo, hi, 200);
-      out[k] = 0.5 * (lo + hi);
+      // float32 bracket on the rounded tridiagonal (float64 data read and
+      // rounded on the fly), widened, checked in float64, then polished
+      float lo32 = (float)glo, hi32 = (float)ghi;
+      bisect_index<float, S>(d, e2, n, k, piv32, lo32, hi32, 100);
+      const double w = 64.0 * (double)FLT_EPSILON * fmax(fabs(glo), fabs(ghi)) + 1e-12;
+      double lo = fmax(glo, (double)lo32 - w), hi = fmin(ghi, (double)hi32 + w);
+      double st;
+      if (sturm_newton64<S>(d, e2, n, lo, st) > k) lo = glo;      // bracket lost: fall back
+      if (sturm_newton64<S>(d, e2, n, hi, st) < k + 1) hi = ghi;
+      out[k] = newton_polish<S>(d, e2, n, k, lo, hi, 60);
     } else {
-      const float piv = 1e-30f * fmaxf(1.0f, (float)emax);
       float lo = (float)glo, hi = (float)ghi;
-      bisect_index<float, S>(d, e2, n, k, piv, lo, hi, 100);
-      double dlo = lo, dhi = hi;
-      const double piv64 = 1e-290 * fmax(1.0, emax);
-      for (int it = 0; it < refine; ++it) {
-        const double mid = 0.5 * (dlo + dhi);
-        if (sturm_count<double, S>(d, e2, n, mid, piv64) >= k + 1) dhi = mid;
-        else dlo = mid;
-      }
-      out[k] = 0.5 * (dlo + dhi);
+      bisect_index<float, S>(d, e2, n, k, piv32, lo, hi, 100);
+      out[k] = refine > 0 ? newton_polish<S>(d, e2, n, k, (double)lo, (double)hi, refine)
+                          : 0.5 * ((double)lo + (double)hi);
     }
   }
 }
 
 template <typename S, int G, int MPB>
 int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int n_max, int64_t n_mat,
-               int refine, double* eigs, cudaStream_t s) {
+               int refine, double* eigs, cudaStream_t s, int chunk) {
   const size_t smem = sizeof(S) * 2 * (size_t)n_max * MPB;
   auto kern = k_bisect<S, G, MPB>;
   IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t blocks = (n_mat + MPB - 1) / MPB;
+  const int64_t groups = n_mat * ((n_max + chunk - 1) / chunk);
+  const int64_t blocks = (groups + MPB - 1) / MPB;
   ProfScope ps(KID_BISECT, s);
   kern<<<(unsigned)blocks, G * MPB, smem, s>>>(reinterpret_cast<const S*>(d), reinterpret_cast<const S*>(e2),
-                                               n_act_cell, K2, n_max, n_mat, refine, eigs);
+                                               n_act_cell, K2, n_max, n_mat, chunk, refine, eigs);
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
 }
@@ -145,12 +209,11 @@ int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int
 template <typename S>
 int bisect_t(int refine, const void* d, const void* e2, const int* n_act_cell, int K2, int n_max,
              int64_t n_mat, double* eigs, cudaStream_t s) {
-  if (n_max <= 32) return run_bisect<S, 32, 8>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s);
-  if (n_max <= 64) return run_bisect<S, 64, 4>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s);
-  if (n_max <= 128) return run_bisect<S, 128, 2>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s);
-  if (n_max <= 256) return run_bisect<S, 256, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s);
-  if (n_max <= 512) return run_bisect<S, 512, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s);
-  return run_bisect<S, 1024, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s);
+  if (n_max <= 32) return run_bisect<S, 32, 8>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max);
+  if (n_max <= 64) return run_bisect<S, 64, 4>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max);
+  if (n_max <= 128) return run_bisect<S, 128, 2>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max);
+  // larger matrices: 128 eigenvalue indices per CTA, so one matrix spreads over n/128 SMs
+  return run_bisect<S, 128, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, 128);
 }
 
 }  // namespace

@@ -11,8 +11,8 @@
 namespace idos {
 
 enum KernelId {
-  KID_MASKS = 0, KID_CORNERS, KID_CELL_MAPS, KID_SMALL_TRIDIAG, KID_LG_ASSEMBLE, KID_LG_START,
-  KID_LG_GEMV, KID_LG_FINISH, KID_LG_HER2K, KID_BISECT, KID_IDOS, KID_LEVEL_STATS, KID_COUNT
+  KID_MASKS = 0, KID_CORNERS, KID_CELL_MAPS, KID_SMALL_TRIDIAG, KID_LG_ASSEMBLE, KID_LG_TRIDIAG,
+  KID_BISECT, KID_IDOS, KID_LEVEL_STATS, KID_COUNT
 };
 
 const char* kernel_name(int kid);
