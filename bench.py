@@ -173,28 +173,26 @@ def n_act_of(masks, N):
     return fine, np.stack(corners, 1)
 
 
-def algorithmic_work(m, levels, M, seed, firsts, fp_bytes=8):
+def algorithmic_work(m, levels, M, seed, firsts, bw=16):
     """Exact algorithmic work of one step from the samples' kept-site counts:
-    flops of the small-matrix Householder kernel (16/3 n^3 per matrix) and
-    bytes of the large-matrix kernel: the trailing block read once per column
-    by the GEMV (sum_j (n-j-1)^2 entries) plus read and written once per panel
-    by the rank-2NB update."""
+    flops of the small-matrix Householder kernel (16/3 n^3 per matrix) and of
+    the large-matrix band reduction: per panel of bw columns with m rows below
+    it, W = A22 (Y T) (8 m^2 bw real flops) and the full-storage rank-2bw
+    update (16 m^2 bw)."""
     import numpy as np
     small_flops = 0.0
-    large_bytes = 0.0
-    nb = 32
+    band_flops = 0.0
 
     def add(n_arr, K2, big):
-        nonlocal small_flops, large_bytes
+        nonlocal small_flops, band_flops
         n = n_arr.astype(np.float64)
         if not big:
             small_flops += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
         else:
-            # sum_{j=0}^{n-2} (n-j-1)^2 = (n-1) n (2n-1) / 6
-            large_bytes += K2 * fp_bytes * float(np.sum((n - 1) * n * (2 * n - 1) / 6.0))
             for nn in n_arr:
-                for jn in range(nb, int(nn), nb):
-                    large_bytes += K2 * 2.0 * fp_bytes * (nn - jn) ** 2
+                for k in range(0, int(nn) - bw, bw):
+                    mm = nn - k - bw
+                    band_flops += K2 * 24.0 * bw * mm * mm
     for l, (N, K) in enumerate(levels):
         if not M[l]:
             continue
@@ -206,13 +204,13 @@ def algorithmic_work(m, levels, M, seed, firsts, fp_bytes=8):
             Kc = levels[l - 1][1]
             bigc = 2 * (N // 2) ** 2 > 160
             add(corners.reshape(-1), Kc * Kc, bigc)
-    return {"k_small_tridiag": small_flops, "k_lg_persist": large_bytes}
+    return {"k_small_tridiag": small_flops, "k_lg_band": band_flops}
 
 
 def roofline(prof, work, steps, pk, pk_kind, clocks):
     """Roofline object for the kernel with the largest event time."""
     ranked = sorted(prof.items(), key=lambda kv: -kv[1][0])
-    models = {"k_lg_persist": "hbm", "k_small_tridiag": "alu"}
+    models = {"k_lg_band": "alu", "k_small_tridiag": "alu"}
     for name, (ms, launches) in ranked:
         if name not in models:
             continue
@@ -318,9 +316,8 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step(idx):
-        for l, Ml in enumerate(M):
-            if Ml:
-                model.sample_level(l, Ml, seed, first_sample=idx * Ml)
+        # every level of the allocation at once (concurrent level streams)
+        model.sample_levels(M, seed, [idx * Ml for Ml in M])
 
     def barrier():
         if world > 1:
@@ -372,7 +369,7 @@ def run_gpu(args):
 
     # algorithmic work of the timed steps (exact kept-site counts)
     firsts_steps = [[(args.warmup + k) * Ml for Ml in M] for k in range(args.steps)]
-    work = {"k_small_tridiag": 0.0, "k_lg_persist": 0.0}
+    work = {"k_small_tridiag": 0.0, "k_lg_band": 0.0}
     for firsts in firsts_steps:
         wk = algorithmic_work(model, levels, M, seed, firsts)
         for k2 in work:

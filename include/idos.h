@@ -127,6 +127,16 @@ int idos_sample_level_detail(idos_model* m, int level, int64_t n_samples, uint64
                              int64_t first_sample, double* per_sample_Y,
                              double* Q_fine, double* Q_coarse);
 
+/* All levels at once: n_samples[l] outcomes of every level l (0 skips a
+ * level), sample indices first_sample[l] ... (or, when first_sample is NULL,
+ * continuing after the samples the level already holds), generator key seed.
+ * Same results as one idos_sample_level call per level; the levels run
+ * concurrently on streams of their own (each with its own workspace), after
+ * the work already queued on the model's stream, so that the latency-bound
+ * phases of the largest matrices overlap the other levels' work.  Returns
+ * when every level is done. */
+int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, const int64_t* first_sample);
+
 /* Read the accumulators of one level: *M samples, sum[n_E], sumsq[n_E]
  * (host, may be NULL), *seconds of GPU time spent on the level (may be NULL). */
 int idos_get_level_stats(const idos_model* m, int level, int64_t* M, double* sum,

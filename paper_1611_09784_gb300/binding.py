@@ -60,6 +60,7 @@ _SYMBOLS = {
     "idos_sample_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_int64, C.c_void_p]),
     "idos_sample_level_detail": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_int64,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_sample_levels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     "idos_get_level_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p,
                                        C.POINTER(C.c_double)]),
     "idos_reset_level_stats": (C.c_int, [C.c_void_p, C.c_int]),
@@ -179,6 +180,12 @@ class Model:
         _check(load_library().idos_sample_level(self._h, level, n_samples, seed, first_sample, _ptr(Y)),
                "idos_sample_level")
         return Y
+
+    def sample_levels(self, n_samples, seed: int, first_samples=None):
+        """All levels at once (concurrent streams); n_samples[l] per level."""
+        ns = np.ascontiguousarray(n_samples, dtype=np.int64)
+        fs = None if first_samples is None else np.ascontiguousarray(first_samples, dtype=np.int64)
+        _check(load_library().idos_sample_levels(self._h, _ptr(ns), seed, _ptr(fs)), "idos_sample_levels")
 
     def sample_level_detail(self, level: int, n_samples: int, seed: int, first_sample: int = 0):
         Y = np.empty((n_samples, self.n_E))

@@ -94,14 +94,15 @@ EnergyGrid grid_of(const idos_model_desc& d) {
 
 // Eigen-solve + IDoS of every cell of `cells` on a Kside grid: Q[count][n_E].
 // `eigs_keep` (optional) receives the device eigenvalue buffer pointer.
-int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double** eigs_keep) {
+int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double** eigs_keep, cudaStream_t st,
+                   Arena& ws) {
   const int n_max = cells.n_sites;
   const int K2 = Kside * Kside;
   const int64_t n_mat = cells.count * (int64_t)K2;
   const size_t ts = tsize(M->d.precision);
-  void* d = M->ws.take<char>(ts * n_mat * n_max);
-  void* e2 = M->ws.take<char>(ts * n_mat * n_max);
-  double* eigs = M->ws.take<double>((size_t)n_mat * n_max);
+  void* d = ws.take<char>(ts * n_mat * n_max);
+  void* e2 = ws.take<char>(ts * n_mat * n_max);
+  double* eigs = ws.take<double>((size_t)n_mat * n_max);
   if (!d || !e2 || !eigs) {
     set_error("workspace too small for the eigen-solve buffers");
     return IDOS_ERR_OUT_OF_MEMORY;
@@ -115,14 +116,13 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.eps = M->d.eps_onsite;
   a.d = d;
   a.e2 = e2;
-  a.stream = M->stream;
-  a.ws = &M->ws;
+  a.stream = st;
+  a.ws = &ws;
   if (small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
-  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs,
-                         M->stream));
+  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
   const double area = (double)cells.N * cells.N * cell_area(M->d.a);
-  IDOS_TRY(launch_idos(eigs, cells.n_act, K2, n_max, cells.count, area, grid_of(M->d), Q, M->stream));
+  IDOS_TRY(launch_idos(eigs, cells.n_act, K2, n_max, cells.count, area, grid_of(M->d), Q, st));
   if (eigs_keep) *eigs_keep = eigs;
   return IDOS_OK;
 }
@@ -159,8 +159,11 @@ size_t large_room(const Model* M, int N, int Kside, int64_t count) {
   return std::max(one, std::min(want, cap));
 }
 
-int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh,
-              double* Qfh, double* Qch) {
+// Samples of one level on stream st with workspace ws.  blocking: wait for
+// the level to finish and add its time and count to the accumulators;
+// otherwise the caller does that after synchronising ev1.
+int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh, double* Qfh,
+              double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, bool blocking) {
   const idos_model_desc& d = M->d;
   const int Nf = d.N[level], Kf = d.Kside[level];
   const bool coarse = level > 0;
@@ -171,52 +174,54 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
                             3 * n_E * sizeof(double);
   int64_t chunk = std::max<int64_t>(1, (int64_t)(kSmallBudget / per_sample));
   chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_samples, 1));
-  IDOS_CUDA_TRY(cudaEventRecord(M->ev0, M->stream));
+  IDOS_CUDA_TRY(cudaEventRecord(ev0, st));
   for (int64_t s0 = 0; s0 < n_samples; s0 += chunk) {
     const int64_t S = std::min(chunk, n_samples - s0);
     const size_t need = S * per_sample + 64 * 1024 + ((S + 63) / 64) * 2 * n_E * 8 +
                         std::max(large_room(M, Nf, Kf, S), coarse ? large_room(M, Nc, Kc, 4 * S) : 0);
-    IDOS_TRY(M->ws.reserve(need, M->stream));
-    M->ws.reset();
+    IDOS_TRY(ws.reserve(need, st));
+    ws.reset();
     CellSet fine, crs;
-    if (!take_cells(M->ws, fine, Nf, S)) { set_error("workspace (fine cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
-    double* Qf = M->ws.take<double>((size_t)S * n_E);
-    double* Y = M->ws.take<double>((size_t)S * n_E);
+    if (!take_cells(ws, fine, Nf, S)) { set_error("workspace (fine cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
+    double* Qf = ws.take<double>((size_t)S * n_E);
+    double* Y = ws.take<double>((size_t)S * n_E);
     double* Qc = nullptr;
     if (coarse) {
-      if (!take_cells(M->ws, crs, Nc, 4 * S)) { set_error("workspace (corner cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
-      Qc = M->ws.take<double>((size_t)4 * S * n_E);
+      if (!take_cells(ws, crs, Nc, 4 * S)) { set_error("workspace (corner cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
+      Qc = ws.take<double>((size_t)4 * S * n_E);
     }
     if (!Qf || !Y || (coarse && !Qc)) { set_error("workspace (IDoS buffers)"); return IDOS_ERR_OUT_OF_MEMORY; }
-    IDOS_TRY(launch_fine_masks(fine.mask, fine.n_sites, S, seed, level, first + s0, d.p, M->stream));
-    IDOS_TRY(launch_cell_maps(fine, M->stream));
+    IDOS_TRY(launch_fine_masks(fine.mask, fine.n_sites, S, seed, level, first + s0, d.p, st));
+    IDOS_TRY(launch_cell_maps(fine, st));
     if (coarse) {
-      IDOS_TRY(launch_corner_masks(fine.mask, Nf, S, crs.mask, M->stream));
-      IDOS_TRY(launch_cell_maps(crs, M->stream));
+      IDOS_TRY(launch_corner_masks(fine.mask, Nf, S, crs.mask, st));
+      IDOS_TRY(launch_cell_maps(crs, st));
     }
     // the large path takes its dense batch from whatever is left, so the
     // bigger solve goes last
-    const size_t mark = M->ws.used;
+    const size_t mark = ws.used;
     if (coarse) {
-      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr));
-      M->ws.used = mark;
+      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st, ws));
+      ws.used = mark;
     }
-    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr));
-    M->ws.used = mark;
+    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws));
+    ws.used = mark;
     double* acc = M->acc + (size_t)level * 2 * n_E;
-    IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, M->ws, M->stream));
-    if (Yh) IDOS_CUDA_TRY(cudaMemcpyAsync(Yh + s0 * n_E, Y, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, M->stream));
-    if (Qfh) IDOS_CUDA_TRY(cudaMemcpyAsync(Qfh + s0 * n_E, Qf, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, M->stream));
+    IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, ws, st));
+    if (Yh) IDOS_CUDA_TRY(cudaMemcpyAsync(Yh + s0 * n_E, Y, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, st));
+    if (Qfh) IDOS_CUDA_TRY(cudaMemcpyAsync(Qfh + s0 * n_E, Qf, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, st));
     if (Qch && coarse)
-      IDOS_CUDA_TRY(cudaMemcpyAsync(Qch + s0 * 4 * n_E, Qc, sizeof(double) * 4 * S * n_E, cudaMemcpyDeviceToHost, M->stream));
-    if (Yh || Qfh || Qch) IDOS_CUDA_TRY(cudaStreamSynchronize(M->stream));
+      IDOS_CUDA_TRY(cudaMemcpyAsync(Qch + s0 * 4 * n_E, Qc, sizeof(double) * 4 * S * n_E, cudaMemcpyDeviceToHost, st));
+    if (Yh || Qfh || Qch) IDOS_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  IDOS_CUDA_TRY(cudaEventRecord(M->ev1, M->stream));
-  IDOS_CUDA_TRY(cudaEventSynchronize(M->ev1));
-  float ms = 0.f;
-  IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, M->ev0, M->ev1));
-  M->M[level] += n_samples;
-  M->seconds[level] += ms * 1e-3;
+  IDOS_CUDA_TRY(cudaEventRecord(ev1, st));
+  if (blocking) {
+    IDOS_CUDA_TRY(cudaEventSynchronize(ev1));
+    float ms = 0.f;
+    IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+    M->M[level] += n_samples;
+    M->seconds[level] += ms * 1e-3;
+  }
   return IDOS_OK;
 }
 
@@ -286,6 +291,12 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
   if (e == cudaSuccess) e = cudaMemsetAsync(m->acc, 0, acc_bytes, m->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
+  for (int l = 0; l < d->n_levels && e == cudaSuccess; ++l) {
+    e = cudaStreamCreateWithFlags(&m->lstream[l], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&m->lev0[l]);
+    if (e == cudaSuccess) e = cudaEventCreate(&m->lev1[l]);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) {
     set_error(std::string("model allocation: ") + cudaGetErrorString(e));
@@ -302,6 +313,16 @@ void idos_destroy_model(idos_model* m) {
   if (m->acc) cudaFree(m->acc);
   if (m->ev0) cudaEventDestroy(m->ev0);
   if (m->ev1) cudaEventDestroy(m->ev1);
+  if (m->fork) cudaEventDestroy(m->fork);
+  for (int l = 0; l < IDOS_MAX_LEVELS; ++l) {
+    if (m->lstream[l]) {
+      cudaStreamSynchronize(m->lstream[l]);
+      cudaStreamDestroy(m->lstream[l]);
+    }
+    if (m->lev0[l]) cudaEventDestroy(m->lev0[l]);
+    if (m->lev1[l]) cudaEventDestroy(m->lev1[l]);
+    m->lws[l].release();
+  }
   m->ws.release();
   delete m;
 }
@@ -313,12 +334,46 @@ int idos_sample_level_detail(idos_model* m, int level, int64_t n_samples, uint64
   if (n_samples < 0 || first_sample < 0) { set_error("negative sample count or index"); return IDOS_ERR_INVALID_ARG; }
   if (n_samples == 0) return IDOS_OK;
   ProfGuard pg(m);
-  return run_level(m, level, n_samples, seed, first_sample, per_sample_Y, Q_fine, Q_coarse);
+  return run_level(m, level, n_samples, seed, first_sample, per_sample_Y, Q_fine, Q_coarse, m->stream, m->ws, m->ev0,
+                   m->ev1, true);
 }
 
 int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed, int64_t first_sample,
                       double* per_sample_Y) {
   return idos_sample_level_detail(m, level, n_samples, seed, first_sample, per_sample_Y, nullptr, nullptr);
+}
+
+int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, const int64_t* first_sample) {
+  if (!m || !n_samples) { set_error("null model or sample counts"); return IDOS_ERR_INVALID_ARG; }
+  const int L = m->d.n_levels;
+  for (int l = 0; l < L; ++l) {
+    if (n_samples[l] < 0 || (first_sample && first_sample[l] < 0)) {
+      set_error("negative sample count or index");
+      return IDOS_ERR_INVALID_ARG;
+    }
+  }
+  ProfGuard pg(m);
+  // every level stream starts after the work already queued on the model's stream
+  IDOS_CUDA_TRY(cudaEventRecord(m->fork, m->stream));
+  for (int l = 0; l < L; ++l) IDOS_CUDA_TRY(cudaStreamWaitEvent(m->lstream[l], m->fork, 0));
+  // costliest level first, so its long latency-bound phases overlap the rest
+  int order[IDOS_MAX_LEVELS];
+  for (int l = 0; l < L; ++l) order[l] = L - 1 - l;
+  for (int q = 0; q < L; ++q) {
+    const int l = order[q];
+    if (n_samples[l] == 0) continue;
+    IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr, nullptr,
+                       m->lstream[l], m->lws[l], m->lev0[l], m->lev1[l], false));
+  }
+  for (int l = 0; l < L; ++l) {
+    if (n_samples[l] == 0) continue;
+    IDOS_CUDA_TRY(cudaEventSynchronize(m->lev1[l]));
+    float ms = 0.f;
+    IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, m->lev0[l], m->lev1[l]));
+    m->M[l] += n_samples[l];
+    m->seconds[l] += ms * 1e-3;
+  }
+  return IDOS_OK;
 }
 
 int idos_get_level_stats(const idos_model* m, int level, int64_t* M, double* sum, double* sumsq,
@@ -370,7 +425,7 @@ int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_
   }
   IDOS_TRY(launch_cell_maps(c, m->stream));
   double* eigs = nullptr;
-  IDOS_TRY(solve_and_idos(m, c, Kside, Q, &eigs));
+  IDOS_TRY(solve_and_idos(m, c, Kside, Q, &eigs, m->stream, m->ws));
   IDOS_CUDA_TRY(cudaMemcpyAsync(idos_out, Q, sizeof(double) * n_E, cudaMemcpyDeviceToHost, m->stream));
   if (eigs_out)
     IDOS_CUDA_TRY(cudaMemcpyAsync(eigs_out, eigs, sizeof(double) * Kside * Kside * c.n_sites,

@@ -66,6 +66,11 @@ struct SolveArgs {
 struct Model {
   idos_model_desc d{};
   cudaStream_t stream = 0;
+  // one stream, workspace and event pair per level for idos_sample_levels
+  cudaStream_t lstream[IDOS_MAX_LEVELS] = {};
+  Arena lws[IDOS_MAX_LEVELS];
+  cudaEvent_t lev0[IDOS_MAX_LEVELS] = {}, lev1[IDOS_MAX_LEVELS] = {};
+  cudaEvent_t fork = nullptr;
   double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
   int64_t M[IDOS_MAX_LEVELS] = {};
   double seconds[IDOS_MAX_LEVELS] = {};

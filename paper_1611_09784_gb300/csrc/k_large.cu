@@ -1,157 +1,53 @@
-// k_large.cu - blocked Householder tridiagonalisation of large Hermitian
-// matrices held in global memory (L2 / HBM), batched, in ONE persistent
-// cooperative kernel per batch.
+// k_large.cu - two-stage reduction of large Hermitian matrices (held in
+// global memory, batched) to real symmetric tridiagonal form.
 //
-// Same reflectors as k_small.cu (real tau, |e_j| = ||x||), organised in
-// panels of NB columns (the LATRD arrangement): inside a panel the trailing
-// matrix keeps its panel-start value and every column is corrected on the fly
-// by the panel's earlier (v, w) pairs,  A_cur = A_start - V W^H - W V^H,  so the
-// matrix-vector product of each column is a GEMV with the panel-start matrix
-// plus thin corrections; after the panel, A -= V W^H + W V^H (rank 2NB).
-//
-// All CTAs of the grid walk the columns in lockstep; one column is two
-// phases separated by grid barriers:
-//   R   rows (256-row tiles): finish column j-1 (p = tau (y - V s1 - W s2),
-//       w = p - K v with K = tau^2/2 (Re v^H y - 2 Re s2^H s1), all from
-//       partials) and start column j: corrected column -> x (kept in V[i]),
-//       d_j, partial ||x||^2, partial W^H x, V^H x
-//   G   GEMV tiles (256 rows x 64 columns): partial y = A22 v and v^H y
-// and every panel ends with the rank-2NB update (two more barriers).
-// Reductions go through per-tile partials (double-buffered by column parity)
-// that every consumer re-sums in a fixed order, so results are deterministic.
-// Data written by other CTAs is read with L1-bypassing loads.
-//
-// Grid barrier: sense-reversal on a global counter; every wait is bounded
-// (~2 s); on timeout the kernel sets an error flag, all CTAs leave, and the
-// host returns IDOS_ERR_TIMEOUT.
+// Stage 1, dense -> band of half-width BW: for every panel of BW columns,
+//   Householder QR of the block below the band, P = Q R with
+//   Q = H_0 ... H_{BW-1} = I - Y T Y^H (compact WY, T upper triangular,
+//   H_c = I - tau_c y_c y_c^H with real tau_c as in k_small.cu), then the
+//   two-sided update of the trailing matrix  A22 <- Q^H A22 Q  as
+//     W = A22 (Y T),  M = Y^H W,  Z = W - 1/2 Y (T^H M),  A22 -= Y Z^H + Z Y^H
+//   (Q^H A Q = A - W Y^H - Y W^H + Y T^H Y^H W Y^H and W^H Y T = T^H Y^H W,
+//   so the update is the Hermitian rank-2BW form above).  Four batched
+//   launches per panel: panel QR (one CTA per matrix), W = A22 YT (tiled,
+//   split over the inner dimension), Z (one CTA per matrix), the rank-2BW
+//   update (tiled).
+// Stage 2, band -> tridiagonal by bulge chasing, one CTA per matrix: sweep i
+//   annihilates column i below the subdiagonal with a length-BW reflector
+//   applied two-sided to the next diagonal block; the reflector's right
+//   application to the block below creates a bulge whose first column the
+//   next reflector annihilates, and so on down the band.  Sweep i runs its
+//   step k at time 3i + k (one warp per active sweep, a CTA barrier per time
+//   step): steps running at the same time touch disjoint blocks, and the
+//   lower bandwidth never exceeds 2 BW.
+// The tridiagonal comes out as d = Re diag, e^2 = |subdiag|^2.
+#include <cooperative_groups.h>
+
 #include "graphene.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace idos {
 
 namespace {
 
-constexpr int NB = 32;    // panel width
-constexpr int PT = 256;   // threads per CTA = rows per tile
-constexpr int CS = 64;    // GEMV column slice
-constexpr int HT = 32;    // her2k tile side
+constexpr int BW = 16;          // band half-width
+constexpr int ND = 2 * BW + 1;  // stored diagonals during the chase
+constexpr int PQ_THREADS = 512; // panel QR / Z kernels
+// Tile sizes keep static shared memory under 48 KB for both element types.
+template <typename T> struct Tiles;
+template <> struct Tiles<float> { static constexpr int GT = 64, WR = 64, WK = 64; };
+template <> struct Tiles<double> { static constexpr int GT = 32, WR = 32, WK = 32; };
+// Warps of the chase kernel (each active sweep needs one; more sweeps than
+// warps are taken in turn), bounded by the kernel's register use.
+template <typename T> struct Chase;
+template <> struct Chase<float> { static constexpr int WARPS = 16; };
+template <> struct Chase<double> { static constexpr int WARPS = 8; };
 
 template <typename T> __device__ __forceinline__ T tiny_rest();
 template <> __device__ __forceinline__ float tiny_rest<float>() { return 1e-30f; }
 template <> __device__ __forceinline__ double tiny_rest<double>() { return 1e-290; }
-
-template <typename T> __device__ __forceinline__ c2<T> ldcg(const c2<T>* p);
-template <> __device__ __forceinline__ float2 ldcg<float>(const float2* p) { return __ldcg(p); }
-template <> __device__ __forceinline__ double2 ldcg<double>(const double2* p) { return __ldcg(p); }
-
-template <typename T>
-struct PState {
-  int n_max, B, K2, ntile, nslice;
-  int64_t mat0;
-  const int* n_act_cell;    // may be null (all n_max)
-  c2<T>* A;                 // [B][n_max][n_max]
-  c2<T>* V;                 // [B][NB][n_max]
-  c2<T>* W;                 // [B][NB][n_max]
-  c2<T>* part;              // [B][nslice][n_max] GEMV partials
-  T* prest;                 // [2][B][ntile]
-  T* gvy;                   // [2][B][ntile][nslice] partials of Re(v^H A22 v)
-  c2<T>* ps;                // [2][B][ntile][2 NB]
-  c2<T>* alpha;             // [2][B]
-  T* d_out;                 // [B][n_max]
-  T* e2_out;                // [B][n_max]
-  unsigned int* bar;        // [0] count, [1] generation
-  int* err;
-};
-
-template <typename T>
-__device__ __forceinline__ int mat_n(const PState<T>& s, int b) {
-  return s.n_act_cell ? s.n_act_cell[(s.mat0 + b) / s.K2] : s.n_max;
-}
-
-// Bounded sense-reversal grid barrier.  Returns false when the grid must stop.
-__device__ __forceinline__ bool grid_sync(unsigned int* bar, int* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = bar + 1;
-    const unsigned int gen = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == gen) {
-        if (*(volatile int*)err) break;
-        if (++spins > (1ll << 24)) {   // ~2 s with the back-off below
-          atomicExch(err, 1);
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    s_ok = *(volatile int*)err == 0;
-  }
-  __syncthreads();
-  return s_ok;
-}
-
-// sigma^2, alpha, tau and v_{j+1} of column j from the partials.
-template <typename T>
-struct Reflector {
-  T rest, sigma2, tau;
-  c2<T> alpha, v1;
-  int tr;
-};
-
-template <typename T>
-__device__ __forceinline__ Reflector<T> reflector(const PState<T>& s, int b, int par) {
-  Reflector<T> R;
-  T rest = T(0);
-  const T* pr = s.prest + ((size_t)par * s.B + b) * s.ntile;
-  for (int t = 0; t < s.ntile; ++t) rest += __ldcg(pr + t);
-  R.rest = rest;
-  R.alpha = ldcg<T>(s.alpha + (size_t)par * s.B + b);
-  const T aa2 = cabs2<T>(R.alpha);
-  R.sigma2 = aa2 + rest;
-  R.tr = rest > tiny_rest<T>();
-  R.tau = T(0);
-  R.v1 = mk<T>(T(0), T(0));
-  if (R.tr) {
-    const T sigma = sqrt(R.sigma2), aa = sqrt(aa2);
-    const c2<T> ph = aa > T(0) ? cscale<T>(R.alpha, T(1) / aa) : mk<T>(T(1), T(0));
-    R.tau = T(1) / (sigma * (sigma + aa));
-    R.v1 = cadd<T>(R.alpha, cscale<T>(ph, sigma));
-  }
-  return R;
-}
-
-// Fixed-order block sum of one value per thread (PT threads).
-template <typename T>
-__device__ __forceinline__ T block_reduce(T v, T* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  T s = T(0);
-#pragma unroll
-  for (int w = 0; w < PT / 32; ++w) s += red[w];
-  return s;
-}
-
-// Everything every row unit needs about column j once its GEMV is done:
-// the reflector, s1 = W^H v, s2 = V^H v (q < i), K, and p at row j + 1.
-template <typename T>
-struct ColumnInfo {
-  Reflector<T> R;
-  T K;
-  c2<T> s1[NB], s2[NB];
-  c2<T> p1;     // p_{j+1}
-};
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -160,373 +56,26 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Reflector of column j computed by one warp (lanes load the tile partials).
 template <typename T>
-__device__ __forceinline__ Reflector<T> reflector_warp(const PState<T>& s, int b, int par) {
-  const int lane = threadIdx.x & 31;
-  T rest = T(0);
-  const T* pr = s.prest + ((size_t)par * s.B + b) * s.ntile;
-  for (int t = lane; t < s.ntile; t += 32) rest += __ldcg(pr + t);
-  rest = warp_sum<T>(rest);
-  Reflector<T> R;
-  R.rest = rest;
-  R.alpha = ldcg<T>(s.alpha + (size_t)par * s.B + b);
-  const T aa2 = cabs2<T>(R.alpha);
-  R.sigma2 = aa2 + rest;
-  R.tr = rest > tiny_rest<T>();
-  R.tau = T(0);
-  R.v1 = mk<T>(T(0), T(0));
-  if (R.tr) {
-    const T sigma = sqrt(R.sigma2), aa = sqrt(aa2);
-    const c2<T> ph = aa > T(0) ? cscale<T>(R.alpha, T(1) / aa) : mk<T>(T(1), T(0));
-    R.tau = T(1) / (sigma * (sigma + aa));
-    R.v1 = cadd<T>(R.alpha, cscale<T>(ph, sigma));
-  }
-  return R;
+__device__ __forceinline__ c2<T> shfl_c(c2<T> v, int src) {
+  return mk<T>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-template <typename T>
-__device__ void column_info(const PState<T>& s, int b, int j, int i, ColumnInfo<T>& ci, T* red) {
-  using C = c2<T>;
-  const int nm = s.n_max, par = j & 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const C* Vb = s.V + (size_t)b * NB * nm;
-  const C* Wb = s.W + (size_t)b * NB * nm;
-  const int n_b = mat_n(s, b);
-  if (warp == 0) {
-    const Reflector<T> R = reflector_warp<T>(s, b, par);
-    if (lane == 0) ci.R = R;
-  }
-  __syncthreads();
-  const C v1 = ci.R.v1;
-  // s1_q (warp 1..) and s2_q: one thread per (q, which), tile partials in order
-  if (threadIdx.x < 2 * i) {
-    const int q = threadIdx.x % i, which = threadIdx.x / i;   // 0: s1 (W), 1: s2 (V)
-    C acc = mk<T>(T(0), T(0));
-    const C* pp = s.ps + ((size_t)par * s.B + b) * s.ntile * (2 * NB);
-    for (int tt = 0; tt < s.ntile; ++tt) acc = cadd<T>(acc, ldcg<T>(pp + (size_t)tt * 2 * NB + which * NB + q));
-    acc = cadd<T>(acc, cjmul<T>(ldcg<T>((which == 0 ? Wb : Vb) + (size_t)q * nm + j + 1), v1));
-    if (which == 0) ci.s1[q] = acc; else ci.s2[q] = acc;
-  }
-  // Re(v^H A22 v) from the GEMV partials of the (tile, slice) units that ran
-  const int ng = s.ntile * s.nslice;
-  T vy = T(0);
-  for (int x = threadIdx.x; x < ng; x += PT) {
-    const int tt = x / s.nslice, sl = x % s.nslice;
-    const bool ran = (tt + 1) * PT > j + 1 && tt * PT < n_b && (sl + 1) * CS > j + 1 && sl * CS < n_b;
-    if (ran) vy += __ldcg(s.gvy + ((size_t)par * s.B + b) * ng + x);
-  }
-  vy = block_reduce<T>(vy, red);   // has __syncthreads: s1/s2 visible afterwards
-  if (warp == 0) {
-    // cross term and p at row j + 1, lanes over q and over slices
-    T cross = T(0);
-    C y = mk<T>(T(0), T(0));
-    for (int q = lane; q < i; q += 32) {
-      cross += ci.s2[q].x * ci.s1[q].x + ci.s2[q].y * ci.s1[q].y;   // Re(conj(s2) s1)
-      y = csub<T>(y, cmul<T>(ldcg<T>(Vb + (size_t)q * nm + j + 1), ci.s1[q]));
-      y = csub<T>(y, cmul<T>(ldcg<T>(Wb + (size_t)q * nm + j + 1), ci.s2[q]));
-    }
-    for (int sl = (j + 1) / CS + lane; sl < s.nslice && sl * CS < n_b; sl += 32)
-      y = cadd<T>(y, ldcg<T>(s.part + ((size_t)b * s.nslice + sl) * nm + j + 1));
-    cross = warp_sum<T>(cross);
-    y.x = warp_sum<T>(y.x);
-    y.y = warp_sum<T>(y.y);
-    if (lane == 0) {
-      const T tau = ci.R.tau;
-      ci.K = T(0.5) * tau * tau * (vy - T(2) * cross);
-      ci.p1 = cscale<T>(y, tau);
-    }
-  }
-  __syncthreads();
+struct Batch {
+  int n_max;
+  int B;
+  int K2;
+  int64_t mat0;
+  const int* n_act_cell;   // may be null (all n_max)
+};
+
+__device__ __forceinline__ int batch_n(const Batch& b, int m) {
+  return b.n_act_cell ? b.n_act_cell[(b.mat0 + m) / b.K2] : b.n_max;
 }
 
-// R3 of column j on the tile's rows r > j: p = tau (y - V s1 - W s2),
-// w = p - K v, stored as W[i][r]; the owner of row j+1 also stores v_{j+1},
-// e_j^2.  No transform: v = w = 0.
-template <typename T>
-__device__ void phase_r3(const PState<T>& s, int b, int t, int j, int i, const ColumnInfo<T>& ci) {
-  using C = c2<T>;
-  const int n = mat_n(s, b);
-  const int nm = s.n_max;
-  C* Vi = s.V + ((size_t)b * NB + i) * nm;
-  C* Wi = s.W + ((size_t)b * NB + i) * nm;
-  const int r = t * PT + threadIdx.x;
-  if (t == (j + 1) / PT && threadIdx.x == 0) {
-    Vi[j + 1] = ci.R.v1;
-    s.e2_out[(size_t)b * nm + j] = ci.R.sigma2;
-  }
-  if (r <= j || r >= n) return;
-  if (!ci.R.tr) {
-    if (r > j + 1) Vi[r] = mk<T>(T(0), T(0));
-    Wi[r] = mk<T>(T(0), T(0));
-    return;
-  }
-  const C* Vb = s.V + (size_t)b * NB * nm;
-  const C* Wb = s.W + (size_t)b * NB * nm;
-  C y = mk<T>(T(0), T(0));
-  const int sl0 = (j + 1) / CS;
-  const int sl1 = min(s.nslice, (n + CS - 1) / CS);
-#pragma unroll 8
-  for (int sl = sl0; sl < sl1; ++sl) y = cadd<T>(y, ldcg<T>(s.part + ((size_t)b * s.nslice + sl) * nm + r));
-  for (int q0 = 0; q0 < i; q0 += 4) {
-    C vq[4], wq[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (q0 + u < i) {
-        vq[u] = ldcg<T>(Vb + (size_t)(q0 + u) * nm + r);
-        wq[u] = ldcg<T>(Wb + (size_t)(q0 + u) * nm + r);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (q0 + u < i) {
-        y = csub<T>(y, cmul<T>(vq[u], ci.s1[q0 + u]));
-        y = csub<T>(y, cmul<T>(wq[u], ci.s2[q0 + u]));
-      }
-    }
-  }
-  const C p = cscale<T>(y, ci.R.tau);
-  const C v = (r == j + 1) ? ci.R.v1 : ldcg<T>(Vi + r);
-  Wi[r] = csub<T>(p, cscale<T>(v, ci.K));
-}
-
-// R1 for column j (panel index i): corrected column j -> x (kept in V[i]),
-// d_j, alpha, partial ||x||^2 and W^H x, V^H x over rows >= j + 2.  For
-// i > 0, v and w of column j-1 at row j are v_prev_j, w_prev_j, computed by
-// every unit (their owner stores them concurrently).
-template <typename T>
-__device__ void phase_r1(const PState<T>& s, int b, int t, int j, int i, c2<T> w_prev_j, c2<T> v_prev_j,
-                         T* red) {
-  using C = c2<T>;
-  __shared__ C sWj[NB], sVj[NB];
-  __shared__ C sa[PT];
-  const int n = mat_n(s, b);
-  const int nm = s.n_max;
-  C* Vb = s.V + (size_t)b * NB * nm;
-  const C* Wb = s.W + (size_t)b * NB * nm;
-  if (threadIdx.x < i) {
-    const int q = threadIdx.x;
-    sVj[q] = (q < i - 1) ? ldcg<T>(Vb + (size_t)q * nm + j) : v_prev_j;
-    sWj[q] = (q < i - 1) ? ldcg<T>(Wb + (size_t)q * nm + j) : w_prev_j;
-  }
-  __syncthreads();
-  const int r = t * PT + threadIdx.x;
-  const int par = j & 1;
-  C a = mk<T>(T(0), T(0));
-  T rest = T(0);
-  if (r >= j && r < n) {
-    a = conjg<T>(ldcg<T>(s.A + ((size_t)b * nm + j) * nm + r));   // A[r][j] = conj(A[j][r])
-    for (int q0 = 0; q0 < i; q0 += 4) {
-      C vq[4], wq[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (q0 + u < i) {
-          vq[u] = (r == j) ? sVj[q0 + u] : ldcg<T>(Vb + (size_t)(q0 + u) * nm + r);
-          wq[u] = (r == j) ? sWj[q0 + u] : ldcg<T>(Wb + (size_t)(q0 + u) * nm + r);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (q0 + u < i) {
-          a = csub<T>(a, cmulc<T>(vq[u], sWj[q0 + u]));
-          a = csub<T>(a, cmulc<T>(wq[u], sVj[q0 + u]));
-        }
-      }
-    }
-    if (r == j) s.d_out[(size_t)b * nm + j] = a.x;
-    else if (r == j + 1) s.alpha[(size_t)par * s.B + b] = a;
-    else rest = cabs2<T>(a);
-    if (r > j) Vb[(size_t)i * nm + r] = a;
-  }
-  sa[threadIdx.x] = (r >= j + 2 && r < n) ? a : mk<T>(T(0), T(0));
-  rest = block_reduce<T>(rest, red);
-  if (threadIdx.x == 0) s.prest[((size_t)par * s.B + b) * s.ntile + t] = rest;
-  // tile partials of W_q^H x and V_q^H x over rows >= j + 2 (warp per q)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C* ps = s.ps + (((size_t)par * s.B + b) * s.ntile + t) * (2 * NB);
-  for (int q = warp; q < i; q += PT / 32) {
-    C a1 = mk<T>(T(0), T(0)), a2 = mk<T>(T(0), T(0));
-#pragma unroll
-    for (int x = lane; x < PT; x += 32) {
-      const int rr = t * PT + x;
-      if (rr < j + 2 || rr >= n) continue;
-      const C xa = sa[x];
-      a1 = cadd<T>(a1, cjmul<T>(ldcg<T>(Wb + (size_t)q * nm + rr), xa));
-      a2 = cadd<T>(a2, cjmul<T>(ldcg<T>(Vb + (size_t)q * nm + rr), xa));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o);
-      a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o);
-      a2.x += __shfl_xor_sync(0xffffffffu, a2.x, o);
-      a2.y += __shfl_xor_sync(0xffffffffu, a2.y, o);
-    }
-    if (lane == 0) {
-      ps[q] = a1;
-      ps[NB + q] = a2;
-    }
-  }
-  __syncthreads();
-}
-
-// G: partial y over one (row tile, column slice): part[b][sl][r] = sum_c conj(A[c][r]) v_c,
-// and the tile-slice partial of v^H y.
-template <typename T>
-__device__ void phase_gemv(const PState<T>& s, int b, int t, int sl, int j, int i, T* red) {
-  using C = c2<T>;
-  __shared__ C sv[CS];
-  __shared__ int s_tr;
-  __shared__ C s_v1;
-  const int n = mat_n(s, b);
-  if (j >= n - 1) return;
-  const int c0 = max(j + 1, sl * CS), c1 = min(n, (sl + 1) * CS);
-  if (c0 >= c1 || t * PT >= n || (t + 1) * PT <= j + 1) return;
-  const int nm = s.n_max;
-  if (threadIdx.x < 32) {
-    const Reflector<T> R = reflector_warp<T>(s, b, j & 1);
-    if (threadIdx.x == 0) {
-      s_tr = R.tr;
-      s_v1 = R.v1;
-    }
-  }
-  __syncthreads();
-  const int tr = s_tr;
-  const C* Vi = s.V + ((size_t)b * NB + i) * nm;
-  if (tr) {
-    for (int c = c0 + threadIdx.x; c < c1; c += PT) sv[c - c0] = (c == j + 1) ? s_v1 : ldcg<T>(Vi + c);
-  }
-  __syncthreads();
-  const int r = t * PT + threadIdx.x;
-  T vy = T(0);
-  if (tr && r > j && r < n) {
-    const C* Ab = s.A + (size_t)b * nm * nm + r;
-    C acc[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = mk<T>(T(0), T(0));
-    int c = c0;
-    for (; c + 8 <= c1; c += 8) {
-      C av[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) av[u] = ldcg<T>(Ab + (size_t)(c + u) * nm);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u & 3] = cadd<T>(acc[u & 3], cjmul<T>(av[u], sv[c + u - c0]));
-    }
-    for (; c < c1; ++c) acc[0] = cadd<T>(acc[0], cjmul<T>(ldcg<T>(Ab + (size_t)c * nm), sv[c - c0]));
-    const C y = cadd<T>(cadd<T>(acc[0], acc[1]), cadd<T>(acc[2], acc[3]));
-    s.part[((size_t)b * s.nslice + sl) * nm + r] = y;
-    const C v = (r == j + 1) ? s_v1 : ldcg<T>(Vi + r);
-    vy = v.x * y.x + v.y * y.y;   // Re(conj(v_r) y_r)
-  }
-  vy = block_reduce<T>(vy, red);
-  if (threadIdx.x == 0)
-    s.gvy[((size_t)(j & 1) * s.B + b) * s.ntile * s.nslice + (size_t)t * s.nslice + sl] = vy;
-  __syncthreads();
-}
-
-// Panel update A[r][c] -= sum_q V[q][r] conj(W[q][c]) + W[q][r] conj(V[q][c]), r, c >= jn.
-template <typename T>
-__device__ void phase_her2k(const PState<T>& s, int b, int tr_, int tc, int jn, c2<T>* sm) {
-  using C = c2<T>;
-  const int n = mat_n(s, b);
-  const int r0 = jn + tr_ * HT, c0 = jn + tc * HT;
-  if (r0 >= n || c0 >= n) return;
-  const int nm = s.n_max;
-  C* sVr = sm;
-  C* sWr = sVr + NB * (HT + 1);
-  C* sVc = sWr + NB * (HT + 1);
-  C* sWc = sVc + NB * (HT + 1);
-  const C* Vb = s.V + (size_t)b * NB * nm;
-  const C* Wb = s.W + (size_t)b * NB * nm;
-  for (int idx = threadIdx.x; idx < NB * HT; idx += PT) {
-    const int q = idx / HT, x = idx % HT;
-    const int r = r0 + x, c = c0 + x;
-    sVr[q * (HT + 1) + x] = r < n ? ldcg<T>(Vb + (size_t)q * nm + r) : mk<T>(T(0), T(0));
-    sWr[q * (HT + 1) + x] = r < n ? ldcg<T>(Wb + (size_t)q * nm + r) : mk<T>(T(0), T(0));
-    sVc[q * (HT + 1) + x] = c < n ? ldcg<T>(Vb + (size_t)q * nm + c) : mk<T>(T(0), T(0));
-    sWc[q * (HT + 1) + x] = c < n ? ldcg<T>(Wb + (size_t)q * nm + c) : mk<T>(T(0), T(0));
-  }
-  __syncthreads();
-  const int cx = threadIdx.x % HT, ry = threadIdx.x / HT;   // 8 row groups
-  C* Ab = s.A + (size_t)b * nm * nm;
-#pragma unroll
-  for (int k = 0; k < HT / 8; ++k) {
-    const int rl = ry + 8 * k;
-    C acc = mk<T>(T(0), T(0));
-#pragma unroll 8
-    for (int q = 0; q < NB; ++q) {
-      acc = cadd<T>(acc, cmulc<T>(sVr[q * (HT + 1) + rl], sWc[q * (HT + 1) + cx]));
-      acc = cadd<T>(acc, cmulc<T>(sWr[q * (HT + 1) + rl], sVc[q * (HT + 1) + cx]));
-    }
-    const int r = r0 + rl, c = c0 + cx;
-    if (r < n && c < n) {
-      C* e = Ab + (size_t)r * nm + c;
-      *e = csub<T>(ldcg<T>(e), acc);
-    }
-  }
-  __syncthreads();
-}
-
-// One column step j of every matrix, in order:
-//   [R3 of column j-1 + R1 of column j]  barrier  [GEMV of column j]  barrier
-// with the panel's rank-2NB update (and its two barriers) when j starts a panel.
-template <typename T>
-__global__ void __launch_bounds__(PT, 3)
-k_lg_persist(PState<T> s) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  c2<T>* sm = reinterpret_cast<c2<T>*>(smem_raw);
-  __shared__ ColumnInfo<T> ci;
-  __shared__ T red[PT / 32];
-  const int nrow_units = s.B * s.ntile;
-  const int ngemv_units = nrow_units * s.nslice;
-  for (int j = 0; j < s.n_max; ++j) {
-    const int j0 = j - j % NB, i = j - j0;
-    const bool panel_start = (i == 0);
-    if (panel_start && j > 0) {
-      // finish the previous panel's last column (R3), then the rank-2NB update
-      for (int u = blockIdx.x; u < nrow_units; u += gridDim.x) {
-        const int b = u / s.ntile, t = u % s.ntile;
-        if (j - 1 >= mat_n(s, b) - 1) continue;
-        column_info<T>(s, b, j - 1, NB - 1, ci, red);
-        phase_r3<T>(s, b, t, j - 1, NB - 1, ci);
-        __syncthreads();
-      }
-      if (!grid_sync(s.bar, s.err)) return;
-      const int nt = (s.n_max - j + HT - 1) / HT;
-      const int units = s.B * nt * nt;
-      for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const int b = u / (nt * nt), rem = u % (nt * nt);
-        phase_her2k<T>(s, b, rem / nt, rem % nt, j, sm);
-      }
-      if (!grid_sync(s.bar, s.err)) return;
-    }
-    // R3 of column j-1 (inside the panel) fused with R1 of column j
-    for (int u = blockIdx.x; u < nrow_units; u += gridDim.x) {
-      const int b = u / s.ntile, t = u % s.ntile;
-      const int n = mat_n(s, b);
-      if (j >= n) continue;
-      c2<T> w_prev = mk<T>(T(0), T(0)), v_prev = mk<T>(T(0), T(0));
-      if (!panel_start) {
-        column_info<T>(s, b, j - 1, i - 1, ci, red);   // j - 1 < n - 1 here
-        phase_r3<T>(s, b, t, j - 1, i - 1, ci);
-        if (ci.R.tr) {
-          v_prev = ci.R.v1;
-          w_prev = csub<T>(ci.p1, cscale<T>(ci.R.v1, ci.K));
-        }
-        __syncthreads();
-      }
-      phase_r1<T>(s, b, t, j, i, w_prev, v_prev, red);
-    }
-    if (!grid_sync(s.bar, s.err)) return;
-    for (int u = blockIdx.x; u < ngemv_units; u += gridDim.x) {
-      const int b = u / (s.ntile * s.nslice), rem = u % (s.ntile * s.nslice);
-      phase_gemv<T>(s, b, rem / s.nslice, rem % s.nslice, j, i, red);
-    }
-    if (!grid_sync(s.bar, s.err)) return;
-  }
-}
-
-// Assembly of H(k) into global memory (rows of kept sites only; the buffer is
-// zeroed beforehand).  One thread per (matrix, row).
+// --------------------------------------------------------------- assembly --
+// H(k) into global memory (rows of kept sites only; the buffer is zeroed
+// beforehand).  One thread per (matrix, row).
 template <typename T>
 __global__ void k_lg_assemble(int64_t n_mat_batch, int64_t mat0, int n_max, int K2,
                               const int* __restrict__ n_act_cell, const int* __restrict__ act,
@@ -564,70 +113,808 @@ __global__ void k_lg_assemble(int64_t n_mat_batch, int64_t mat0, int n_max, int 
   }
 }
 
-template <typename T>
-size_t per_matrix_bytes(int nm) {
-  using C = c2<T>;
-  const int ntile = (nm + PT - 1) / PT, nslice = (nm + CS - 1) / CS;
-  return sizeof(C) * ((size_t)nm * nm + 2 * (size_t)NB * nm + (size_t)nslice * nm) +
-         2 * (sizeof(T) * ntile * (1 + nslice) + sizeof(C) * ntile * 2 * NB + sizeof(C)) + 512;
+// ------------------------------------------------------------ block sums --
+template <typename T, int NT>
+__device__ __forceinline__ T block_sum_t(T v, T* red) {
+  v = warp_sum<T>(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = T(0);
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) s += red[w];
+  return s;
 }
+
+// ------------------------------------------------------------- panel QR --
+// One CTA per matrix.  Panel P[r][c] = A[k+BW+r][k+c], r < m = n-k-BW, c < BW,
+// factored in place in shared memory when it fits (else in global memory).
+// Outputs Y[c][r] (reflector c, zero above row c), YT = Y T, T; writes R back
+// (upper triangle) and zeros below it.
+template <typename T>
+__global__ void __launch_bounds__(PQ_THREADS, 1)
+k_ts_panel(Batch bt, int k, c2<T>* __restrict__ A, c2<T>* __restrict__ Y, c2<T>* __restrict__ YT,
+           c2<T>* __restrict__ Tm, int use_smem) {
+  using C = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[PQ_THREADS / 32];
+  __shared__ C sw[BW];
+  __shared__ C swp[PQ_THREADS / 32][BW];
+  __shared__ C sG[BW][BW];
+  __shared__ C sT[BW][BW];
+  __shared__ T stau[BW];
+  __shared__ C salpha;
+  const int b = blockIdx.x;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int m = n - k - BW;
+  if (m <= 0) return;
+  C* Ab = A + (size_t)b * nm * nm;
+  C* P;
+  int ld;
+  if (use_smem) {
+    P = reinterpret_cast<C*>(smem_raw);
+    ld = BW;
+    for (int idx = threadIdx.x; idx < m * BW; idx += PQ_THREADS) {
+      const int r = idx / BW, c = idx % BW;
+      P[idx] = Ab[(size_t)(k + BW + r) * nm + k + c];
+    }
+    __syncthreads();
+  } else {
+    P = Ab + (size_t)(k + BW) * nm + k;
+    ld = nm;
+  }
+  C* Yb = Y + (size_t)b * BW * nm;
+  for (int c = 0; c < BW; ++c) {
+    // x = P[c:, c]; rest = sum_{r > c} |x_r|^2
+    T rest = T(0);
+    for (int r = c + 1 + threadIdx.x; r < m; r += PQ_THREADS) rest += cabs2<T>(P[(size_t)r * ld + c]);
+    rest = block_sum_t<T, PQ_THREADS>(rest, red);
+    if (threadIdx.x == 0) salpha = c < m ? P[(size_t)c * ld + c] : mk<T>(T(0), T(0));
+    __syncthreads();
+    const C alpha = salpha;
+    const bool tr = c < m && rest > tiny_rest<T>();
+    T tau = T(0);
+    C v0 = alpha, beta = alpha;
+    if (tr) {
+      const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
+      const C ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+      tau = T(1) / (sigma * (sigma + aa));
+      v0 = cadd<T>(alpha, cscale<T>(ph, sigma));
+      beta = cscale<T>(ph, -sigma);
+    }
+    if (threadIdx.x == 0) stau[c] = tau;
+    // y_c: zero above row c, v below
+    for (int r = threadIdx.x; r < m; r += PQ_THREADS) {
+      C y = mk<T>(T(0), T(0));
+      if (tr && r >= c) y = (r == c) ? v0 : P[(size_t)r * ld + c];
+      Yb[(size_t)c * nm + r] = y;
+    }
+    if (tr) {
+      // w_d = v^H P[c:, d] for all d > c at once.  Thread t works on column
+      // d = t % BW over the rows r = g (mod G), g = t / BW, G = PQ_THREADS / BW;
+      // lanes l and l + 16 share d, then warps are summed in a fixed order.
+      constexpr int G = PQ_THREADS / BW;
+      const int d = threadIdx.x % BW, g = threadIdx.x / BW;
+      C acc = mk<T>(T(0), T(0));
+      if (d > c) {
+        for (int r = c + ((g - c % G) + G) % G; r < m; r += G) {
+          const C v = (r == c) ? v0 : P[(size_t)r * ld + c];
+          acc = cadd<T>(acc, cjmul<T>(v, P[(size_t)r * ld + d]));
+        }
+      }
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+      if ((threadIdx.x & 31) < BW) swp[threadIdx.x >> 5][d] = acc;
+      __syncthreads();
+      if (threadIdx.x < BW) {
+        C sum = mk<T>(T(0), T(0));
+        for (int w2 = 0; w2 < PQ_THREADS / 32; ++w2) sum = cadd<T>(sum, swp[w2][threadIdx.x]);
+        sw[threadIdx.x] = sum;
+      }
+      __syncthreads();
+      if (d > c) {
+        const C wd = cscale<T>(sw[d], tau);
+        for (int r = c + ((g - c % G) + G) % G; r < m; r += G) {
+          const C v = (r == c) ? v0 : P[(size_t)r * ld + c];
+          P[(size_t)r * ld + d] = csub<T>(P[(size_t)r * ld + d], cmul<T>(v, wd));
+        }
+      }
+      __syncthreads();
+      // column c becomes (beta, 0, ..., 0) below the band row
+      for (int r = c + threadIdx.x; r < m; r += PQ_THREADS) P[(size_t)r * ld + c] = (r == c) ? beta : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+  }
+  // Gram matrix G[q][c] = y_q^H y_c (q < c), warp per pair
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int pr = warp; pr < BW * BW; pr += PQ_THREADS / 32) {
+    const int q = pr / BW, c = pr % BW;
+    if (q >= c) continue;
+    C acc = mk<T>(T(0), T(0));
+    for (int r = c + lane; r < m; r += 32)
+      acc = cadd<T>(acc, cjmul<T>(Yb[(size_t)q * nm + r], Yb[(size_t)c * nm + r]));
+    acc.x = warp_sum<T>(acc.x);
+    acc.y = warp_sum<T>(acc.y);
+    if (lane == 0) sG[q][c] = acc;
+  }
+  __syncthreads();
+  // T (forward, columnwise): T[c][c] = tau_c, T[0:c, c] = -tau_c T[0:c, 0:c] G[0:c, c]
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < BW; ++c) {
+      for (int q = 0; q < BW; ++q) sT[q][c] = mk<T>(T(0), T(0));
+      sT[c][c] = mk<T>(stau[c], T(0));
+      for (int q = 0; q < c; ++q) {
+        C acc = mk<T>(T(0), T(0));
+        for (int u = q; u < c; ++u) acc = cadd<T>(acc, cmul<T>(sT[q][u], sG[u][c]));
+        sT[q][c] = cscale<T>(acc, -stau[c]);
+      }
+    }
+  }
+  __syncthreads();
+  C* Tb = Tm + (size_t)b * BW * BW;
+  for (int idx = threadIdx.x; idx < BW * BW; idx += PQ_THREADS) Tb[idx] = sT[idx / BW][idx % BW];
+  // YT[c][r] = sum_{q <= c} Y[q][r] T[q][c]
+  C* YTb = YT + (size_t)b * BW * nm;
+  for (int r = threadIdx.x; r < m; r += PQ_THREADS) {
+    C yr[BW];
+#pragma unroll
+    for (int q = 0; q < BW; ++q) yr[q] = Yb[(size_t)q * nm + r];
+#pragma unroll 1
+    for (int c = 0; c < BW; ++c) {
+      C acc = mk<T>(T(0), T(0));
+#pragma unroll
+      for (int q = 0; q < BW; ++q)
+        if (q <= c) acc = cadd<T>(acc, cmul<T>(yr[q], sT[q][c]));
+      YTb[(size_t)c * nm + r] = acc;
+    }
+  }
+  if (use_smem) {
+    for (int idx = threadIdx.x; idx < m * BW; idx += PQ_THREADS) {
+      const int r = idx / BW, c = idx % BW;
+      Ab[(size_t)(k + BW + r) * nm + k + c] = P[idx];
+    }
+  }
+}
+
+// --------------------------------------------------------- W = A22 (Y T) --
+// Wp[s][c][r] = sum over the s-th inner chunk of A22[r][x] YT[c][x].
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ts_w(Batch bt, int k, const c2<T>* __restrict__ A, const c2<T>* __restrict__ YT, c2<T>* __restrict__ Wp,
+       int nsplit) {
+  using C = c2<T>;
+  constexpr int WR = Tiles<T>::WR, WK = Tiles<T>::WK, RPT = WR / 16;
+  __shared__ C sA[WR][WK + 1];
+  __shared__ C sY[BW][WK + 1];
+  const int b = blockIdx.z / nsplit, sp = blockIdx.z % nsplit;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int m = n - k - BW;
+  const int r0 = blockIdx.x * WR;
+  if (m <= 0 || r0 >= m) return;
+  const int chunk = ((m + nsplit - 1) / nsplit + WK - 1) / WK * WK;
+  const int x_lo = sp * chunk, x_hi = min(m, x_lo + chunk);
+  const C* A22 = A + (size_t)b * nm * nm + (size_t)(k + BW) * nm + (k + BW);
+  const C* YTb = YT + (size_t)b * BW * nm;
+  const int tc = threadIdx.x % BW, tr = threadIdx.x / BW;   // 16 x 16 threads: RPT rows each
+  C acc[RPT];
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) acc[u] = mk<T>(T(0), T(0));
+  for (int x0 = x_lo; x0 < x_hi; x0 += WK) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < WR * WK; idx += 256) {
+      const int rr = idx / WK, xx = idx % WK;
+      const int r = r0 + rr, x = x0 + xx;
+      sA[rr][xx] = (r < m && x < x_hi) ? A22[(size_t)r * nm + x] : mk<T>(T(0), T(0));
+    }
+    for (int idx = threadIdx.x; idx < BW * WK; idx += 256) {
+      const int c = idx / WK, xx = idx % WK;
+      const int x = x0 + xx;
+      sY[c][xx] = x < x_hi ? YTb[(size_t)c * nm + x] : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int xx = 0; xx < WK; ++xx) {
+      const C y = sY[tc][xx];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) acc[u] = cadd<T>(acc[u], cmul<T>(sA[tr * RPT + u][xx], y));
+    }
+  }
+  C* W = Wp + ((size_t)b * nsplit + sp) * BW * nm;
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int r = r0 + tr * RPT + u;
+    if (r < m) W[(size_t)tc * nm + r] = acc[u];
+  }
+}
+
+// ----------------------------------------------- Z = W - 1/2 Y (T^H M) --
+template <typename T>
+__global__ void __launch_bounds__(PQ_THREADS, 1)
+k_ts_z(Batch bt, int k, const c2<T>* __restrict__ Y, const c2<T>* __restrict__ Tm, const c2<T>* __restrict__ Wp,
+       int nsplit, c2<T>* __restrict__ Z) {
+  using C = c2<T>;
+  __shared__ C sM[BW][BW];
+  __shared__ C sP[BW][BW];
+  const int b = blockIdx.x;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int m = n - k - BW;
+  if (m <= 0) return;
+  const C* Yb = Y + (size_t)b * BW * nm;
+  C* Zb = Z + (size_t)b * BW * nm;
+  // W = sum of the split partials, kept in Z
+  for (int idx = threadIdx.x; idx < BW * m; idx += PQ_THREADS) {
+    const int c = idx / m, r = idx % m;
+    C w = mk<T>(T(0), T(0));
+    for (int sp = 0; sp < nsplit; ++sp) w = cadd<T>(w, Wp[((size_t)b * nsplit + sp) * BW * nm + (size_t)c * nm + r]);
+    Zb[(size_t)c * nm + r] = w;
+  }
+  __syncthreads();
+  // M = Y^H W (warp per entry)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int pr = warp; pr < BW * BW; pr += PQ_THREADS / 32) {
+    const int q = pr / BW, c = pr % BW;
+    C acc = mk<T>(T(0), T(0));
+    for (int r = q + lane; r < m; r += 32) acc = cadd<T>(acc, cjmul<T>(Yb[(size_t)q * nm + r], Zb[(size_t)c * nm + r]));
+    acc.x = warp_sum<T>(acc.x);
+    acc.y = warp_sum<T>(acc.y);
+    if (lane == 0) sM[q][c] = acc;
+  }
+  __syncthreads();
+  // P = T^H M
+  const C* Tb = Tm + (size_t)b * BW * BW;
+  if (threadIdx.x < BW * BW) {
+    const int q = threadIdx.x / BW, c = threadIdx.x % BW;
+    C acc = mk<T>(T(0), T(0));
+    for (int u = 0; u <= q; ++u) acc = cadd<T>(acc, cjmul<T>(Tb[u * BW + q], sM[u][c]));   // conj(T[u][q]) M[u][c]
+    sP[q][c] = acc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += PQ_THREADS) {
+    C yr[BW];
+#pragma unroll
+    for (int q = 0; q < BW; ++q) yr[q] = Yb[(size_t)q * nm + r];
+#pragma unroll 1
+    for (int c = 0; c < BW; ++c) {
+      C acc = mk<T>(T(0), T(0));
+#pragma unroll
+      for (int q = 0; q < BW; ++q) acc = cadd<T>(acc, cmul<T>(yr[q], sP[q][c]));
+      Zb[(size_t)c * nm + r] = csub<T>(Zb[(size_t)c * nm + r], cscale<T>(acc, T(0.5)));
+    }
+  }
+}
+
+// ----------------------------------------- A22 -= Y Z^H + Z Y^H (tiles) --
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ts_her2k(Batch bt, int k, c2<T>* __restrict__ A, const c2<T>* __restrict__ Y, const c2<T>* __restrict__ Z) {
+  using C = c2<T>;
+  constexpr int GT = Tiles<T>::GT, PB = GT / 16;   // PB x PB outputs per thread
+  __shared__ C sYr[BW][GT], sZr[BW][GT], sYc[BW][GT], sZc[BW][GT];
+  const int b = blockIdx.z;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int m = n - k - BW;
+  const int r0 = blockIdx.y * GT, c0 = blockIdx.x * GT;
+  if (m <= 0 || r0 >= m || c0 >= m) return;
+  const C* Yb = Y + (size_t)b * BW * nm;
+  const C* Zb = Z + (size_t)b * BW * nm;
+  for (int idx = threadIdx.x; idx < BW * GT; idx += 256) {
+    const int q = idx / GT, x = idx % GT;
+    const int r = r0 + x, c = c0 + x;
+    sYr[q][x] = r < m ? Yb[(size_t)q * nm + r] : mk<T>(T(0), T(0));
+    sZr[q][x] = r < m ? Zb[(size_t)q * nm + r] : mk<T>(T(0), T(0));
+    sYc[q][x] = c < m ? Yb[(size_t)q * nm + c] : mk<T>(T(0), T(0));
+    sZc[q][x] = c < m ? Zb[(size_t)q * nm + c] : mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  C acc[PB][PB];
+#pragma unroll
+  for (int a = 0; a < PB; ++a)
+#pragma unroll
+    for (int d = 0; d < PB; ++d) acc[a][d] = mk<T>(T(0), T(0));
+#pragma unroll 4
+  for (int q = 0; q < BW; ++q) {
+    C yr[PB], zr[PB], yc[PB], zc[PB];
+#pragma unroll
+    for (int a = 0; a < PB; ++a) {
+      yr[a] = sYr[q][ty + 16 * a];
+      zr[a] = sZr[q][ty + 16 * a];
+      yc[a] = sYc[q][tx + 16 * a];
+      zc[a] = sZc[q][tx + 16 * a];
+    }
+#pragma unroll
+    for (int a = 0; a < PB; ++a)
+#pragma unroll
+      for (int d = 0; d < PB; ++d) {
+        acc[a][d] = cadd<T>(acc[a][d], cmulc<T>(yr[a], zc[d]));
+        acc[a][d] = cadd<T>(acc[a][d], cmulc<T>(zr[a], yc[d]));
+      }
+  }
+  C* A22 = A + (size_t)b * nm * nm + (size_t)(k + BW) * nm + (k + BW);
+#pragma unroll
+  for (int a = 0; a < PB; ++a)
+#pragma unroll
+    for (int d = 0; d < PB; ++d) {
+      const int r = r0 + ty + 16 * a, c = c0 + tx + 16 * d;
+      if (r < m && c < m) {
+        C* e = A22 + (size_t)r * nm + c;
+        *e = csub<T>(*e, acc[a][d]);
+      }
+    }
+}
+
+// ----------------------------------------------------------- to band --
+// Bd[d][c] = A[c+d][c] for d <= BW, 0 for BW < d < ND.
+template <typename T>
+__global__ void k_ts_to_band(Batch bt, const c2<T>* __restrict__ A, c2<T>* __restrict__ Bd) {
+  using C = c2<T>;
+  const int b = blockIdx.y;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const C* Ab = A + (size_t)b * nm * nm;
+  C* Bb = Bd + (size_t)b * ND * nm;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < ND * nm; idx += gridDim.x * blockDim.x) {
+    const int d = idx / nm, c = idx % nm;
+    C v = mk<T>(T(0), T(0));
+    if (d <= BW && c + d < n) v = Ab[(size_t)(c + d) * nm + c];
+    Bb[idx] = v;
+  }
+}
+
+// ------------------------------------------------------------ chase --
+template <typename T>
+struct Band {
+  c2<T>* p;
+  int ld;
+  __device__ __forceinline__ c2<T> get(int r, int c) const {
+    return r >= c ? p[(size_t)(r - c) * ld + c] : conjg<T>(p[(size_t)(c - r) * ld + r]);
+  }
+  __device__ __forceinline__ void set(int r, int c, c2<T> v) const { p[(size_t)(r - c) * ld + c] = v; }
+};
+
+// Warp reflector from x (lane l < L holds x_l): tau, v_l, beta = -ph sigma.
+template <typename T>
+__device__ __forceinline__ bool warp_reflector(c2<T> x, int L, T& tau, c2<T>& v, c2<T>& beta) {
+  const int lane = threadIdx.x & 31;
+  T rest = (lane >= 1 && lane < L) ? cabs2<T>(x) : T(0);
+  rest = warp_sum<T>(rest);
+  const c2<T> alpha = shfl_c<T>(x, 0);
+  tau = T(0);
+  v = x;
+  beta = alpha;
+  if (!(rest > tiny_rest<T>())) return false;
+  const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
+  const c2<T> ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+  tau = T(1) / (sigma * (sigma + aa));
+  if (lane == 0) v = cadd<T>(alpha, cscale<T>(ph, sigma));
+  beta = cscale<T>(ph, -sigma);
+  return true;
+}
+
+// Per-warp scratch of the chase: the current reflector v, the vector w, the
+// previous reflector, and a BW x (BW+1) buffer for column reductions.
+template <typename T>
+struct WarpScratch {
+  c2<T> v[BW], w[BW], vp[BW];
+  c2<T> m[BW][BW + 1];
+};
+
+// Two-sided D <- H D H on the Hermitian block D = A(r0.., r0..) of size L;
+// lane l holds v_l, ws->v holds v.  Only the lower triangle is stored.
+template <typename T>
+__device__ __forceinline__ void load_block(const Band<T>& bd, int r0, int c0, int Lr, int Lc, c2<T>* out) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < BW; ++c) out[c] = (lane < Lr && c < Lc) ? bd.get(r0 + lane, c0 + c) : mk<T>(T(0), T(0));
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_two_sided(const Band<T>& bd, int r0, int L, T tau, c2<T> v,
+                                               WarpScratch<T>* ws, const c2<T>* drow) {
+  using C = c2<T>;
+  const int lane = threadIdx.x & 31;
+  C p = mk<T>(T(0), T(0));
+#pragma unroll
+  for (int c = 0; c < BW; ++c) p = cadd<T>(p, cmul<T>(drow[c], ws->v[c]));
+  p = cscale<T>(p, tau);
+  const T kp = lane < L ? (v.x * p.x + v.y * p.y) : T(0);
+  const T K = T(0.5) * tau * warp_sum<T>(kp);
+  const C w = csub<T>(p, cscale<T>(v, K));
+  if (lane < BW) ws->w[lane] = lane < L ? w : mk<T>(T(0), T(0));
+  __syncwarp();
+  if (lane < L) {
+#pragma unroll
+    for (int c = 0; c < BW; ++c) {
+      if (c <= lane) {
+        C d = drow[c];
+        d = csub<T>(d, cmulc<T>(v, ws->w[c]));
+        d = csub<T>(d, cmulc<T>(w, ws->v[c]));
+        if (c == lane) d.y = T(0);
+        bd.set(r0 + lane, r0 + c, d);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// band_in_smem: the band is copied into shared memory first (when it fits)
+// and the chase runs there; otherwise it runs on the band in global memory.
+template <typename T>
+__global__ void __launch_bounds__(32 * Chase<T>::WARPS)
+k_ts_chase(Batch bt, c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restrict__ e2_out,
+           int slots, int band_in_smem) {
+  using C = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nwarps = blockDim.x >> 5;
+  WarpScratch<T>* wsc = reinterpret_cast<WarpScratch<T>*>(smem_raw);
+  C* sv = reinterpret_cast<C*>(wsc + nwarps);                   // [slots][BW]
+  T* stau = reinterpret_cast<T*>(sv + (size_t)slots * BW);      // [slots]
+  const int b = blockIdx.x;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  C* gband = Bd + (size_t)b * ND * nm;
+  C* band = gband;
+  if (band_in_smem) {
+    const size_t head = sizeof(WarpScratch<T>) * nwarps + (sizeof(C) * BW + sizeof(T)) * (size_t)slots;
+    band = reinterpret_cast<C*>(smem_raw + ((head + 255) & ~size_t(255)));
+    for (int idx = threadIdx.x; idx < ND * nm; idx += blockDim.x) band[idx] = gband[idx];
+    __syncthreads();
+  }
+  const Band<T> bd{band, nm};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpScratch<T>* ws = wsc + warp;
+  if (n >= 3) {
+    const int T_total = 3 * (n - 3) + 1;
+    for (int tstep = 0; tstep < T_total; ++tstep) {
+      const int ihi = min(tstep / 3, n - 3);
+      for (int i = ihi - warp; i >= 0; i -= nwarps) {
+        const int k = tstep - 3 * i;
+        const int nsteps = (n - 2 - i) / BW + 1;   // step k while row i + 1 + k BW exists
+        if (k >= nsteps) break;                    // older sweeps are done too
+        const int slot = i % slots;
+        if (k == 0) {
+          // annihilate column i below the subdiagonal within the band
+          const int L = min(BW, n - 1 - i);
+          const C x = lane < L ? bd.get(i + 1 + lane, i) : mk<T>(T(0), T(0));
+          C drow[BW];
+          load_block<T>(bd, i + 1, i + 1, L, L, drow);
+          T tau;
+          C v, beta;
+          const bool tr = warp_reflector<T>(x, L, tau, v, beta);
+          if (tr) {
+            if (lane < L) bd.set(i + 1 + lane, i, lane == 0 ? beta : mk<T>(T(0), T(0)));
+            if (lane < BW) ws->v[lane] = lane < L ? v : mk<T>(T(0), T(0));
+            __syncwarp();
+            warp_two_sided<T>(bd, i + 1, L, tau, v, ws, drow);
+          }
+          if (lane < BW) sv[slot * BW + lane] = (tr && lane < L) ? v : mk<T>(T(0), T(0));
+          if (lane == 0) stau[slot] = tau;
+        } else {
+          const int j0 = i + 1 + (k - 1) * BW;
+          const int Lp = min(BW, n - j0);
+          const int r0 = j0 + BW;
+          const int Lr = min(BW, n - r0);
+          const T tprev = stau[slot];
+          if (lane < BW) ws->vp[lane] = sv[slot * BW + lane];
+          // E = A(r0.., j0..) and D = A(r0.., r0..), both loaded up front: lane l holds row l
+          C e[BW], drow[BW];
+          load_block<T>(bd, r0, j0, Lr, Lp, e);
+          load_block<T>(bd, r0, r0, Lr, Lr, drow);
+          __syncwarp();
+          if (tprev != T(0)) {
+            // E <- E H_prev
+            C u = mk<T>(T(0), T(0));
+#pragma unroll
+            for (int c = 0; c < BW; ++c) u = cadd<T>(u, cmul<T>(e[c], ws->vp[c]));
+            u = cscale<T>(u, tprev);
+#pragma unroll
+            for (int c = 0; c < BW; ++c) e[c] = csub<T>(e[c], cmulc<T>(u, ws->vp[c]));
+          }
+          // new reflector from E's first column
+          T tau;
+          C v, beta;
+          const bool tr = warp_reflector<T>(e[0], Lr, tau, v, beta);
+          if (tr) {
+            // E <- H E: column sums w_c = sum_l conj(v_l) e_l[c] through the scratch matrix
+            if (lane < BW) {
+#pragma unroll
+              for (int c = 0; c < BW; ++c) ws->m[lane][c] = lane < Lr ? cjmul<T>(v, e[c]) : mk<T>(T(0), T(0));
+            }
+            __syncwarp();
+            if (lane < BW) {
+              C acc = mk<T>(T(0), T(0));
+#pragma unroll
+              for (int l = 0; l < BW; ++l) acc = cadd<T>(acc, ws->m[l][lane]);
+              ws->w[lane] = acc;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int c = 1; c < BW; ++c) e[c] = csub<T>(e[c], cscale<T>(cmul<T>(v, ws->w[c]), tau));
+            e[0] = lane == 0 ? beta : mk<T>(T(0), T(0));
+          }
+          if (lane < Lr) {
+#pragma unroll
+            for (int c = 0; c < BW; ++c)
+              if (c < Lp) bd.set(r0 + lane, j0 + c, e[c]);
+          }
+          if (tr) {
+            if (lane < BW) ws->v[lane] = lane < Lr ? v : mk<T>(T(0), T(0));
+            __syncwarp();
+            warp_two_sided<T>(bd, r0, Lr, tau, v, ws, drow);
+          }
+          if (lane < BW) sv[slot * BW + lane] = (tr && lane < Lr) ? v : mk<T>(T(0), T(0));
+          if (lane == 0) stau[slot] = tau;
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    d_out[(size_t)b * nm + c] = bd.get(c, c).x;
+    if (c < n - 1) e2_out[(size_t)b * nm + c] = cabs2<T>(bd.get(c + 1, c));
+  }
+}
+
+// Cluster variant of the chase: the band of one matrix is spread over the
+// shared memory of a cluster of CS CTAs (CTA q holds columns
+// [q CW, (q+1) CW)), every warp of the cluster takes the sweeps i = gw
+// (mod GW) (at most one active sweep per warp), and a cluster barrier ends
+// each time step.  Blocks crossing a CTA boundary are reached through
+// distributed shared memory.
+template <typename T>
+struct CBand {
+  c2<T>* local;   // this CTA's band storage [ND][cw]
+  int cw;
+  __device__ __forceinline__ c2<T>* addr(int d, int c) const {
+    const int o = c / cw;
+    c2<T>* p = local + (size_t)d * cw + (c - o * cw);
+    return cg::this_cluster().map_shared_rank(p, o);
+  }
+  __device__ __forceinline__ c2<T> get(int r, int c) const {
+    return r >= c ? *addr(r - c, c) : conjg<T>(*addr(c - r, r));
+  }
+  __device__ __forceinline__ void set(int r, int c, c2<T> v) const { *addr(r - c, c) = v; }
+};
+
+template <typename T, typename BandT>
+__device__ __forceinline__ void cload_block(const BandT& bd, int r0, int c0, int Lr, int Lc, c2<T>* out) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < BW; ++c) out[c] = (lane < Lr && c < Lc) ? bd.get(r0 + lane, c0 + c) : mk<T>(T(0), T(0));
+}
+
+template <typename T, typename BandT>
+__device__ __forceinline__ void cwarp_two_sided(const BandT& bd, int r0, int L, T tau, c2<T> v, WarpScratch<T>* ws,
+                                                const c2<T>* drow) {
+  using C = c2<T>;
+  const int lane = threadIdx.x & 31;
+  C p = mk<T>(T(0), T(0));
+#pragma unroll
+  for (int c = 0; c < BW; ++c) p = cadd<T>(p, cmul<T>(drow[c], ws->v[c]));
+  p = cscale<T>(p, tau);
+  const T kp = lane < L ? (v.x * p.x + v.y * p.y) : T(0);
+  const T K = T(0.5) * tau * warp_sum<T>(kp);
+  const C w = csub<T>(p, cscale<T>(v, K));
+  if (lane < BW) ws->w[lane] = lane < L ? w : mk<T>(T(0), T(0));
+  __syncwarp();
+  if (lane < L) {
+#pragma unroll
+    for (int c = 0; c < BW; ++c) {
+      if (c <= lane) {
+        C d = drow[c];
+        d = csub<T>(d, cmulc<T>(v, ws->w[c]));
+        d = csub<T>(d, cmulc<T>(w, ws->v[c]));
+        if (c == lane) d.y = T(0);
+        bd.set(r0 + lane, r0 + c, d);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * Chase<T>::WARPS)
+k_ts_chase_cluster(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restrict__ e2_out, int cw) {
+  using C = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int CSZ = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int nwarps = blockDim.x >> 5;
+  WarpScratch<T>* wsc = reinterpret_cast<WarpScratch<T>*>(smem_raw);
+  C* slot_v = reinterpret_cast<C*>(wsc + nwarps);               // [nwarps][BW]: sweep state of each warp
+  T* slot_tau = reinterpret_cast<T*>(slot_v + (size_t)nwarps * BW);
+  const size_t head = sizeof(WarpScratch<T>) * nwarps + (sizeof(C) * BW + sizeof(T)) * (size_t)nwarps;
+  C* local = reinterpret_cast<C*>(smem_raw + ((head + 255) & ~size_t(255)));
+  const int b = blockIdx.x / CSZ;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const C* gband = Bd + (size_t)b * ND * nm;
+  // load this CTA's columns of the band
+  for (int idx = threadIdx.x; idx < ND * cw; idx += blockDim.x) {
+    const int d = idx / cw, cl_ = idx % cw, c = rank * cw + cl_;
+    local[idx] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
+  }
+  cl.sync();
+  const CBand<T> bd{local, cw};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int GW = CSZ * nwarps, gw = rank * nwarps + warp;
+  WarpScratch<T>* ws = wsc + warp;
+  if (n >= 3) {
+    const int T_total = 3 * (n - 3) + 1;
+    for (int tstep = 0; tstep < T_total; ++tstep) {
+      const int ihi = min(tstep / 3, n - 3);
+      // the sweeps of this warp: i = gw (mod GW); at most one is active
+      int i = ihi - ((ihi - gw) % GW + GW) % GW;
+      for (; i >= 0; i -= GW) {
+        const int k = tstep - 3 * i;
+        const int nsteps = (n - 2 - i) / BW + 1;
+        if (k >= nsteps) break;
+        if (k == 0) {
+          const int L = min(BW, n - 1 - i);
+          const C x = lane < L ? bd.get(i + 1 + lane, i) : mk<T>(T(0), T(0));
+          C drow[BW];
+          cload_block<T>(bd, i + 1, i + 1, L, L, drow);
+          T tau;
+          C v, beta;
+          const bool tr = warp_reflector<T>(x, L, tau, v, beta);
+          if (tr) {
+            if (lane < L) bd.set(i + 1 + lane, i, lane == 0 ? beta : mk<T>(T(0), T(0)));
+            if (lane < BW) ws->v[lane] = lane < L ? v : mk<T>(T(0), T(0));
+            __syncwarp();
+            cwarp_two_sided<T>(bd, i + 1, L, tau, v, ws, drow);
+          }
+          if (lane < BW) slot_v[warp * BW + lane] = (tr && lane < L) ? v : mk<T>(T(0), T(0));
+          if (lane == 0) slot_tau[warp] = tau;
+        } else {
+          const int j0 = i + 1 + (k - 1) * BW;
+          const int Lp = min(BW, n - j0);
+          const int r0 = j0 + BW;
+          const int Lr = min(BW, n - r0);
+          const T tprev = slot_tau[warp];
+          if (lane < BW) ws->vp[lane] = slot_v[warp * BW + lane];
+          C e[BW], drow[BW];
+          cload_block<T>(bd, r0, j0, Lr, Lp, e);
+          cload_block<T>(bd, r0, r0, Lr, Lr, drow);
+          __syncwarp();
+          if (tprev != T(0)) {
+            C u = mk<T>(T(0), T(0));
+#pragma unroll
+            for (int c = 0; c < BW; ++c) u = cadd<T>(u, cmul<T>(e[c], ws->vp[c]));
+            u = cscale<T>(u, tprev);
+#pragma unroll
+            for (int c = 0; c < BW; ++c) e[c] = csub<T>(e[c], cmulc<T>(u, ws->vp[c]));
+          }
+          T tau;
+          C v, beta;
+          const bool tr = warp_reflector<T>(e[0], Lr, tau, v, beta);
+          if (tr) {
+            if (lane < BW) {
+#pragma unroll
+              for (int c = 0; c < BW; ++c) ws->m[lane][c] = lane < Lr ? cjmul<T>(v, e[c]) : mk<T>(T(0), T(0));
+            }
+            __syncwarp();
+            if (lane < BW) {
+              C acc = mk<T>(T(0), T(0));
+#pragma unroll
+              for (int l = 0; l < BW; ++l) acc = cadd<T>(acc, ws->m[l][lane]);
+              ws->w[lane] = acc;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int c = 1; c < BW; ++c) e[c] = csub<T>(e[c], cscale<T>(cmul<T>(v, ws->w[c]), tau));
+            e[0] = lane == 0 ? beta : mk<T>(T(0), T(0));
+          }
+          if (lane < Lr) {
+#pragma unroll
+            for (int c = 0; c < BW; ++c)
+              if (c < Lp) bd.set(r0 + lane, j0 + c, e[c]);
+          }
+          if (tr) {
+            if (lane < BW) ws->v[lane] = lane < Lr ? v : mk<T>(T(0), T(0));
+            __syncwarp();
+            cwarp_two_sided<T>(bd, r0, Lr, tau, v, ws, drow);
+          }
+          if (lane < BW) slot_v[warp * BW + lane] = (tr && lane < Lr) ? v : mk<T>(T(0), T(0));
+          if (lane == 0) slot_tau[warp] = tau;
+        }
+        __syncwarp();
+      }
+      cl.sync();
+    }
+  }
+  for (int cl_ = threadIdx.x; cl_ < cw; cl_ += blockDim.x) {
+    const int c = rank * cw + cl_;
+    if (c < n) {
+      d_out[(size_t)b * nm + c] = bd.get(c, c).x;
+      if (c < n - 1) e2_out[(size_t)b * nm + c] = cabs2<T>(bd.get(c + 1, c));
+    }
+  }
+  cl.sync();   // no CTA leaves while others may still read its shared memory
+}
+
+template <typename T>
+size_t per_matrix_bytes(int nm, int nsplit) {
+  using C = c2<T>;
+  return sizeof(C) * ((size_t)nm * nm + (size_t)(3 + nsplit) * BW * nm + BW * BW + (size_t)ND * nm) + 2048;
+}
+
+constexpr int kMaxSplit = 8;
 
 template <typename T>
 int solve_large_t(const SolveArgs& a) {
   using C = c2<T>;
   const int nm = a.n_max;
-  const int ntile = (nm + PT - 1) / PT;
-  const int nslice = (nm + CS - 1) / CS;
   const CellSet* cells = a.cells;
   const int K2 = a.Kside * a.Kside;
-  const size_t smem = sizeof(C) * 4 * NB * (HT + 1);   // her2k tiles
-  auto kern = k_lg_persist<T>;
-  IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, sms = 0, per_sm = 0, coop = 0;
-  IDOS_CUDA_TRY(cudaGetDevice(&dev));
-  IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  IDOS_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  IDOS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PT, smem));
-  if (!coop || per_sm < 1) {
-    set_error("cooperative launch of the large-matrix kernel is not possible on this device");
-    return IDOS_ERR_UNSUPPORTED;
-  }
-  const int grid = sms * std::min(per_sm, 4);
-  // per-matrix bytes: A + V + W + P + GEMV partials (+ small partials)
-  const size_t per_mat = per_matrix_bytes<T>(nm);
+  const size_t per_mat = per_matrix_bytes<T>(nm, kMaxSplit);
   const size_t room = a.ws->cap > a.ws->used ? a.ws->cap - a.ws->used : 0;
   int64_t batch = std::max<int64_t>(1, (int64_t)((room > 65536 ? room - 65536 : 0) / per_mat));
   batch = std::min<int64_t>(batch, a.n_mat);
   const size_t mark = a.ws->used;
-  PState<T> s{};
-  s.n_max = nm;
-  s.K2 = K2;
-  s.ntile = ntile;
-  s.nslice = nslice;
-  s.n_act_cell = cells ? cells->n_act : nullptr;
-  s.A = a.ws->take<C>((size_t)batch * nm * nm);
-  s.V = a.ws->take<C>((size_t)batch * NB * nm);
-  s.W = a.ws->take<C>((size_t)batch * NB * nm);
-  s.part = a.ws->take<C>((size_t)batch * nslice * nm);
-  s.prest = a.ws->take<T>((size_t)2 * batch * ntile);
-  s.gvy = a.ws->take<T>((size_t)2 * batch * ntile * nslice);
-  s.ps = a.ws->take<C>((size_t)2 * batch * ntile * 2 * NB);
-  s.alpha = a.ws->take<C>((size_t)2 * batch);
-  s.bar = a.ws->take<unsigned int>(2);
-  s.err = a.ws->take<int>(1);
-  if (!s.A || !s.V || !s.W || !s.part || !s.prest || !s.gvy || !s.ps || !s.alpha || !s.bar || !s.err) {
+  C* A = a.ws->take<C>((size_t)batch * nm * nm);
+  C* Y = a.ws->take<C>((size_t)batch * BW * nm);
+  C* YT = a.ws->take<C>((size_t)batch * BW * nm);
+  C* Z = a.ws->take<C>((size_t)batch * BW * nm);
+  C* Wp = a.ws->take<C>((size_t)batch * kMaxSplit * BW * nm);
+  C* Tm = a.ws->take<C>((size_t)batch * BW * BW);
+  C* Bd = a.ws->take<C>((size_t)batch * ND * nm);
+  if (!A || !Y || !YT || !Z || !Wp || !Tm || !Bd) {
     set_error("large-matrix workspace does not fit");
     return IDOS_ERR_OUT_OF_MEMORY;
   }
+  // panel QR in shared memory when the (n - BW) x BW panel fits
+  const size_t panel_smem = sizeof(C) * (size_t)(nm - BW) * BW;
+  const int use_smem = panel_smem <= 160 * 1024 ? 1 : 0;
+  if (use_smem)
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+  int dev = 0, sms = 0;
+  IDOS_CUDA_TRY(cudaGetDevice(&dev));
+  IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // chase: one warp per concurrently active sweep (at most n/(3 BW) + 2)
+  const int active = nm / (3 * BW) + 2;
+  const int chase_threads = 32 * std::min(Chase<T>::WARPS, std::max(2, active));
+  const int slots = 2 * active + 2;
+  const size_t head_bytes = sizeof(WarpScratch<T>) * (chase_threads / 32) + (sizeof(C) * BW + sizeof(T)) * (size_t)slots;
+  const size_t slot_bytes = (head_bytes + 255) & ~size_t(255);
+  const size_t band_bytes = sizeof(C) * (size_t)ND * nm;
+  const int band_in_smem = slot_bytes + band_bytes <= 200 * 1024 ? 1 : 0;
+  const size_t chase_smem = slot_bytes + (band_in_smem ? band_bytes : 0) + 64;
+  IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chase_smem));
+  // cluster chase: the smallest cluster (<= 16 CTAs) whose shared memory holds
+  // the band with one warp per concurrently active sweep; csz = 0 keeps the
+  // single-CTA kernel (band in its shared memory or, failing that, in HBM)
+  int csz = 0, cwarps = 0, ccw = 0;
+  size_t csmem = 0;
+  if (!band_in_smem) {
+    for (int q = 2; q <= 16 && csz == 0; q *= 2) {
+      const int w = std::min(Chase<T>::WARPS, std::max(2, (active + q - 1) / q));
+      const int cwq = (nm + q - 1) / q;
+      const size_t hb = (sizeof(WarpScratch<T>) * w + (sizeof(C) * BW + sizeof(T)) * (size_t)w + 255) & ~size_t(255);
+      const size_t need = hb + sizeof(C) * (size_t)ND * cwq + 64;
+      if (need <= 200 * 1024 && w * q >= active) {
+        csz = q;
+        cwarps = w;
+        ccw = cwq;
+        csmem = need;
+      }
+    }
+    if (csz > 0) {
+      IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+      if (csz > 8)
+        IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
+  }
   for (int64_t m0 = 0; m0 < a.n_mat; m0 += batch) {
     const int64_t nb_mat = std::min<int64_t>(batch, a.n_mat - m0);
-    s.B = (int)nb_mat;
-    s.mat0 = m0;
-    s.d_out = reinterpret_cast<T*>(a.d) + m0 * nm;
-    s.e2_out = reinterpret_cast<T*>(a.e2) + m0 * nm;
-    IDOS_CUDA_TRY(cudaMemsetAsync(s.A, 0, sizeof(C) * (size_t)nb_mat * nm * nm, a.stream));
-    IDOS_CUDA_TRY(cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned int), a.stream));
-    IDOS_CUDA_TRY(cudaMemsetAsync(s.err, 0, sizeof(int), a.stream));
+    Batch bt{nm, (int)nb_mat, K2, m0, cells ? cells->n_act : nullptr};
+    IDOS_CUDA_TRY(cudaMemsetAsync(A, 0, sizeof(C) * (size_t)nb_mat * nm * nm, a.stream));
     {
       const int64_t total = nb_mat * (int64_t)nm;
       const int64_t blocks = std::min<int64_t>((total + 127) / 128, 152 * 16);
@@ -635,20 +922,55 @@ int solve_large_t(const SolveArgs& a) {
       k_lg_assemble<T><<<(unsigned)blocks, 128, 0, a.stream>>>(
           nb_mat, m0, nm, K2, cells ? cells->n_act : nullptr, cells ? cells->act : nullptr,
           cells ? cells->inv : nullptr, cells ? cells->N : 0, a.Kside, a.t, a.eps,
-          a.H ? a.H + m0 * (int64_t)nm * nm : nullptr, s.A);
+          a.H ? a.H + m0 * (int64_t)nm * nm : nullptr, A);
       IDOS_CHECK_LAUNCH();
     }
     {
-      ProfScope ps(KID_LG_TRIDIAG, a.stream);
-      void* args[] = {&s};
-      IDOS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(PT), args, smem, a.stream));
+      ProfScope ps(KID_LG_BAND, a.stream);
+      for (int k = 0; k + BW < nm; k += BW) {
+        const int m = nm - k - BW;
+        {
+          ProfScope p1(KID_LG_PANEL, a.stream);
+          k_ts_panel<T><<<(unsigned)nb_mat, PQ_THREADS, use_smem ? panel_smem : 0, a.stream>>>(bt, k, A, Y, YT, Tm, use_smem);
+        }
+        const int rt = (m + Tiles<T>::WR - 1) / Tiles<T>::WR;
+        const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (2 * sms + rt * nb_mat - 1) / (rt * nb_mat)));
+        {
+          ProfScope p2(KID_LG_W, a.stream);
+          k_ts_w<T><<<dim3(rt, 1, (unsigned)(nb_mat * nsplit)), 256, 0, a.stream>>>(bt, k, A, YT, Wp, nsplit);
+          k_ts_z<T><<<(unsigned)nb_mat, PQ_THREADS, 0, a.stream>>>(bt, k, Y, Tm, Wp, nsplit, Z);
+        }
+        {
+          ProfScope p3(KID_LG_HER2K, a.stream);
+          const int gt = (m + Tiles<T>::GT - 1) / Tiles<T>::GT;
+          k_ts_her2k<T><<<dim3(gt, gt, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, k, A, Y, Z);
+        }
+      }
+      IDOS_CHECK_LAUNCH();
     }
-    int herr = 0;
-    IDOS_CUDA_TRY(cudaMemcpyAsync(&herr, s.err, sizeof(int), cudaMemcpyDeviceToHost, a.stream));
-    IDOS_CUDA_TRY(cudaStreamSynchronize(a.stream));
-    if (herr) {
-      set_error("large-matrix kernel: a grid barrier wait timed out");
-      return IDOS_ERR_TIMEOUT;
+    {
+      ProfScope ps(KID_LG_CHASE, a.stream);
+      k_ts_to_band<T><<<dim3(64, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, A, Bd);
+      if (csz > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nb_mat * csz));
+        cfg.blockDim = dim3(32 * cwarps);
+        cfg.dynamicSmemBytes = csmem;
+        cfg.stream = a.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = csz;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        IDOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ts_chase_cluster<T>, bt, (const C*)Bd,
+                                         reinterpret_cast<T*>(a.d) + m0 * nm, reinterpret_cast<T*>(a.e2) + m0 * nm, ccw));
+      } else {
+        k_ts_chase<T><<<(unsigned)nb_mat, chase_threads, chase_smem, a.stream>>>(
+            bt, Bd, reinterpret_cast<T*>(a.d) + m0 * nm, reinterpret_cast<T*>(a.e2) + m0 * nm, slots, band_in_smem);
+      }
+      IDOS_CHECK_LAUNCH();
     }
   }
   a.ws->used = mark;
@@ -658,7 +980,8 @@ int solve_large_t(const SolveArgs& a) {
 }  // namespace
 
 size_t large_path_bytes(int precision, int n_max, int64_t n_mat) {
-  const size_t per = precision == IDOS_FP64 ? per_matrix_bytes<double>(n_max) : per_matrix_bytes<float>(n_max);
+  const size_t per = precision == IDOS_FP64 ? per_matrix_bytes<double>(n_max, kMaxSplit)
+                                            : per_matrix_bytes<float>(n_max, kMaxSplit);
   return per * (size_t)std::max<int64_t>(n_mat, 1) + 65536 + 12 * 256;
 }
 

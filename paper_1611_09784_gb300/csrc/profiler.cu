@@ -9,7 +9,7 @@ void set_active_profiler(Profiler* p) { g_active = p; }
 
 const char* kernel_name(int kid) {
   static const char* names[KID_COUNT] = {
-      "k_fine_masks", "k_corner_masks", "k_cell_maps", "k_small_tridiag", "k_lg_assemble", "k_lg_persist",
+      "k_fine_masks", "k_corner_masks", "k_cell_maps", "k_small_tridiag", "k_lg_assemble", "k_lg_band", "k_lg_band.panel", "k_lg_band.w_z", "k_lg_band.her2k", "k_lg_chase",
       "k_bisect", "k_idos", "k_level_stats"};
   return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }

@@ -11,7 +11,7 @@
 namespace idos {
 
 enum KernelId {
-  KID_MASKS = 0, KID_CORNERS, KID_CELL_MAPS, KID_SMALL_TRIDIAG, KID_LG_ASSEMBLE, KID_LG_TRIDIAG,
+  KID_MASKS = 0, KID_CORNERS, KID_CELL_MAPS, KID_SMALL_TRIDIAG, KID_LG_ASSEMBLE, KID_LG_BAND, KID_LG_PANEL, KID_LG_W, KID_LG_HER2K, KID_LG_CHASE,
   KID_BISECT, KID_IDOS, KID_LEVEL_STATS, KID_COUNT
 };
 

@@ -169,3 +169,21 @@ def test_invalid_arguments_on_gpu(model):
         m.sample_level(9, 1, 0)
     with pytest.raises(pkg.IdosError):
         m.eval_idos(0, 1)
+
+
+def test_sample_levels_matches_per_level_calls(model):
+    """The concurrent all-levels call gives exactly the per-level results."""
+    m, w, prm, prec = model
+    counts = [5, 3, 2, 1]
+    firsts = [40, 41, 42, 43]
+    m.reset_level_stats(-1)
+    for l, c in enumerate(counts):
+        m.sample_level(l, c, w["seed"], firsts[l])
+    ref = [m.get_level_stats(l) for l in range(4)]
+    m.reset_level_stats(-1)
+    m.sample_levels(counts, w["seed"], firsts)
+    for l in range(4):
+        M, s1, s2, secs = m.get_level_stats(l)
+        assert M == ref[l][0]
+        assert np.array_equal(s1, ref[l][1]) and np.array_equal(s2, ref[l][2])
+        assert secs > 0
