@@ -28,6 +28,20 @@ __device__ __forceinline__ double2 graphene_phase(int N, int K, int kidx, int b)
   return make_double2(c, s);
 }
 
+// float32 variant: the same integer reduction, then one float32 sincospi of
+// a fraction in [0, 2) (relative rounding below 2^-23).
+__device__ __forceinline__ float2 graphene_phase_f(int N, int K, int kidx, int b) {
+  const int i1 = kidx % K, i2 = kidx / K;
+  const int U1 = 2 * i1 - K + 1, U2 = 2 * i2 - K + 1;
+  const int c1 = (b == 1) ? -2 : 1, c2 = (b == 2) ? -2 : 1;
+  const int D = 6 * N * K;
+  int num = (U1 * c1 + U2 * c2) % D;
+  if (num < 0) num += D;
+  float s, c;
+  sincospif((float)num / (float)(3 * N * K), &s, &c);
+  return make_float2(c, s);
+}
+
 // The three neighbours of site m; conj_phase = true for a B site (bond -R_b).
 __device__ __forceinline__ void graphene_neighbours(int N, int m, int nb[3], bool& from_B) {
   const int cell = m >> 1, s = m & 1;

@@ -2,13 +2,12 @@
 // the MLMC level difference with its float64 statistics (eq. (2.6) and the
 // variance display after it).
 //
-// Q(eps_j) = 1/(|F| K^2) sum_k sum_n g((E_n(k) - eps_j)/delta).  Per grid
-// point the eigenvalues are ascending, so for every energy the terms with
-// (E - eps_j)/delta < -c contribute exactly 1 and those above +c exactly 0
-// (to below float64 resolution for c = 8.5 with the Gaussian; exactly for
-// the compact polynomial with c = 1): a binary search gives the count below
-// the window and only the window's terms are evaluated.  All sums float64.
+// Q(eps_j) = 1/(|F| K^2) sum_k sum_n g((E_n(k) - eps_j)/delta).  Only the
+// terms inside a window of smoothing widths around eps_j are evaluated; the
+// eigenvalues below it count 1 each (see k_idos).
 #include <cfloat>
+#include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -18,47 +17,65 @@ namespace {
 
 constexpr int IDOS_THREADS = 256;
 
-__device__ __forceinline__ double smooth_g(double x, int smoothing, int fp32_erfc) {
-  if (smoothing == IDOS_SMOOTH_POLY) {
-    if (x <= -1.0) return 1.0;
-    if (x >= 1.0) return 0.0;
-    return 0.5 - 1.125 * x + 0.625 * x * x * x;
-  }
-  if (fp32_erfc) return 0.5 * (double)erfcf((float)(x * 0.70710678118654752440));
-  return 0.5 * erfc(x * 0.70710678118654752440);
-}
-
-// One CTA per cell; threads stride over energies.
+// One CTA per cell; threads stride over energies.  Per grid point the
+// eigenvalues (ascending) are mapped to grid coordinates u = (E - e_min)/h
+// (float64), split into the bucket ju = floor(u) and the fraction f = u - ju;
+// then for energy j, x_j(E) = (E - eps_j)/delta = ((ju - j) + f) h/delta.
+// Eigenvalues with ju < j - W have x < -c (their term is 1 to below the
+// working precision), those with ju > j + W have x > c (term 0), so the sum
+// is a count (a binary search on the non-decreasing ju) plus the terms of
+// the 2W + 1 buckets around j.  F32: the window terms and their sum are
+// float32 (erfcf), the count and the sums over k are float64.
+template <bool F32>
 __global__ void __launch_bounds__(IDOS_THREADS)
-k_idos(const double* __restrict__ eigs, const int* __restrict__ n_act_cell, int K2, int n_max,
-       double inv_norm, double e_min, double span, double delta, int n_E, int smoothing, int fp32_erfc,
-       double* __restrict__ Q) {
-  extern __shared__ double sE[];
+k_idos(const double* __restrict__ eigs, const int* __restrict__ n_act_cell, int K2, int n_max, double inv_norm,
+       double e_min, double inv_h, double h_over_delta, int W, int n_E, int smoothing, double* __restrict__ Q) {
+  using R = typename std::conditional<F32, float, double>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* sju = reinterpret_cast<int*>(smem_raw);
+  R* sf = reinterpret_cast<R*>(smem_raw + (((size_t)n_max * sizeof(int) + 15) & ~size_t(15)));
   const int64_t cell = blockIdx.x;
   const int n = n_act_cell ? n_act_cell[cell] : n_max;
-  const double c = (smoothing == IDOS_SMOOTH_POLY) ? 1.0 : 8.5;
-  const double inv_delta = 1.0 / delta;
+  const R r = (R)h_over_delta;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};   // up to 4 energies per thread (n_E <= 1024)
   for (int k = 0; k < K2; ++k) {
     const double* E = eigs + (cell * K2 + k) * (int64_t)n_max;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sE[i] = E[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double u = (E[i] - e_min) * inv_h;
+      const double fl = floor(u);
+      sju[i] = (int)fl;
+      sf[i] = (R)(u - fl);
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = threadIdx.x + q * IDOS_THREADS;
       if (j >= n_E) break;
-      const double eps = e_min + ((double)j * span) / (double)(n_E - 1);   // eps_j as defined
-      const double lo = eps - c * delta, hi = eps + c * delta;
-      // first index with E >= lo
-      int a = 0, b = n;
-      while (a < b) {
-        const int m = (a + b) >> 1;
-        if (sE[m] < lo) a = m + 1; else b = m;
+      // lo: first index with ju >= j - W;  hi: first index with ju > j + W
+      int lo = 0, hi = n;
+      {
+        int a = 0, b = n;
+        while (a < b) { const int m = (a + b) >> 1; if (sju[m] < j - W) a = m + 1; else b = m; }
+        lo = a;
+        b = n;
+        while (a < b) { const int m = (a + b) >> 1; if (sju[m] <= j + W) a = m + 1; else b = m; }
+        hi = a;
       }
-      double s = (double)a;
-      for (int i = a; i < n && sE[i] < hi; ++i) s += smooth_g((sE[i] - eps) * inv_delta, smoothing, fp32_erfc);
-      acc[q] += s;
+      R sum = R(0);
+      for (int i = lo; i < hi; ++i) {
+        const R x = ((R)(sju[i] - j) + sf[i]) * r;
+        R g;
+        if (smoothing == IDOS_SMOOTH_POLY) {
+          g = x <= R(-1) ? R(1) : (x >= R(1) ? R(0) : R(0.5) - R(1.125) * x + R(0.625) * x * x * x);
+        } else if constexpr (F32) {
+          g = 0.5f * erfcf(x * 0.70710678118654752440f);
+        } else {
+          g = 0.5 * erfc(x * 0.70710678118654752440);
+        }
+        sum += g;
+      }
+      acc[q] += (double)lo + (double)sum;
     }
   }
 #pragma unroll
@@ -114,13 +131,24 @@ int launch_idos(const double* eigs, const int* n_act_cell, int K2, int n_max, in
     set_error("n_E above 1024 is not supported by the IDoS kernel");
     return IDOS_ERR_UNSUPPORTED;
   }
-  const double span = g.e_max - g.e_min;
+  const double h = (g.e_max - g.e_min) / (g.n_E - 1);
   const double inv_norm = 1.0 / (area * K2);
-  const size_t smem = sizeof(double) * (size_t)n_max;
-  IDOS_CUDA_TRY(cudaFuncSetAttribute(k_idos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // half-width of the window in smoothing widths: the Gaussian tail beyond
+  // 8.5 (float64) / 6.5 (float32) standard deviations is below the working
+  // precision; the compact polynomial vanishes beyond 1
+  const double c = g.smoothing == IDOS_SMOOTH_POLY ? 1.0 : (g.fp32_erfc ? 6.5 : 8.5);
+  const int W = (int)std::ceil(c * g.delta / h) + 1;
+  const size_t smem = (((size_t)n_max * sizeof(int) + 15) & ~size_t(15)) + sizeof(double) * (size_t)n_max;
   ProfScope ps(KID_IDOS, s);
-  k_idos<<<(unsigned)n_cells, IDOS_THREADS, smem, s>>>(eigs, n_act_cell, K2, n_max, inv_norm, g.e_min, span,
-                                                       g.delta, g.n_E, g.smoothing, g.fp32_erfc, Q);
+  if (g.fp32_erfc) {
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_idos<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_idos<true><<<(unsigned)n_cells, IDOS_THREADS, smem, s>>>(eigs, n_act_cell, K2, n_max, inv_norm, g.e_min,
+                                                               1.0 / h, h / g.delta, W, g.n_E, g.smoothing, Q);
+  } else {
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_idos<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_idos<false><<<(unsigned)n_cells, IDOS_THREADS, smem, s>>>(eigs, n_act_cell, K2, n_max, inv_norm, g.e_min,
+                                                                1.0 / h, h / g.delta, W, g.n_E, g.smoothing, Q);
+  }
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
 }

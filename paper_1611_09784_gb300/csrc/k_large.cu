@@ -661,20 +661,48 @@ k_ts_chase(Batch bt, c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restric
   }
 }
 
-// Cluster variant of the chase: the band of one matrix is spread over the
-// shared memory of a cluster of CS CTAs (CTA q holds columns
-// [q CW, (q+1) CW)), every warp of the cluster takes the sweeps i = gw
-// (mod GW) (at most one active sweep per warp), and a cluster barrier ends
-// each time step.  Blocks crossing a CTA boundary are reached through
-// distributed shared memory.
-template <typename T>
-struct CBand {
+// Dataflow chase on a cluster of CS CTAs (CS = 1: one CTA).  The band of a
+// matrix is spread over the CTAs' shared memory (CTA q holds the columns
+// [q CW, (q+1) CW), CW a power of two).  Warp gw of the cluster runs the
+// sweeps i = gw (mod GW) in order, a whole warp per step (lane l and l+16
+// share row l, eight columns each).  Instead of a barrier per time step,
+// sweep i starts step k once sweep i-1 has completed min(k+3, its steps):
+// those are the blocks the step overlaps, and all later steps of earlier
+// sweeps lie further down the band.  Completion counters are published with
+// release stores and read with acquire loads at cluster scope; every wait
+// is bounded and sets the error flag when it gives up.
+template <bool CL>
+__device__ __forceinline__ void st_release(int* p, int v) {
+  if constexpr (CL) asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+  else asm volatile("st.release.cta.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <bool CL>
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  if constexpr (CL) asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  else asm volatile("ld.acquire.cta.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+template <bool CL>
+__device__ __forceinline__ void fence_acq_rel() {
+  if constexpr (CL) asm volatile("fence.acq_rel.cluster;" ::: "memory");
+  else asm volatile("fence.acq_rel.cta;" ::: "memory");
+}
+
+// CL = false: the whole band is in this CTA (no distributed addressing).
+template <typename T, bool CL>
+struct DBand {
   c2<T>* local;   // this CTA's band storage [ND][cw]
-  int cw;
+  int cwl;        // log2 of the columns per CTA
+  int rank;
   __device__ __forceinline__ c2<T>* addr(int d, int c) const {
-    const int o = c / cw;
-    c2<T>* p = local + (size_t)d * cw + (c - o * cw);
-    return cg::this_cluster().map_shared_rank(p, o);
+    if constexpr (!CL) {
+      return local + ((size_t)d << cwl) + c;
+    } else {
+      const int o = c >> cwl;
+      c2<T>* p = local + ((size_t)d << cwl) + (c & ((1 << cwl) - 1));
+      return o == rank ? p : cg::this_cluster().map_shared_rank(p, o);
+    }
   }
   __device__ __forceinline__ c2<T> get(int r, int c) const {
     return r >= c ? *addr(r - c, c) : conjg<T>(*addr(c - r, r));
@@ -682,161 +710,229 @@ struct CBand {
   __device__ __forceinline__ void set(int r, int c, c2<T> v) const { *addr(r - c, c) = v; }
 };
 
+constexpr int HB = BW / 2;   // columns per lane
+
+template <typename T>
+struct DScratch {
+  c2<T> v[BW], w[BW], vp[BW];
+  c2<T> m[BW][BW + 1];
+  T tau_prev;
+};
+
+// Load row (r0 + l) columns c0 + h*HB + q of a block (Lr rows, Lc columns).
 template <typename T, typename BandT>
-__device__ __forceinline__ void cload_block(const BandT& bd, int r0, int c0, int Lr, int Lc, c2<T>* out) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void dload(const BandT& bd, int r0, int c0, int Lr, int Lc, c2<T>* out) {
+  const int l = threadIdx.x & 15, h = (threadIdx.x >> 4) & 1;
 #pragma unroll
-  for (int c = 0; c < BW; ++c) out[c] = (lane < Lr && c < Lc) ? bd.get(r0 + lane, c0 + c) : mk<T>(T(0), T(0));
+  for (int q = 0; q < HB; ++q) {
+    const int c = h * HB + q;
+    out[q] = (l < Lr && c < Lc) ? bd.get(r0 + l, c0 + c) : mk<T>(T(0), T(0));
+  }
 }
 
+// Reflector from x (lanes l < L of the first half hold x_l; both halves
+// return v_l of their row).
+template <typename T>
+__device__ __forceinline__ bool dreflector(c2<T> x, int L, T& tau, c2<T>& v, c2<T>& beta) {
+  const int lane = threadIdx.x & 31, l = lane & 15;
+  T rest = (lane < 16 && l >= 1 && l < L) ? cabs2<T>(x) : T(0);
+  rest = warp_sum<T>(rest);
+  const c2<T> alpha = shfl_c<T>(x, 0);
+  const c2<T> xl = shfl_c<T>(x, l);
+  tau = T(0);
+  v = xl;
+  beta = alpha;
+  if (!(rest > tiny_rest<T>())) return false;
+  const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
+  const c2<T> ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+  tau = T(1) / (sigma * (sigma + aa));
+  if (l == 0) v = cadd<T>(alpha, cscale<T>(ph, sigma));
+  beta = cscale<T>(ph, -sigma);
+  return true;
+}
+
+// D <- H D H on A(r0.., r0..) (L rows), lower triangle stored.  ws->v holds v.
 template <typename T, typename BandT>
-__device__ __forceinline__ void cwarp_two_sided(const BandT& bd, int r0, int L, T tau, c2<T> v, WarpScratch<T>* ws,
-                                                const c2<T>* drow) {
+__device__ __forceinline__ void dtwo_sided(const BandT& bd, int r0, int L, T tau, c2<T> v, DScratch<T>* ws,
+                                           const c2<T>* dr) {
   using C = c2<T>;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, l = lane & 15, h = lane >> 4;
   C p = mk<T>(T(0), T(0));
 #pragma unroll
-  for (int c = 0; c < BW; ++c) p = cadd<T>(p, cmul<T>(drow[c], ws->v[c]));
+  for (int q = 0; q < HB; ++q) p = cadd<T>(p, cmul<T>(dr[q], ws->v[h * HB + q]));
+  p.x += __shfl_xor_sync(0xffffffffu, p.x, 16);
+  p.y += __shfl_xor_sync(0xffffffffu, p.y, 16);
   p = cscale<T>(p, tau);
-  const T kp = lane < L ? (v.x * p.x + v.y * p.y) : T(0);
+  const T kp = (h == 0 && l < L) ? (v.x * p.x + v.y * p.y) : T(0);
   const T K = T(0.5) * tau * warp_sum<T>(kp);
   const C w = csub<T>(p, cscale<T>(v, K));
-  if (lane < BW) ws->w[lane] = lane < L ? w : mk<T>(T(0), T(0));
+  if (h == 0) ws->w[l] = l < L ? w : mk<T>(T(0), T(0));
   __syncwarp();
-  if (lane < L) {
+  if (l < L) {
 #pragma unroll
-    for (int c = 0; c < BW; ++c) {
-      if (c <= lane) {
-        C d = drow[c];
+    for (int q = 0; q < HB; ++q) {
+      const int c = h * HB + q;
+      if (c <= l) {
+        C d = dr[q];
         d = csub<T>(d, cmulc<T>(v, ws->w[c]));
         d = csub<T>(d, cmulc<T>(w, ws->v[c]));
-        if (c == lane) d.y = T(0);
-        bd.set(r0 + lane, r0 + c, d);
+        if (c == l) d.y = T(0);
+        bd.set(r0 + l, r0 + c, d);
       }
     }
   }
   __syncwarp();
 }
 
-template <typename T>
+template <typename T, bool CL>
 __global__ void __launch_bounds__(32 * Chase<T>::WARPS)
-k_ts_chase_cluster(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restrict__ e2_out, int cw) {
+k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restrict__ e2_out, int cwl,
+                int* __restrict__ err) {
   using C = c2<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cg::cluster_group cl = cg::this_cluster();
-  const int CSZ = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
+  const int CSZ = CL ? (int)cg::this_cluster().num_blocks() : 1;
+  const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
   const int nwarps = blockDim.x >> 5;
-  WarpScratch<T>* wsc = reinterpret_cast<WarpScratch<T>*>(smem_raw);
-  C* slot_v = reinterpret_cast<C*>(wsc + nwarps);               // [nwarps][BW]: sweep state of each warp
-  T* slot_tau = reinterpret_cast<T*>(slot_v + (size_t)nwarps * BW);
-  const size_t head = sizeof(WarpScratch<T>) * nwarps + (sizeof(C) * BW + sizeof(T)) * (size_t)nwarps;
-  C* local = reinterpret_cast<C*>(smem_raw + ((head + 255) & ~size_t(255)));
+  const int cw = 1 << cwl;
   const int b = blockIdx.x / CSZ;
   const int n = batch_n(bt, b);
   const int nm = bt.n_max;
+  const int GW = CSZ * nwarps;
+  const int per_warp = (nm + GW - 1) / GW + 1;   // sweeps per warp (upper bound)
+  DScratch<T>* wsc = reinterpret_cast<DScratch<T>*>(smem_raw);
+  int* prog = reinterpret_cast<int*>(wsc + nwarps);             // [per_warp][nwarps] completed steps
+  const size_t head = sizeof(DScratch<T>) * nwarps + sizeof(int) * (size_t)per_warp * nwarps;
+  C* local = reinterpret_cast<C*>(smem_raw + ((head + 255) & ~size_t(255)));
   const C* gband = Bd + (size_t)b * ND * nm;
-  // load this CTA's columns of the band
   for (int idx = threadIdx.x; idx < ND * cw; idx += blockDim.x) {
-    const int d = idx / cw, cl_ = idx % cw, c = rank * cw + cl_;
+    const int d = idx >> cwl, c = rank * cw + (idx & (cw - 1));
     local[idx] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
   }
-  cl.sync();
-  const CBand<T> bd{local, cw};
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int GW = CSZ * nwarps, gw = rank * nwarps + warp;
-  WarpScratch<T>* ws = wsc + warp;
-  if (n >= 3) {
-    const int T_total = 3 * (n - 3) + 1;
-    for (int tstep = 0; tstep < T_total; ++tstep) {
-      const int ihi = min(tstep / 3, n - 3);
-      // the sweeps of this warp: i = gw (mod GW); at most one is active
-      int i = ihi - ((ihi - gw) % GW + GW) % GW;
-      for (; i >= 0; i -= GW) {
-        const int k = tstep - 3 * i;
-        const int nsteps = (n - 2 - i) / BW + 1;
-        if (k >= nsteps) break;
-        if (k == 0) {
-          const int L = min(BW, n - 1 - i);
-          const C x = lane < L ? bd.get(i + 1 + lane, i) : mk<T>(T(0), T(0));
-          C drow[BW];
-          cload_block<T>(bd, i + 1, i + 1, L, L, drow);
-          T tau;
-          C v, beta;
-          const bool tr = warp_reflector<T>(x, L, tau, v, beta);
-          if (tr) {
-            if (lane < L) bd.set(i + 1 + lane, i, lane == 0 ? beta : mk<T>(T(0), T(0)));
-            if (lane < BW) ws->v[lane] = lane < L ? v : mk<T>(T(0), T(0));
-            __syncwarp();
-            cwarp_two_sided<T>(bd, i + 1, L, tau, v, ws, drow);
+  for (int idx = threadIdx.x; idx < per_warp * nwarps; idx += blockDim.x) prog[idx] = 0;
+  if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
+  const DBand<T, CL> bd{local, cwl, rank};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, l = lane & 15, h = lane >> 4;
+  const int gw = rank * nwarps + warp;
+  DScratch<T>* ws = wsc + warp;
+  bool ok = true;
+  for (int i = gw; ok && i <= n - 3; i += GW) {
+    const int nsteps = (n - 2 - i) / BW + 1;
+    int* my_prog = prog + (size_t)(i / GW) * nwarps + warp;
+    const int* dep = nullptr;
+    int dep_steps = 0;
+    if (i > 0) {
+      const int ip = i - 1, gwp = ip % GW;
+      int* dp = prog + (size_t)(ip / GW) * nwarps + (gwp % nwarps);
+      if constexpr (CL) dep = cg::this_cluster().map_shared_rank(dp, gwp / nwarps);
+      else dep = dp;
+      dep_steps = (n - 2 - ip) / BW + 1;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+      if (dep) {
+        const int need = min(k + 3, dep_steps);
+        if (lane == 0) {
+          long long spins = 0;
+          while (ld_acquire<CL>(dep) < need) {
+            if (++spins > (1ll << 25) || *(volatile int*)err) {
+              atomicExch(err, 1);
+              ok = false;
+              break;
+            }
+            __nanosleep(32);
           }
-          if (lane < BW) slot_v[warp * BW + lane] = (tr && lane < L) ? v : mk<T>(T(0), T(0));
-          if (lane == 0) slot_tau[warp] = tau;
-        } else {
-          const int j0 = i + 1 + (k - 1) * BW;
-          const int Lp = min(BW, n - j0);
-          const int r0 = j0 + BW;
-          const int Lr = min(BW, n - r0);
-          const T tprev = slot_tau[warp];
-          if (lane < BW) ws->vp[lane] = slot_v[warp * BW + lane];
-          C e[BW], drow[BW];
-          cload_block<T>(bd, r0, j0, Lr, Lp, e);
-          cload_block<T>(bd, r0, r0, Lr, Lr, drow);
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+        fence_acq_rel<CL>();   // every lane sees what the release published
+      }
+      if (k == 0) {
+        const int L = min(BW, n - 1 - i);
+        const C x = (h == 0 && l < L) ? bd.get(i + 1 + l, i) : mk<T>(T(0), T(0));
+        C dr[HB];
+        dload<T>(bd, i + 1, i + 1, L, L, dr);
+        T tau;
+        C v, beta;
+        const bool tr = dreflector<T>(x, L, tau, v, beta);
+        if (tr) {
+          if (h == 0 && l < L) bd.set(i + 1 + l, i, l == 0 ? beta : mk<T>(T(0), T(0)));
+          if (h == 0) ws->v[l] = l < L ? v : mk<T>(T(0), T(0));
           __syncwarp();
-          if (tprev != T(0)) {
-            C u = mk<T>(T(0), T(0));
+          dtwo_sided<T>(bd, i + 1, L, tau, v, ws, dr);
+        }
+        if (h == 0) ws->vp[l] = (tr && l < L) ? v : mk<T>(T(0), T(0));
+        if (lane == 0) ws->tau_prev = tau;
+      } else {
+        const int j0 = i + 1 + (k - 1) * BW;
+        const int Lp = min(BW, n - j0);
+        const int r0 = j0 + BW;
+        const int Lr = min(BW, n - r0);
+        C e[HB], dr[HB];
+        dload<T>(bd, r0, j0, Lr, Lp, e);
+        dload<T>(bd, r0, r0, Lr, Lr, dr);
+        __syncwarp();
+        const T tprev = ws->tau_prev;
+        if (tprev != T(0)) {
+          C u = mk<T>(T(0), T(0));
 #pragma unroll
-            for (int c = 0; c < BW; ++c) u = cadd<T>(u, cmul<T>(e[c], ws->vp[c]));
-            u = cscale<T>(u, tprev);
+          for (int q = 0; q < HB; ++q) u = cadd<T>(u, cmul<T>(e[q], ws->vp[h * HB + q]));
+          u.x += __shfl_xor_sync(0xffffffffu, u.x, 16);
+          u.y += __shfl_xor_sync(0xffffffffu, u.y, 16);
+          u = cscale<T>(u, tprev);
 #pragma unroll
-            for (int c = 0; c < BW; ++c) e[c] = csub<T>(e[c], cmulc<T>(u, ws->vp[c]));
-          }
-          T tau;
-          C v, beta;
-          const bool tr = warp_reflector<T>(e[0], Lr, tau, v, beta);
-          if (tr) {
-            if (lane < BW) {
+          for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cmulc<T>(u, ws->vp[h * HB + q]));
+        }
+        // reflector from E's first column (held by lanes of the first half, q = 0)
+        T tau;
+        C v, beta;
+        const bool tr = dreflector<T>(e[0], Lr, tau, v, beta);
+        if (tr) {
+          // E <- H E, column sums through the scratch matrix
 #pragma unroll
-              for (int c = 0; c < BW; ++c) ws->m[lane][c] = lane < Lr ? cjmul<T>(v, e[c]) : mk<T>(T(0), T(0));
-            }
+          for (int q = 0; q < HB; ++q) ws->m[l][h * HB + q] = l < Lr ? cjmul<T>(v, e[q]) : mk<T>(T(0), T(0));
+          __syncwarp();
+          {
+            const int c = l;   // lanes l and l + 16 sum half of the rows of column l each
+            C acc = mk<T>(T(0), T(0));
+#pragma unroll
+            for (int rr = 0; rr < HB; ++rr) acc = cadd<T>(acc, ws->m[h * HB + rr][c]);
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
             __syncwarp();
-            if (lane < BW) {
-              C acc = mk<T>(T(0), T(0));
-#pragma unroll
-              for (int l = 0; l < BW; ++l) acc = cadd<T>(acc, ws->m[l][lane]);
-              ws->w[lane] = acc;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int c = 1; c < BW; ++c) e[c] = csub<T>(e[c], cscale<T>(cmul<T>(v, ws->w[c]), tau));
-            e[0] = lane == 0 ? beta : mk<T>(T(0), T(0));
+            if (h == 0) ws->w[c] = acc;
           }
-          if (lane < Lr) {
+          __syncwarp();
 #pragma unroll
-            for (int c = 0; c < BW; ++c)
-              if (c < Lp) bd.set(r0 + lane, j0 + c, e[c]);
-          }
-          if (tr) {
-            if (lane < BW) ws->v[lane] = lane < Lr ? v : mk<T>(T(0), T(0));
-            __syncwarp();
-            cwarp_two_sided<T>(bd, r0, Lr, tau, v, ws, drow);
-          }
-          if (lane < BW) slot_v[warp * BW + lane] = (tr && lane < Lr) ? v : mk<T>(T(0), T(0));
-          if (lane == 0) slot_tau[warp] = tau;
+          for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cscale<T>(cmul<T>(v, ws->w[h * HB + q]), tau));
+          if (h == 0) e[0] = l == 0 ? beta : mk<T>(T(0), T(0));
+        }
+        if (l < Lr) {
+#pragma unroll
+          for (int q = 0; q < HB; ++q)
+            if (h * HB + q < Lp) bd.set(r0 + l, j0 + h * HB + q, e[q]);
+        }
+        if (tr) {
+          if (h == 0) ws->v[l] = l < Lr ? v : mk<T>(T(0), T(0));
+          __syncwarp();
+          dtwo_sided<T>(bd, r0, Lr, tau, v, ws, dr);
         }
         __syncwarp();
+        if (h == 0) ws->vp[l] = (tr && l < Lr) ? v : mk<T>(T(0), T(0));
+        if (lane == 0) ws->tau_prev = tau;
       }
-      cl.sync();
+      fence_acq_rel<CL>();   // every lane's band writes before the release
+      __syncwarp();
+      if (lane == 0) st_release<CL>(my_prog, k + 1);
     }
   }
-  for (int cl_ = threadIdx.x; cl_ < cw; cl_ += blockDim.x) {
-    const int c = rank * cw + cl_;
+  if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
+  for (int c_ = threadIdx.x; c_ < cw; c_ += blockDim.x) {
+    const int c = rank * cw + c_;
     if (c < n) {
       d_out[(size_t)b * nm + c] = bd.get(c, c).x;
       if (c < n - 1) e2_out[(size_t)b * nm + c] = cabs2<T>(bd.get(c + 1, c));
     }
   }
-  cl.sync();   // no CTA leaves while others may still read its shared memory
+  if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while others may still read its shared memory
 }
 
 template <typename T>
@@ -887,30 +983,40 @@ int solve_large_t(const SolveArgs& a) {
   const int band_in_smem = slot_bytes + band_bytes <= 200 * 1024 ? 1 : 0;
   const size_t chase_smem = slot_bytes + (band_in_smem ? band_bytes : 0) + 64;
   IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chase_smem));
-  // cluster chase: the smallest cluster (<= 16 CTAs) whose shared memory holds
-  // the band with one warp per concurrently active sweep; csz = 0 keeps the
-  // single-CTA kernel (band in its shared memory or, failing that, in HBM)
-  int csz = 0, cwarps = 0, ccw = 0;
+  // dataflow chase: the smallest cluster (1 .. 16 CTAs) whose shared memory
+  // holds the band (power-of-two column split) with one warp per
+  // concurrently active sweep; csz = 0 keeps the barrier-per-step kernel
+  // with the band in HBM (bands too large for 16 CTAs)
+  int csz = 0, cwarps = 0, ccwl = 0;
   size_t csmem = 0;
-  if (!band_in_smem) {
-    for (int q = 2; q <= 16 && csz == 0; q *= 2) {
-      const int w = std::min(Chase<T>::WARPS, std::max(2, (active + q - 1) / q));
-      const int cwq = (nm + q - 1) / q;
-      const size_t hb = (sizeof(WarpScratch<T>) * w + (sizeof(C) * BW + sizeof(T)) * (size_t)w + 255) & ~size_t(255);
-      const size_t need = hb + sizeof(C) * (size_t)ND * cwq + 64;
-      if (need <= 200 * 1024 && w * q >= active) {
-        csz = q;
-        cwarps = w;
-        ccw = cwq;
-        csmem = need;
-      }
-    }
-    if (csz > 0) {
-      IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
-      if (csz > 8)
-        IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  for (int q = 1; q <= 16 && csz == 0; q *= 2) {
+    const int w = std::min(Chase<T>::WARPS, std::max(2, (active + q - 1) / q));
+    int cwl = 0;
+    while ((1 << cwl) * q < nm) ++cwl;
+    const int GWq = w * q;
+    const int per_warp = (nm + GWq - 1) / GWq + 1;
+    const size_t hb = (sizeof(DScratch<T>) * w + sizeof(int) * (size_t)per_warp * w + 255) & ~size_t(255);
+    const size_t need = hb + sizeof(C) * (size_t)ND * ((size_t)1 << cwl) + 64;
+    if (need <= 200 * 1024 && GWq >= active) {
+      csz = q;
+      cwarps = w;
+      ccwl = cwl;
+      csmem = need;
     }
   }
+  if (csz == 1) {
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_flow<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+  } else if (csz > 1) {
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_flow<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+    if (csz > 8)
+      IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_flow<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  }
+  int* d_err = a.ws->take<int>(1);
+  if (!d_err) {
+    set_error("large-matrix workspace does not fit");
+    return IDOS_ERR_OUT_OF_MEMORY;
+  }
+  IDOS_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), a.stream));
   for (int64_t m0 = 0; m0 < a.n_mat; m0 += batch) {
     const int64_t nb_mat = std::min<int64_t>(batch, a.n_mat - m0);
     Batch bt{nm, (int)nb_mat, K2, m0, cells ? cells->n_act : nullptr};
@@ -951,7 +1057,10 @@ int solve_large_t(const SolveArgs& a) {
     {
       ProfScope ps(KID_LG_CHASE, a.stream);
       k_ts_to_band<T><<<dim3(64, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, A, Bd);
-      if (csz > 0) {
+      if (csz == 1) {
+        k_ts_chase_flow<T, false><<<(unsigned)nb_mat, 32 * cwarps, csmem, a.stream>>>(
+            bt, (const C*)Bd, reinterpret_cast<T*>(a.d) + m0 * nm, reinterpret_cast<T*>(a.e2) + m0 * nm, ccwl, d_err);
+      } else if (csz > 1) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nb_mat * csz));
         cfg.blockDim = dim3(32 * cwarps);
@@ -964,13 +1073,23 @@ int solve_large_t(const SolveArgs& a) {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        IDOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ts_chase_cluster<T>, bt, (const C*)Bd,
-                                         reinterpret_cast<T*>(a.d) + m0 * nm, reinterpret_cast<T*>(a.e2) + m0 * nm, ccw));
+        IDOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ts_chase_flow<T, true>, bt, (const C*)Bd,
+                                         reinterpret_cast<T*>(a.d) + m0 * nm, reinterpret_cast<T*>(a.e2) + m0 * nm, ccwl,
+                                         d_err));
       } else {
         k_ts_chase<T><<<(unsigned)nb_mat, chase_threads, chase_smem, a.stream>>>(
             bt, Bd, reinterpret_cast<T*>(a.d) + m0 * nm, reinterpret_cast<T*>(a.e2) + m0 * nm, slots, band_in_smem);
       }
       IDOS_CHECK_LAUNCH();
+    }
+  }
+  if (csz > 0) {
+    int herr = 0;
+    IDOS_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, a.stream));
+    IDOS_CUDA_TRY(cudaStreamSynchronize(a.stream));
+    if (herr) {
+      set_error("band chase: a dependency wait timed out");
+      return IDOS_ERR_TIMEOUT;
     }
   }
   a.ws->used = mark;

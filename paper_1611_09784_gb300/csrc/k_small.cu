@@ -67,8 +67,13 @@ k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
   } else {
     const int n_sites = 2 * N * N;
     if (tid < 3) {
-      const double2 p = graphene_phase(N, K, kidx, tid);
-      ph[tid] = mk<T>((T)(t_hop * p.x), (T)(t_hop * p.y));
+      if constexpr (sizeof(T) == 4) {
+        const float2 p = graphene_phase_f(N, K, kidx, tid);
+        ph[tid] = mk<T>((T)t_hop * p.x, (T)t_hop * p.y);
+      } else {
+        const double2 p = graphene_phase(N, K, kidx, tid);
+        ph[tid] = mk<T>((T)(t_hop * p.x), (T)(t_hop * p.y));
+      }
     }
     for (int i = tid; i < n * n; i += NT) A[i] = mk<T>(T(0), T(0));
     group_sync<NT, MPB>(gid);
