@@ -178,21 +178,27 @@ def algorithmic_work(m, levels, M, seed, firsts, bw=16):
     flops of the small-matrix Householder kernel (16/3 n^3 per matrix) and of
     the large-matrix band reduction: per panel of bw columns with m rows below
     it, W = A22 (Y T) (8 m^2 bw real flops) and the full-storage rank-2bw
-    update (16 m^2 bw)."""
+    update (16 m^2 bw); and of the bulge chase: per sweep step the right and
+    left reflector applications to the bw x bw bulge block (2 x 8 bw^2) and
+    the two-sided update of the bw x bw diagonal block (3 x 8 bw^2)."""
     import numpy as np
     small_flops = 0.0
     band_flops = 0.0
+    chase_flops = 0.0
 
     def add(n_arr, K2, big):
-        nonlocal small_flops, band_flops
+        nonlocal small_flops, band_flops, chase_flops
         n = n_arr.astype(np.float64)
         if not big:
             small_flops += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
         else:
             for nn in n_arr:
-                for k in range(0, int(nn) - bw, bw):
+                nn = int(nn)
+                for k in range(0, nn - bw, bw):
                     mm = nn - k - bw
                     band_flops += K2 * 24.0 * bw * mm * mm
+                steps = sum((nn - 2 - i) // bw + 1 for i in range(0, nn - 2))
+                chase_flops += K2 * 40.0 * bw * bw * steps
     for l, (N, K) in enumerate(levels):
         if not M[l]:
             continue
@@ -204,13 +210,13 @@ def algorithmic_work(m, levels, M, seed, firsts, bw=16):
             Kc = levels[l - 1][1]
             bigc = 2 * (N // 2) ** 2 > 160
             add(corners.reshape(-1), Kc * Kc, bigc)
-    return {"k_small_tridiag": small_flops, "k_lg_band": band_flops}
+    return {"k_small_tridiag": small_flops, "k_lg_band": band_flops, "k_lg_chase": chase_flops}
 
 
 def roofline(prof, work, steps, pk, pk_kind, clocks):
     """Roofline object for the kernel with the largest event time."""
     ranked = sorted(prof.items(), key=lambda kv: -kv[1][0])
-    models = {"k_lg_band": "alu", "k_small_tridiag": "alu"}
+    models = {"k_lg_band": "alu", "k_small_tridiag": "alu", "k_lg_chase": "alu"}
     for name, (ms, launches) in ranked:
         if name not in models:
             continue
@@ -328,8 +334,6 @@ def run_gpu(args):
         step(i)
     torch.cuda.synchronize()
     model.reset_level_stats(-1)
-    model.reset_profile()
-    model.set_profiling(True)
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -347,20 +351,29 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    model.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
+    # Per-kernel CUDA-event times: the timed steps run the levels on
+    # concurrent streams, where one kernel's event span includes time spent
+    # waiting for SMs held by kernels of other levels.  So the kernels are
+    # timed on the same work (the timed steps' samples) replayed level by
+    # level, events on the launching stream around every launch.
+    model.reset_profile()
+    model.set_profiling(True)
+    for k in range(args.steps):
+        for l, Ml in enumerate(M):
+            if Ml:
+                model.sample_level(l, Ml, seed, first_sample=(args.warmup + k) * Ml)
+    torch.cuda.synchronize()
+    model.set_profiling(False)
     prof = model.get_profile()
-    # combine (eq. (2.6)) on the host from the device accumulators: the estimate
-    mean = np.zeros(w["n_E"])
-    var = np.zeros(w["n_E"])
-    for l in range(len(M)):
-        if not M[l]:
-            continue
-        Ml, s1, s2, _ = model.get_level_stats(l)
-        mu = s1 / Ml
-        mean += mu
-        var += np.maximum(s2 - Ml * mu * mu, 0) / (Ml - 1) / Ml
+    # combine (eq. (2.6)) from the device accumulators, summed over replicas
+    from paper_1611_09784_gb300 import replicas
+    counts, sums = replicas.model_stats(model)
+    if world > 1:
+        counts, sums = replicas.merge(counts, sums, device=dev)
+    used = [l for l in range(len(M)) if M[l]]
+    mean, var = replicas.combine(counts[used], sums[used])
     t_max = torch.tensor([total_ms], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
@@ -369,7 +382,7 @@ def run_gpu(args):
 
     # algorithmic work of the timed steps (exact kept-site counts)
     firsts_steps = [[(args.warmup + k) * Ml for Ml in M] for k in range(args.steps)]
-    work = {"k_small_tridiag": 0.0, "k_lg_band": 0.0}
+    work = {"k_small_tridiag": 0.0, "k_lg_band": 0.0, "k_lg_chase": 0.0}
     for firsts in firsts_steps:
         wk = algorithmic_work(model, levels, M, seed, firsts)
         for k2 in work:
@@ -444,6 +457,7 @@ def run_gpu(args):
                             "speedup_mlmc_vs_mc": mc_s / statistics.median(e2e_s)},
             "gpu_launches": int(sum(v[1] for v in prof.values()) // args.steps),
             "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
+            "kernels_timing": "CUDA events per launch, the timed steps' samples replayed level by level (unprofiled timed steps run the levels concurrently)",
             "roofline": roof,
             "clocks": clk,
             "cpu_baseline": cpu,
