@@ -353,6 +353,14 @@ def run_gpu(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
+    # combine (eq. (2.6)) from the device accumulators, summed over replicas
+    from paper_1611_09784_gb300 import replicas
+    counts, sums = replicas.model_stats(model)
+    level_span_ms = [round(model.get_level_stats(l)[3] * 1e3 / args.steps, 3) for l in range(len(M))]
+    if world > 1:
+        counts, sums = replicas.merge(counts, sums, device=dev)
+    used = [l for l in range(len(M)) if M[l]]
+    mean, var = replicas.combine(counts[used], sums[used])
     # Per-kernel CUDA-event times: the timed steps run the levels on
     # concurrent streams, where one kernel's event span includes time spent
     # waiting for SMs held by kernels of other levels.  So the kernels are
@@ -367,13 +375,6 @@ def run_gpu(args):
     torch.cuda.synchronize()
     model.set_profiling(False)
     prof = model.get_profile()
-    # combine (eq. (2.6)) from the device accumulators, summed over replicas
-    from paper_1611_09784_gb300 import replicas
-    counts, sums = replicas.model_stats(model)
-    if world > 1:
-        counts, sums = replicas.merge(counts, sums, device=dev)
-    used = [l for l in range(len(M)) if M[l]]
-    mean, var = replicas.combine(counts[used], sums[used])
     t_max = torch.tensor([total_ms], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
@@ -395,6 +396,7 @@ def run_gpu(args):
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                               "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
                               "partial": "timed steps only (--skip-extras)", "samples_per_level": M,
+                              "level_span_ms_per_step": level_span_ms,
                               "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
                               "roofline": roof, "clocks": clk}), flush=True)
         model.close()
@@ -457,6 +459,7 @@ def run_gpu(args):
                             "speedup_mlmc_vs_mc": mc_s / statistics.median(e2e_s)},
             "gpu_launches": int(sum(v[1] for v in prof.values()) // args.steps),
             "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
+            "level_span_ms_per_step": level_span_ms,
             "kernels_timing": "CUDA events per launch, the timed steps' samples replayed level by level (unprofiled timed steps run the levels concurrently)",
             "roofline": roof,
             "clocks": clk,

@@ -95,7 +95,7 @@ EnergyGrid grid_of(const idos_model_desc& d) {
 // Eigen-solve + IDoS of every cell of `cells` on a Kside grid: Q[count][n_E].
 // `eigs_keep` (optional) receives the device eigenvalue buffer pointer.
 int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double** eigs_keep, cudaStream_t st,
-                   Arena& ws) {
+                   Arena& ws, int* err) {
   const int n_max = cells.n_sites;
   const int K2 = Kside * Kside;
   const int64_t n_mat = cells.count * (int64_t)K2;
@@ -118,6 +118,7 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.e2 = e2;
   a.stream = st;
   a.ws = &ws;
+  a.err = err;
   if (small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
   IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
@@ -159,11 +160,22 @@ size_t large_room(const Model* M, int N, int Kside, int64_t count) {
   return std::max(one, std::min(want, cap));
 }
 
+// Reads a device status word once the work that may set it has completed.
+int check_status_word(const int* err) {
+  int h = 0;
+  IDOS_CUDA_TRY(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    set_error("band chase: a dependency wait timed out");
+    return IDOS_ERR_TIMEOUT;
+  }
+  return IDOS_OK;
+}
+
 // Samples of one level on stream st with workspace ws.  blocking: wait for
 // the level to finish and add its time and count to the accumulators;
 // otherwise the caller does that after synchronising ev1.
 int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh, double* Qfh,
-              double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, bool blocking) {
+              double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, bool blocking) {
   const idos_model_desc& d = M->d;
   const int Nf = d.N[level], Kf = d.Kside[level];
   const bool coarse = level > 0;
@@ -174,6 +186,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
                             3 * n_E * sizeof(double);
   int64_t chunk = std::max<int64_t>(1, (int64_t)(kSmallBudget / per_sample));
   chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_samples, 1));
+  IDOS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
   IDOS_CUDA_TRY(cudaEventRecord(ev0, st));
   for (int64_t s0 = 0; s0 < n_samples; s0 += chunk) {
     const int64_t S = std::min(chunk, n_samples - s0);
@@ -201,10 +214,10 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     // bigger solve goes last
     const size_t mark = ws.used;
     if (coarse) {
-      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st, ws));
+      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st, ws, err));
       ws.used = mark;
     }
-    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws));
+    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err));
     ws.used = mark;
     double* acc = M->acc + (size_t)level * 2 * n_E;
     IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, ws, st));
@@ -217,6 +230,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
   IDOS_CUDA_TRY(cudaEventRecord(ev1, st));
   if (blocking) {
     IDOS_CUDA_TRY(cudaEventSynchronize(ev1));
+    IDOS_TRY(check_status_word(err));
     float ms = 0.f;
     IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
     M->M[level] += n_samples;
@@ -289,11 +303,21 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
   const size_t acc_bytes = sizeof(double) * 2 * d->n_E * d->n_levels;
   cudaError_t e = cudaMalloc(&m->acc, acc_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->acc, 0, acc_bytes, m->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int) * (IDOS_MAX_LEVELS + 1));
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int) * (IDOS_MAX_LEVELS + 1), m->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
+  // Level streams get scheduling priorities by cost: the finest level's few
+  // large matrices form the critical path of a concurrent step (long chains
+  // of small, latency-bound launches), so its blocks are dispatched first
+  // whenever the many-matrix levels release an SM.
+  int prio_least = 0, prio_greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   for (int l = 0; l < d->n_levels && e == cudaSuccess; ++l) {
-    e = cudaStreamCreateWithFlags(&m->lstream[l], cudaStreamNonBlocking);
+    int prio = prio_greatest + (d->n_levels - 1 - l);   // greatest priority is the lowest number
+    if (prio > prio_least) prio = prio_least;
+    e = cudaStreamCreateWithPriority(&m->lstream[l], cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev0[l]);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev1[l]);
   }
@@ -311,6 +335,7 @@ void idos_destroy_model(idos_model* m) {
   if (!m) return;
   cudaStreamSynchronize(m->stream);
   if (m->acc) cudaFree(m->acc);
+  if (m->err) cudaFree(m->err);
   if (m->ev0) cudaEventDestroy(m->ev0);
   if (m->ev1) cudaEventDestroy(m->ev1);
   if (m->fork) cudaEventDestroy(m->fork);
@@ -335,7 +360,7 @@ int idos_sample_level_detail(idos_model* m, int level, int64_t n_samples, uint64
   if (n_samples == 0) return IDOS_OK;
   ProfGuard pg(m);
   return run_level(m, level, n_samples, seed, first_sample, per_sample_Y, Q_fine, Q_coarse, m->stream, m->ws, m->ev0,
-                   m->ev1, true);
+                   m->ev1, m->err + IDOS_MAX_LEVELS, true);
 }
 
 int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed, int64_t first_sample,
@@ -363,11 +388,12 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     const int l = order[q];
     if (n_samples[l] == 0) continue;
     IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr, nullptr,
-                       m->lstream[l], m->lws[l], m->lev0[l], m->lev1[l], false));
+                       m->lstream[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false));
   }
   for (int l = 0; l < L; ++l) {
     if (n_samples[l] == 0) continue;
     IDOS_CUDA_TRY(cudaEventSynchronize(m->lev1[l]));
+    IDOS_TRY(check_status_word(m->err + l));
     float ms = 0.f;
     IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, m->lev0[l], m->lev1[l]));
     m->M[l] += n_samples[l];
@@ -425,13 +451,15 @@ int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_
   }
   IDOS_TRY(launch_cell_maps(c, m->stream));
   double* eigs = nullptr;
-  IDOS_TRY(solve_and_idos(m, c, Kside, Q, &eigs, m->stream, m->ws));
+  int* err = m->err + IDOS_MAX_LEVELS;
+  IDOS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), m->stream));
+  IDOS_TRY(solve_and_idos(m, c, Kside, Q, &eigs, m->stream, m->ws, err));
   IDOS_CUDA_TRY(cudaMemcpyAsync(idos_out, Q, sizeof(double) * n_E, cudaMemcpyDeviceToHost, m->stream));
   if (eigs_out)
     IDOS_CUDA_TRY(cudaMemcpyAsync(eigs_out, eigs, sizeof(double) * Kside * Kside * c.n_sites,
                                   cudaMemcpyDeviceToHost, m->stream));
   IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
-  return IDOS_OK;
+  return check_status_word(err);
 }
 
 int idos_vacancy_masks(idos_model* m, int N, int level, uint64_t seed, int64_t first_sample, int64_t n_samples,
@@ -570,10 +598,15 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   int64_t d2h = 0;
   int rounds = 0;
   for (int round = 0; round <= o->max_rounds; ++round) {
+    // every level's extra samples in one concurrent call (level streams)
+    int64_t extra[IDOS_MAX_LEVELS] = {}, first[IDOS_MAX_LEVELS] = {};
+    bool any = false;
     for (int l = 0; l < L; ++l) {
-      const int64_t extra = target[l] - m->M[l];
-      if (extra > 0) IDOS_TRY(idos_sample_level(m, l, extra, o->seed, m->M[l], nullptr));
+      extra[l] = std::max<int64_t>(0, target[l] - m->M[l]);
+      first[l] = m->M[l];
+      any = any || extra[l] > 0;
     }
+    if (any) IDOS_TRY(idos_sample_levels(m, extra, o->seed, first));
     if (round == o->max_rounds) break;
     // V_l (max over the grid of the unbiased sample variance), W_l
     for (int l = 0; l < L; ++l) {

@@ -61,6 +61,10 @@ struct SolveArgs {
   void* e2 = nullptr;       // T[n_mat][n_max] squared off-diagonal (e2[i] couples i, i+1)
   cudaStream_t stream = 0;
   Arena* ws = nullptr;
+  // Device status word, zero on entry, set nonzero by a kernel whose bounded
+  // dependency wait ran out.  With it the caller checks after its own
+  // synchronisation; without it the large path checks (and synchronises).
+  int* err = nullptr;
 };
 
 struct Model {
@@ -72,6 +76,7 @@ struct Model {
   cudaEvent_t lev0[IDOS_MAX_LEVELS] = {}, lev1[IDOS_MAX_LEVELS] = {};
   cudaEvent_t fork = nullptr;
   double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
+  int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream
   int64_t M[IDOS_MAX_LEVELS] = {};
   double seconds[IDOS_MAX_LEVELS] = {};
   Arena ws;

@@ -1011,12 +1011,13 @@ int solve_large_t(const SolveArgs& a) {
     if (csz > 8)
       IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_flow<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   }
-  int* d_err = a.ws->take<int>(1);
+  const bool own_err = a.err == nullptr;
+  int* d_err = own_err ? a.ws->take<int>(1) : a.err;
   if (!d_err) {
     set_error("large-matrix workspace does not fit");
     return IDOS_ERR_OUT_OF_MEMORY;
   }
-  IDOS_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), a.stream));
+  if (own_err) IDOS_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), a.stream));
   for (int64_t m0 = 0; m0 < a.n_mat; m0 += batch) {
     const int64_t nb_mat = std::min<int64_t>(batch, a.n_mat - m0);
     Batch bt{nm, (int)nb_mat, K2, m0, cells ? cells->n_act : nullptr};
@@ -1083,7 +1084,7 @@ int solve_large_t(const SolveArgs& a) {
       IDOS_CHECK_LAUNCH();
     }
   }
-  if (csz > 0) {
+  if (csz > 0 && own_err) {
     int herr = 0;
     IDOS_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, a.stream));
     IDOS_CUDA_TRY(cudaStreamSynchronize(a.stream));
