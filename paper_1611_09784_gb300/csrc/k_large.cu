@@ -16,10 +16,12 @@
 //   annihilates column i below the subdiagonal with a length-BW reflector
 //   applied two-sided to the next diagonal block; the reflector's right
 //   application to the block below creates a bulge whose first column the
-//   next reflector annihilates, and so on down the band.  Sweep i runs its
-//   step k at time 3i + k (one warp per active sweep, a CTA barrier per time
-//   step): steps running at the same time touch disjoint blocks, and the
-//   lower bandwidth never exceeds 2 BW.
+//   next reflector annihilates, and so on down the band.  Step k of sweep i
+//   touches only entries with rows and columns in [i+1+(k-1)BW, i+1+(k+1)BW)
+//   and rows below i+1+(k+1)BW, so it is independent of steps k+2, k+3, ...
+//   of sweep i-1 (whose entries all have rows >= i+(k+2)BW): sweep i runs
+//   its step k at time 2i + k (one warp per active sweep, a CTA barrier per
+//   time step), and the lower bandwidth never exceeds 2 BW.
 // The tridiagonal comes out as d = Re diag, e^2 = |subdiag|^2.
 #include <cooperative_groups.h>
 
@@ -277,6 +279,177 @@ k_ts_panel(Batch bt, int k, c2<T>* __restrict__ A, c2<T>* __restrict__ Y, c2<T>*
   }
 }
 
+// ---------------------------------------------------- panel QR (cluster) --
+// The panel of one matrix spread over a cluster of PC CTAs (PC = 1: one
+// CTA); CTA q holds the panel rows [q RC, (q+1) RC), RC = ceil(m / PC), in
+// shared memory.  Column c needs, besides local rows, only
+//   h_d = sum_{r > c} conj(P[r][c]) P[r][d]   (d >= c; Re h_c = rest)
+// and row c of the panel: with v = x + ph sigma e_c,
+//   w_d = v^H P[:, d] = h_d + conj(v_c) P[c][d],
+// so one cluster exchange per column suffices.  Every CTA adds the PC
+// partials in rank order, so all hold bit-identical reflectors.  The Gram
+// matrix of Y, needed for T, is exchanged the same way once per panel.
+template <typename T, bool CL>
+__global__ void __launch_bounds__(PQ_THREADS, 1)
+k_ts_panel_cl(Batch bt, int k, c2<T>* __restrict__ A, c2<T>* __restrict__ Y, c2<T>* __restrict__ YT,
+              c2<T>* __restrict__ Tm, int rc_max) {
+  using C = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ C part[2][2 * BW];   // [buffer][h_0..h_{BW-1}, row c entries]
+  __shared__ C gpart[BW][BW];
+  __shared__ C swp[PQ_THREADS / 32][BW];
+  __shared__ C sH[BW], sRow[BW], sbeta[BW];
+  __shared__ C sG[BW][BW], sT[BW][BW];
+  __shared__ T stau[BW];
+  const int PC = CL ? (int)cg::this_cluster().num_blocks() : 1;
+  const int q = CL ? (int)cg::this_cluster().block_rank() : 0;
+  const int b = blockIdx.x / PC;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int m = n - k - BW;
+  if (m <= 0) return;   // the same for every CTA of the cluster
+  const int RC = (m + PC - 1) / PC;
+  const int rlo = q * RC, rhi = min(m, rlo + RC);
+  const int nr = max(0, rhi - rlo);
+  C* P = reinterpret_cast<C*>(smem_raw);   // [rc_max][BW]
+  C* Yl = P + (size_t)rc_max * BW;         // [rc_max][BW]
+  C* Ab = A + (size_t)b * nm * nm;
+  for (int idx = threadIdx.x; idx < nr * BW; idx += PQ_THREADS) {
+    const int r = idx / BW, c = idx % BW;
+    P[idx] = Ab[(size_t)(k + BW + rlo + r) * nm + k + c];
+  }
+  __syncthreads();
+  constexpr int G = PQ_THREADS / BW;
+  const int d = threadIdx.x % BW, g = threadIdx.x / BW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = 0; c < BW; ++c) {
+    const int buf = c & 1;
+    // local partial h_d over rows r > c
+    C acc = mk<T>(T(0), T(0));
+    if (d >= c) {
+      for (int r = g; r < nr; r += G)
+        if (rlo + r > c) acc = cadd<T>(acc, cjmul<T>(P[(size_t)r * BW + c], P[(size_t)r * BW + d]));
+    }
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+    if (lane < BW) swp[warp][d] = acc;
+    __syncthreads();
+    if (threadIdx.x < BW) {
+      C sum = mk<T>(T(0), T(0));
+      for (int w2 = 0; w2 < PQ_THREADS / 32; ++w2) sum = cadd<T>(sum, swp[w2][threadIdx.x]);
+      part[buf][threadIdx.x] = sum;
+    } else if (threadIdx.x < 2 * BW) {
+      const int dd = threadIdx.x - BW;
+      part[buf][threadIdx.x] = (c >= rlo && c < rhi && dd >= c) ? P[(size_t)(c - rlo) * BW + dd] : mk<T>(T(0), T(0));
+    }
+    if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
+    if (threadIdx.x < 2 * BW) {
+      C sum = mk<T>(T(0), T(0));
+      for (int o = 0; o < PC; ++o) {
+        const C* pp = &part[buf][threadIdx.x];
+        if constexpr (CL) pp = cg::this_cluster().map_shared_rank(pp, o);
+        sum = cadd<T>(sum, *pp);
+      }
+      if (threadIdx.x < BW) sH[threadIdx.x] = sum;
+      else sRow[threadIdx.x - BW] = sum;
+    }
+    __syncthreads();
+    // reflector (every thread computes the same values)
+    const C alpha = sRow[c];
+    const T rest = sH[c].x;
+    const bool tr = c < m && rest > tiny_rest<T>();
+    T tau = T(0);
+    C vc = alpha, beta = alpha;
+    if (tr) {
+      const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
+      const C ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+      tau = T(1) / (sigma * (sigma + aa));
+      vc = cadd<T>(alpha, cscale<T>(ph, sigma));
+      beta = cscale<T>(ph, -sigma);
+    }
+    if (threadIdx.x == 0) {
+      stau[c] = tau;
+      sbeta[c] = beta;
+    }
+    if (tr && d > c) {
+      const C wd = cscale<T>(cadd<T>(sH[d], cjmul<T>(vc, sRow[d])), tau);
+      for (int r = g; r < nr; r += G) {
+        const int rg = rlo + r;
+        if (rg < c) continue;
+        const C v = rg == c ? vc : P[(size_t)r * BW + c];
+        P[(size_t)r * BW + d] = csub<T>(P[(size_t)r * BW + d], cmul<T>(v, wd));
+      }
+    } else if (d == c) {
+      for (int r = g; r < nr; r += G) {
+        const int rg = rlo + r;
+        Yl[(size_t)r * BW + c] = (!tr || rg < c) ? mk<T>(T(0), T(0)) : (rg == c ? vc : P[(size_t)r * BW + c]);
+      }
+    }
+    __syncthreads();
+  }
+  // Gram matrix G[u][c] = y_u^H y_c (u < c): local partials, one exchange
+  if (threadIdx.x < BW * BW) {
+    const int u = threadIdx.x / BW, c = threadIdx.x % BW;
+    C a2 = mk<T>(T(0), T(0));
+    if (u < c)
+      for (int r = 0; r < nr; ++r) a2 = cadd<T>(a2, cjmul<T>(Yl[(size_t)r * BW + u], Yl[(size_t)r * BW + c]));
+    gpart[u][c] = a2;
+  }
+  if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
+  if (threadIdx.x < BW * BW) {
+    const int u = threadIdx.x / BW, c = threadIdx.x % BW;
+    C sum = mk<T>(T(0), T(0));
+    for (int o = 0; o < PC; ++o) {
+      const C* pp = &gpart[u][c];
+      if constexpr (CL) pp = cg::this_cluster().map_shared_rank(pp, o);
+      sum = cadd<T>(sum, *pp);
+    }
+    sG[u][c] = sum;
+  }
+  __syncthreads();
+  // T (forward, columnwise): T[c][c] = tau_c, T[u][c] = -tau_c sum_{u <= s < c} T[u][s] G[s][c]
+  if (warp == 0) {
+    for (int c = 0; c < BW; ++c) {
+      if (lane < BW) {
+        C t = mk<T>(T(0), T(0));
+        if (lane == c) {
+          t = mk<T>(stau[c], T(0));
+        } else if (lane < c) {
+          C a3 = mk<T>(T(0), T(0));
+          for (int s2 = lane; s2 < c; ++s2) a3 = cadd<T>(a3, cmul<T>(sT[lane][s2], sG[s2][c]));
+          t = cscale<T>(a3, -stau[c]);
+        }
+        sT[lane][c] = t;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (q == 0) {
+    C* Tb = Tm + (size_t)b * BW * BW;
+    for (int idx = threadIdx.x; idx < BW * BW; idx += PQ_THREADS) Tb[idx] = sT[idx / BW][idx % BW];
+  }
+  // Y, YT = Y T and the panel (R above its diagonal, beta on it, zeros below)
+  C* Yb = Y + (size_t)b * BW * nm;
+  C* YTb = YT + (size_t)b * BW * nm;
+  for (int idx = threadIdx.x; idx < nr * BW; idx += PQ_THREADS) {
+    const int c = idx / nr, r = idx % nr;   // consecutive threads: consecutive rows
+    const int rg = rlo + r;
+    C a4 = mk<T>(T(0), T(0));
+#pragma unroll 4
+    for (int u = 0; u <= c; ++u) a4 = cadd<T>(a4, cmul<T>(Yl[(size_t)r * BW + u], sT[u][c]));
+    Yb[(size_t)c * nm + rg] = Yl[(size_t)r * BW + c];
+    YTb[(size_t)c * nm + rg] = a4;
+  }
+  for (int idx = threadIdx.x; idx < nr * BW; idx += PQ_THREADS) {
+    const int r = idx / BW, c = idx % BW;
+    const int rg = rlo + r;
+    const C v = rg == c ? sbeta[c] : (rg > c ? mk<T>(T(0), T(0)) : P[idx]);
+    Ab[(size_t)(k + BW + rg) * nm + k + c] = v;
+  }
+  if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while others may read its partials
+}
+
 // --------------------------------------------------------- W = A22 (Y T) --
 // Wp[s][c][r] = sum over the s-th inner chunk of A22[r][x] YT[c][x].
 template <typename T>
@@ -330,59 +503,86 @@ k_ts_w(Batch bt, int k, const c2<T>* __restrict__ A, const c2<T>* __restrict__ Y
 }
 
 // ----------------------------------------------- Z = W - 1/2 Y (T^H M) --
+// Two wide launches over row chunks of ZR rows: k_ts_wm sums the split
+// partials of W (kept in Z) and forms the chunk's share of M = Y^H W;
+// k_ts_zc adds the shares in chunk order, P = T^H M, Z = W - 1/2 Y P.
+constexpr int ZR = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(PQ_THREADS, 1)
-k_ts_z(Batch bt, int k, const c2<T>* __restrict__ Y, const c2<T>* __restrict__ Tm, const c2<T>* __restrict__ Wp,
-       int nsplit, c2<T>* __restrict__ Z) {
+__global__ void __launch_bounds__(256)
+k_ts_wm(Batch bt, int k, const c2<T>* __restrict__ Y, const c2<T>* __restrict__ Wp, int nsplit,
+        c2<T>* __restrict__ Z, c2<T>* __restrict__ Mp, int nchunk) {
   using C = c2<T>;
-  __shared__ C sM[BW][BW];
-  __shared__ C sP[BW][BW];
-  const int b = blockIdx.x;
+  __shared__ C sY[BW][ZR + 1], sW[BW][ZR + 1];
+  const int b = blockIdx.y;
   const int n = batch_n(bt, b);
   const int nm = bt.n_max;
   const int m = n - k - BW;
+  const int r0 = blockIdx.x * ZR;
+  C* Mb = Mp + ((size_t)b * nchunk + blockIdx.x) * BW * BW;
   if (m <= 0) return;
+  if (r0 >= m) {   // chunk past this matrix's rows: a zero share
+    for (int idx = threadIdx.x; idx < BW * BW; idx += 256) Mb[idx] = mk<T>(T(0), T(0));
+    return;
+  }
   const C* Yb = Y + (size_t)b * BW * nm;
   C* Zb = Z + (size_t)b * BW * nm;
-  // W = sum of the split partials, kept in Z
-  for (int idx = threadIdx.x; idx < BW * m; idx += PQ_THREADS) {
-    const int c = idx / m, r = idx % m;
-    C w = mk<T>(T(0), T(0));
-    for (int sp = 0; sp < nsplit; ++sp) w = cadd<T>(w, Wp[((size_t)b * nsplit + sp) * BW * nm + (size_t)c * nm + r]);
-    Zb[(size_t)c * nm + r] = w;
-  }
-  __syncthreads();
-  // M = Y^H W (warp per entry)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int pr = warp; pr < BW * BW; pr += PQ_THREADS / 32) {
-    const int q = pr / BW, c = pr % BW;
-    C acc = mk<T>(T(0), T(0));
-    for (int r = q + lane; r < m; r += 32) acc = cadd<T>(acc, cjmul<T>(Yb[(size_t)q * nm + r], Zb[(size_t)c * nm + r]));
-    acc.x = warp_sum<T>(acc.x);
-    acc.y = warp_sum<T>(acc.y);
-    if (lane == 0) sM[q][c] = acc;
-  }
-  __syncthreads();
-  // P = T^H M
-  const C* Tb = Tm + (size_t)b * BW * BW;
-  if (threadIdx.x < BW * BW) {
-    const int q = threadIdx.x / BW, c = threadIdx.x % BW;
-    C acc = mk<T>(T(0), T(0));
-    for (int u = 0; u <= q; ++u) acc = cadd<T>(acc, cjmul<T>(Tb[u * BW + q], sM[u][c]));   // conj(T[u][q]) M[u][c]
-    sP[q][c] = acc;
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < m; r += PQ_THREADS) {
-    C yr[BW];
-#pragma unroll
-    for (int q = 0; q < BW; ++q) yr[q] = Yb[(size_t)q * nm + r];
-#pragma unroll 1
-    for (int c = 0; c < BW; ++c) {
-      C acc = mk<T>(T(0), T(0));
-#pragma unroll
-      for (int q = 0; q < BW; ++q) acc = cadd<T>(acc, cmul<T>(yr[q], sP[q][c]));
-      Zb[(size_t)c * nm + r] = csub<T>(Zb[(size_t)c * nm + r], cscale<T>(acc, T(0.5)));
+  for (int idx = threadIdx.x; idx < BW * ZR; idx += 256) {
+    const int c = idx / ZR, rr = idx % ZR;
+    const int r = r0 + rr;
+    C w = mk<T>(T(0), T(0)), y = mk<T>(T(0), T(0));
+    if (r < m) {
+      for (int sp = 0; sp < nsplit; ++sp) w = cadd<T>(w, Wp[((size_t)b * nsplit + sp) * BW * nm + (size_t)c * nm + r]);
+      y = Yb[(size_t)c * nm + r];
+      Zb[(size_t)c * nm + r] = w;
     }
+    sW[c][rr] = w;
+    sY[c][rr] = y;
+  }
+  __syncthreads();
+  const int u = threadIdx.x / BW, c = threadIdx.x % BW;
+  C acc = mk<T>(T(0), T(0));
+#pragma unroll 4
+  for (int rr = 0; rr < ZR; ++rr) acc = cadd<T>(acc, cjmul<T>(sY[u][rr], sW[c][rr]));
+  Mb[u * BW + c] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ts_zc(Batch bt, int k, const c2<T>* __restrict__ Y, const c2<T>* __restrict__ Tm, const c2<T>* __restrict__ Mp,
+        int nchunk, c2<T>* __restrict__ Z) {
+  using C = c2<T>;
+  __shared__ C sM[BW][BW], sP[BW][BW];
+  const int b = blockIdx.y;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int m = n - k - BW;
+  const int r0 = blockIdx.x * ZR;
+  if (m <= 0 || r0 >= m) return;
+  {
+    const int u = threadIdx.x / BW, c = threadIdx.x % BW;
+    C acc = mk<T>(T(0), T(0));
+    for (int ch = 0; ch < nchunk; ++ch) acc = cadd<T>(acc, Mp[((size_t)b * nchunk + ch) * BW * BW + u * BW + c]);
+    sM[u][c] = acc;
+  }
+  __syncthreads();
+  const C* Tb = Tm + (size_t)b * BW * BW;
+  {
+    const int u = threadIdx.x / BW, c = threadIdx.x % BW;
+    C acc = mk<T>(T(0), T(0));
+    for (int s2 = 0; s2 <= u; ++s2) acc = cadd<T>(acc, cjmul<T>(Tb[s2 * BW + u], sM[s2][c]));   // conj(T[s][u]) M[s][c]
+    sP[u][c] = cscale<T>(acc, T(0.5));
+  }
+  __syncthreads();
+  const C* Yb = Y + (size_t)b * BW * nm;
+  C* Zb = Z + (size_t)b * BW * nm;
+  for (int idx = threadIdx.x; idx < BW * ZR; idx += 256) {
+    const int c = idx / ZR, r = r0 + idx % ZR;
+    if (r >= m) continue;
+    C acc = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int u = 0; u < BW; ++u) acc = cadd<T>(acc, cmul<T>(Yb[(size_t)u * nm + r], sP[u][c]));
+    Zb[(size_t)c * nm + r] = csub<T>(Zb[(size_t)c * nm + r], acc);
   }
 }
 
@@ -568,11 +768,11 @@ k_ts_chase(Batch bt, c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restric
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpScratch<T>* ws = wsc + warp;
   if (n >= 3) {
-    const int T_total = 3 * (n - 3) + 1;
+    const int T_total = 2 * (n - 3) + 1;
     for (int tstep = 0; tstep < T_total; ++tstep) {
-      const int ihi = min(tstep / 3, n - 3);
+      const int ihi = min(tstep / 2, n - 3);
       for (int i = ihi - warp; i >= 0; i -= nwarps) {
-        const int k = tstep - 3 * i;
+        const int k = tstep - 2 * i;
         const int nsteps = (n - 2 - i) / BW + 1;   // step k while row i + 1 + k BW exists
         if (k >= nsteps) break;                    // older sweeps are done too
         const int slot = i % slots;
@@ -666,9 +866,9 @@ k_ts_chase(Batch bt, c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restric
 // [q CW, (q+1) CW), CW a power of two).  Warp gw of the cluster runs the
 // sweeps i = gw (mod GW) in order, a whole warp per step (lane l and l+16
 // share row l, eight columns each).  Instead of a barrier per time step,
-// sweep i starts step k once sweep i-1 has completed min(k+3, its steps):
-// those are the blocks the step overlaps, and all later steps of earlier
-// sweeps lie further down the band.  Completion counters are published with
+// sweep i starts step k once sweep i-1 has completed min(k+2, its steps):
+// those are the steps whose entries it shares, and all later steps of
+// earlier sweeps touch only entries further down the band.  Completion counters are published with
 // release stores and read with acquire loads at cluster scope; every wait
 // is bounded and sets the error flag when it gives up.
 template <bool CL>
@@ -829,7 +1029,7 @@ k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
     }
     for (int k = 0; k < nsteps; ++k) {
       if (dep) {
-        const int need = min(k + 3, dep_steps);
+        const int need = min(k + 2, dep_steps);
         if (lane == 0) {
           long long spins = 0;
           while (ld_acquire<CL>(dep) < need) {
@@ -938,7 +1138,9 @@ k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
 template <typename T>
 size_t per_matrix_bytes(int nm, int nsplit) {
   using C = c2<T>;
-  return sizeof(C) * ((size_t)nm * nm + (size_t)(3 + nsplit) * BW * nm + BW * BW + (size_t)ND * nm) + 2048;
+  const size_t nchunk = (size_t)(nm + ZR - 1) / ZR;
+  return sizeof(C) * ((size_t)nm * nm + (size_t)(3 + nsplit) * BW * nm + BW * BW + (size_t)ND * nm +
+                      nchunk * BW * BW) + 2048;
 }
 
 constexpr int kMaxSplit = 8;
@@ -961,7 +1163,9 @@ int solve_large_t(const SolveArgs& a) {
   C* Wp = a.ws->take<C>((size_t)batch * kMaxSplit * BW * nm);
   C* Tm = a.ws->take<C>((size_t)batch * BW * BW);
   C* Bd = a.ws->take<C>((size_t)batch * ND * nm);
-  if (!A || !Y || !YT || !Z || !Wp || !Tm || !Bd) {
+  const int nchunk_max = (nm + ZR - 1) / ZR;
+  C* Mp = a.ws->take<C>((size_t)batch * nchunk_max * BW * BW);
+  if (!A || !Y || !YT || !Z || !Wp || !Tm || !Bd || !Mp) {
     set_error("large-matrix workspace does not fit");
     return IDOS_ERR_OUT_OF_MEMORY;
   }
@@ -973,8 +1177,29 @@ int solve_large_t(const SolveArgs& a) {
   int dev = 0, sms = 0;
   IDOS_CUDA_TRY(cudaGetDevice(&dev));
   IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // chase: one warp per concurrently active sweep (at most n/(3 BW) + 2)
-  const int active = nm / (3 * BW) + 2;
+  // cluster panel QR: the smallest cluster (<= 8 CTAs) whose shared memory
+  // holds the first panel, grown while the batch leaves SMs idle and each CTA
+  // keeps at least 64 rows; pc = 0 keeps the one-CTA kernel above
+  int pc = 0, pc_rows = 0;
+  for (int q = 1; q <= 8; q *= 2) {
+    const int rows = (nm - BW + q - 1) / q;
+    const size_t smem = 2 * sizeof(C) * (size_t)rows * BW;
+    if (smem > 200 * 1024) continue;
+    if (pc == 0 || (batch * q <= sms && rows >= 64)) {
+      pc = q;
+      pc_rows = rows;
+    } else {
+      break;
+    }
+  }
+  const size_t pc_smem = 2 * sizeof(C) * (size_t)pc_rows * BW;
+  if (pc == 1) {
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel_cl<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+  } else if (pc > 1) {
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel_cl<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+  }
+  // chase: one warp per concurrently active sweep (at most n/(2 BW) + 2)
+  const int active = nm / (2 * BW) + 2;
   const int chase_threads = 32 * std::min(Chase<T>::WARPS, std::max(2, active));
   const int slots = 2 * active + 2;
   const size_t head_bytes = sizeof(WarpScratch<T>) * (chase_threads / 32) + (sizeof(C) * BW + sizeof(T)) * (size_t)slots;
@@ -987,21 +1212,31 @@ int solve_large_t(const SolveArgs& a) {
   // holds the band (power-of-two column split) with one warp per
   // concurrently active sweep; csz = 0 keeps the barrier-per-step kernel
   // with the band in HBM (bands too large for 16 CTAs)
+  // The smallest cluster that holds the band, grown (while the batch leaves
+  // SMs idle) until its warps cover the active sweeps; fewer warps than
+  // active sweeps only serialise sweeps.
   int csz = 0, cwarps = 0, ccwl = 0;
   size_t csmem = 0;
-  for (int q = 1; q <= 16 && csz == 0; q *= 2) {
-    const int w = std::min(Chase<T>::WARPS, std::max(2, (active + q - 1) / q));
-    int cwl = 0;
+  auto chase_cfg = [&](int q, int& w, int& cwl, size_t& need) {
+    w = std::min(Chase<T>::WARPS, std::max(2, (active + q - 1) / q));
+    cwl = 0;
     while ((1 << cwl) * q < nm) ++cwl;
-    const int GWq = w * q;
-    const int per_warp = (nm + GWq - 1) / GWq + 1;
+    const int per_warp = (nm + w * q - 1) / (w * q) + 1;
     const size_t hb = (sizeof(DScratch<T>) * w + sizeof(int) * (size_t)per_warp * w + 255) & ~size_t(255);
-    const size_t need = hb + sizeof(C) * (size_t)ND * ((size_t)1 << cwl) + 64;
-    if (need <= 200 * 1024 && GWq >= active) {
+    need = hb + sizeof(C) * (size_t)ND * ((size_t)1 << cwl) + 64;
+    return need <= 200 * 1024;
+  };
+  for (int q = 1; q <= 16; q *= 2) {
+    int w, cwl;
+    size_t need;
+    if (!chase_cfg(q, w, cwl, need)) continue;
+    if (csz == 0 || (cwarps * csz < active && batch * q <= sms)) {
       csz = q;
       cwarps = w;
       ccwl = cwl;
       csmem = need;
+    } else {
+      break;
     }
   }
   if (csz == 1) {
@@ -1038,14 +1273,35 @@ int solve_large_t(const SolveArgs& a) {
         const int m = nm - k - BW;
         {
           ProfScope p1(KID_LG_PANEL, a.stream);
-          k_ts_panel<T><<<(unsigned)nb_mat, PQ_THREADS, use_smem ? panel_smem : 0, a.stream>>>(bt, k, A, Y, YT, Tm, use_smem);
+          if (pc == 1) {
+            k_ts_panel_cl<T, false><<<(unsigned)nb_mat, PQ_THREADS, pc_smem, a.stream>>>(bt, k, A, Y, YT, Tm, pc_rows);
+          } else if (pc > 1) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(nb_mat * pc));
+            cfg.blockDim = dim3(PQ_THREADS);
+            cfg.dynamicSmemBytes = pc_smem;
+            cfg.stream = a.stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = pc;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            IDOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ts_panel_cl<T, true>, bt, k, A, Y, YT, Tm, pc_rows));
+          } else {
+            k_ts_panel<T><<<(unsigned)nb_mat, PQ_THREADS, use_smem ? panel_smem : 0, a.stream>>>(bt, k, A, Y, YT, Tm,
+                                                                                              use_smem);
+          }
         }
         const int rt = (m + Tiles<T>::WR - 1) / Tiles<T>::WR;
         const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (2 * sms + rt * nb_mat - 1) / (rt * nb_mat)));
         {
           ProfScope p2(KID_LG_W, a.stream);
           k_ts_w<T><<<dim3(rt, 1, (unsigned)(nb_mat * nsplit)), 256, 0, a.stream>>>(bt, k, A, YT, Wp, nsplit);
-          k_ts_z<T><<<(unsigned)nb_mat, PQ_THREADS, 0, a.stream>>>(bt, k, Y, Tm, Wp, nsplit, Z);
+          const int nchunk = (m + ZR - 1) / ZR;
+          k_ts_wm<T><<<dim3(nchunk, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, k, Y, Wp, nsplit, Z, Mp, nchunk);
+          k_ts_zc<T><<<dim3(nchunk, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, k, Y, Tm, Mp, nchunk, Z);
         }
         {
           ProfScope p3(KID_LG_HER2K, a.stream);
