@@ -861,20 +861,31 @@ k_ts_chase(Batch bt, c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restric
   }
 }
 
-// Dataflow chase on a cluster of CS CTAs (CS = 1: one CTA).  The band of a
-// matrix is spread over the CTAs' shared memory (CTA q holds the columns
-// [q CW, (q+1) CW), CW a power of two).  Warp gw of the cluster runs the
-// sweeps i = gw (mod GW) in order, a whole warp per step (lane l and l+16
-// share row l, eight columns each).  Instead of a barrier per time step,
-// sweep i starts step k once sweep i-1 has completed min(k+2, its steps):
-// those are the steps whose entries it shares, and all later steps of
-// earlier sweeps touch only entries further down the band.  Completion counters are published with
-// release stores and read with acquire loads at cluster scope; every wait
-// is bounded and sets the error flag when it gives up.
+// Dataflow chase on a cluster of CS CTAs (CS = 1: one CTA), owner
+// computes.  CTA q holds the band columns [q CW, (q+1) CW) (CW a power of
+// two) and runs every step whose anchor column (i for step 0 of sweep i,
+// i + 1 + (k-1) BW for step k >= 1) it holds: a step touches only columns
+// [anchor, anchor + 2 BW), so all but the steps within 2 BW of the right
+// edge work on local shared memory.  Warp w of every CTA runs the sweeps
+// i = w (mod NW) in order.  Instead of a barrier per time step, step k of
+// sweep i starts once sweep i-1 has completed min(k+2, its steps) (the
+// steps whose entries it shares; later steps of earlier sweeps touch only
+// entries further down the band) and, at its first step in a CTA, once the
+// CTA on the left has finished step k-1 and left its reflector in this
+// CTA's mailbox.  Completion counts, tagged with the sweep (i * 1024 + steps)
+// in a ring of NSL slots, are published with release stores at cluster
+// scope to the owning CTA and both neighbours, which hold every step that
+// waits on them; every wait is bounded and sets the error flag when it
+// gives up.
 template <bool CL>
 __device__ __forceinline__ void st_release(int* p, int v) {
   if constexpr (CL) asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
   else asm volatile("st.release.cta.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <bool CL>
+__device__ __forceinline__ void st_relaxed(int* p, int v) {
+  if constexpr (CL) asm volatile("st.relaxed.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+  else asm volatile("st.relaxed.cta.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 template <bool CL>
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -984,6 +995,118 @@ __device__ __forceinline__ void dtwo_sided(const BandT& bd, int r0, int L, T tau
   __syncwarp();
 }
 
+// Columns [lo, lo + 2^cwl) of the band, all in this CTA.
+template <typename T>
+struct LBand {
+  c2<T>* local;
+  int cwl;
+  int lo;
+  __device__ __forceinline__ c2<T>* addr(int d, int c) const { return local + ((size_t)d << cwl) + (c - lo); }
+  __device__ __forceinline__ c2<T> get(int r, int c) const {
+    return r >= c ? *addr(r - c, c) : conjg<T>(*addr(c - r, r));
+  }
+  __device__ __forceinline__ void set(int r, int c, c2<T> v) const { *addr(r - c, c) = v; }
+};
+
+// One step of the chase (k = 0: annihilate column i; k >= 1: apply the
+// previous reflector to the bulge block, annihilate its first column, apply
+// the new reflector two-sided to the next diagonal block).  The previous
+// reflector and its tau are in ws on entry and are replaced on exit.
+template <typename T, typename BandT>
+__device__ __forceinline__ void chase_step(const BandT& bd, int n, int i, int k, DScratch<T>* ws) {
+  using C = c2<T>;
+  const int lane = threadIdx.x & 31, l = lane & 15, h = lane >> 4;
+  if (k == 0) {
+    const int L = min(BW, n - 1 - i);
+    const C x = (h == 0 && l < L) ? bd.get(i + 1 + l, i) : mk<T>(T(0), T(0));
+    C dr[HB];
+    dload<T>(bd, i + 1, i + 1, L, L, dr);
+    T tau;
+    C v, beta;
+    const bool tr = dreflector<T>(x, L, tau, v, beta);
+    if (tr) {
+      if (h == 0 && l < L) bd.set(i + 1 + l, i, l == 0 ? beta : mk<T>(T(0), T(0)));
+      if (h == 0) ws->v[l] = l < L ? v : mk<T>(T(0), T(0));
+      __syncwarp();
+      dtwo_sided<T>(bd, i + 1, L, tau, v, ws, dr);
+    }
+    if (h == 0) ws->vp[l] = (tr && l < L) ? v : mk<T>(T(0), T(0));
+    if (lane == 0) ws->tau_prev = tau;
+    return;
+  }
+  const int j0 = i + 1 + (k - 1) * BW;
+  const int Lp = min(BW, n - j0);
+  const int r0 = j0 + BW;
+  const int Lr = min(BW, n - r0);
+  C e[HB], dr[HB];
+  dload<T>(bd, r0, j0, Lr, Lp, e);
+  dload<T>(bd, r0, r0, Lr, Lr, dr);
+  __syncwarp();
+  const T tprev = ws->tau_prev;
+  if (tprev != T(0)) {
+    C u = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int q = 0; q < HB; ++q) u = cadd<T>(u, cmul<T>(e[q], ws->vp[h * HB + q]));
+    u.x += __shfl_xor_sync(0xffffffffu, u.x, 16);
+    u.y += __shfl_xor_sync(0xffffffffu, u.y, 16);
+    u = cscale<T>(u, tprev);
+#pragma unroll
+    for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cmulc<T>(u, ws->vp[h * HB + q]));
+  }
+  // reflector from E's first column (held by lanes of the first half, q = 0)
+  T tau;
+  C v, beta;
+  const bool tr = dreflector<T>(e[0], Lr, tau, v, beta);
+  if (tr) {
+    // E <- H E, column sums through the scratch matrix
+#pragma unroll
+    for (int q = 0; q < HB; ++q) ws->m[l][h * HB + q] = l < Lr ? cjmul<T>(v, e[q]) : mk<T>(T(0), T(0));
+    __syncwarp();
+    {
+      const int c = l;   // lanes l and l + 16 sum half of the rows of column l each
+      C acc = mk<T>(T(0), T(0));
+#pragma unroll
+      for (int rr = 0; rr < HB; ++rr) acc = cadd<T>(acc, ws->m[h * HB + rr][c]);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+      __syncwarp();
+      if (h == 0) ws->w[c] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cscale<T>(cmul<T>(v, ws->w[h * HB + q]), tau));
+    if (h == 0) e[0] = l == 0 ? beta : mk<T>(T(0), T(0));
+  }
+  if (l < Lr) {
+#pragma unroll
+    for (int q = 0; q < HB; ++q)
+      if (h * HB + q < Lp) bd.set(r0 + l, j0 + h * HB + q, e[q]);
+  }
+  if (tr) {
+    if (h == 0) ws->v[l] = l < Lr ? v : mk<T>(T(0), T(0));
+    __syncwarp();
+    dtwo_sided<T>(bd, r0, Lr, tau, v, ws, dr);
+  }
+  __syncwarp();
+  if (h == 0) ws->vp[l] = (tr && l < Lr) ? v : mk<T>(T(0), T(0));
+  if (lane == 0) ws->tau_prev = tau;
+}
+
+// Reflector hand-over slot of a sweep entering a CTA.
+template <typename T>
+struct Mailbox {
+  c2<T> v[BW];
+  T tau;
+};
+constexpr int NMB = 16;   // mailbox ring (a slot is reused only after its sweep moved two CTAs on)
+
+__host__ __device__ constexpr int chase_ring(int cw) {
+  // progress ring: a slot is reused once its sweep is three CTAs ahead
+  int r = 64;
+  while (r < 4 * cw / (BW - 1) + 8) r *= 2;
+  return r;
+}
+
 template <typename T, bool CL>
 __global__ void __launch_bounds__(32 * Chase<T>::WARPS)
 k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restrict__ e2_out, int cwl,
@@ -994,139 +1117,107 @@ k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
   const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
   const int nwarps = blockDim.x >> 5;
   const int cw = 1 << cwl;
+  const int NSL = chase_ring(cw);
   const int b = blockIdx.x / CSZ;
   const int n = batch_n(bt, b);
   const int nm = bt.n_max;
-  const int GW = CSZ * nwarps;
-  const int per_warp = (nm + GW - 1) / GW + 1;   // sweeps per warp (upper bound)
+  const int lo = rank * cw, hi = lo + cw;
   DScratch<T>* wsc = reinterpret_cast<DScratch<T>*>(smem_raw);
-  int* prog = reinterpret_cast<int*>(wsc + nwarps);             // [per_warp][nwarps] completed steps
-  const size_t head = sizeof(DScratch<T>) * nwarps + sizeof(int) * (size_t)per_warp * nwarps;
+  Mailbox<T>* mbox = reinterpret_cast<Mailbox<T>*>(wsc + nwarps);   // [NMB]
+  int* prog = reinterpret_cast<int*>(mbox + NMB);                  // [NSL]
+  const size_t head = sizeof(DScratch<T>) * nwarps + sizeof(Mailbox<T>) * NMB + sizeof(int) * (size_t)NSL;
   C* local = reinterpret_cast<C*>(smem_raw + ((head + 255) & ~size_t(255)));
   const C* gband = Bd + (size_t)b * ND * nm;
   for (int idx = threadIdx.x; idx < ND * cw; idx += blockDim.x) {
-    const int d = idx >> cwl, c = rank * cw + (idx & (cw - 1));
+    const int d = idx >> cwl, c = lo + (idx & (cw - 1));
     local[idx] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
   }
-  for (int idx = threadIdx.x; idx < per_warp * nwarps; idx += blockDim.x) prog[idx] = 0;
+  for (int idx = threadIdx.x; idx < NSL; idx += blockDim.x) prog[idx] = 0;
   if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
   const DBand<T, CL> bd{local, cwl, rank};
+  const LBand<T> lb{local, cwl, lo};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, l = lane & 15, h = lane >> 4;
-  const int gw = rank * nwarps + warp;
   DScratch<T>* ws = wsc + warp;
-  bool ok = true;
-  for (int i = gw; ok && i <= n - 3; i += GW) {
-    const int nsteps = (n - 2 - i) / BW + 1;
-    int* my_prog = prog + (size_t)(i / GW) * nwarps + warp;
-    const int* dep = nullptr;
-    int dep_steps = 0;
-    if (i > 0) {
-      const int ip = i - 1, gwp = ip % GW;
-      int* dp = prog + (size_t)(ip / GW) * nwarps + (gwp % nwarps);
-      if constexpr (CL) dep = cg::this_cluster().map_shared_rank(dp, gwp / nwarps);
-      else dep = dp;
-      dep_steps = (n - 2 - ip) / BW + 1;
+  // Bounded wait until the local counter slot reaches `want`.  Every lane
+  // polls with its own acquire load (one broadcast read per poll), so each
+  // lane is ordered after the release it observed; the error flag in global
+  // memory is read only every 1024 polls.
+  auto wait_for = [&](int slot, int want) -> bool {
+    bool ok = true;
+    int spins = 0;
+    while (ld_acquire<CL>(prog + slot) < want) {
+      ++spins;
+      if ((spins & 1023) == 0 && (spins >= (1 << 25) || *(volatile int*)err)) {
+        atomicExch(err, 1);
+        ok = false;
+        break;
+      }
+      if (spins > 256) __nanosleep(20);
     }
-    for (int k = 0; k < nsteps; ++k) {
-      if (dep) {
-        const int need = min(k + 2, dep_steps);
-        if (lane == 0) {
-          long long spins = 0;
-          while (ld_acquire<CL>(dep) < need) {
-            if (++spins > (1ll << 25) || *(volatile int*)err) {
-              atomicExch(err, 1);
-              ok = false;
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    return __all_sync(0xffffffffu, ok);
+  };
+  bool ok = true;
+  for (int i = warp; ok && i <= n - 3 && i < hi; i += nwarps) {
+    const int nsteps = (n - 2 - i) / BW + 1;
+    // steps of sweep i anchored in [lo, hi): k in [klo, khi)
+    const int klo = i >= lo ? 0 : (lo - i - 1 + BW - 1) / BW + 1;
+    const int khi = min(nsteps, (hi - i - 1 + BW - 1) / BW + 1);
+    if (klo >= khi) continue;
+    const int dep_steps = i > 0 ? (n - 1 - i) / BW + 1 : 0;   // steps of sweep i-1
+    for (int k = klo; k < khi; ++k) {
+      if (k == klo && klo > 0) {
+        // hand-over: step k-1 done in the CTA on the left, reflector in the mailbox
+        ok = wait_for(i % NSL, i * 1024 + k);
         if (!ok) break;
-        fence_acq_rel<CL>();   // every lane sees what the release published
-      }
-      if (k == 0) {
-        const int L = min(BW, n - 1 - i);
-        const C x = (h == 0 && l < L) ? bd.get(i + 1 + l, i) : mk<T>(T(0), T(0));
-        C dr[HB];
-        dload<T>(bd, i + 1, i + 1, L, L, dr);
-        T tau;
-        C v, beta;
-        const bool tr = dreflector<T>(x, L, tau, v, beta);
-        if (tr) {
-          if (h == 0 && l < L) bd.set(i + 1 + l, i, l == 0 ? beta : mk<T>(T(0), T(0)));
-          if (h == 0) ws->v[l] = l < L ? v : mk<T>(T(0), T(0));
-          __syncwarp();
-          dtwo_sided<T>(bd, i + 1, L, tau, v, ws, dr);
-        }
-        if (h == 0) ws->vp[l] = (tr && l < L) ? v : mk<T>(T(0), T(0));
-        if (lane == 0) ws->tau_prev = tau;
-      } else {
-        const int j0 = i + 1 + (k - 1) * BW;
-        const int Lp = min(BW, n - j0);
-        const int r0 = j0 + BW;
-        const int Lr = min(BW, n - r0);
-        C e[HB], dr[HB];
-        dload<T>(bd, r0, j0, Lr, Lp, e);
-        dload<T>(bd, r0, r0, Lr, Lr, dr);
+        const Mailbox<T>* mb = mbox + (i % NMB);
+        if (h == 0) ws->vp[l] = mb->v[l];
+        if (lane == 0) ws->tau_prev = mb->tau;
         __syncwarp();
-        const T tprev = ws->tau_prev;
-        if (tprev != T(0)) {
-          C u = mk<T>(T(0), T(0));
-#pragma unroll
-          for (int q = 0; q < HB; ++q) u = cadd<T>(u, cmul<T>(e[q], ws->vp[h * HB + q]));
-          u.x += __shfl_xor_sync(0xffffffffu, u.x, 16);
-          u.y += __shfl_xor_sync(0xffffffffu, u.y, 16);
-          u = cscale<T>(u, tprev);
-#pragma unroll
-          for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cmulc<T>(u, ws->vp[h * HB + q]));
-        }
-        // reflector from E's first column (held by lanes of the first half, q = 0)
-        T tau;
-        C v, beta;
-        const bool tr = dreflector<T>(e[0], Lr, tau, v, beta);
-        if (tr) {
-          // E <- H E, column sums through the scratch matrix
-#pragma unroll
-          for (int q = 0; q < HB; ++q) ws->m[l][h * HB + q] = l < Lr ? cjmul<T>(v, e[q]) : mk<T>(T(0), T(0));
-          __syncwarp();
-          {
-            const int c = l;   // lanes l and l + 16 sum half of the rows of column l each
-            C acc = mk<T>(T(0), T(0));
-#pragma unroll
-            for (int rr = 0; rr < HB; ++rr) acc = cadd<T>(acc, ws->m[h * HB + rr][c]);
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-            __syncwarp();
-            if (h == 0) ws->w[c] = acc;
-          }
-          __syncwarp();
-#pragma unroll
-          for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cscale<T>(cmul<T>(v, ws->w[h * HB + q]), tau));
-          if (h == 0) e[0] = l == 0 ? beta : mk<T>(T(0), T(0));
-        }
-        if (l < Lr) {
-#pragma unroll
-          for (int q = 0; q < HB; ++q)
-            if (h * HB + q < Lp) bd.set(r0 + l, j0 + h * HB + q, e[q]);
-        }
-        if (tr) {
-          if (h == 0) ws->v[l] = l < Lr ? v : mk<T>(T(0), T(0));
-          __syncwarp();
-          dtwo_sided<T>(bd, r0, Lr, tau, v, ws, dr);
-        }
-        __syncwarp();
-        if (h == 0) ws->vp[l] = (tr && l < Lr) ? v : mk<T>(T(0), T(0));
-        if (lane == 0) ws->tau_prev = tau;
       }
-      fence_acq_rel<CL>();   // every lane's band writes before the release
+      if (i > 0) {
+        ok = wait_for((i - 1) % NSL, (i - 1) * 1024 + min(k + 2, dep_steps));
+        if (!ok) break;
+      }
+      const int anchor = k == 0 ? i : i + 1 + (k - 1) * BW;
+      if (!CL || anchor + 2 * BW <= hi) chase_step<T>(lb, n, i, k, ws);
+      else chase_step<T>(bd, n, i, k, ws);
+      const bool handover = CL && k == khi - 1 && k + 1 < nsteps;
+      if (handover) {
+        // the next step of this sweep runs in the CTA on the right
+        Mailbox<T>* mb = mbox + (i % NMB);
+        if constexpr (CL) mb = cg::this_cluster().map_shared_rank(mb, rank + 1);
+        __syncwarp();
+        if (h == 0) mb->v[l] = ws->vp[l];
+        if (lane == 0) mb->tau = ws->tau_prev;
+      }
+      // Release: the warp barrier orders every lane's band (and mailbox)
+      // writes before lane 0's fence, and the fence with the strong stores
+      // after it forms one release pattern for the counter copies.  At a
+      // hand-over the right copy is itself a release store, so the CTA that
+      // continues the sweep also sees this CTA's earlier counter writes (its
+      // own later writes to the same slots come after them).
       __syncwarp();
-      if (lane == 0) st_release<CL>(my_prog, k + 1);
+      if (lane == 0) {
+        const int tagv = i * 1024 + k + 1;
+        int* own = prog + (i % NSL);
+        fence_acq_rel<CL>();
+        if constexpr (CL) {
+          if (rank > 0) st_relaxed<CL>(cg::this_cluster().map_shared_rank(own, rank - 1), tagv);
+          st_relaxed<CL>(own, tagv);
+          if (rank + 1 < CSZ) {
+            int* right = cg::this_cluster().map_shared_rank(own, rank + 1);
+            if (handover) st_release<CL>(right, tagv);
+            else st_relaxed<CL>(right, tagv);
+          }
+        } else {
+          st_relaxed<CL>(own, tagv);
+        }
+      }
     }
   }
   if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
   for (int c_ = threadIdx.x; c_ < cw; c_ += blockDim.x) {
-    const int c = rank * cw + c_;
+    const int c = lo + c_;
     if (c < n) {
       d_out[(size_t)b * nm + c] = bd.get(c, c).x;
       if (c < n - 1) e2_out[(size_t)b * nm + c] = cabs2<T>(bd.get(c + 1, c));
@@ -1217,20 +1308,22 @@ int solve_large_t(const SolveArgs& a) {
   // active sweeps only serialise sweeps.
   int csz = 0, cwarps = 0, ccwl = 0;
   size_t csmem = 0;
+  // A CTA of the cluster sees at most CW / (2 BW) + 2 active sweeps at a time.
   auto chase_cfg = [&](int q, int& w, int& cwl, size_t& need) {
-    w = std::min(Chase<T>::WARPS, std::max(2, (active + q - 1) / q));
     cwl = 0;
     while ((1 << cwl) * q < nm) ++cwl;
-    const int per_warp = (nm + w * q - 1) / (w * q) + 1;
-    const size_t hb = (sizeof(DScratch<T>) * w + sizeof(int) * (size_t)per_warp * w + 255) & ~size_t(255);
+    w = std::min(Chase<T>::WARPS, std::max(2, std::min(active, (1 << cwl) / (2 * BW) + 2)));
+    const size_t hb = (sizeof(DScratch<T>) * w + sizeof(Mailbox<T>) * NMB + sizeof(int) * (size_t)chase_ring(1 << cwl) +
+                       255) & ~size_t(255);
     need = hb + sizeof(C) * (size_t)ND * ((size_t)1 << cwl) + 64;
     return need <= 200 * 1024;
   };
+  auto covered = [&](int w, int cwl) { return w >= std::min(active, (1 << cwl) / (2 * BW) + 2); };
   for (int q = 1; q <= 16; q *= 2) {
     int w, cwl;
     size_t need;
     if (!chase_cfg(q, w, cwl, need)) continue;
-    if (csz == 0 || (cwarps * csz < active && batch * q <= sms)) {
+    if (csz == 0 || (!covered(cwarps, ccwl) && batch * q <= sms)) {
       csz = q;
       cwarps = w;
       ccwl = cwl;
