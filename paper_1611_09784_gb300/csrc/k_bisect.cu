@@ -46,27 +46,36 @@ __device__ __forceinline__ int sturm_count(const S* __restrict__ d, const S* __r
   return cnt;
 }
 
-// One float64 pass: count of eigenvalues below x and the Newton step
-// -p_n(x)/p_n'(x) of the characteristic polynomial.
-template <typename S>
-__device__ __forceinline__ int sturm_newton64(const S* __restrict__ d, const S* __restrict__ e2, int n, double x,
-                                              double& step) {
-  double p0 = 1.0, p1 = (double)d[0] - x;       // p_{i-1}, p_i
+// Sign, zero and exponent tests on the bit pattern (integer pipe); the
+// float64 pipe is kept for the recurrence itself.
+__device__ __forceinline__ bool dneg(double v) { return __double2hiint(v) < 0; }
+__device__ __forceinline__ bool dzero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+// One float64 pass over (d, e^2) held in float64: count of eigenvalues below
+// x and the Newton step -p_n(x)/p_n'(x) of the characteristic polynomial.
+// Five float64 operations per row: t = d_i - x, p' = t p - b p_prev and
+// q' = t q - (b q_prev + p) as two fused pairs.
+__device__ __forceinline__ int sturm_newton64(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                                              double x, double& step) {
+  double p0 = 1.0, p1 = d[0] - x;               // p_{i-1}, p_i
   double q0 = 0.0, q1 = -1.0;                   // derivatives
-  if (p1 == 0.0) p1 = -0x1p-1000;              // exact zero pivot counts as negative
-  int cnt = p1 < 0.0;
+  if (dzero(p1)) p1 = -0x1p-1000;              // exact zero pivot counts as negative
+  int cnt = dneg(p1);
   for (int i = 1; i < n; ++i) {
-    const double t = (double)d[i] - x, b = (double)e2[i - 1];
-    double p2 = t * p1 - b * p0;
-    const double q2 = t * q1 - b * q0 - p1;
-    if (p2 == 0.0) p2 = -copysign(fmax(fabs(p1) * 0x1p-52, 0x1p-1000), p1);   // zero pivot -> negative
-    cnt += (p2 < 0.0) != (p1 < 0.0);
+    const double t = d[i] - x, b = e2[i - 1];
+    double p2 = fma(t, p1, -(b * p0));
+    const double q2 = fma(t, q1, -fma(b, q0, p1));
+    if (dzero(p2)) p2 = -copysign(fmax(fabs(p1) * 0x1p-52, 0x1p-1000), p1);   // zero pivot -> negative
+    cnt += dneg(p2) != dneg(p1);
     p0 = p1; p1 = p2; q0 = q1; q1 = q2;
-    if ((i & 15) == 0) {                       // keep the sequence in range: exact 2^-e scaling
-      const double m = fmax(fmax(fabs(p0), fabs(p1)), fmax(fabs(q0), fabs(q1)));
-      if (m > 0x1p+400 || (m < 0x1p-400 && m > 0.0)) {
-        const int e = ilogb(m);
-        p0 = scalbn(p0, -e); p1 = scalbn(p1, -e); q0 = scalbn(q0, -e); q1 = scalbn(q1, -e);
+    if ((i & 15) == 0) {
+      // keep the sequence in range: exact scaling by 2^-e, e the largest
+      // binary exponent (biased exponent fields compared as integers)
+      const int eb = max(max(dexp(p0), dexp(p1)), max(dexp(q0), dexp(q1)));
+      if ((eb > 1023 + 400 && eb < 2047) || (eb > 0 && eb < 1023 - 400)) {
+        const double sc = __hiloint2double((2046 - eb) << 20, 0);   // 2^(1023 - eb)
+        p0 *= sc; p1 *= sc; q0 *= sc; q1 *= sc;
       }
     }
   }
@@ -75,13 +84,12 @@ __device__ __forceinline__ int sturm_newton64(const S* __restrict__ d, const S* 
 }
 
 // Safeguarded Newton for eigenvalue k inside [lo, hi] (count(lo) <= k < count(hi)).
-template <typename S>
-__device__ __forceinline__ double newton_polish(const S* d, const S* e2, int n, int k, double lo, double hi,
+__device__ __forceinline__ double newton_polish(const double* d, const double* e2, int n, int k, double lo, double hi,
                                                 int passes) {
   double x = 0.5 * (lo + hi);
   for (int it = 0; it < passes; ++it) {
     double step;
-    const int c = sturm_newton64<S>(d, e2, n, x, step);
+    const int c = sturm_newton64(d, e2, n, x, step);
     if (c >= k + 1) hi = x; else lo = x;
     const double xn = x + step;
     const bool inside = xn > lo && xn < hi;
@@ -129,6 +137,11 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   if (mat >= n_mat) return;
   S* d = reinterpret_cast<S*>(smem_raw) + (size_t)gid * 2 * n_max;
   S* e2 = d + n_max;
+  // float64 copy for the float64 passes (the same arrays when S is double)
+  double* dd;
+  if constexpr (sizeof(S) == 8) dd = reinterpret_cast<double*>(d);
+  else dd = reinterpret_cast<double*>(smem_raw + sizeof(S) * 2 * (size_t)n_max * MPB) + (size_t)gid * 2 * n_max;
+  double* ee = dd + n_max;
   __shared__ double red_lo[MPB][G / 32], red_hi[MPB][G / 32], red_e[MPB][G / 32];
   const int n = n_act_cell ? n_act_cell[mat / K2] : n_max;
   double* out = eigs + mat * n_max;
@@ -143,6 +156,10 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
     const S ei = (i < n - 1) ? e2_in[mat * n_max + i] : S(0);
     d[i] = di;
     e2[i] = ei;
+    if constexpr (sizeof(S) == 4) {
+      dd[i] = (double)di;
+      ee[i] = (double)ei;
+    }
     const double el = (i > 0) ? sqrt((double)e2_in[mat * n_max + i - 1]) : 0.0;
     const double er = sqrt((double)ei);
     glo = fmin(glo, (double)di - el - er);
@@ -179,13 +196,13 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
       const double w = 64.0 * (double)FLT_EPSILON * fmax(fabs(glo), fabs(ghi)) + 1e-12;
       double lo = fmax(glo, (double)lo32 - w), hi = fmin(ghi, (double)hi32 + w);
       double st;
-      if (sturm_newton64<S>(d, e2, n, lo, st) > k) lo = glo;      // bracket lost: fall back
-      if (sturm_newton64<S>(d, e2, n, hi, st) < k + 1) hi = ghi;
-      out[k] = newton_polish<S>(d, e2, n, k, lo, hi, 60);
+      if (sturm_newton64(dd, ee, n, lo, st) > k) lo = glo;      // bracket lost: fall back
+      if (sturm_newton64(dd, ee, n, hi, st) < k + 1) hi = ghi;
+      out[k] = newton_polish(dd, ee, n, k, lo, hi, 60);
     } else {
       float lo = (float)glo, hi = (float)ghi;
       bisect_index<float, S>(d, e2, n, k, piv32, lo, hi, 100);
-      out[k] = refine > 0 ? newton_polish<S>(d, e2, n, k, (double)lo, (double)hi, refine)
+      out[k] = refine > 0 ? newton_polish(dd, ee, n, k, (double)lo, (double)hi, refine)
                           : 0.5 * ((double)lo + (double)hi);
     }
   }
@@ -194,7 +211,7 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
 template <typename S, int G, int MPB>
 int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int n_max, int64_t n_mat,
                int refine, double* eigs, cudaStream_t s, int chunk) {
-  const size_t smem = sizeof(S) * 2 * (size_t)n_max * MPB;
+  const size_t smem = (sizeof(S) + (sizeof(S) == 4 ? 8 : 0)) * 2 * (size_t)n_max * MPB;
   auto kern = k_bisect<S, G, MPB>;
   IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t groups = n_mat * ((n_max + chunk - 1) / chunk);
