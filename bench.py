@@ -142,8 +142,9 @@ def kernel_source_hash(name):
 
 def ncu_traffic(kernel, algorithmic_per_launch):
     """DRAM bytes per launch of `kernel`: the committed ncu capture's DRAM bytes
-    per algorithmic byte times this run's algorithmic bytes per launch; None
-    when there is no capture or the kernel source changed since it was taken."""
+    per algorithmic unit (flop or byte) times this run's algorithmic units per
+    launch; None when there is no capture or the kernel's source file changed
+    since it was taken."""
     try:
         with open(TRAFFIC_FILE) as f:
             for ln in f:
@@ -174,72 +175,69 @@ def n_act_of(masks, N):
 
 
 def algorithmic_work(m, levels, M, seed, firsts, bw=16):
-    """Exact algorithmic work of one step from the samples' kept-site counts:
-    flops of the small-matrix Householder kernel (16/3 n^3 per matrix) and of
-    the large-matrix band reduction: per panel of bw columns with m rows below
-    it, W = A22 (Y T) (8 m^2 bw real flops) and the full-storage rank-2bw
-    update (16 m^2 bw); and of the bulge chase: per sweep step the right and
-    left reflector applications to the bw x bw bulge block (2 x 8 bw^2) and
-    the two-sided update of the bw x bw diagonal block (3 x 8 bw^2)."""
+    """Exact algorithmic work of one step from the samples' kept-site counts,
+    in real flops per kernel: the small-matrix Householder kernel (16/3 n^3
+    per matrix); per stage-1 panel of bw columns with m rows below it,
+    W = A22 (Y T) (m^2 bw complex multiply-adds, 8 m^2 bw) and the
+    full-storage rank-2bw update (16 m^2 bw); the bulge chase, per sweep step
+    the right and left reflector applications to the bw x bw bulge block
+    (2 x 8 bw^2) and the two-sided update of the bw x bw diagonal block
+    (3 x 8 bw^2)."""
     import numpy as np
-    small_flops = 0.0
-    band_flops = 0.0
-    chase_flops = 0.0
+    work = {"k_small_tridiag": 0.0, "k_ts_w": 0.0, "k_ts_her2k": 0.0, "k_ts_chase": 0.0}
 
     def add(n_arr, K2, big):
-        nonlocal small_flops, band_flops, chase_flops
         n = n_arr.astype(np.float64)
         if not big:
-            small_flops += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
-        else:
-            for nn in n_arr:
-                nn = int(nn)
-                for k in range(0, nn - bw, bw):
-                    mm = nn - k - bw
-                    band_flops += K2 * 24.0 * bw * mm * mm
-                steps = sum((nn - 2 - i) // bw + 1 for i in range(0, nn - 2))
-                chase_flops += K2 * 40.0 * bw * bw * steps
+            work["k_small_tridiag"] += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
+            return
+        for nn in n_arr:
+            nn = int(nn)
+            for k in range(0, nn - bw, bw):
+                mm = nn - k - bw
+                work["k_ts_w"] += K2 * 8.0 * bw * mm * mm
+                work["k_ts_her2k"] += K2 * 16.0 * bw * mm * mm
+            steps = sum((nn - 2 - i) // bw + 1 for i in range(0, nn - 2))
+            work["k_ts_chase"] += K2 * 40.0 * bw * bw * steps
     for l, (N, K) in enumerate(levels):
         if not M[l]:
             continue
         masks = m.vacancy_masks(N, l, seed, firsts[l], M[l])
         fine, corners = n_act_of(masks, N)
-        big = 2 * N * N > 160
-        add(fine, K * K, big)
+        add(fine, K * K, 2 * N * N > 160)
         if l > 0:
             Kc = levels[l - 1][1]
-            bigc = 2 * (N // 2) ** 2 > 160
-            add(corners.reshape(-1), Kc * Kc, bigc)
-    return {"k_small_tridiag": small_flops, "k_lg_band": band_flops, "k_lg_chase": chase_flops}
+            add(corners.reshape(-1), Kc * Kc, 2 * (N // 2) ** 2 > 160)
+    return work
+
+
+AGGREGATE_SCOPES = ("k_lg_band (stage 1, all)",)
 
 
 def roofline(prof, work, steps, pk, pk_kind, clocks):
-    """Roofline object for the kernel with the largest event time."""
-    ranked = sorted(prof.items(), key=lambda kv: -kv[1][0])
-    models = {"k_lg_band": "alu", "k_small_tridiag": "alu", "k_lg_chase": "alu"}
-    for name, (ms, launches) in ranked:
-        if name not in models:
+    """Roofline objects of the modelled kernels; the first is the single kernel
+    (not an aggregate scope) with the largest event time."""
+    singles = sorted(((k, v) for k, v in prof.items() if k not in AGGREGATE_SCOPES), key=lambda kv: -kv[1][0])
+    models = {"k_small_tridiag": "alu", "k_ts_w": "alu", "k_ts_her2k": "alu", "k_ts_chase": "alu"}
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    out = []
+    for name, (ms, launches) in singles:
+        if name not in models or not launches or not ms:
             continue
         per_launch_s = ms * 1e-3 / launches
         units_per_launch = work[name] * steps / launches
-        bound = models[name]
-        if bound == "hbm":
-            achieved = units_per_launch / per_launch_s / 1e9
-            peak = pk["hbm_gbs"]
-            unit = "GB/s"
-        else:
-            achieved = units_per_launch / per_launch_s / 1e12
-            mhz = pk.get("sm_max_mhz", 2070.0)
-            peak = 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-            unit = "TFLOP/s"
-        tr = ncu_traffic(name, units_per_launch) if bound == "hbm" else None
-        return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": tr, "algorithmic_per_launch": units_per_launch,
-                "launches": launches, "avg_launch_ms": per_launch_s * 1e3,
-                "peak_source": f"{pk_kind}" + (" HBM copy" if bound == "hbm" else
-                                               " SM clock x 152 SMs x 128 FP32 lanes x 2"),
-                "dominant_by_event_time": ranked[0][0]}
-    return None
+        achieved = units_per_launch / per_launch_s / 1e12
+        out.append({"kernel": name, "bound": models[name], "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": ncu_traffic(name, units_per_launch),
+                    "algorithmic_per_launch": units_per_launch, "launches": launches,
+                    "avg_launch_ms": per_launch_s * 1e3,
+                    "peak_source": f"{pk_kind} SM clock x 152 SMs x 128 FP32 lanes x 2 (FP32 FMA issue rate)"})
+    dominant = singles[0][0] if singles else None
+    first = next((r for r in out if r["kernel"] == dominant), out[0] if out else None)
+    if first is not None:
+        first = dict(first, dominant_by_event_time=dominant)
+    return first, out
 
 
 # ------------------------------------------------------------- oracle (CPU) --
@@ -383,13 +381,13 @@ def run_gpu(args):
 
     # algorithmic work of the timed steps (exact kept-site counts)
     firsts_steps = [[(args.warmup + k) * Ml for Ml in M] for k in range(args.steps)]
-    work = {"k_small_tridiag": 0.0, "k_lg_band": 0.0, "k_lg_chase": 0.0}
+    work = {}
     for firsts in firsts_steps:
         wk = algorithmic_work(model, levels, M, seed, firsts)
-        for k2 in work:
-            work[k2] += wk[k2] / args.steps
+        for k2 in wk:
+            work[k2] = work.get(k2, 0.0) + wk[k2] / args.steps
     pk, pk_kind = peaks()
-    roof = roofline(prof, work, args.steps, pk, pk_kind, clk)
+    roof, roofs = roofline(prof, work, args.steps, pk, pk_kind, clk)
 
     if args.skip_extras:
         if rank == 0:
@@ -462,6 +460,7 @@ def run_gpu(args):
             "level_span_ms_per_step": level_span_ms,
             "kernels_timing": "CUDA events per launch, the timed steps' samples replayed level by level (unprofiled timed steps run the levels concurrently)",
             "roofline": roof,
+            "rooflines": roofs,
             "clocks": clk,
             "cpu_baseline": cpu,
             "estimate_check": {"Q_at_e_max": float(mean[-1]), "max_std": float(np.sqrt(np.max(var)))},

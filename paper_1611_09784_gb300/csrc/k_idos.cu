@@ -163,7 +163,7 @@ int launch_level_stats(const double* Qf, const double* Qc, int64_t S, int n_E, d
     return IDOS_ERR_OUT_OF_MEMORY;
   }
   const dim3 grid((n_E + 127) / 128, (unsigned)n_chunks);
-  ProfScope ps(KID_LEVEL_STATS, s);
+  ProfScope ps(KID_LEVEL_STATS, s, 2);
   k_level_partial<<<grid, 128, 0, s>>>(Qf, Qc, S, n_E, Y, partial);
   IDOS_CHECK_LAUNCH();
   k_level_final<<<(n_E + 127) / 128, 128, 0, s>>>(partial, n_chunks, n_E, acc);

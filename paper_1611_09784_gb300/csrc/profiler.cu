@@ -9,12 +9,12 @@ void set_active_profiler(Profiler* p) { g_active = p; }
 
 const char* kernel_name(int kid) {
   static const char* names[KID_COUNT] = {
-      "k_fine_masks", "k_corner_masks", "k_cell_maps", "k_small_tridiag", "k_lg_assemble", "k_lg_band", "k_lg_band.panel", "k_lg_band.w_z", "k_lg_band.her2k", "k_lg_chase",
+      "k_fine_masks", "k_corner_masks", "k_cell_maps", "k_small_tridiag", "k_lg_assemble", "k_lg_band (stage 1, all)", "k_ts_panel", "k_ts_w", "k_ts_z", "k_ts_her2k", "k_ts_chase",
       "k_bisect", "k_idos", "k_level_stats"};
   return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
-int Profiler::begin(int kid, cudaStream_t s) {
+int Profiler::begin(int kid, cudaStream_t s, int n_launch) {
   const size_t pair = pending_kid.size();
   while (pool.size() < 2 * (pair + 1)) {
     cudaEvent_t e;
@@ -23,6 +23,7 @@ int Profiler::begin(int kid, cudaStream_t s) {
   }
   if (cudaEventRecord(pool[2 * pair], s) != cudaSuccess) return -1;
   pending_kid.push_back(kid);
+  pending_n.push_back(n_launch);
   return (int)pair;
 }
 
@@ -33,14 +34,16 @@ void Profiler::resolve() {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) {
       ms[pending_kid[i]] += t;
-      launches[pending_kid[i]] += 1;
+      launches[pending_kid[i]] += pending_n[i];
     }
   }
   pending_kid.clear();
+  pending_n.clear();
 }
 
 void Profiler::clear() {
   pending_kid.clear();
+  pending_n.clear();
   for (int k = 0; k < KID_COUNT; ++k) { ms[k] = 0; launches[k] = 0; }
 }
 
