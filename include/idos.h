@@ -89,6 +89,11 @@ typedef struct idos_model_desc {
   int32_t refine64_iters; /* float64 Newton/Sturm passes (FP32_REFINE64)  */
   uint64_t model_seed; /* parameter seed of the TMDC-shaped model           */
   int64_t workspace_bytes; /* device workspace cap; 0 = library default      */
+  int32_t tc_products; /* IDOS_FP32_REFINE64, n > 160: trailing rank-2BW update
+                          of the two-stage reduction on the FP32 pipe (0) or on
+                          the tensor cores with 3 or 6 split-bfloat16 products
+                          (6: float32-class sums, 3: ~5x their error)        */
+  int32_t reserved0;   /* must be 0                                         */
 } idos_model_desc;
 
 typedef struct idos_model idos_model;
@@ -221,10 +226,24 @@ int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t
 
 /* All eigenvalues of `batch` dense Hermitian n x n matrices (host complex128,
  * row-major, interleaved re/im, float64[batch * 2 n^2]) through the hot
- * path's Householder reduction and Sturm bisection in `precision`; eigs_out:
- * host float64[batch * n], ascending per matrix.  cuda_stream as above. */
-int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const double* H,
-                  double* eigs_out, void* cuda_stream);
+ * path's Householder reduction and Sturm bisection in `precision`
+ * (tc_products as in idos_model_desc); eigs_out: host float64[batch * n],
+ * ascending per matrix.  cuda_stream as above. */
+int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int64_t batch,
+                  const double* H, double* eigs_out, void* cuda_stream);
+
+/* The trailing update of one stage-1 panel of the two-stage reduction
+ * (compact-WY form of the two-sided Householder update, Sec. 4.2's dense
+ * eigensolver): A_out = A - (Y Z^H + Z Y^H) for `batch` complex n x n
+ * matrices, computed in float32 storage by the kernel the large path runs:
+ * tc_products = 0 on the FP32 pipe, 3 or 6 on the tensor cores with that many
+ * split-bfloat16 products (see idos_model_desc).  A: host complex128
+ * float64[batch * 2 n^2] row-major; Y, Z: host complex128 float64[batch * 2 *
+ * 16 n], column c of matrix b at Y[b][c][0..n) (the 16 = band half-width
+ * columns of one panel); A_out: host float64[batch * 2 n^2].  Inputs are
+ * rounded to float32.  Allocates and frees its own device buffers; blocking. */
+int idos_her2k(int tc_products, int n, int64_t batch, const double* A, const double* Y, const double* Z,
+               double* A_out);
 
 /* ---- allocation-free evaluation ----
  * The paper has no counterpart to this entry point; it exists for callers

@@ -13,6 +13,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 MAX_LEVELS = 8
+# Trailing update of the float32 two-stage reduction on the tensor cores with
+# six split-bfloat16 products (float32-quality sums).
+DEFAULT_TC_PRODUCTS = 6
 GRAPHENE, TMDC = 0, 1
 FP64, FP32_REFINE64 = 0, 1
 SMOOTH_GAUSS, SMOOTH_POLY = 0, 1
@@ -28,7 +31,7 @@ class ModelDesc(C.Structure):
         ("t", C.c_double), ("eps_onsite", C.c_double), ("a", C.c_double), ("p", C.c_double),
         ("sentinel", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double), ("delta", C.c_double),
         ("n_E", C.c_int32), ("refine64_iters", C.c_int32), ("model_seed", C.c_uint64),
-        ("workspace_bytes", C.c_int64),
+        ("workspace_bytes", C.c_int64), ("tc_products", C.c_int32), ("reserved0", C.c_int32),
     ]
 
 
@@ -70,7 +73,8 @@ _SYMBOLS = {
     "idos_vacancy_masks": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int64, C.c_int64,
                                      C.c_void_p]),
     "idos_hamiltonian": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
-    "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_her2k": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "idos_profile_count": (C.c_int, []),
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -140,6 +144,7 @@ def make_desc(cfg: dict) -> ModelDesc:
     d.refine64_iters = int(cfg.get("refine64_iters", 0))
     d.model_seed = int(cfg.get("model_seed", 0))
     d.workspace_bytes = int(cfg.get("workspace_bytes", 0))
+    d.tc_products = int(cfg.get("tc_products", DEFAULT_TC_PRODUCTS))
     return d
 
 
@@ -270,15 +275,32 @@ def create_model(cfg: dict, stream: int | None = None) -> Model:
     return Model(cfg, stream)
 
 
-def eigvalsh(H, precision="fp32", refine64_iters: int = 0, stream: int | None = None):
+def eigvalsh(H, precision="fp32", refine64_iters: int = 0, stream: int | None = None,
+             tc_products: int | None = None):
     """Eigenvalues of a batch of Hermitian matrices through the GPU path."""
     H = np.ascontiguousarray(H, dtype=np.complex128)
     if H.ndim == 2:
         H = H[None]
     batch, n, _ = H.shape
     out = np.empty((batch, n))
-    _check(load_library().idos_eigvalsh(_PRECISION[precision], refine64_iters, n, batch, _ptr(H), _ptr(out),
+    tc = DEFAULT_TC_PRODUCTS if tc_products is None else int(tc_products)
+    _check(load_library().idos_eigvalsh(_PRECISION[precision], refine64_iters, tc, n, batch, _ptr(H), _ptr(out),
                                         C.c_void_p(stream or 0)), "idos_eigvalsh")
+    return out
+
+
+def her2k(A, Y, Z, tc_products: int = DEFAULT_TC_PRODUCTS):
+    """A - (Y Z^H + Z Y^H) through the large path's trailing-update kernel
+    (float32 storage; tc_products 0 = FP32 pipe, 3 or 6 = tensor cores).
+    A: (batch, n, n) complex; Y, Z: (batch, 16, n) complex (panel columns)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    Y = np.ascontiguousarray(Y, dtype=np.complex128)
+    Z = np.ascontiguousarray(Z, dtype=np.complex128)
+    batch, n, _ = A.shape
+    if Y.shape != (batch, 16, n) or Z.shape != (batch, 16, n):
+        raise ValueError("Y and Z must have shape (batch, 16, n)")
+    out = np.empty_like(A)
+    _check(load_library().idos_her2k(int(tc_products), n, batch, _ptr(A), _ptr(Y), _ptr(Z), _ptr(out)), "idos_her2k")
     return out
 
 

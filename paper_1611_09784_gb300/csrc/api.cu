@@ -39,11 +39,7 @@ void Arena::release() {
   cap = used = 0;
 }
 
-namespace {
-
-constexpr size_t kDefaultWorkspace = size_t(3) << 30;   // 3 GiB
-constexpr size_t kSmallBudget = size_t(768) << 20;      // per-chunk small buffers
-
+// The current device must be a GB300 (sm_103); sm_count receives its SM count.
 int check_device(int& sm_count) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -61,6 +57,12 @@ int check_device(int& sm_count) {
   sm_count = p.multiProcessorCount;
   return IDOS_OK;
 }
+
+namespace {
+
+constexpr size_t kDefaultWorkspace = size_t(3) << 30;   // 3 GiB
+constexpr size_t kSmallBudget = size_t(768) << 20;      // per-chunk small buffers
+
 
 int validate(const idos_model_desc* d) {
   auto bad = [](const char* m) { set_error(m); return IDOS_ERR_INVALID_ARG; };
@@ -83,6 +85,8 @@ int validate(const idos_model_desc* d) {
   if (d->n_E < 2 || d->n_E > 1024) return bad("n_E must lie in 2..1024");
   if (d->refine64_iters < 0 || d->refine64_iters > 64) return bad("refine64_iters must lie in 0..64");
   if (!(d->a > 0.0)) return bad("lattice constant must be positive");
+  if (d->tc_products != 0 && d->tc_products != 3 && d->tc_products != 6)
+    return bad("tc_products must be 0, 3 or 6");
   return IDOS_OK;
 }
 
@@ -119,6 +123,7 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.stream = st;
   a.ws = &ws;
   a.err = err;
+  a.tc_np = M->d.tc_products;
   if (small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
   IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
@@ -503,10 +508,14 @@ int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t
   return IDOS_OK;
 }
 
-int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const double* H, double* eigs_out,
-                  void* cuda_stream) {
+int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int64_t batch, const double* H,
+                  double* eigs_out, void* cuda_stream) {
   if (!H || !eigs_out) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
   if (precision != IDOS_FP64 && precision != IDOS_FP32_REFINE64) { set_error("precision"); return IDOS_ERR_INVALID_ARG; }
+  if (tc_products != 0 && tc_products != 3 && tc_products != 6) {
+    set_error("tc_products must be 0, 3 or 6");
+    return IDOS_ERR_INVALID_ARG;
+  }
   if (n < 1 || n > 8192 || batch < 0 || refine64_iters < 0 || refine64_iters > 64) {
     set_error("n, batch or refine64_iters out of range");
     return IDOS_ERR_INVALID_ARG;
@@ -543,6 +552,7 @@ int idos_eigvalsh(int precision, int refine64_iters, int n, int64_t batch, const
     a.e2 = e2;
     a.stream = s;
     a.ws = &ws;
+    a.tc_np = tc_products;
     rc = small ? solve_small(precision, a) : solve_large(precision, a);
   }
   if (rc == IDOS_OK) rc = launch_bisect(precision, refine64_iters, d, e2, nullptr, 1, n, batch, eigs, s);

@@ -50,6 +50,8 @@ struct CellSet {
 // Inputs of one batched eigen-solve: every cell of a CellSet at every point
 // of a Kside x Kside grid (matrix index = cell * K^2 + k), or `count`
 // explicit Hermitian matrices (H != nullptr, Kside = 1, n_act = n_max).
+int check_device(int& sm_count);   // IDOS_ERR_NO_DEVICE unless the current device is sm_103
+
 struct SolveArgs {
   const CellSet* cells = nullptr;
   int Kside = 1;
@@ -65,6 +67,9 @@ struct SolveArgs {
   // dependency wait ran out.  With it the caller checks after its own
   // synchronisation; without it the large path checks (and synchronises).
   int* err = nullptr;
+  // float32 large path: 0 = trailing update on the FP32 pipe, 3 or 6 =
+  // tensor cores with that many split-bfloat16 products
+  int tc_np = 0;
 };
 
 struct Model {

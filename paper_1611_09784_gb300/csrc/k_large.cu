@@ -15,6 +15,8 @@
 // Stage 2, band -> tridiagonal by bulge chasing, is in k_chase.cu.
 #include <cooperative_groups.h>
 
+#include <vector>
+
 #include "graphene.cuh"
 #include "large.cuh"
 
@@ -607,8 +609,9 @@ template <typename T>
 size_t per_matrix_bytes(int nm, int nsplit) {
   using C = c2<T>;
   const size_t nchunk = (size_t)(nm + ZR - 1) / ZR;
+  const size_t tc = sizeof(T) == 4 ? tc_operand_bytes(nm, 6) : 0;   // tensor-core operands (float32 only)
   return sizeof(C) * ((size_t)nm * nm + (size_t)(3 + nsplit) * BW * nm + BW * BW + (size_t)ND * nm +
-                      nchunk * BW * BW) + 2048;
+                      nchunk * BW * BW) + tc + 2048;
 }
 
 constexpr int kMaxSplit = 8;
@@ -636,6 +639,19 @@ int solve_large_t(const SolveArgs& a) {
   if (!A || !Y || !YT || !Z || !Wp || !Tm || !Bd || !Mp) {
     set_error("large-matrix workspace does not fit");
     return IDOS_ERR_OUT_OF_MEMORY;
+  }
+  // tensor-core trailing update (float32 storage only)
+  const bool use_tc = sizeof(T) == 4 && a.tc_np != 0 && nm % 2 == 0;
+  TcPlan tcp;
+  if (use_tc) {
+    const size_t half = tc_operand_bytes(nm, a.tc_np) / 3;   // Aop: one third, Bop: two thirds
+    void* Aop = a.ws->take<char>((size_t)batch * half);
+    void* Bop = a.ws->take<char>((size_t)batch * 2 * half);
+    if (!Aop || !Bop) {
+      set_error("large-matrix workspace does not fit the tensor-core operands");
+      return IDOS_ERR_OUT_OF_MEMORY;
+    }
+    IDOS_TRY(tc_plan(tcp, nm, batch, a.tc_np, Aop, Bop, A));
   }
   // panel QR in shared memory when the (n - BW) x BW panel fits
   const size_t panel_smem = sizeof(C) * (size_t)(nm - BW) * BW;
@@ -728,7 +744,11 @@ int solve_large_t(const SolveArgs& a) {
           k_ts_wm<T><<<dim3(nchunk, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, k, Y, Wp, nsplit, Z, Mp, nchunk);
           k_ts_zc<T><<<dim3(nchunk, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, k, Y, Tm, Mp, nchunk, Z);
         }
-        {
+        if (use_tc) {
+          ProfScope p3(KID_LG_HER2K, a.stream, 2);
+          IDOS_TRY(tc_her2k(tcp, bt, k, reinterpret_cast<const c2<float>*>(Y), reinterpret_cast<const c2<float>*>(Z),
+                            d_err, a.stream));
+        } else {
           ProfScope p3(KID_LG_HER2K, a.stream);
           const int gt = (m + Tiles<T>::GT - 1) / Tiles<T>::GT;
           k_ts_her2k<T><<<dim3(gt, gt, (unsigned)nb_mat), 256, 0, a.stream>>>(bt, k, A, Y, Z);
@@ -742,12 +762,12 @@ int solve_large_t(const SolveArgs& a) {
                             d_err, a.stream));
     }
   }
-  if (cp.csz > 0 && own_err) {
+  if ((cp.csz > 0 || use_tc) && own_err) {
     int herr = 0;
     IDOS_CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, a.stream));
     IDOS_CUDA_TRY(cudaStreamSynchronize(a.stream));
     if (herr) {
-      set_error("band chase: a dependency wait timed out");
+      set_error("large path: a bounded wait (band chase or tensor-core pipeline) timed out");
       return IDOS_ERR_TIMEOUT;
     }
   }
@@ -769,3 +789,74 @@ int solve_large(int precision, const SolveArgs& a) {
 }
 
 }  // namespace idos
+
+// ------------------------------------------------- trailing-update parity --
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+extern "C" int idos_her2k(int tc_products, int n, int64_t batch, const double* A, const double* Y, const double* Z,
+                          double* A_out) {
+  using namespace idos;
+  using namespace idos::lg;
+  if (!A || !Y || !Z || !A_out) {
+    set_error("null argument");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  if ((tc_products != 0 && tc_products != 3 && tc_products != 6) || n < 1 || n > 8192 || batch < 1 ||
+      batch > 65535) {
+    set_error("tc_products (0, 3, 6), n (1..8192) or batch (1..65535) out of range");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  int sms = 0;
+  IDOS_TRY(check_device(sms));
+  const size_t nn = (size_t)n * n;
+  const size_t na = (size_t)batch * nn, ny = (size_t)batch * BW * n;
+  std::vector<float> hA(2 * na), hY(2 * ny), hZ(2 * ny);
+  for (size_t i = 0; i < 2 * na; ++i) hA[i] = (float)A[i];
+  for (size_t i = 0; i < 2 * ny; ++i) {
+    hY[i] = (float)Y[i];
+    hZ[i] = (float)Z[i];
+  }
+  DevBuf dA, dY, dZ, dErr, dOp;
+  IDOS_CUDA_TRY(cudaMalloc(&dA.p, sizeof(float) * 2 * na));
+  IDOS_CUDA_TRY(cudaMalloc(&dY.p, sizeof(float) * 2 * ny));
+  IDOS_CUDA_TRY(cudaMalloc(&dZ.p, sizeof(float) * 2 * ny));
+  IDOS_CUDA_TRY(cudaMalloc(&dErr.p, sizeof(int)));
+  IDOS_CUDA_TRY(cudaMemcpy(dA.p, hA.data(), sizeof(float) * 2 * na, cudaMemcpyHostToDevice));
+  IDOS_CUDA_TRY(cudaMemcpy(dY.p, hY.data(), sizeof(float) * 2 * ny, cudaMemcpyHostToDevice));
+  IDOS_CUDA_TRY(cudaMemcpy(dZ.p, hZ.data(), sizeof(float) * 2 * ny, cudaMemcpyHostToDevice));
+  IDOS_CUDA_TRY(cudaMemset(dErr.p, 0, sizeof(int)));
+  const Batch bt{n, (int)batch, 1, 0, nullptr};
+  auto* cA = reinterpret_cast<c2<float>*>(dA.p);
+  auto* cY = reinterpret_cast<c2<float>*>(dY.p);
+  auto* cZ = reinterpret_cast<c2<float>*>(dZ.p);
+  if (tc_products) {
+    const size_t a_bytes = ((size_t)batch * n * tc_products * 4 * BW * 2 + 255) & ~size_t(255);
+    IDOS_CUDA_TRY(cudaMalloc(&dOp.p, a_bytes * 3));
+    TcPlan p;
+    IDOS_TRY(tc_plan(p, n, batch, tc_products, dOp.p, static_cast<char*>(dOp.p) + a_bytes, dA.p));
+    IDOS_TRY(tc_her2k(p, bt, -BW, cY, cZ, static_cast<int*>(dErr.p), 0));
+  } else {
+    const int gt = (n + Tiles<float>::GT - 1) / Tiles<float>::GT;
+    k_ts_her2k<float><<<dim3(gt, gt, (unsigned)batch), 256>>>(bt, -BW, cA, cY, cZ);
+    IDOS_CHECK_LAUNCH();
+  }
+  IDOS_CUDA_TRY(cudaDeviceSynchronize());
+  int herr = 0;
+  IDOS_CUDA_TRY(cudaMemcpy(&herr, dErr.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) {
+    set_error("tensor-core trailing update: a bounded wait timed out");
+    return IDOS_ERR_TIMEOUT;
+  }
+  IDOS_CUDA_TRY(cudaMemcpy(hA.data(), dA.p, sizeof(float) * 2 * na, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < 2 * na; ++i) A_out[i] = (double)hA[i];
+  return IDOS_OK;
+}

@@ -2,6 +2,8 @@
 // reduction (k_large.cu: dense -> band; k_chase.cu: band -> tridiagonal).
 #pragma once
 
+#include <cuda.h>
+
 #include "internal.h"
 
 namespace idos {
@@ -59,6 +61,30 @@ int chase_plan(int n_max, int64_t batch, int sms, ChasePlan& p);
 // err: device status word, set when a dataflow wait gives up.
 template <typename T>
 int chase_run(const ChasePlan& p, const Batch& bt, const c2<T>* A, c2<T>* Bd, T* d, T* e2, int* err, cudaStream_t s);
+
+// Tensor-core trailing update (k_tc.cu), float32 storage: per batch, the
+// split-bfloat16 operand buffers (Aop [B][n_max][64 np], Bop [B][2 n_max][64 np])
+// and their TMA descriptors.
+struct TcPlan {
+  CUtensorMap mapA, mapB, mapC;
+  int np = 6;
+  int n_max = 0;
+  void* Aop = nullptr;
+  void* Bop = nullptr;
+};
+
+// Device bytes of the operand buffers per matrix of capacity n_max.
+size_t tc_operand_bytes(int n_max, int np);
+
+// Encodes the TMA descriptors of the operand buffers and of the dense batch A
+// ([batch][n_max][n_max] complex float32, n_max even) for `batch` matrices and
+// sets the kernel's shared-memory attribute.  np = 3 or 6 split products.
+int tc_plan(TcPlan& p, int n_max, int64_t batch, int np, void* Aop, void* Bop, void* A);
+
+// A22 -= Y Z^H + Z Y^H for every matrix of the batch at panel offset k (the
+// trailing block starts at row and column k + BW; k = -BW updates the whole
+// matrix).  Y, Z: [B][BW][n_max] complex float32; A is the plan's batch.
+int tc_her2k(const TcPlan& p, const Batch& bt, int k, const c2<float>* Y, const c2<float>* Z, int* err, cudaStream_t s);
 
 }  // namespace lg
 }  // namespace idos

@@ -1,0 +1,90 @@
+"""The trailing update of the two-stage reduction (A22 -= Y Z^H + Z Y^H) on the
+tensor cores (split-bfloat16 products, float32 accumulation) and on the FP32
+pipe, through the C ABI, against the same update in float64 on the host; and
+the whole eigen-solve with either update against LAPACK."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(batch, n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((batch, n, n)) + 1j * rng.standard_normal((batch, n, n))
+    A = (A + np.conj(np.swapaxes(A, 1, 2))) / 2
+    Y = rng.standard_normal((batch, 16, n)) + 1j * rng.standard_normal((batch, 16, n))
+    Z = 0.3 * (rng.standard_normal((batch, 16, n)) + 1j * rng.standard_normal((batch, 16, n)))
+    return A, Y, Z
+
+
+def _reference(A, Y, Z):
+    # columns of Y and Z are the 16 panel vectors: U V^H with U = Y^T (n x 16)
+    Yt = np.swapaxes(Y, 1, 2)
+    Zt = np.swapaxes(Z, 1, 2)
+    return A - Yt @ np.conj(np.swapaxes(Zt, 1, 2)) - Zt @ np.conj(np.swapaxes(Yt, 1, 2))
+
+
+# float32 rounding of the inputs alone moves the result by ~2^-24 of the
+# largest term; the products add their own error (measured on GB300 at n = 256:
+# 3e-8, 1.5e-7 and 7e-7 of the largest term for tc = 0, 6 and 3).
+TOL = {0: 2e-6, 6: 2e-6, 3: 1e-4}
+
+
+@pytest.mark.parametrize("tc", [0, 6, 3])
+@pytest.mark.parametrize("n,batch", [(38, 1), (300, 2), (514, 1)])
+def test_her2k_matches_float64(tc, n, batch):
+    import paper_1611_09784_gb300 as pkg
+    A, Y, Z = _inputs(batch, n, 7 + n)
+    got = pkg.her2k(A, Y, Z, tc_products=tc)
+    ref = _reference(A, Y, Z)
+    scale = np.max(np.abs(A)) + 32 * np.max(np.abs(Y)) * np.max(np.abs(Z))
+    err = np.max(np.abs(got - ref)) / scale
+    assert err < TOL[tc], f"tc={tc} n={n}: relative error {err:.3e}"
+
+
+def test_her2k_six_products_are_float32_class():
+    # Six split products drop only terms below ~3 * 2^-24 relative; what
+    # remains is the tensor cores' own float32 accumulation (a few ulp of the
+    # partial sums), within an order of magnitude of the FP32 pipe's error and
+    # below the three-product form, which adds the bfloat16 rounding of the
+    # low part.
+    import paper_1611_09784_gb300 as pkg
+    A, Y, Z = _inputs(2, 256, 3)
+    ref = _reference(A, Y, Z)
+    e6 = np.max(np.abs(pkg.her2k(A, Y, Z, tc_products=6) - ref))
+    e3 = np.max(np.abs(pkg.her2k(A, Y, Z, tc_products=3) - ref))
+    e0 = np.max(np.abs(pkg.her2k(A, Y, Z, tc_products=0) - ref))
+    assert e6 <= 10 * e0 + 1e-12, (e6, e0)
+    assert 2 * e6 <= e3, (e6, e3)
+
+
+def test_her2k_leaves_rows_and_columns_of_zero_operands_unchanged():
+    import paper_1611_09784_gb300 as pkg
+    A, Y, Z = _inputs(1, 200, 11)
+    Y[:, :, 150:] = 0
+    Z[:, :, 150:] = 0
+    got = pkg.her2k(A, Y, Z, tc_products=6)
+    assert np.array_equal(got[:, 150:, 150:], A[:, 150:, 150:].astype(np.complex64).astype(np.complex128))
+
+
+@pytest.mark.parametrize("tc", [0, 6, 3])
+@pytest.mark.parametrize("n", [162, 600])
+def test_eigvalsh_with_either_trailing_update(tc, n):
+    import paper_1611_09784_gb300 as pkg
+    rng = np.random.default_rng(n)
+    H = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H = (H + H.conj().T) / 2
+    got = pkg.eigvalsh(H, precision="fp32", refine64_iters=1, tc_products=tc)[0]
+    ref = np.linalg.eigvalsh(H)
+    norm = np.max(np.abs(ref))
+    tol = (2e-5 if tc != 3 else 5e-4) * norm
+    assert np.max(np.abs(np.sort(got) - ref)) < tol
+
+
+def test_her2k_tensor_cores_need_even_dimension():
+    import paper_1611_09784_gb300 as pkg
+    A, Y, Z = _inputs(1, 37, 1)
+    with pytest.raises(pkg.IdosError):
+        pkg.her2k(A, Y, Z, tc_products=6)
+    got = pkg.her2k(A, Y, Z, tc_products=0)   # the FP32 pipe takes any dimension
+    assert np.max(np.abs(got - _reference(A, Y, Z))) < 1e-4
