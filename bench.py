@@ -313,7 +313,8 @@ def run_gpu(args):
         M = [Ml if l in keep else 0 for l, Ml in enumerate(M)]
     stream = torch.cuda.Stream(device=dev)
     cfg = dict(w["model"], p=w["p"], levels=levels, e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
-               delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64)
+               delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64,
+               sm_split=args.sm_split)
     model = pkg.create_model(cfg, stream=stream.cuda_stream)
     seed = w["seed"] + 1000 * rank
     eig_step = sum(Ml * eigsolves_per_sample(levels, l) for l, Ml in enumerate(M))
@@ -510,6 +511,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--levels", default=None,
                     help="comma list of level indices to run (profiling a part of the workload)")
+    ap.add_argument("--sm-split", type=int, default=-1,
+                    help="SMs reserved for the finest level (0: shared SMs, -1: library default)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the timed steps: no e2e / plain-MC / CPU-baseline measurements")
     args = ap.parse_args()

@@ -93,7 +93,11 @@ typedef struct idos_model_desc {
                           of the two-stage reduction on the FP32 pipe (0) or on
                           the tensor cores with 3 or 6 split-bfloat16 products
                           (6: float32-class sums, 3: ~5x their error)        */
-  int32_t reserved0;   /* must be 0                                         */
+  int32_t sm_split;    /* idos_sample_levels: SMs reserved (green context)
+                          for the finest level, the other levels share the
+                          rest; 0 = all levels share all SMs, -1 = library
+                          default.  Rounded up to the device's partition
+                          granularity (8 SMs on sm_103).                     */
 } idos_model_desc;
 
 typedef struct idos_model idos_model;
@@ -105,6 +109,12 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
 
 /* Free every device buffer of the model (synchronises its stream). NULL ok. */
 void idos_destroy_model(idos_model* m);
+
+/* The SM partition idos_sample_levels uses: *sms_finest SMs for the finest
+ * level and *sms_rest for the others, or 0 and 0 when all levels share all
+ * SMs (sm_split = 0, one level, or no green-context support in the driver;
+ * *why then holds the reason, a static string, "" when none). */
+int idos_get_partition(const idos_model* m, int* sms_finest, int* sms_rest, const char** why);
 
 /* Static text for a status code. */
 const char* idos_status_string(int status);

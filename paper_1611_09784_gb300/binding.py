@@ -31,7 +31,7 @@ class ModelDesc(C.Structure):
         ("t", C.c_double), ("eps_onsite", C.c_double), ("a", C.c_double), ("p", C.c_double),
         ("sentinel", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double), ("delta", C.c_double),
         ("n_E", C.c_int32), ("refine64_iters", C.c_int32), ("model_seed", C.c_uint64),
-        ("workspace_bytes", C.c_int64), ("tc_products", C.c_int32), ("reserved0", C.c_int32),
+        ("workspace_bytes", C.c_int64), ("tc_products", C.c_int32), ("sm_split", C.c_int32),
     ]
 
 
@@ -75,6 +75,7 @@ _SYMBOLS = {
     "idos_hamiltonian": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_her2k": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_get_partition": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_char_p)]),
     "idos_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "idos_profile_count": (C.c_int, []),
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -145,6 +146,7 @@ def make_desc(cfg: dict) -> ModelDesc:
     d.model_seed = int(cfg.get("model_seed", 0))
     d.workspace_bytes = int(cfg.get("workspace_bytes", 0))
     d.tc_products = int(cfg.get("tc_products", DEFAULT_TC_PRODUCTS))
+    d.sm_split = int(cfg.get("sm_split", -1))
     return d
 
 
@@ -200,6 +202,12 @@ class Model:
                                                        _ptr(Y), _ptr(Qf), _ptr(Qc)),
                "idos_sample_level_detail")
         return Y, Qf, Qc
+
+    def get_partition(self):
+        """(SMs of the finest level, SMs of the others, reason when unsplit)."""
+        a, b, why = C.c_int(0), C.c_int(0), C.c_char_p()
+        _check(load_library().idos_get_partition(self._h, C.byref(a), C.byref(b), C.byref(why)), "idos_get_partition")
+        return a.value, b.value, (why.value or b"").decode()
 
     def get_level_stats(self, level: int):
         s1 = np.empty(self.n_E)

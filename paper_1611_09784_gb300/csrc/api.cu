@@ -62,6 +62,7 @@ namespace {
 
 constexpr size_t kDefaultWorkspace = size_t(3) << 30;   // 3 GiB
 constexpr size_t kSmallBudget = size_t(768) << 20;      // per-chunk small buffers
+constexpr int kDefaultSmSplit = 48;                      // SMs reserved for the finest level
 
 
 int validate(const idos_model_desc* d) {
@@ -87,6 +88,7 @@ int validate(const idos_model_desc* d) {
   if (!(d->a > 0.0)) return bad("lattice constant must be positive");
   if (d->tc_products != 0 && d->tc_products != 3 && d->tc_products != 6)
     return bad("tc_products must be 0, 3 or 6");
+  if (d->sm_split < -1 || d->sm_split > 4096) return bad("sm_split must be -1, 0 or a positive SM count");
   return IDOS_OK;
 }
 
@@ -99,7 +101,7 @@ EnergyGrid grid_of(const idos_model_desc& d) {
 // Eigen-solve + IDoS of every cell of `cells` on a Kside grid: Q[count][n_E].
 // `eigs_keep` (optional) receives the device eigenvalue buffer pointer.
 int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double** eigs_keep, cudaStream_t st,
-                   Arena& ws, int* err) {
+                   Arena& ws, int* err, int sm_avail = 0) {
   const int n_max = cells.n_sites;
   const int K2 = Kside * Kside;
   const int64_t n_mat = cells.count * (int64_t)K2;
@@ -124,6 +126,8 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.ws = &ws;
   a.err = err;
   a.tc_np = M->d.tc_products;
+  a.sm_avail = sm_avail;
+  a.max_cluster = sm_avail ? 8 : 16;
   if (small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
   IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
@@ -180,7 +184,8 @@ int check_status_word(const int* err) {
 // the level to finish and add its time and count to the accumulators;
 // otherwise the caller does that after synchronising ev1.
 int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh, double* Qfh,
-              double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, bool blocking) {
+              double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, bool blocking,
+              int sm_avail = 0) {
   const idos_model_desc& d = M->d;
   const int Nf = d.N[level], Kf = d.Kside[level];
   const bool coarse = level > 0;
@@ -219,10 +224,10 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     // bigger solve goes last
     const size_t mark = ws.used;
     if (coarse) {
-      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st, ws, err));
+      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st, ws, err, sm_avail));
       ws.used = mark;
     }
-    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err));
+    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err, sm_avail));
     ws.used = mark;
     double* acc = M->acc + (size_t)level * 2 * n_E;
     IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, ws, st));
@@ -319,10 +324,30 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
   // whenever the many-matrix levels release an SM.
   int prio_least = 0, prio_greatest = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  // SM partition: the finest level on a reserved set of SMs, the others on
+  // the rest (a failure to create it leaves every level on all SMs)
+  const int split = d->sm_split == -1 ? kDefaultSmSplit : d->sm_split;
+  bool parted = false;
+  if (e == cudaSuccess && split > 0 && d->n_levels >= 2 && split < sms) {
+    parted = partition_create(split, m->part) == IDOS_OK;
+    if (!parted) {
+      m->part_note = get_error();
+      set_error("");
+    }
+  }
   for (int l = 0; l < d->n_levels && e == cudaSuccess; ++l) {
     int prio = prio_greatest + (d->n_levels - 1 - l);   // greatest priority is the lowest number
     if (prio > prio_least) prio = prio_least;
-    e = cudaStreamCreateWithPriority(&m->lstream[l], cudaStreamNonBlocking, prio);
+    if (parted) {
+      const int which = l == d->n_levels - 1 ? 0 : 1;
+      if (partition_stream(m->part, which, prio, &m->lstream[l]) != IDOS_OK) {
+        e = cudaErrorUnknown;
+        break;
+      }
+      m->lsms[l] = m->part.sms[which];
+    } else {
+      e = cudaStreamCreateWithPriority(&m->lstream[l], cudaStreamNonBlocking, prio);
+    }
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev0[l]);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev1[l]);
   }
@@ -353,6 +378,7 @@ void idos_destroy_model(idos_model* m) {
     if (m->lev1[l]) cudaEventDestroy(m->lev1[l]);
     m->lws[l].release();
   }
+  partition_destroy(m->part);   // after its streams
   m->ws.release();
   delete m;
 }
@@ -393,7 +419,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     const int l = order[q];
     if (n_samples[l] == 0) continue;
     IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr, nullptr,
-                       m->lstream[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false));
+                       m->lstream[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false, m->lsms[l]));
   }
   for (int l = 0; l < L; ++l) {
     if (n_samples[l] == 0) continue;
@@ -674,3 +700,12 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
 }
 
 }  // extern "C"
+
+int idos_get_partition(const idos_model* m, int* sms_finest, int* sms_rest, const char** why) {
+  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  const bool on = m->part.ctx[0] != nullptr;
+  if (sms_finest) *sms_finest = on ? m->part.sms[0] : 0;
+  if (sms_rest) *sms_rest = on ? m->part.sms[1] : 0;
+  if (why) *why = m->part_note.c_str();
+  return IDOS_OK;
+}

@@ -70,7 +70,23 @@ struct SolveArgs {
   // float32 large path: 0 = trailing update on the FP32 pipe, 3 or 6 =
   // tensor cores with that many split-bfloat16 products
   int tc_np = 0;
+  // SMs the launches of this call run on (0 = the whole device; launch
+  // shapes do not depend on it) and the largest thread-block cluster they may
+  // form (SM partitions guarantee 8; the band chase computes the same values
+  // for every cluster size, the panel QR never exceeds 8)
+  int sm_avail = 0;
+  int max_cluster = 16;
 };
+
+// Two green contexts splitting the device's SMs (partition.cu): ctx[0] has
+// sms[0] SMs (reserved for one stream's work), ctx[1] the rest.
+struct SmPartition {
+  void* ctx[2] = {nullptr, nullptr};
+  int sms[2] = {0, 0};
+};
+int partition_create(int big_sms, SmPartition& p);
+int partition_stream(const SmPartition& p, int which, int priority, cudaStream_t* out);
+void partition_destroy(SmPartition& p);
 
 struct Model {
   idos_model_desc d{};
@@ -80,6 +96,9 @@ struct Model {
   Arena lws[IDOS_MAX_LEVELS];
   cudaEvent_t lev0[IDOS_MAX_LEVELS] = {}, lev1[IDOS_MAX_LEVELS] = {};
   cudaEvent_t fork = nullptr;
+  SmPartition part;               // SM split of idos_sample_levels (ctx null: shared SMs)
+  std::string part_note;          // why there is no split (empty when there is one or none was asked)
+  int lsms[IDOS_MAX_LEVELS] = {};  // SMs of each level stream's partition (0: whole device)
   double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream
   int64_t M[IDOS_MAX_LEVELS] = {};

@@ -610,7 +610,7 @@ k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
 }
 
 template <typename T>
-int chase_plan_t(int nm, int64_t batch, int sms, ChasePlan& p) {
+int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p) {
   using C = c2<T>;
   p = ChasePlan{};
   // barrier kernel: one warp per concurrently active sweep (at most n/(2 BW) + 2)
@@ -638,7 +638,7 @@ int chase_plan_t(int nm, int64_t batch, int sms, ChasePlan& p) {
     return need <= 200 * 1024;
   };
   auto covered = [&](int w, int cwl) { return w >= std::min(active, (1 << cwl) / (2 * BW) + 2); };
-  for (int q = 1; q <= 16; q *= 2) {
+  for (int q = 1; q <= std::min(16, max_cluster); q *= 2) {
     int w, cwl;
     size_t need;
     if (!cfg(q, w, cwl, need)) continue;
@@ -692,15 +692,15 @@ int chase_run_t(const ChasePlan& p, const Batch& bt, const c2<T>* A, c2<T>* Bd, 
 }  // namespace
 
 template <typename T>
-int chase_plan(int n_max, int64_t batch, int sms, ChasePlan& p) {
-  return chase_plan_t<T>(n_max, batch, sms, p);
+int chase_plan(int n_max, int64_t batch, int sms, int max_cluster, ChasePlan& p) {
+  return chase_plan_t<T>(n_max, batch, sms, max_cluster, p);
 }
 template <typename T>
 int chase_run(const ChasePlan& p, const Batch& bt, const c2<T>* A, c2<T>* Bd, T* d, T* e2, int* err, cudaStream_t s) {
   return chase_run_t<T>(p, bt, A, Bd, d, e2, err, s);
 }
-template int chase_plan<float>(int, int64_t, int, ChasePlan&);
-template int chase_plan<double>(int, int64_t, int, ChasePlan&);
+template int chase_plan<float>(int, int64_t, int, int, ChasePlan&);
+template int chase_plan<double>(int, int64_t, int, int, ChasePlan&);
 template int chase_run<float>(const ChasePlan&, const Batch&, const c2<float>*, c2<float>*, float*, float*, int*,
                               cudaStream_t);
 template int chase_run<double>(const ChasePlan&, const Batch&, const c2<double>*, c2<double>*, double*, double*, int*,

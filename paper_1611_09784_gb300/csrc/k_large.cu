@@ -661,11 +661,13 @@ int solve_large_t(const SolveArgs& a) {
   int dev = 0, sms = 0;
   IDOS_CUDA_TRY(cudaGetDevice(&dev));
   IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // (launch shapes follow the device's SM count even inside an SM partition,
+  // so that results do not depend on how the SMs are shared)
   // cluster panel QR: the smallest cluster (<= 8 CTAs) whose shared memory
   // holds the first panel, grown while the batch leaves SMs idle and each CTA
   // keeps at least 64 rows; pc = 0 keeps the one-CTA kernel above
   int pc = 0, pc_rows = 0;
-  for (int q = 1; q <= 8; q *= 2) {
+  for (int q = 1; q <= std::min(8, a.max_cluster); q *= 2) {
     const int rows = (nm - BW + q - 1) / q;
     const size_t smem = 2 * sizeof(C) * (size_t)rows * BW;
     if (smem > 200 * 1024) continue;
@@ -683,7 +685,7 @@ int solve_large_t(const SolveArgs& a) {
     IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel_cl<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
   }
   ChasePlan cp;
-  IDOS_TRY(chase_plan<T>(nm, batch, sms, cp));
+  IDOS_TRY(chase_plan<T>(nm, batch, sms, a.max_cluster, cp));
   const bool own_err = a.err == nullptr;
   int* d_err = own_err ? a.ws->take<int>(1) : a.err;
   if (!d_err) {

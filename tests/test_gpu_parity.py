@@ -187,3 +187,26 @@ def test_sample_levels_matches_per_level_calls(model):
         assert M == ref[l][0]
         assert np.array_equal(s1, ref[l][1]) and np.array_equal(s2, ref[l][2])
         assert secs > 0
+
+
+def test_sm_partition_is_default_and_does_not_change_results():
+    """idos_sample_levels on an SM partition (finest level on its own green
+    context) gives bit-identical level statistics to shared SMs."""
+    import paper_1611_09784_gb300 as pkg
+    w, cfg, prm = cfg_and_prm(precision="fp32")
+    counts = [6, 3, 2, 1]
+    firsts = [7, 8, 9, 10]
+    stats = {}
+    for split in (0, -1):
+        m = pkg.create_model(dict(cfg, sm_split=split))
+        fin, rest, why = m.get_partition()
+        if split == 0:
+            assert (fin, rest) == (0, 0)
+        else:
+            assert fin >= 8 and rest >= 8 and fin + rest <= 152, (fin, rest, why)
+        m.sample_levels(counts, w["seed"], firsts)
+        stats[split] = [m.get_level_stats(l)[:3] for l in range(4)]
+        m.close()
+    for a, b in zip(stats[0], stats[-1]):
+        assert a[0] == b[0]
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
