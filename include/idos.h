@@ -95,9 +95,12 @@ typedef struct idos_model_desc {
                           (6: float32-class sums, 3: ~5x their error)        */
   int32_t sm_split;    /* idos_sample_levels: SMs reserved (green context)
                           for the finest level, the other levels share the
-                          rest; 0 = all levels share all SMs, -1 = library
-                          default.  Rounded up to the device's partition
-                          granularity (8 SMs on sm_103).                     */
+                          rest, in calls where the other levels' work (flop
+                          model, sum of n^3) is at least half the finest
+                          level's; 0 = all levels always share all SMs,
+                          -1 = library default (48).  Rounded up to the
+                          device's partition granularity (8 SMs on sm_103).
+                          Results do not depend on it.                       */
 } idos_model_desc;
 
 typedef struct idos_model idos_model;

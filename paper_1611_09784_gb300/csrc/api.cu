@@ -340,14 +340,13 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
     if (prio > prio_least) prio = prio_least;
     if (parted) {
       const int which = l == d->n_levels - 1 ? 0 : 1;
-      if (partition_stream(m->part, which, prio, &m->lstream[l]) != IDOS_OK) {
+      if (partition_stream(m->part, which, prio, &m->pstream[l]) != IDOS_OK) {
         e = cudaErrorUnknown;
         break;
       }
       m->lsms[l] = m->part.sms[which];
-    } else {
-      e = cudaStreamCreateWithPriority(&m->lstream[l], cudaStreamNonBlocking, prio);
     }
+    e = cudaStreamCreateWithPriority(&m->lstream[l], cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev0[l]);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev1[l]);
   }
@@ -373,6 +372,10 @@ void idos_destroy_model(idos_model* m) {
     if (m->lstream[l]) {
       cudaStreamSynchronize(m->lstream[l]);
       cudaStreamDestroy(m->lstream[l]);
+    }
+    if (m->pstream[l]) {
+      cudaStreamSynchronize(m->pstream[l]);
+      cudaStreamDestroy(m->pstream[l]);
     }
     if (m->lev0[l]) cudaEventDestroy(m->lev0[l]);
     if (m->lev1[l]) cudaEventDestroy(m->lev1[l]);
@@ -409,9 +412,17 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     }
   }
   ProfGuard pg(m);
+  // The SM partition pays when the other levels have enough work to fill
+  // their part while the finest level runs its latency-bound chains on its
+  // own (flop model: at least half the finest level's work); otherwise every
+  // level shares all SMs.
+  double w_fin = 0.0, w_rest = 0.0;
+  for (int l = 0; l < L; ++l) (l == L - 1 ? w_fin : w_rest) += (double)n_samples[l] * flop_model(m->d, l);
+  const bool parted = m->pstream[L - 1] != nullptr && w_fin > 0.0 && w_rest >= 0.5 * w_fin;
+  cudaStream_t* streams = parted ? m->pstream : m->lstream;
   // every level stream starts after the work already queued on the model's stream
   IDOS_CUDA_TRY(cudaEventRecord(m->fork, m->stream));
-  for (int l = 0; l < L; ++l) IDOS_CUDA_TRY(cudaStreamWaitEvent(m->lstream[l], m->fork, 0));
+  for (int l = 0; l < L; ++l) IDOS_CUDA_TRY(cudaStreamWaitEvent(streams[l], m->fork, 0));
   // costliest level first, so its long latency-bound phases overlap the rest
   int order[IDOS_MAX_LEVELS];
   for (int l = 0; l < L; ++l) order[l] = L - 1 - l;
@@ -419,7 +430,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     const int l = order[q];
     if (n_samples[l] == 0) continue;
     IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr, nullptr,
-                       m->lstream[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false, m->lsms[l]));
+                       streams[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false, parted ? m->lsms[l] : 0));
   }
   for (int l = 0; l < L; ++l) {
     if (n_samples[l] == 0) continue;

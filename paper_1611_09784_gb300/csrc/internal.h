@@ -83,6 +83,7 @@ struct SolveArgs {
 struct SmPartition {
   void* ctx[2] = {nullptr, nullptr};
   int sms[2] = {0, 0};
+  bool shared = false;   // owned by the process-wide cache (never destroyed by a model)
 };
 int partition_create(int big_sms, SmPartition& p);
 int partition_stream(const SmPartition& p, int which, int priority, cudaStream_t* out);
@@ -92,7 +93,8 @@ struct Model {
   idos_model_desc d{};
   cudaStream_t stream = 0;
   // one stream, workspace and event pair per level for idos_sample_levels
-  cudaStream_t lstream[IDOS_MAX_LEVELS] = {};
+  cudaStream_t lstream[IDOS_MAX_LEVELS] = {};   // shared SMs, priorities by cost
+  cudaStream_t pstream[IDOS_MAX_LEVELS] = {};   // the same on the SM partition (null without one)
   Arena lws[IDOS_MAX_LEVELS];
   cudaEvent_t lev0[IDOS_MAX_LEVELS] = {}, lev1[IDOS_MAX_LEVELS] = {};
   cudaEvent_t fork = nullptr;

@@ -61,7 +61,7 @@ int fail(const char* what, CUresult r) {
 
 }  // namespace
 
-int partition_create(int big_sms, SmPartition& p) {
+int partition_create_new(int big_sms, SmPartition& p) {
   p = SmPartition{};
   const GreenApi& g = api();
   if (!g.ok) {
@@ -108,6 +108,34 @@ int partition_create(int big_sms, SmPartition& p) {
   return IDOS_OK;
 }
 
+// One partition per (device, reserved SM count), created on first use and
+// kept for the life of the process: kernels are loaded into a context on
+// their first launch there, so models created later reuse warm contexts.
+int partition_create(int big_sms, SmPartition& p) {
+  struct Entry {
+    int dev, sms;
+    SmPartition part;
+  };
+  static std::mutex mu;
+  static Entry cache[64];
+  static int n_cached = 0;
+  int dev = 0;
+  IDOS_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < n_cached; ++i) {
+    if (cache[i].dev == dev && cache[i].sms == big_sms) {
+      p = cache[i].part;
+      return IDOS_OK;
+    }
+  }
+  IDOS_TRY(partition_create_new(big_sms, p));
+  if (n_cached < 64) {
+    p.shared = true;   // the cache keeps it; a full cache leaves it to the model
+    cache[n_cached++] = Entry{dev, big_sms, p};
+  }
+  return IDOS_OK;
+}
+
 int partition_stream(const SmPartition& p, int which, int priority, cudaStream_t* out) {
   CUstream s = nullptr;
   const CUresult r =
@@ -119,7 +147,7 @@ int partition_stream(const SmPartition& p, int which, int priority, cudaStream_t
 
 void partition_destroy(SmPartition& p) {
   for (int i = 0; i < 2; ++i) {
-    if (p.ctx[i]) api().ctx_destroy(reinterpret_cast<CUgreenCtx>(p.ctx[i]));
+    if (p.ctx[i] && !p.shared) api().ctx_destroy(reinterpret_cast<CUgreenCtx>(p.ctx[i]));
     p.ctx[i] = nullptr;
   }
 }
