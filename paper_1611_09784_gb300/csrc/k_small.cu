@@ -176,6 +176,189 @@ k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
   }
 }
 
+// Row-group variant for 32 < n <= NC: thread t works on column c = t / RG
+// and on the rows r = j + 1 + (t % RG) (mod RG) of the trailing block, so NC
+// columns keep NC * RG threads busy and every step's column loops are RG times
+// shorter; the RG partial products of a column are added with shuffles (the
+// RG threads of a column are consecutive lanes).  Rows are LD complex entries
+// apart (LD = 8 mod 16), which spreads the RG rows a warp touches at once over
+// different shared-memory banks.
+template <typename T>
+struct RgLayout {
+  // row stride: n_max rounded up to 16, plus 8 (rows 16 banks apart)
+  __host__ __device__ static int ld(int n_max) { return ((n_max + 15) & ~15) + 8; }
+  __host__ __device__ static size_t bytes(int n_max, int nc) {
+    const size_t b = sizeof(c2<T>) * ((size_t)n_max * ld(n_max) + 4 * (size_t)nc + 3) + sizeof(T) * 64;
+    return (b + 15) & ~size_t(15);
+  }
+};
+
+template <typename T, int NC, int RG>
+__global__ void __launch_bounds__(NC* RG)
+k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv,
+                   int N, int K, int n_max, int64_t n_mat, double t_hop, double eps, const double2* __restrict__ Hin,
+                   T* __restrict__ d_out, T* __restrict__ e2_out) {
+  using C = c2<T>;
+  constexpr int NT = NC * RG;
+  const int LD = RgLayout<T>::ld(n_max);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int64_t mat = blockIdx.x;
+  if (mat >= n_mat) return;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* vb0 = A + (size_t)n_max * LD;
+  C* vb1 = vb0 + NC;
+  C* wb0 = vb1 + NC;
+  C* wb1 = wb0 + NC;
+  C* ph = wb1 + NC;
+  T* scratch = reinterpret_cast<T*>(ph + 3);
+
+  const int K2 = K * K;
+  const int64_t cell = mat / K2;
+  const int kidx = (int)(mat - cell * K2);
+  const int n = Hin ? n_max : n_act_cell[cell];
+  T* dO = d_out + mat * n_max;
+  T* eO = e2_out + mat * n_max;
+  if (n <= 0) return;
+
+  // ---------------------------------------------------------- assembly ---
+  if (Hin) {
+    const double2* src = Hin + mat * (int64_t)n * n;
+    for (int i = tid; i < n * n; i += NT) A[(i / n) * LD + i % n] = mk<T>((T)src[i].x, (T)src[i].y);
+  } else {
+    const int n_sites = 2 * N * N;
+    if (tid < 3) {
+      if constexpr (sizeof(T) == 4) {
+        const float2 p = graphene_phase_f(N, K, kidx, tid);
+        ph[tid] = mk<T>((T)t_hop * p.x, (T)t_hop * p.y);
+      } else {
+        const double2 p = graphene_phase(N, K, kidx, tid);
+        ph[tid] = mk<T>((T)(t_hop * p.x), (T)(t_hop * p.y));
+      }
+    }
+    for (int i = tid; i < n * LD; i += NT) A[i] = mk<T>(T(0), T(0));
+    __syncthreads();
+    const int* actc = act + cell * n_sites;
+    const int* invc = inv + cell * n_sites;
+    for (int a = tid; a < n; a += NT) {
+      int nb[3];
+      bool fromB;
+      graphene_neighbours(N, actc[a], nb, fromB);
+      C* row = A + (size_t)a * LD;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int col = invc[nb[b]];
+        if (col < 0) continue;
+        const C hp = fromB ? conjg<T>(ph[b]) : ph[b];
+        row[col] = cadd<T>(row[col], hp);
+      }
+      row[a].x += (T)eps;
+    }
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------ tridiagonalise ---
+  const int c_own = tid / RG, rg = tid % RG;
+  C* v = vb0; C* w = wb0;
+  C* nv = vb1; C* nw = wb1;
+  bool pend = false;
+  for (int j = 0; j < n - 1; ++j) {
+    // (a) row j of the trailing block, columns c >= j
+    if (pend) {
+      const C vj = v[j], wj = w[j];
+      for (int c = j + tid; c < n; c += NT) {
+        C a = A[(size_t)j * LD + c];
+        a = csub<T>(a, cmulc<T>(vj, w[c]));
+        a = csub<T>(a, cmulc<T>(wj, v[c]));
+        A[(size_t)j * LD + c] = a;
+      }
+    }
+    __syncthreads();
+    // (b) x_c = conj(A[j][c]), c > j
+    T rest = T(0);
+    for (int c = j + 2 + tid; c < n; c += NT) rest += cabs2<T>(A[(size_t)j * LD + c]);
+    rest = group_sum<NT, 1, T>(rest, scratch, 0);
+    const C alpha = conjg<T>(A[(size_t)j * LD + j + 1]);
+    const T aa2 = cabs2<T>(alpha);
+    const T sigma2 = aa2 + rest;
+    if (tid == 0) {
+      dO[j] = A[(size_t)j * LD + j].x;
+      eO[j] = sigma2;
+    }
+    const bool tr = rest > (sizeof(T) == 4 ? T(1e-30f) : T(1e-290));
+    T tau = T(0);
+    if (tr) {
+      const T sigma = sqrt(sigma2), aa = sqrt(aa2);
+      const C phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+      tau = T(1) / (sigma * (sigma + aa));
+      for (int c = j + 1 + tid; c < n; c += NT)
+        nv[c] = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * LD + c]);
+    }
+    __syncthreads();
+    // (c) fused pass over the trailing block: this thread's column, every
+    //     RG-th row; partial products of the column's RG threads added after
+    T kpart = T(0);
+    {
+      const int c = c_own;
+      const bool act_c = c > j && c < n;
+      C p = mk<T>(T(0), T(0));
+      if (act_c) {
+        const C wc = pend ? w[c] : mk<T>(T(0), T(0));
+        const C vc = pend ? v[c] : mk<T>(T(0), T(0));
+        for (int r = j + 1 + rg; r < n; r += RG) {
+          C a = A[(size_t)r * LD + c];
+          if (pend) {
+            a = csub<T>(a, cmulc<T>(v[r], wc));
+            a = csub<T>(a, cmulc<T>(w[r], vc));
+            A[(size_t)r * LD + c] = a;
+          }
+          if (tr) p = cadd<T>(p, cjmul<T>(a, nv[r]));
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < RG; o <<= 1) {
+        p.x += __shfl_xor_sync(0xffffffffu, p.x, o);
+        p.y += __shfl_xor_sync(0xffffffffu, p.y, o);
+      }
+      if (tr && act_c && rg == 0) {
+        p = cscale<T>(p, tau);
+        nw[c] = p;
+        kpart = nv[c].x * p.x + nv[c].y * p.y;
+      }
+    }
+    if (tr) {
+      const T Kc = T(0.5) * tau * group_sum<NT, 1, T>(kpart, scratch, 0);
+      for (int c = j + 1 + tid; c < n; c += NT) nw[c] = csub<T>(nw[c], cscale<T>(nv[c], Kc));
+    }
+    pend = tr;
+    C* tv = v; v = nv; nv = tv;
+    C* tw = w; w = nw; nw = tw;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    C a = A[(size_t)(n - 1) * LD + (n - 1)];
+    if (pend) {
+      a = csub<T>(a, cmulc<T>(v[n - 1], w[n - 1]));
+      a = csub<T>(a, cmulc<T>(w[n - 1], v[n - 1]));
+    }
+    dO[n - 1] = a.x;
+  }
+}
+
+template <typename T, int NC, int RG>
+int run_small_rg(const SolveArgs& a) {
+  const size_t smem = RgLayout<T>::bytes(a.n_max, NC);
+  auto kern = k_small_tridiag_rg<T, NC, RG>;
+  IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const CellSet* c = a.cells;
+  ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
+  kern<<<(unsigned)a.n_mat, NC * RG, smem, a.stream>>>(
+      c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside, a.n_max, a.n_mat,
+      a.t, a.eps, a.H, reinterpret_cast<T*>(a.d), reinterpret_cast<T*>(a.e2));
+  IDOS_CHECK_LAUNCH();
+  return IDOS_OK;
+}
+
 template <typename T, int NT, int MPB>
 int run_small(const SolveArgs& a) {
   const size_t smem = SmallLayout<T>::bytes(a.n_max) * MPB;
@@ -196,9 +379,14 @@ constexpr size_t kSmemLimit = 227 * 1024;
 }  // namespace
 
 bool small_path_fits(int precision, int n_max) {
-  const size_t b = precision == IDOS_FP64 ? SmallLayout<double>::bytes(n_max)
-                                          : SmallLayout<float>::bytes(n_max);
-  return n_max <= 256 && b <= kSmemLimit;
+  if (n_max <= 32) {
+    const size_t b = precision == IDOS_FP64 ? SmallLayout<double>::bytes(n_max) : SmallLayout<float>::bytes(n_max);
+    return b <= kSmemLimit;
+  }
+  if (n_max > 256) return false;
+  const int nc = n_max <= 64 ? 64 : n_max <= 128 ? 128 : 256;
+  const size_t b = precision == IDOS_FP64 ? RgLayout<double>::bytes(n_max, nc) : RgLayout<float>::bytes(n_max, nc);
+  return b <= kSmemLimit;
 }
 
 template <typename T>
@@ -208,9 +396,9 @@ static int solve_small_t(const SolveArgs& a) {
     if (SmallLayout<T>::bytes(a.n_max) * 4 <= kSmemLimit) return run_small<T, 32, 4>(a);
     return run_small<T, 32, 1>(a);
   }
-  if (a.n_max <= 64) return run_small<T, 64, 1>(a);
-  if (a.n_max <= 128) return run_small<T, 128, 1>(a);
-  return run_small<T, 256, 1>(a);
+  if (a.n_max <= 64) return run_small_rg<T, 64, 4>(a);
+  if (a.n_max <= 128) return run_small_rg<T, 128, 4>(a);
+  return run_small_rg<T, 256, 4>(a);
 }
 
 int solve_small(int precision, const SolveArgs& a) {
