@@ -7,4 +7,4 @@ contains none of the method's arithmetic: vacancy patterns and model
 parameters are drawn inside each implementation by the counter-based
 generator, from the seeds given here.
 """
-from .workloads import (BASE_SEED, GRAPHENE, WORKLOADS, workload, model_params)  # noqa: F401
+from .workloads import (BASE_SEED, GRAPHENE, TMDC, WORKLOADS, workload, model_params)  # noqa: F401
