@@ -176,3 +176,13 @@ def pair_mask(prm, N: int, level: int, sample: int, seed: int) -> np.ndarray:
     """u8[N^2]: the chalcogen pairs of sample `sample` on `level` that are removed
     (the vacancy generator with site index = cell index, Sec. 3.2)."""
     return philox.vacancy_mask(seed, level, sample, N * N, prm["p"])
+
+
+def corner_masks(mask, N: int):
+    """The four (N/2) x (N/2) corner pair masks of a fine pair mask (Sec. 3.3:
+    corner r = ri + 2 rj takes cells i in [ri N/2, (ri+1) N/2), j in
+    [rj N/2, (rj+1) N/2); local cell i' + (N/2) j')."""
+    h = N // 2
+    m = np.asarray(mask, dtype=np.uint8).reshape(N, N)   # [j][i]
+    return [m[rj * h:(rj + 1) * h, ri * h:(ri + 1) * h].reshape(-1).copy() for rj in range(2) for ri in range(2)]
+

@@ -115,3 +115,27 @@ def test_idos_saturates_at_active_orbitals():
     n_act = 11 * N * N - 6
     assert abs(Q[-1] - n_act / lattice.supercell_area(N, prm["a"])) < 1e-12
     assert abs(Q[0]) < 1e-12
+
+
+def test_corner_tiling_identity():
+    # a pristine N x N supercell on a K grid is the 2 x 2 tiling of its
+    # (N/2) x (N/2) corners on a 2K grid (for even K both Monkhorst-Pack grids
+    # fold onto the same primitive momenta): same spectrum multiset, same IDoS
+    prm = _prm(e_min=-12.0, e_max=12.0, n_E=25, delta=0.3)
+    N, K = 2, 2
+    fine = np.zeros(N * N, dtype=np.uint8)
+    corners = tmdc.corner_masks(fine, N)
+    assert len(corners) == 4 and all(c.shape == (1,) for c in corners)
+    qf = tmdc.sample_idos(N, K, fine, prm)
+    qc = tmdc.sample_idos(N // 2, 2 * K, corners[0], prm)
+    assert np.allclose(qf, qc, atol=1e-12)
+
+
+def test_corner_masks_partition_the_cells():
+    rng = np.random.default_rng(2)
+    N = 6
+    mask = (rng.random(N * N) < 0.5).astype(np.uint8)
+    c = tmdc.corner_masks(mask, N)
+    assert sum(int(x.sum()) for x in c) == int(mask.sum())
+    m = mask.reshape(N, N)
+    assert c[1][0] == m[0, 3] and c[2][0] == m[3, 0] and c[3][-1] == m[5, 5]
