@@ -50,6 +50,20 @@ enum idos_status {
   IDOS_ERR_NO_DEVICE = -7      /* no CUDA device of compute capability 10.3     */
 };
 
+/* Model kinds (Sec. 3.1).  Sizes below use V = vacancy sites and n = orbitals
+ * of an N x N supercell:
+ * IDOS_GRAPHENE: nearest-neighbour pz model, eq. (3.2a)-(3.2b): V = n = 2 N^2
+ *   (site m = 2(i + N j) + s, one orbital each; a vacancy removes the site).
+ * IDOS_TMDC: the TMDC-shaped 11-orbital model (the MoS2 example of Sec. 3.1
+ *   with the pair vacancies of Sec. 3.2): metal with 5 d orbitals on the A
+ *   site, chalcogen pair with 6 p orbitals on the B site; V = N^2 (site = the
+ *   pair of cell c = i + N j), n = 11 N^2 (orbital 11 c + q, q < 5 metal);
+ *   a vacancy removes the pair's 6 orbitals.  Real parameters drawn from
+ *   model_seed (Philox4x64-10, counter (i, 0, 0, 0), key (model_seed, 2),
+ *   value -2 + 4 (w0 >> 11) 2^-53 eV): 11 on-site energies, metal -> pair
+ *   blocks (5 x 6) for the bonds tau_B, tau_B - a1, tau_B - a2, second-neighbour
+ *   metal (5 x 5) and pair (6 x 6) blocks along a1, a2, a2 - a1 (transposed
+ *   for the reverse hop); t, eps_onsite are unused.  N <= 24. */
 enum idos_kind { IDOS_GRAPHENE = 0, IDOS_TMDC = 1 };
 
 /* Arithmetic of the per-k eigen-solve.
@@ -164,10 +178,11 @@ int idos_get_level_stats(const idos_model* m, int level, int64_t* M, double* sum
 int idos_reset_level_stats(idos_model* m, int level);
 
 /* IDoS Q(eps_j) of eq. (4.1)-(4.2) for ONE supercell configuration: side N,
- * Kside x Kside grid.  mask: host u8[2 N^2] (1 = site removed), or NULL to
- * draw it from (seed, level, sample) exactly as idos_sample_level does.
- * idos_out: host float64[n_E].  eigs_out: NULL or host float64[Kside^2 * 2N^2]:
- * per k the ascending eigenvalues of the active block, then NaN padding to 2N^2. */
+ * Kside x Kside grid.  mask: host u8[V] (1 = vacancy site removed; V as in
+ * idos_kind), or NULL to draw it from (seed, level, sample) exactly as
+ * idos_sample_level does.  idos_out: host float64[n_E].  eigs_out: NULL or
+ * host float64[Kside^2 * n]: per k the ascending eigenvalues of the active
+ * block, then NaN padding to n. */
 int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_t seed,
                    int level, int64_t sample, double* idos_out, double* eigs_out);
 
@@ -224,16 +239,17 @@ int idos_reset_profile(idos_model* m);
 /* ---- parity / diagnostic entry points (same kernels as the hot path) ---- */
 
 /* Vacancy masks of samples first_sample .. first_sample + n_samples - 1 of
- * `level` for an N x N cell: host u8[n_samples * 2 N^2] (1 = removed),
+ * `level` for an N x N cell: host u8[n_samples * V] (1 = removed),
  * computed on the device by the hot path's generator (Philox4x64-10, key
  * (seed, 1), counter (site, sample, level, 0), vacant iff word0 < p 2^64). */
 int idos_vacancy_masks(idos_model* m, int N, int level, uint64_t seed, int64_t first_sample,
                        int64_t n_samples, uint8_t* out);
 
-/* H(k) of eq. (3.2a)-(3.2b) for one configuration and one grid point, as the
- * assembly kernel builds it, written as a full 2N^2 x 2N^2 complex128 matrix
- * (row-major, interleaved re/im: host float64[2 * (2N^2)^2]) with removed
- * sites' rows and columns zero and m->sentinel on their diagonal. */
+/* H(k) of the model for one configuration (mask: host u8[V]) and one grid
+ * point, as the assembly kernel builds it, written as a full n x n complex128
+ * matrix (row-major, interleaved re/im: host float64[2 n^2]) with removed
+ * orbitals' rows and columns zero and m->sentinel on their diagonal.
+ * N <= 32 (graphene), <= 12 (TMDC-shaped). */
 int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t* mask,
                      double* out);
 

@@ -159,6 +159,10 @@ class Model:
         self.desc = make_desc(cfg)
         self.n_E = self.desc.n_E
         self.n_levels = self.desc.n_levels
+        self.kind = self.desc.kind
+        # orbitals and vacancy sites per unit cell (graphene: 2 and 2; TMDC-shaped: 11 and 1)
+        self.orb_per_cell = 11 if self.kind == TMDC else 2
+        self.vac_per_cell = 1 if self.kind == TMDC else 2
         h = C.c_void_p()
         _check(lib.idos_create_model(C.byref(self.desc), C.c_void_p(stream or 0), C.byref(h)),
                "idos_create_model")
@@ -224,7 +228,7 @@ class Model:
     def eval_idos(self, N: int, K: int, mask=None, seed: int = 0, level: int = 0, sample: int = 0,
                   want_eigs: bool = False):
         Q = np.empty(self.n_E)
-        E = np.empty((K * K, 2 * N * N)) if want_eigs else None
+        E = np.empty((K * K, self.orb_per_cell * N * N)) if want_eigs else None
         m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
         _check(load_library().idos_eval_idos(self._h, N, K, _ptr(m), seed, level, sample, _ptr(Q), _ptr(E)),
                "idos_eval_idos")
@@ -266,13 +270,13 @@ class Model:
         return out
 
     def vacancy_masks(self, N: int, level: int, seed: int, first_sample: int, n_samples: int):
-        out = np.empty((n_samples, 2 * N * N), dtype=np.uint8)
+        out = np.empty((n_samples, self.vac_per_cell * N * N), dtype=np.uint8)
         _check(load_library().idos_vacancy_masks(self._h, N, level, seed, first_sample, n_samples, _ptr(out)),
                "idos_vacancy_masks")
         return out
 
     def hamiltonian(self, N: int, K: int, k_index: int, mask):
-        n = 2 * N * N
+        n = self.orb_per_cell * N * N
         out = np.empty((n, n), dtype=np.complex128)
         m = np.ascontiguousarray(mask, dtype=np.uint8)
         _check(load_library().idos_hamiltonian(self._h, N, K, k_index, _ptr(m), _ptr(out)), "idos_hamiltonian")

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tmdc.cuh"
 
 namespace idos {
 
@@ -63,20 +64,20 @@ namespace {
 constexpr size_t kDefaultWorkspace = size_t(3) << 30;   // 3 GiB
 constexpr size_t kSmallBudget = size_t(768) << 20;      // per-chunk small buffers
 constexpr int kDefaultSmSplit = 48;                      // SMs reserved for the finest level
+// TMDC-shaped model: parameter range (uniform on [lo, hi) eV)
+constexpr double kTmdcParamLo = -2.0, kTmdcParamHi = 2.0;
 
 
 int validate(const idos_model_desc* d) {
   auto bad = [](const char* m) { set_error(m); return IDOS_ERR_INVALID_ARG; };
   if (!d) return bad("null descriptor");
-  if (d->kind != IDOS_GRAPHENE) {
-    set_error("only the graphene model is implemented in this build");
-    return IDOS_ERR_UNSUPPORTED;
-  }
+  if (d->kind != IDOS_GRAPHENE && d->kind != IDOS_TMDC) return bad("kind");
   if (d->precision != IDOS_FP64 && d->precision != IDOS_FP32_REFINE64) return bad("precision");
   if (d->smoothing != IDOS_SMOOTH_GAUSS && d->smoothing != IDOS_SMOOTH_POLY) return bad("smoothing");
   if (d->n_levels < 1 || d->n_levels > IDOS_MAX_LEVELS) return bad("n_levels out of range");
   for (int l = 0; l < d->n_levels; ++l) {
-    if (d->N[l] < 1 || d->N[l] > 64) return bad("N[l] must lie in 1..64");
+    if (d->N[l] < 1 || d->N[l] > (d->kind == IDOS_TMDC ? 24 : 64))
+      return bad("N[l] must lie in 1..64 (graphene) or 1..24 (TMDC-shaped model)");
     if (d->Kside[l] < 1 || d->Kside[l] > 64) return bad("Kside[l] must lie in 1..64");
     if (l > 0 && d->N[l] != 2 * d->N[l - 1]) return bad("N[l] must equal 2 N[l-1]");
   }
@@ -126,9 +127,11 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.ws = &ws;
   a.err = err;
   a.tc_np = M->d.tc_products;
+  a.kind = M->d.kind;
+  a.tmdc_p = M->tmdc_p;
   a.sm_avail = sm_avail;
   a.max_cluster = sm_avail ? 8 : 16;
-  if (small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
+  if (M->d.kind == IDOS_GRAPHENE && small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
   IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
   const double area = (double)cells.N * cells.N * cell_area(M->d.a);
@@ -137,32 +140,35 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   return IDOS_OK;
 }
 
-bool take_cells(Arena& ws, CellSet& c, int N, int64_t count) {
+bool take_cells(Arena& ws, CellSet& c, int N, int64_t count, int kind) {
+  c.kind = kind;
   c.N = N;
-  c.n_sites = 2 * N * N;
+  c.n_sites = orb_per_cell(kind) * N * N;
+  c.n_vac = vac_per_cell(kind) * N * N;
   c.count = count;
   c.mask = ws.take<uint8_t>((size_t)count * c.n_sites);
+  c.vmask = kind == IDOS_TMDC ? ws.take<uint8_t>((size_t)count * c.n_vac) : c.mask;
   c.n_act = ws.take<int>((size_t)count);
   c.act = ws.take<int>((size_t)count * c.n_sites);
   c.inv = ws.take<int>((size_t)count * c.n_sites);
-  return c.mask && c.n_act && c.act && c.inv;
+  return c.mask && c.vmask && c.n_act && c.act && c.inv;
 }
 
-size_t cells_bytes(int N, int64_t count) {
-  const size_t ns = 2 * (size_t)N * N;
-  return count * (ns * 9 + 4) + 4 * 256;
+size_t cells_bytes(int N, int64_t count, int kind) {
+  const size_t ns = (size_t)orb_per_cell(kind) * N * N;
+  return count * (ns * 9 + (size_t)vac_per_cell(kind) * N * N + 4) + 5 * 256;
 }
 
-size_t solve_bytes(int precision, int N, int Kside, int64_t count, int n_E) {
-  const size_t ns = 2 * (size_t)N * N;
+size_t solve_bytes(int precision, int N, int Kside, int64_t count, int n_E, int kind) {
+  const size_t ns = (size_t)orb_per_cell(kind) * N * N;
   const size_t nmat = (size_t)count * Kside * Kside;
   return nmat * ns * (2 * tsize(precision) + 8) + count * (size_t)n_E * 8 + 3 * 256;
 }
 
 // Room the large-matrix path wants for its dense batch (0 if the small path runs).
 size_t large_room(const Model* M, int N, int Kside, int64_t count) {
-  const int n = 2 * N * N;
-  if (small_path_fits(M->d.precision, n)) return 0;
+  const int n = orb_per_cell(M->d.kind) * N * N;
+  if (M->d.kind == IDOS_GRAPHENE && small_path_fits(M->d.precision, n)) return 0;
   const size_t one = large_path_bytes(M->d.precision, n, 1);
   const size_t cap = M->d.workspace_bytes > 0 ? (size_t)M->d.workspace_bytes : kDefaultWorkspace;
   const size_t want = large_path_bytes(M->d.precision, n, count * (int64_t)Kside * Kside);
@@ -191,8 +197,9 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
   const bool coarse = level > 0;
   const int Nc = coarse ? Nf / 2 : 0, Kc = coarse ? d.Kside[level - 1] : 0;
   const int n_E = d.n_E;
-  const size_t per_sample = cells_bytes(Nf, 1) + solve_bytes(d.precision, Nf, Kf, 1, n_E) +
-                            (coarse ? cells_bytes(Nc, 4) + solve_bytes(d.precision, Nc, Kc, 4, n_E) : 0) +
+  const size_t per_sample = cells_bytes(Nf, 1, d.kind) + solve_bytes(d.precision, Nf, Kf, 1, n_E, d.kind) +
+                            (coarse ? cells_bytes(Nc, 4, d.kind) + solve_bytes(d.precision, Nc, Kc, 4, n_E, d.kind)
+                                    : 0) +
                             3 * n_E * sizeof(double);
   int64_t chunk = std::max<int64_t>(1, (int64_t)(kSmallBudget / per_sample));
   chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_samples, 1));
@@ -205,19 +212,24 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     IDOS_TRY(ws.reserve(need, st));
     ws.reset();
     CellSet fine, crs;
-    if (!take_cells(ws, fine, Nf, S)) { set_error("workspace (fine cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
+    if (!take_cells(ws, fine, Nf, S, d.kind)) { set_error("workspace (fine cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
     double* Qf = ws.take<double>((size_t)S * n_E);
     double* Y = ws.take<double>((size_t)S * n_E);
     double* Qc = nullptr;
     if (coarse) {
-      if (!take_cells(ws, crs, Nc, 4 * S)) { set_error("workspace (corner cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
+      if (!take_cells(ws, crs, Nc, 4 * S, d.kind)) {
+        set_error("workspace (corner cells)");
+        return IDOS_ERR_OUT_OF_MEMORY;
+      }
       Qc = ws.take<double>((size_t)4 * S * n_E);
     }
     if (!Qf || !Y || (coarse && !Qc)) { set_error("workspace (IDoS buffers)"); return IDOS_ERR_OUT_OF_MEMORY; }
-    IDOS_TRY(launch_fine_masks(fine.mask, fine.n_sites, S, seed, level, first + s0, d.p, st));
+    IDOS_TRY(launch_fine_masks(fine.vmask, fine.n_vac, S, seed, level, first + s0, d.p, st));
+    if (d.kind == IDOS_TMDC) IDOS_TRY(launch_orbital_masks(fine.vmask, Nf, S, fine.mask, st));
     IDOS_TRY(launch_cell_maps(fine, st));
     if (coarse) {
-      IDOS_TRY(launch_corner_masks(fine.mask, Nf, S, crs.mask, st));
+      IDOS_TRY(launch_corner_masks(fine.vmask, Nf, vac_per_cell(d.kind), S, crs.vmask, st));
+      if (d.kind == IDOS_TMDC) IDOS_TRY(launch_orbital_masks(crs.vmask, Nc, 4 * S, crs.mask, st));
       IDOS_TRY(launch_cell_maps(crs, st));
     }
     // the large path takes its dense batch from whatever is left, so the
@@ -252,7 +264,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
 double flop_model(const idos_model_desc& d, int level) {
   // work per sample ~ sum over eigen-solves of n^3 (Sec. 4.4: cost per solve ~ N^6)
   auto cube = [](double x) { return x * x * x; };
-  const double nf = 2.0 * d.N[level] * d.N[level];
+  const double nf = (double)orb_per_cell(d.kind) * d.N[level] * d.N[level];
   double w = (double)d.Kside[level] * d.Kside[level] * cube(nf);
   if (level > 0) {
     const double nc = nf / 4.0;
@@ -314,6 +326,12 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
   cudaError_t e = cudaMalloc(&m->acc, acc_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->acc, 0, acc_bytes, m->stream);
   if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int) * (IDOS_MAX_LEVELS + 1));
+  if (e == cudaSuccess && d->kind == IDOS_TMDC) {
+    double hp[kTmdcParams];
+    tmdc_draw_params(d->model_seed, kTmdcParamLo, kTmdcParamHi, hp);
+    e = cudaMalloc(&m->tmdc_p, sizeof(hp));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->tmdc_p, hp, sizeof(hp), cudaMemcpyHostToDevice, m->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int) * (IDOS_MAX_LEVELS + 1), m->stream);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
@@ -365,6 +383,7 @@ void idos_destroy_model(idos_model* m) {
   cudaStreamSynchronize(m->stream);
   if (m->acc) cudaFree(m->acc);
   if (m->err) cudaFree(m->err);
+  if (m->tmdc_p) cudaFree(m->tmdc_p);
   if (m->ev0) cudaEventDestroy(m->ev0);
   if (m->ev1) cudaEventDestroy(m->ev1);
   if (m->fork) cudaEventDestroy(m->fork);
@@ -478,19 +497,21 @@ int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_
   if (N < 1 || N > 64 || Kside < 1 || Kside > 64 || sample < 0) { set_error("N, Kside or sample out of range"); return IDOS_ERR_INVALID_ARG; }
   const int n_E = m->d.n_E;
   ProfGuard pg(m);
-  const size_t need = cells_bytes(N, 1) + solve_bytes(m->d.precision, N, Kside, 1, n_E) + 8 * n_E + 65536 +
+  const size_t need = cells_bytes(N, 1, m->d.kind) + solve_bytes(m->d.precision, N, Kside, 1, n_E, m->d.kind) +
+                      8 * n_E + 65536 +
                       large_room(m, N, Kside, 1);
   IDOS_TRY(m->ws.reserve(need, m->stream));
   m->ws.reset();
   CellSet c;
-  if (!take_cells(m->ws, c, N, 1)) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
+  if (!take_cells(m->ws, c, N, 1, m->d.kind)) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
   double* Q = m->ws.take<double>(n_E);
   if (!Q) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
   if (mask) {
-    IDOS_CUDA_TRY(cudaMemcpyAsync(c.mask, mask, c.n_sites, cudaMemcpyHostToDevice, m->stream));
+    IDOS_CUDA_TRY(cudaMemcpyAsync(c.vmask, mask, c.n_vac, cudaMemcpyHostToDevice, m->stream));
   } else {
-    IDOS_TRY(launch_fine_masks(c.mask, c.n_sites, 1, seed, level, sample, m->d.p, m->stream));
+    IDOS_TRY(launch_fine_masks(c.vmask, c.n_vac, 1, seed, level, sample, m->d.p, m->stream));
   }
+  if (m->d.kind == IDOS_TMDC) IDOS_TRY(launch_orbital_masks(c.vmask, N, 1, c.mask, m->stream));
   IDOS_TRY(launch_cell_maps(c, m->stream));
   double* eigs = nullptr;
   int* err = m->err + IDOS_MAX_LEVELS;
@@ -508,12 +529,13 @@ int idos_vacancy_masks(idos_model* m, int N, int level, uint64_t seed, int64_t f
                        uint8_t* out) {
   if (!m || !out) { set_error("null model or output"); return IDOS_ERR_INVALID_ARG; }
   if (N < 1 || N > 64 || n_samples < 0 || first_sample < 0) { set_error("bad size"); return IDOS_ERR_INVALID_ARG; }
-  const size_t bytes = (size_t)n_samples * 2 * N * N;
+  const int nv = vac_per_cell(m->d.kind) * N * N;
+  const size_t bytes = (size_t)n_samples * nv;
   IDOS_TRY(m->ws.reserve(bytes + 4096, m->stream));
   m->ws.reset();
   uint8_t* buf = m->ws.take<uint8_t>(bytes);
   if (!buf) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
-  IDOS_TRY(launch_fine_masks(buf, 2 * N * N, n_samples, seed, level, first_sample, m->d.p, m->stream));
+  IDOS_TRY(launch_fine_masks(buf, nv, n_samples, seed, level, first_sample, m->d.p, m->stream));
   IDOS_CUDA_TRY(cudaMemcpyAsync(out, buf, bytes, cudaMemcpyDeviceToHost, m->stream));
   IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
   return IDOS_OK;
@@ -521,23 +543,26 @@ int idos_vacancy_masks(idos_model* m, int N, int level, uint64_t seed, int64_t f
 
 int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t* mask, double* out) {
   if (!m || !mask || !out) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
-  if (N < 1 || N > 32 || Kside < 1 || k_index < 0 || k_index >= Kside * Kside) {
-    set_error("N (<= 32), Kside or k_index out of range");
+  const int n_cap = m->d.kind == IDOS_TMDC ? 12 : 32;
+  if (N < 1 || N > n_cap || Kside < 1 || k_index < 0 || k_index >= Kside * Kside) {
+    set_error("N (<= 32 graphene, <= 12 TMDC), Kside or k_index out of range");
     return IDOS_ERR_INVALID_ARG;
   }
-  const int n = 2 * N * N;
-  IDOS_TRY(m->ws.reserve(cells_bytes(N, 1) + sizeof(double2) * (size_t)n * n + 8192, m->stream));
+  const int n = orb_per_cell(m->d.kind) * N * N;
+  IDOS_TRY(m->ws.reserve(cells_bytes(N, 1, m->d.kind) + sizeof(double2) * (size_t)n * n + 8192, m->stream));
   m->ws.reset();
   CellSet c;
-  if (!take_cells(m->ws, c, N, 1)) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
+  if (!take_cells(m->ws, c, N, 1, m->d.kind)) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
   double2* H = m->ws.take<double2>((size_t)n * n);
   if (!H) { set_error("workspace"); return IDOS_ERR_OUT_OF_MEMORY; }
-  IDOS_CUDA_TRY(cudaMemcpyAsync(c.mask, mask, n, cudaMemcpyHostToDevice, m->stream));
+  IDOS_CUDA_TRY(cudaMemcpyAsync(c.vmask, mask, c.n_vac, cudaMemcpyHostToDevice, m->stream));
   SolveArgs a;
   a.cells = &c;
   a.Kside = Kside;
   a.t = m->d.t;
   a.eps = m->d.eps_onsite;
+  a.kind = m->d.kind;
+  a.tmdc_p = m->tmdc_p;
   a.stream = m->stream;
   IDOS_TRY(launch_assemble_dense(a, k_index, H, m->d.sentinel));
   IDOS_CUDA_TRY(cudaMemcpyAsync(out, H, sizeof(double2) * (size_t)n * n, cudaMemcpyDeviceToHost, m->stream));

@@ -35,16 +35,25 @@ struct Arena {
   void release();
 };
 
+// Vacancy sites and orbitals per unit cell of each model kind: graphene has
+// two sites with one orbital each; the TMDC-shaped model one removable
+// chalcogen pair and 11 orbitals (5 metal + 6 pair).
+inline int vac_per_cell(int kind) { return kind == IDOS_TMDC ? 1 : 2; }
+inline int orb_per_cell(int kind) { return kind == IDOS_TMDC ? 11 : 2; }
+
 // One set of supercell configurations of equal side N ("cells"): vacancy
-// masks and the compaction maps from site index to active row.
+// masks and the compaction maps from orbital index to active row.
 struct CellSet {
+  int kind = IDOS_GRAPHENE;
   int N = 0;
-  int n_sites = 0;   // 2 N^2
+  int n_sites = 0;   // orbitals per cell: orb_per_cell(kind) N^2
+  int n_vac = 0;     // vacancy sites per cell: vac_per_cell(kind) N^2
   int64_t count = 0;
-  uint8_t* mask = nullptr;  // [count][n_sites], 1 = removed
+  uint8_t* vmask = nullptr; // [count][n_vac], 1 = removed (the same buffer as mask for graphene)
+  uint8_t* mask = nullptr;  // [count][n_sites], 1 = orbital removed
   int* n_act = nullptr;     // [count]
-  int* act = nullptr;       // [count][n_sites] active sites, ascending
-  int* inv = nullptr;       // [count][n_sites] site -> active row, or -1
+  int* act = nullptr;       // [count][n_sites] active orbitals, ascending
+  int* inv = nullptr;       // [count][n_sites] orbital -> active row, or -1
 };
 
 // Inputs of one batched eigen-solve: every cell of a CellSet at every point
@@ -55,9 +64,11 @@ int check_device(int& sm_count);   // IDOS_ERR_NO_DEVICE unless the current devi
 struct SolveArgs {
   const CellSet* cells = nullptr;
   int Kside = 1;
-  int n_max = 0;            // matrix dimension capacity = 2 N^2
+  int n_max = 0;            // matrix dimension capacity = orbitals per cell
   int64_t n_mat = 0;
-  double t = 0, eps = 0;    // hopping and on-site energy
+  double t = 0, eps = 0;    // graphene: hopping and on-site energy
+  int kind = IDOS_GRAPHENE;
+  const double* tmdc_p = nullptr;   // TMDC-shaped model: device parameter table
   const double2* H = nullptr;
   void* d = nullptr;        // T[n_mat][n_max] diagonal of the tridiagonal
   void* e2 = nullptr;       // T[n_mat][n_max] squared off-diagonal (e2[i] couples i, i+1)
@@ -102,6 +113,7 @@ struct Model {
   std::string part_note;          // why there is no split (empty when there is one or none was asked)
   int lsms[IDOS_MAX_LEVELS] = {};  // SMs of each level stream's partition (0: whole device)
   double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
+  double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream
   int64_t M[IDOS_MAX_LEVELS] = {};
   double seconds[IDOS_MAX_LEVELS] = {};
@@ -114,9 +126,15 @@ struct Model {
 // ---- stage launchers (return idos_status) ----
 int launch_fine_masks(uint8_t* out, int n_sites, int64_t count, uint64_t seed, int level,
                       int64_t first_sample, double p, cudaStream_t s);
-int launch_corner_masks(const uint8_t* fine, int N, int64_t count, uint8_t* out, cudaStream_t s);
+int launch_corner_masks(const uint8_t* fine, int N, int per_cell, int64_t count, uint8_t* out, cudaStream_t s);
+// TMDC-shaped model: orbital masks [count][11 N^2] from pair masks [count][N^2]
+int launch_orbital_masks(const uint8_t* pairs, int N, int64_t count, uint8_t* out, cudaStream_t s);
 int launch_cell_maps(CellSet& c, cudaStream_t s);
 int launch_assemble_dense(const SolveArgs& a, int k_index, double2* out, double sentinel);
+// The TMDC-shaped model's parameter table (kTmdcParams doubles, host) drawn
+// from model_seed: value i = lo + (hi - lo) u_i, u_i = (w0 >> 11) 2^-53 with w0
+// word 0 of Philox4x64-10(counter (i, 0, 0, 0), key (model_seed, 2)).
+void tmdc_draw_params(uint64_t model_seed, double lo, double hi, double* out);
 
 // Householder reduction to real symmetric tridiagonal (d, e^2).
 bool small_path_fits(int precision, int n_max);

@@ -19,6 +19,7 @@
 
 #include "graphene.cuh"
 #include "large.cuh"
+#include "tmdc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -70,6 +71,36 @@ __global__ void k_lg_assemble(int64_t n_mat_batch, int64_t mat0, int n_max, int 
       row[col] = cadd<T>(row[col], mk<T>((T)(t_hop * p.x), (T)(t_hop * im)));
     }
     row[a].x += (T)eps;
+  }
+}
+
+// H(k) of the TMDC-shaped model into global memory, rows of kept orbitals
+// only, built by tmdc_row (hops into removed pairs are skipped; the buffer is
+// zeroed beforehand).  One thread per (matrix, row).
+template <typename T>
+__global__ void k_lg_assemble_tmdc(int64_t n_mat_batch, int64_t mat0, int n_max, int K2,
+                                   const int* __restrict__ n_act_cell, const int* __restrict__ act,
+                                   const int* __restrict__ inv, const uint8_t* __restrict__ pairs, int N, int K,
+                                   const double* __restrict__ P, c2<T>* __restrict__ A) {
+  using C = c2<T>;
+  const int64_t total = n_mat_batch * (int64_t)n_max;
+  const int n_orb = kTmdcOrb * N * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t mat = idx / n_max;
+    const int a = (int)(idx - mat * n_max);
+    const int64_t gmat = mat0 + mat;
+    const int64_t cell = gmat / K2;
+    const int kidx = (int)(gmat - cell * K2);
+    if (a >= n_act_cell[cell]) continue;
+    C* row = A + mat * (int64_t)n_max * n_max + (int64_t)a * n_max;
+    const int* invc = inv + cell * n_orb;
+    const uint8_t* pc = pairs + cell * (N * N);
+    tmdc_row(N, K, kidx, act[cell * n_orb + a], P, [&](int c) { return pc[c] != 0; },
+             [&](int o2, double2 v) {
+               const int col = invc[o2];
+               if (col >= 0) row[col] = cadd<T>(row[col], mk<T>((T)v.x, (T)v.y));
+             });
   }
 }
 
@@ -701,10 +732,16 @@ int solve_large_t(const SolveArgs& a) {
       const int64_t total = nb_mat * (int64_t)nm;
       const int64_t blocks = std::min<int64_t>((total + 127) / 128, 152 * 16);
       ProfScope ps(KID_LG_ASSEMBLE, a.stream);
-      k_lg_assemble<T><<<(unsigned)blocks, 128, 0, a.stream>>>(
-          nb_mat, m0, nm, K2, cells ? cells->n_act : nullptr, cells ? cells->act : nullptr,
-          cells ? cells->inv : nullptr, cells ? cells->N : 0, a.Kside, a.t, a.eps,
-          a.H ? a.H + m0 * (int64_t)nm * nm : nullptr, A);
+      if (a.kind == IDOS_TMDC && cells && !a.H) {
+        k_lg_assemble_tmdc<T><<<(unsigned)blocks, 128, 0, a.stream>>>(nb_mat, m0, nm, K2, cells->n_act, cells->act,
+                                                                      cells->inv, cells->vmask, cells->N, a.Kside,
+                                                                      a.tmdc_p, A);
+      } else {
+        k_lg_assemble<T><<<(unsigned)blocks, 128, 0, a.stream>>>(
+            nb_mat, m0, nm, K2, cells ? cells->n_act : nullptr, cells ? cells->act : nullptr,
+            cells ? cells->inv : nullptr, cells ? cells->N : 0, a.Kside, a.t, a.eps,
+            a.H ? a.H + m0 * (int64_t)nm * nm : nullptr, A);
+      }
       IDOS_CHECK_LAUNCH();
     }
     {

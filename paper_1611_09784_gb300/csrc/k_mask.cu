@@ -4,6 +4,7 @@
 
 #include "graphene.cuh"
 #include "internal.h"
+#include "tmdc.cuh"
 
 namespace idos {
 
@@ -38,32 +39,65 @@ int launch_fine_masks(uint8_t* out, int n_sites, int64_t count, uint64_t seed, i
 }
 
 // Corner r = ri + 2 rj of a fine N x N cell: cells i in [ri h, (ri+1) h),
-// j in [rj h, (rj+1) h), h = N/2; local site 2(i' + h j') + s.
-__global__ void k_corner_masks(const uint8_t* __restrict__ fine, int N, int64_t total,
+// j in [rj h, (rj+1) h), h = N/2; vacancy site `sub` (0 .. per-1) of local
+// cell (i', j') is per (i' + h j') + sub.
+__global__ void k_corner_masks(const uint8_t* __restrict__ fine, int N, int per, int64_t total,
                                uint8_t* __restrict__ out) {
-  const int h = N / 2, nsc = 2 * h * h, nsf = 2 * N * N;
+  const int h = N / 2, nsc = per * h * h, nsf = per * N * N;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t inst = idx / nsc;          // 4 s + r
     const int ml = (int)(idx - inst * nsc);
     const int64_t smp = inst >> 2;
     const int r = (int)(inst & 3), ri = r & 1, rj = r >> 1;
-    const int sub = ml & 1, cl = ml >> 1, il = cl % h, jl = cl / h;
-    const int mf = 2 * ((il + ri * h) + N * (jl + rj * h)) + sub;
+    const int sub = ml % per, cl = ml / per, il = cl % h, jl = cl / h;
+    const int mf = per * ((il + ri * h) + N * (jl + rj * h)) + sub;
     out[idx] = fine[smp * nsf + mf];
   }
 }
 
-int launch_corner_masks(const uint8_t* fine, int N, int64_t count, uint8_t* out, cudaStream_t s) {
+int launch_corner_masks(const uint8_t* fine, int N, int per, int64_t count, uint8_t* out, cudaStream_t s) {
   const int h = N / 2;
-  const int64_t total = count * 4 * (int64_t)(2 * h * h);
+  const int64_t total = count * 4 * (int64_t)(per * h * h);
   if (total == 0) return IDOS_OK;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
   ProfScope ps(KID_CORNERS, s);
-  k_corner_masks<<<(unsigned)blocks, threads, 0, s>>>(fine, N, total, out);
+  k_corner_masks<<<(unsigned)blocks, threads, 0, s>>>(fine, N, per, total, out);
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
+}
+
+// TMDC-shaped model: orbital o = 11 c + q is removed iff q >= 5 (a pair
+// orbital) and cell c's pair is removed.
+__global__ void k_orbital_masks(const uint8_t* __restrict__ pairs, int nc, int64_t total, uint8_t* __restrict__ out) {
+  const int no = kTmdcOrb * nc;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx / no;
+    const int o = (int)(idx - s * no);
+    const int c = o / kTmdcOrb, q = o - c * kTmdcOrb;
+    out[idx] = (q >= kTmdcM && pairs[s * nc + c]) ? 1 : 0;
+  }
+}
+
+int launch_orbital_masks(const uint8_t* pairs, int N, int64_t count, uint8_t* out, cudaStream_t s) {
+  const int64_t total = count * (int64_t)kTmdcOrb * N * N;
+  if (total == 0) return IDOS_OK;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
+  ProfScope ps(KID_CORNERS, s);
+  k_orbital_masks<<<(unsigned)blocks, threads, 0, s>>>(pairs, N * N, total, out);
+  IDOS_CHECK_LAUNCH();
+  return IDOS_OK;
+}
+
+void tmdc_draw_params(uint64_t model_seed, double lo, double hi, double* out) {
+  for (int i = 0; i < kTmdcParams; ++i) {
+    const u64x4 r = philox4x64_10((uint64_t)i, 0ull, 0ull, 0ull, model_seed, kStreamParams);
+    const double u = std::ldexp((double)(r.w[0] >> 11), -53);
+    out[i] = lo + (hi - lo) * u;
+  }
 }
 
 // One CTA per cell: ascending list of kept sites and the inverse map.
@@ -135,11 +169,37 @@ __global__ void k_assemble_dense(const uint8_t* __restrict__ mask, int N, int K,
   }
 }
 
+// TMDC-shaped model in the full orbital basis: rows built by tmdc_row (the
+// function the large-path assembly uses), removed pairs' orbitals with zero
+// rows and columns and `sentinel` on the diagonal.
+__global__ void k_assemble_dense_tmdc(const uint8_t* __restrict__ pairs, int N, int K, int kidx,
+                                      const double* __restrict__ P, double sentinel, double2* __restrict__ out) {
+  const int n = kTmdcOrb * N * N;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    double2* row = out + (int64_t)o * n;
+    const int c = o / kTmdcOrb, q = o % kTmdcOrb;
+    if (q >= kTmdcM && pairs[c]) {
+      row[o] = make_double2(sentinel, 0.0);
+      continue;
+    }
+    tmdc_row(N, K, kidx, o, P, [&](int cell) { return pairs[cell] != 0; },
+             [&](int o2, double2 v) {
+               row[o2].x += v.x;
+               row[o2].y += v.y;
+             });
+  }
+}
+
 int launch_assemble_dense(const SolveArgs& a, int k_index, double2* out, double sentinel) {
-  const int N = a.cells->N, n = 2 * N * N;
+  const int N = a.cells->N, n = a.cells->n_sites;
   IDOS_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)n * n, a.stream));
-  k_assemble_dense<<<(n + 127) / 128, 128, 0, a.stream>>>(a.cells->mask, N, a.Kside, k_index, a.t,
-                                                          a.eps, sentinel, out);
+  if (a.kind == IDOS_TMDC) {
+    k_assemble_dense_tmdc<<<(n + 127) / 128, 128, 0, a.stream>>>(a.cells->vmask, N, a.Kside, k_index, a.tmdc_p,
+                                                                 sentinel, out);
+  } else {
+    k_assemble_dense<<<(n + 127) / 128, 128, 0, a.stream>>>(a.cells->mask, N, a.Kside, k_index, a.t, a.eps,
+                                                            sentinel, out);
+  }
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
 }

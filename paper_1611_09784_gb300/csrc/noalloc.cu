@@ -75,7 +75,10 @@ size_t scratch_need(int precision, int n_sites, int K2, bool own_mask, bool own_
 int check_desc(const idos_model_desc* d) {
   auto bad = [](const char* m) { set_error(m); return IDOS_ERR_INVALID_ARG; };
   if (!d) return bad("null descriptor");
-  if (d->kind != IDOS_GRAPHENE) { set_error("only the graphene model is implemented"); return IDOS_ERR_UNSUPPORTED; }
+  if (d->kind != IDOS_GRAPHENE) {
+    set_error("the allocation-free entry point takes the graphene model only");
+    return IDOS_ERR_UNSUPPORTED;
+  }
   if (d->precision != IDOS_FP64 && d->precision != IDOS_FP32_REFINE64) return bad("precision");
   if (d->smoothing != IDOS_SMOOTH_GAUSS && d->smoothing != IDOS_SMOOTH_POLY) return bad("smoothing");
   if (!(d->p >= 0.0 && d->p <= 1.0)) return bad("p must lie in [0, 1]");
