@@ -297,6 +297,55 @@ def oracle_measure(pool, cores, alloc, levels, frac=1.0 / 16, first=50_000_000, 
             "seconds_per_step_extrapolated": full_wall}
 
 
+# ------------------------------------------------ other workloads (extras) --
+def tmdc_sweep(pkg, torch, stream, samples=(32, 32, 32, 8)):
+    """TMDC-shaped 11-orbital model, N = 4, 8, 12, 16 (n = 176 .. 2816), 4 x 4
+    grid, float32 reduction + one float64 refinement pass: eigen-solves/s of
+    one sample_level call per size (CUDA events on the model stream)."""
+    from synthetic import workload
+    w = workload("tmdc_sweep")
+    out = []
+    for N, S in zip(w["sizes"], samples):
+        cfg = dict(w["model"], p=w["p"], levels=[(N, w["K"])], e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
+                   delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64,
+                   tc_products=TC_PRODUCTS)
+        m = pkg.create_model(cfg, stream=stream.cuda_stream)
+        m.sample_level(0, 1, w["seed"] + 1, 0)          # warm-up (workspace, first launches)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.sample_level(0, S, w["seed"], 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out.append({"N": N, "n": 11 * N * N, "K": w["K"], "samples": S, "ms": round(ms, 2),
+                    "eigsolves_per_s": S * w["K"] ** 2 / (ms * 1e-3)})
+        m.close()
+    return out
+
+
+def stress(pkg, torch, stream):
+    """Graphene N = 64 (n = 8192), p = 0.02, 2 x 2 grid: one sample (4 solves)
+    on the float32 path with the tensor-core trailing update."""
+    from synthetic import workload
+    w = workload("graphene_stress")
+    cfg = dict(w["model"], p=w["p"], levels=w["levels"], e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
+               delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64,
+               tc_products=TC_PRODUCTS)
+    m = pkg.create_model(cfg, stream=stream.cuda_stream)
+    m.sample_level(0, 1, w["seed"] + 1, 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    m.sample_level(0, 1, w["seed"], 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m.close()
+    return {"N": 64, "n": 8192, "K": 2, "samples": 1, "ms": round(ms, 1), "eigsolves_per_s": 4 / (ms * 1e-3),
+            "precision": f"fp32 reduction, tensor-core trailing update ({TC_PRODUCTS} split-bf16 products)"}
+
+
 # ------------------------------------------------------------------- GPU arm --
 def run_gpu(args):
     import numpy as np
@@ -451,6 +500,9 @@ def run_gpu(args):
     mc_s = time.perf_counter() - t0
     mc.close()
 
+    sweep = tmdc_sweep(pkg, torch, stream)
+    stress_line = stress(pkg, torch, stream)
+
     cpu = None
     if pool is not None:
         cpu = oracle_measure(pool, cores, alloc, levels)
@@ -477,6 +529,8 @@ def run_gpu(args):
             "rooflines": roofs,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "tmdc_sweep": sweep,
+            "stress": stress_line,
             "estimate_check": {"Q_at_e_max": float(mean[-1]), "max_std": float(np.sqrt(np.max(var)))},
         }
         print(json.dumps(line), flush=True)

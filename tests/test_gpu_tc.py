@@ -88,3 +88,24 @@ def test_her2k_tensor_cores_need_even_dimension():
         pkg.her2k(A, Y, Z, tc_products=6)
     got = pkg.her2k(A, Y, Z, tc_products=0)   # the FP32 pipe takes any dimension
     assert np.max(np.abs(got - _reference(A, Y, Z))) < 1e-4
+
+
+def test_fp32_tensor_path_against_fp64_path_full_size_graphene():
+    """The large-level comparison of the float32 path (tensor-core trailing
+    update) with the float64-only GPU path, at N = 32 (n = 2048), one sample:
+    eigenvalues within 1e-4 eV and IDoS within 1e-5."""
+    import paper_1611_09784_gb300 as pkg
+    from synthetic import workload
+    w = workload("graphene_stress")
+    out = {}
+    for prec in ("fp32", "fp64"):
+        cfg = dict(w["model"], p=w["p"], levels=[(32, 1)], e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
+                   delta=w["delta"], smoothing=w["smoothing"], precision=prec, refine64_iters=1, tc_products=6)
+        m = pkg.create_model(cfg)
+        out[prec] = m.eval_idos(32, 1, None, w["seed"], 0, 3, want_eigs=True)
+        m.close()
+    (q32, e32), (q64, e64) = out["fp32"], out["fp64"]
+    keep = ~np.isnan(e64[0])
+    assert np.array_equal(keep, ~np.isnan(e32[0]))
+    assert np.max(np.abs(np.sort(e32[0][keep]) - np.sort(e64[0][keep]))) < 1e-4
+    assert np.max(np.abs(q32 - q64)) < 1e-5
