@@ -274,6 +274,40 @@ int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int
 int idos_her2k(int tc_products, int n, int64_t batch, const double* A, const double* Y, const double* Z,
                double* A_out);
 
+/* ---- serving ----
+ * A request loop over the level sampler (a scheduler thread inside the
+ * library).  Requests arrive from any host thread; they are admitted in
+ * arrival order onto n_workers device streams, each with its own workspace,
+ * while the summed workspace of the requests in flight (their HBM footprint)
+ * stays within hbm_budget_bytes (0 = 8 GiB; a request larger than the budget
+ * still runs when nothing else is in flight), so requests of different levels
+ * and sizes overlap on the device.  A request's result is the float64 sum of
+ * Y and of Y^2 (the level terms of eq. (2.6), Y as in idos_sample_level) over
+ * its samples first_sample .. first_sample + n_samples - 1 of `level`; its
+ * launch shapes depend only on the request, so the result is the same whether
+ * it runs alone or among others.  The model described by d is created inside
+ * the server (its sm_split is ignored). */
+typedef struct idos_server idos_server;
+int idos_server_create(const idos_model_desc* d, int n_workers, int64_t hbm_budget_bytes, idos_server** out);
+
+/* Queue one request; *ticket identifies it.  Does not block. */
+int idos_server_submit(idos_server* s, int level, int64_t n_samples, uint64_t seed, int64_t first_sample,
+                       int64_t* ticket);
+
+/* Block until the request is done; sum, sumsq: host float64[n_E] (nullable);
+ * latency_s: seconds from submission to completion; device_ms: CUDA-event
+ * time of its work.  Returns the request's status; the ticket is then freed. */
+int idos_server_wait(idos_server* s, int64_t ticket, double* sum, double* sumsq, double* latency_s,
+                     double* device_ms);
+
+/* Counters: requests completed, queued, bytes of the workspace in flight now
+ * and at peak (all nullable). */
+int idos_server_info(const idos_server* s, int64_t* completed, int64_t* queued, int64_t* in_flight_bytes,
+                     int64_t* peak_bytes);
+
+/* Finish the queued requests, stop the loop, free everything.  NULL ok. */
+void idos_server_destroy(idos_server* s);
+
 /* ---- allocation-free evaluation ----
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc: code that owns all device memory through its

@@ -76,6 +76,13 @@ _SYMBOLS = {
     "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_her2k": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_get_partition": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_char_p)]),
+    "idos_server_create": (C.c_int, [C.POINTER(ModelDesc), C.c_int, C.c_int64, C.POINTER(C.c_void_p)]),
+    "idos_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_int64, C.POINTER(C.c_int64)]),
+    "idos_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
+    "idos_server_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64)]),
+    "idos_server_destroy": (None, [C.c_void_p]),
     "idos_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "idos_profile_count": (C.c_int, []),
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -281,6 +288,50 @@ class Model:
         m = np.ascontiguousarray(mask, dtype=np.uint8)
         _check(load_library().idos_hamiltonian(self._h, N, K, k_index, _ptr(m), _ptr(out)), "idos_hamiltonian")
         return out
+
+
+class Server:
+    """Request loop over the level sampler (idos_server_*): submit() queues a
+    request and returns a ticket, wait() returns (sum Y, sum Y^2, latency in
+    seconds, device milliseconds) of its samples."""
+
+    def __init__(self, cfg: dict, n_workers: int = 4, hbm_budget_bytes: int = 0):
+        self.desc = make_desc(cfg)
+        self.n_E = self.desc.n_E
+        h = C.c_void_p()
+        _check(load_library().idos_server_create(C.byref(self.desc), n_workers, hbm_budget_bytes, C.byref(h)),
+               "idos_server_create")
+        self._h = h
+
+    def submit(self, level: int, n_samples: int, seed: int, first_sample: int = 0) -> int:
+        t = C.c_int64(0)
+        _check(load_library().idos_server_submit(self._h, level, n_samples, seed, first_sample, C.byref(t)),
+               "idos_server_submit")
+        return t.value
+
+    def wait(self, ticket: int):
+        s1 = np.empty(self.n_E)
+        s2 = np.empty(self.n_E)
+        lat, dev = C.c_double(0), C.c_double(0)
+        _check(load_library().idos_server_wait(self._h, ticket, _ptr(s1), _ptr(s2), C.byref(lat), C.byref(dev)),
+               "idos_server_wait")
+        return s1, s2, lat.value, dev.value
+
+    def info(self):
+        vals = [C.c_int64(0) for _ in range(4)]
+        _check(load_library().idos_server_info(self._h, *[C.byref(v) for v in vals]), "idos_server_info")
+        return dict(zip(("completed", "queued", "in_flight_bytes", "peak_bytes"), (v.value for v in vals)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().idos_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def create_model(cfg: dict, stream: int | None = None) -> Model:

@@ -191,7 +191,7 @@ int check_status_word(const int* err) {
 // otherwise the caller does that after synchronising ev1.
 int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh, double* Qfh,
               double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, bool blocking,
-              int sm_avail = 0) {
+              int sm_avail = 0, double* acc_out = nullptr) {
   const idos_model_desc& d = M->d;
   const int Nf = d.N[level], Kf = d.Kside[level];
   const bool coarse = level > 0;
@@ -241,7 +241,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     }
     IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err, sm_avail));
     ws.used = mark;
-    double* acc = M->acc + (size_t)level * 2 * n_E;
+    double* acc = acc_out ? acc_out : M->acc + (size_t)level * 2 * n_E;
     IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, ws, st));
     if (Yh) IDOS_CUDA_TRY(cudaMemcpyAsync(Yh + s0 * n_E, Y, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, st));
     if (Qfh) IDOS_CUDA_TRY(cudaMemcpyAsync(Qfh + s0 * n_E, Qf, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, st));
@@ -259,6 +259,23 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     M->seconds[level] += ms * 1e-3;
   }
   return IDOS_OK;
+}
+
+// Device workspace one run_level call of n_samples on `level` reserves.
+size_t level_workspace(const Model* M, int level, int64_t n_samples) {
+  const idos_model_desc& d = M->d;
+  const int Nf = d.N[level], Kf = d.Kside[level];
+  const bool coarse = level > 0;
+  const int Nc = coarse ? Nf / 2 : 0, Kc = coarse ? d.Kside[level - 1] : 0;
+  const int n_E = d.n_E;
+  const size_t per_sample = cells_bytes(Nf, 1, d.kind) + solve_bytes(d.precision, Nf, Kf, 1, n_E, d.kind) +
+                            (coarse ? cells_bytes(Nc, 4, d.kind) + solve_bytes(d.precision, Nc, Kc, 4, n_E, d.kind)
+                                    : 0) +
+                            3 * n_E * sizeof(double);
+  int64_t chunk = std::max<int64_t>(1, (int64_t)(kSmallBudget / per_sample));
+  chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_samples, 1));
+  return chunk * per_sample + 64 * 1024 + ((chunk + 63) / 64) * 2 * n_E * 8 +
+         std::max(large_room(M, Nf, Kf, chunk), coarse ? large_room(M, Nc, Kc, 4 * chunk) : 0);
 }
 
 double flop_model(const idos_model_desc& d, int level) {
@@ -288,11 +305,17 @@ struct ProfGuard {
 };
 
 }  // namespace
+
+int level_run_async(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, cudaStream_t st,
+                    Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, double* acc) {
+  return run_level(M, level, n_samples, seed, first, nullptr, nullptr, nullptr, st, ws, ev0, ev1, err, false, 0, acc);
+}
+size_t level_footprint(const Model* M, int level, int64_t n_samples) { return level_workspace(M, level, n_samples); }
+int read_status_word(const int* err) { return check_status_word(err); }
+
 }  // namespace idos
 
 using namespace idos;
-
-struct idos_model : public idos::Model {};
 
 extern "C" {
 

@@ -160,4 +160,18 @@ int launch_level_stats(const double* Qf, const double* Qc, int64_t S, int n_E, d
 
 double cell_area(double a);   // |a1 x a2| = sqrt(3)/2 a^2
 
+// Level sampling for other drivers (api.cu): n_samples of `level` on stream st
+// with workspace ws, float64 sums Y, Y^2 added to acc [2][n_E] (device, zeroed
+// by the caller), err (device status word) zeroed first; ev0 / ev1 recorded
+// around the work; returns without waiting.
+int level_run_async(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, cudaStream_t st,
+                    Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, double* acc);
+// Device workspace such a call reserves (its HBM footprint).
+size_t level_footprint(const Model* M, int level, int64_t n_samples);
+// Reads a status word after the work that sets it completed.
+int read_status_word(const int* err);
+
 }  // namespace idos
+
+// The opaque handle of the C ABI is the model object itself.
+struct idos_model : public idos::Model {};
