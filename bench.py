@@ -346,6 +346,46 @@ def stress(pkg, torch, stream):
             "precision": f"fp32 reduction, tensor-core trailing update ({TC_PRODUCTS} split-bf16 products)"}
 
 
+def serving(pkg, cfg, levels, seed, rates=(300.0, 1000.0), n_req=120, trace_seed=7):
+    """The request loop under Poisson arrivals of level requests like the ones
+    the adaptive driver emits: level l with probability 0.4, 0.3, 0.2, 0.1,
+    batch log-uniform in [1, B_l] samples (B = 512, 512, 32, 4: fewer samples on
+    costlier levels).  The same trace is served by 4 worker streams
+    (concurrent) and by 1 (one request at a time).  Latency = submission to
+    completion (library clock); throughput = eigen-solves / (last completion -
+    first arrival)."""
+    import numpy as np
+    rng = np.random.default_rng(trace_seed)
+    bmax = [512, 512, 32, 4]
+    out = []
+    for rate in rates:
+        gaps = rng.exponential(1.0 / rate, n_req)
+        lv = rng.choice(4, size=n_req, p=[0.4, 0.3, 0.2, 0.1])
+        nb = [int(round(math.exp(rng.uniform(0.0, math.log(bmax[l]))))) for l in lv]
+        arrive = np.cumsum(gaps)
+        eig = sum(n * eigsolves_per_sample(levels, int(l)) for l, n in zip(lv, nb))
+        row = {"rate_per_s": rate, "requests": n_req, "eigsolves": int(eig)}
+        for workers in (4, 1):
+            srv = pkg.Server(dict(cfg, sm_split=0), n_workers=workers)
+            for l in range(4):                      # warm-up: workspaces, first launches
+                srv.wait(srv.submit(l, 1, seed + 5, 0))
+            t0 = time.perf_counter()
+            tickets = []
+            for i in range(n_req):
+                dt = t0 + arrive[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(int(lv[i]), nb[i], seed, 1_000_000 + 10_000 * i))
+            lat = [srv.wait(t)[2] for t in tickets]
+            elapsed = time.perf_counter() - t0
+            srv.close()
+            key = "concurrent_4" if workers == 4 else "one_at_a_time"
+            row[key] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                        "eigsolves_per_s": eig / elapsed, "wall_s": elapsed}
+        out.append(row)
+    return out
+
+
 # ------------------------------------------------------------------- GPU arm --
 def run_gpu(args):
     import numpy as np
@@ -502,6 +542,7 @@ def run_gpu(args):
 
     sweep = tmdc_sweep(pkg, torch, stream)
     stress_line = stress(pkg, torch, stream)
+    serve = serving(pkg, cfg, levels, seed)
 
     cpu = None
     if pool is not None:
@@ -529,6 +570,7 @@ def run_gpu(args):
             "rooflines": roofs,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "serving": serve,
             "tmdc_sweep": sweep,
             "stress": stress_line,
             "estimate_check": {"Q_at_e_max": float(mean[-1]), "max_std": float(np.sqrt(np.max(var)))},
