@@ -67,3 +67,22 @@ def hamiltonian(N: int, k, mask, t: float, eps_onsite: float, a: float,
             H[:, m] = 0.0
             H[m, m] = sentinel
     return H
+
+
+def overlap(N: int, k, mask, s: float, a: float) -> np.ndarray:
+    """complex128[2N^2, 2N^2] S(k) of eq. (3.2c)-(3.2d): 1 on the diagonal,
+    s exp(i k . R_mn) on every nearest-neighbour bond (found by the same
+    brute-force search as H); a removed site keeps only its diagonal 1, so
+    its generalized eigenvalue is H's sentinel."""
+    n = 2 * N * N
+    ms, ns, rs = bonds(N, a)
+    S = np.zeros((n, n), dtype=np.complex128)
+    np.add.at(S, (ms, ns), s * np.exp(1j * (rs @ np.asarray(k, dtype=np.float64))))
+    mask = np.asarray(mask)
+    for m in range(n):
+        if mask[m]:
+            S[m, :] = 0.0
+            S[:, m] = 0.0
+    S[np.arange(n), np.arange(n)] += 1.0
+    return S
+

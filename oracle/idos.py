@@ -25,6 +25,7 @@ particle-hole identity Q(e) + Q(-e) = n_act/|F|, band folding, closed form.
 from __future__ import annotations
 
 import numpy as np
+from scipy.linalg import eigh
 from scipy.special import erfc
 
 from . import hamiltonian, lattice
@@ -59,15 +60,32 @@ def eigenvalues(H: np.ndarray, n_vac: int) -> np.ndarray:
     return E[keep]
 
 
+def generalized_eigenvalues(H: np.ndarray, S: np.ndarray, n_vac: int) -> np.ndarray:
+    """Ascending eigenvalues E of H u = E S u (eq. (3.1), S Hermitian positive
+    definite) below E_CUT, by LAPACK's generalized Hermitian solver; asserts
+    that exactly n_vac sentinel eigenvalues were dropped."""
+    E = eigh(H, S, eigvals_only=True)
+    keep = E < E_CUT
+    if int((~keep).sum()) != n_vac:
+        raise AssertionError("sentinel eigenvalue count differs from vacancy count")
+    return np.sort(E[keep])
+
+
 def band_energies(N: int, K: int, mask, prm) -> np.ndarray:
-    """float64[K^2, n_act]: E_n(k) for every grid point (graphene model)."""
+    """float64[K^2, n_act]: E_n(k) for every grid point (graphene model); with
+    a nonzero overlap prm["s"] the generalized problem H u = E S u of
+    eq. (3.1)-(3.2d)."""
     mask = np.asarray(mask, dtype=np.uint8)
     n_vac = int(mask.sum())
     ks = lattice.kpoints(N, K, prm["a"])
+    s = float(prm.get("s", 0.0))
     out = []
     for k in ks:
         H = hamiltonian.hamiltonian(N, k, mask, prm["t"], prm["eps_onsite"], prm["a"], prm["sentinel"])
-        out.append(eigenvalues(H, n_vac))
+        if s != 0.0:
+            out.append(generalized_eigenvalues(H, hamiltonian.overlap(N, k, mask, s, prm["a"]), n_vac))
+        else:
+            out.append(eigenvalues(H, n_vac))
     return np.array(out)
 
 
@@ -88,3 +106,18 @@ def sample_idos(N: int, K: int, mask, prm) -> np.ndarray:
     en = energy_grid(prm["e_min"], prm["e_max"], prm["n_E"])
     return idos_from_bands(E, lattice.supercell_area(N, prm["a"]), en, prm["delta"],
                            prm.get("smoothing", "gauss"))
+
+
+def dos_from_idos(Q, e_min: float, e_max: float) -> np.ndarray:
+    """Density of states from an IDoS on the uniform grid by numerical
+    differentiation (Sec. 4.3): central differences (Q_{j+1} - Q_{j-1})/(2h)
+    inside, one-sided differences at the two ends; h = (e_max - e_min)/(n_E - 1)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    n = Q.shape[-1]
+    h = (e_max - e_min) / (n - 1)
+    D = np.empty_like(Q)
+    D[..., 1:-1] = (Q[..., 2:] - Q[..., :-2]) / (2.0 * h)
+    D[..., 0] = (Q[..., 1] - Q[..., 0]) / h
+    D[..., -1] = (Q[..., -1] - Q[..., -2]) / h
+    return D
+

@@ -183,3 +183,54 @@ def test_corner_tiling_identity(Nf, K):
     qf = idos.sample_idos(Nf, K, fine, P)
     qc = idos.sample_idos(h, 2 * K, c, P)
     assert np.allclose(qf, qc, atol=1e-12)
+
+
+# ---- overlap s != 0 (eq. (3.2c)-(3.2d)) and the DoS -----------------------
+S_OV = 0.129
+T_PAPER = -3.033
+
+
+def test_overlap_n1_closed_form():
+    """With S_AB = s f, H_AB = t f (f = sum of the three bond phases), the 2x2
+    generalized problem has E = (eps + t|f|)/(1 + s|f|) and (eps - t|f|)/(1 - s|f|)."""
+    rng = np.random.default_rng(4)
+    av = lattice.primitive_vectors(A)
+    for _ in range(10):
+        k = random_k(rng, 1)
+        mask = np.zeros(2, np.uint8)
+        H = hamiltonian.hamiltonian(1, k, mask, T_PAPER, 0.0, A, 1e3)
+        S = hamiltonian.overlap(1, k, mask, S_OV, A)
+        f = abs(1 + np.exp(1j * (k @ av[0])) + np.exp(1j * (k @ av[1])))
+        ref = np.sort([T_PAPER * f / (1 + S_OV * f), -T_PAPER * f / (1 - S_OV * f)])
+        assert np.allclose(idos.generalized_eigenvalues(H, S, 0), ref, atol=1e-12)
+
+
+def test_overlap_zero_is_the_standard_problem():
+    rng = np.random.default_rng(5)
+    N = 3
+    mask = (rng.random(2 * N * N) < 0.2).astype(np.uint8)
+    p0 = prm(s=0.0)
+    p1 = prm(s=1e-14)
+    assert np.allclose(idos.band_energies(N, 2, mask, p0), idos.band_energies(N, 2, mask, p1), atol=1e-11)
+
+
+def test_overlap_generalized_eigenpairs_solve_the_pencil():
+    rng = np.random.default_rng(6)
+    N = 2
+    mask = np.array([0, 1, 0, 0, 0, 0, 1, 0], dtype=np.uint8)
+    k = random_k(rng, N)
+    H = hamiltonian.hamiltonian(N, k, mask, T_PAPER, 0.0, A, 1e3)
+    S = hamiltonian.overlap(N, k, mask, S_OV, A)
+    assert np.allclose(S, S.conj().T) and np.min(np.linalg.eigvalsh(S)) > 1 - 3 * S_OV - 1e-12
+    for E in idos.generalized_eigenvalues(H, S, 2):
+        sv = np.linalg.svd(H - E * S, compute_uv=False)
+        assert sv[-1] < 1e-9 * np.max(sv)
+
+
+def test_dos_differentiation_is_exact_on_quadratics():
+    e = idos.energy_grid(-3.0, 5.0, 33)
+    Q = 0.7 * e ** 2 - 1.3 * e + 2.0
+    D = idos.dos_from_idos(Q, -3.0, 5.0)
+    assert np.allclose(D[1:-1], 1.4 * e[1:-1] - 1.3, atol=1e-12)
+    h = e[1] - e[0]
+    assert np.isclose(D[0], (Q[1] - Q[0]) / h) and np.isclose(D[-1], (Q[-1] - Q[-2]) / h)
