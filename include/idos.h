@@ -115,6 +115,12 @@ typedef struct idos_model_desc {
                           -1 = library default (48).  Rounded up to the
                           device's partition granularity (8 SMs on sm_103).
                           Results do not depend on it.                       */
+  double overlap_s;    /* graphene: nearest-neighbour overlap s of eq. (3.2c)-
+                          (3.2d), |s| < 1/3; 0 = the standard problem.  With
+                          S = I + s B and H = eps_onsite I + t B (B the bond-
+                          phase matrix on the kept sites) the generalized
+                          eigenvalues of eq. (3.1) are E = (eps_onsite + l) /
+                          (1 + (s/t) l), l the eigenvalues of t B.           */
 } idos_model_desc;
 
 typedef struct idos_model idos_model;
@@ -273,6 +279,13 @@ int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int
  * rounded to float32.  Allocates and frees its own device buffers; blocking. */
 int idos_her2k(int tc_products, int n, int64_t batch, const double* A, const double* Y, const double* Z,
                double* A_out);
+
+/* Density of states from an IDoS on the uniform energy grid (host float64
+ * Q[n_E], n_E >= 2) by numerical differentiation, as the paper suggests for
+ * the expected IDoS: central differences (Q[j+1] - Q[j-1]) / (2h) inside,
+ * one-sided differences at the ends, h = (e_max - e_min) / (n_E - 1); dos:
+ * host float64[n_E].  Host arithmetic only (no device needed). */
+int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, double* dos);
 
 /* ---- serving ----
  * A request loop over the level sampler (a scheduler thread inside the

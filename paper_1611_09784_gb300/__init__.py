@@ -8,5 +8,5 @@ library has not been built: there is no CPU fallback.
 """
 from .binding import (  # noqa: F401
     FP32_REFINE64, FP64, GRAPHENE, SMOOTH_GAUSS, SMOOTH_POLY, TMDC, IdosError, Model, Server, create_model,
-    eigvalsh, her2k, lib_path, load_library, status_string,
+    dos_from_idos, eigvalsh, her2k, lib_path, load_library, status_string,
 )

@@ -31,7 +31,7 @@ class ModelDesc(C.Structure):
         ("t", C.c_double), ("eps_onsite", C.c_double), ("a", C.c_double), ("p", C.c_double),
         ("sentinel", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double), ("delta", C.c_double),
         ("n_E", C.c_int32), ("refine64_iters", C.c_int32), ("model_seed", C.c_uint64),
-        ("workspace_bytes", C.c_int64), ("tc_products", C.c_int32), ("sm_split", C.c_int32),
+        ("workspace_bytes", C.c_int64), ("tc_products", C.c_int32), ("sm_split", C.c_int32), ("overlap_s", C.c_double),
     ]
 
 
@@ -83,6 +83,7 @@ _SYMBOLS = {
     "idos_server_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int64)]),
     "idos_server_destroy": (None, [C.c_void_p]),
+    "idos_dos_from_idos": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p]),
     "idos_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "idos_profile_count": (C.c_int, []),
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -154,6 +155,7 @@ def make_desc(cfg: dict) -> ModelDesc:
     d.workspace_bytes = int(cfg.get("workspace_bytes", 0))
     d.tc_products = int(cfg.get("tc_products", DEFAULT_TC_PRODUCTS))
     d.sm_split = int(cfg.get("sm_split", -1))
+    d.overlap_s = float(cfg.get("s", 0.0))
     return d
 
 
@@ -332,6 +334,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def dos_from_idos(Q, e_min: float, e_max: float):
+    """Density of states from an IDoS on the uniform grid (idos_dos_from_idos)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    out = np.empty_like(Q)
+    _check(load_library().idos_dos_from_idos(_ptr(Q), Q.shape[-1], e_min, e_max, _ptr(out)), "idos_dos_from_idos")
+    return out
 
 
 def create_model(cfg: dict, stream: int | None = None) -> Model:

@@ -90,6 +90,9 @@ int validate(const idos_model_desc* d) {
   if (d->tc_products != 0 && d->tc_products != 3 && d->tc_products != 6)
     return bad("tc_products must be 0, 3 or 6");
   if (d->sm_split < -1 || d->sm_split > 4096) return bad("sm_split must be -1, 0 or a positive SM count");
+  if (!(std::fabs(d->overlap_s) < 1.0 / 3.0)) return bad("overlap_s must satisfy |s| < 1/3 (S positive definite)");
+  if (d->overlap_s != 0.0 && d->kind != IDOS_GRAPHENE) return bad("overlap_s applies to the graphene model only");
+  if (d->overlap_s != 0.0 && d->t == 0.0) return bad("overlap_s needs a nonzero hopping t");
   return IDOS_OK;
 }
 
@@ -120,7 +123,8 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.n_max = n_max;
   a.n_mat = n_mat;
   a.t = M->d.t;
-  a.eps = M->d.eps_onsite;
+  // with an overlap the solve runs on t B; eps enters through the map below
+  a.eps = M->d.overlap_s != 0.0 ? 0.0 : M->d.eps_onsite;
   a.d = d;
   a.e2 = e2;
   a.stream = st;
@@ -134,6 +138,8 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   if (M->d.kind == IDOS_GRAPHENE && small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
   IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
+  if (M->d.overlap_s != 0.0)
+    IDOS_TRY(launch_overlap_map(eigs, cells.n_act, K2, n_max, n_mat, M->d.eps_onsite, M->d.overlap_s / M->d.t, st));
   const double area = (double)cells.N * cells.N * cell_area(M->d.a);
   IDOS_TRY(launch_idos(eigs, cells.n_act, K2, n_max, cells.count, area, grid_of(M->d), Q, st));
   if (eigs_keep) *eigs_keep = eigs;
@@ -768,3 +774,16 @@ int idos_get_partition(const idos_model* m, int* sms_finest, int* sms_rest, cons
   if (why) *why = m->part_note.c_str();
   return IDOS_OK;
 }
+
+int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, double* dos) {
+  if (!Q || !dos || n_E < 2 || !(e_max > e_min)) {
+    set_error("null array, n_E < 2 or e_max <= e_min");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  const double h = (e_max - e_min) / (n_E - 1);
+  for (int j = 1; j + 1 < n_E; ++j) dos[j] = (Q[j + 1] - Q[j - 1]) / (2.0 * h);
+  dos[0] = (Q[1] - Q[0]) / h;
+  dos[n_E - 1] = (Q[n_E - 1] - Q[n_E - 2]) / h;
+  return IDOS_OK;
+}
+

@@ -148,6 +148,11 @@ int launch_bisect(int precision, int refine64_iters, const void* d, const void* 
                   const int* n_act_cell, int K2, int n_max, int64_t n_mat, double* eigs,
                   cudaStream_t s);
 
+// Overlap s != 0 (graphene): eigenvalues l of t B -> generalized eigenvalues
+// (eps + l) / (1 + sigma l), sigma = s / t, kept ascending.
+int launch_overlap_map(double* eigs, const int* n_act_cell, int K2, int n_max, int64_t n_mat, double eps,
+                       double sigma, cudaStream_t s);
+
 // Smoothed IDoS per cell (eq. (4.1)-(4.2)): Q[cell][n_E].
 struct EnergyGrid { double e_min, e_max, delta; int n_E; int smoothing; int fp32_erfc; };
 int launch_idos(const double* eigs, const int* n_act_cell, int K2, int n_max, int64_t n_cells,

@@ -235,6 +235,40 @@ int bisect_t(int refine, const void* d, const void* e2, const int* n_act_cell, i
 
 }  // namespace
 
+// Generalized eigenvalues of the graphene pencil (H, S) = (eps I + t B,
+// I + s B): E = (eps + l) / (1 + sigma l), sigma = s / t, l the eigenvalues of
+// t B (ascending on entry).  The map is monotone, increasing when
+// 1 - sigma eps > 0 and decreasing otherwise; thread i maps the pair (i,
+// n-1-i) and writes it back ascending either way.
+__global__ void k_overlap_map(double* __restrict__ eigs, const int* __restrict__ n_act_cell, int K2, int n_max,
+                              int64_t n_mat, double eps, double sigma) {
+  const int64_t mat = blockIdx.x;
+  if (mat >= n_mat) return;
+  const int n = n_act_cell ? n_act_cell[mat / K2] : n_max;
+  double* e = eigs + mat * n_max;
+  const bool rev = 1.0 - sigma * eps < 0.0;
+  for (int i = threadIdx.x; i < (n + 1) / 2; i += blockDim.x) {
+    const int jj = n - 1 - i;
+    const double a = e[i], b = e[jj];
+    const double fa = (eps + a) / (1.0 + sigma * a), fb = (eps + b) / (1.0 + sigma * b);
+    if (rev) {
+      e[i] = fb;
+      e[jj] = fa;
+    } else {
+      e[i] = fa;
+      e[jj] = fb;
+    }
+  }
+}
+
+int launch_overlap_map(double* eigs, const int* n_act_cell, int K2, int n_max, int64_t n_mat, double eps,
+                       double sigma, cudaStream_t s) {
+  if (n_mat == 0) return IDOS_OK;
+  k_overlap_map<<<(unsigned)n_mat, 128, 0, s>>>(eigs, n_act_cell, K2, n_max, n_mat, eps, sigma);
+  IDOS_CHECK_LAUNCH();
+  return IDOS_OK;
+}
+
 int launch_bisect(int precision, int refine64_iters, const void* d, const void* e2,
                   const int* n_act_cell, int K2, int n_max, int64_t n_mat, double* eigs,
                   cudaStream_t s) {

@@ -3,6 +3,7 @@
 // memory.  Its scratch (kept-site maps, tridiagonals, eigenvalues) lives in
 // one file-scope static device array instead of a model's workspace, so the
 // call itself performs no cudaMalloc / cudaFree and needs no model handle.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -85,6 +86,8 @@ int check_desc(const idos_model_desc* d) {
   if (!(d->delta > 0.0) || !(d->e_max > d->e_min) || !(d->a > 0.0)) return bad("delta, energy range or a");
   if (d->n_E < 2 || d->n_E > 1024) return bad("n_E must lie in 2..1024");
   if (d->refine64_iters < 0 || d->refine64_iters > 64) return bad("refine64_iters must lie in 0..64");
+  if (!(std::fabs(d->overlap_s) < 1.0 / 3.0) || (d->overlap_s != 0.0 && d->t == 0.0))
+    return bad("overlap_s must satisfy |s| < 1/3 with a nonzero t");
   return IDOS_OK;
 }
 
@@ -140,12 +143,13 @@ extern "C" int idos_eval_idos_noalloc(const idos_model_desc* d, int N, int Kside
   a.n_max = n_sites;
   a.n_mat = K2;
   a.t = d->t;
-  a.eps = d->eps_onsite;
+  a.eps = d->overlap_s != 0.0 ? 0.0 : d->eps_onsite;
   a.d = dd;
   a.e2 = e2;
   a.stream = s;
   IDOS_TRY(solve_small(d->precision, a));
   IDOS_TRY(launch_bisect(d->precision, d->refine64_iters, dd, e2, cells.n_act, K2, n_sites, K2, eigs, s));
+  if (d->overlap_s != 0.0) IDOS_TRY(launch_overlap_map(eigs, cells.n_act, K2, n_sites, K2, d->eps_onsite, d->overlap_s / d->t, s));
   const double area = (double)N * N * cell_area(d->a);
   const EnergyGrid g{d->e_min, d->e_max, d->delta, d->n_E, d->smoothing, d->precision == IDOS_FP32_REFINE64 ? 1 : 0};
   IDOS_TRY(launch_idos(eigs, cells.n_act, K2, n_sites, 1, area, g, idos_dev_out, s));

@@ -62,3 +62,18 @@ def test_no_oracle_import_in_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_dos_from_idos_matches_oracle():
+    """idos_dos_from_idos is host arithmetic (no device): central differences
+    of the IDoS against the oracle's."""
+    import numpy as np
+    import paper_1611_09784_gb300 as pkg
+    from oracle import idos as oidos
+    rng = np.random.default_rng(3)
+    Q = np.cumsum(rng.random(201)) * 1e-3
+    got = pkg.dos_from_idos(Q, -9.0, 9.0)
+    ref = oidos.dos_from_idos(Q, -9.0, 9.0)
+    assert np.allclose(got, ref, rtol=1e-14, atol=0)
+    with pytest.raises(pkg.IdosError):
+        pkg.dos_from_idos(Q[:1], -9.0, 9.0)
