@@ -422,6 +422,10 @@ def run_gpu(args):
     eig_step = sum(Ml * eigsolves_per_sample(levels, l) for l, Ml in enumerate(M))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # the project's autotuner picks the SM partition and the small/two-stage
+    # cutoff for this allocation (timed on sample indices outside the run's)
+    tuning = model.autotune(M, reps=1)
+
     def step(idx):
         # every level of the allocation at once (concurrent level streams)
         model.sample_levels(M, seed, [idx * Ml for Ml in M])
@@ -570,6 +574,7 @@ def run_gpu(args):
             "rooflines": roofs,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "autotune": tuning,
             "serving": serve,
             "tmdc_sweep": sweep,
             "stress": stress_line,

@@ -287,6 +287,28 @@ int idos_her2k(int tc_products, int n, int64_t batch, const double* A, const dou
  * host float64[n_E].  Host arithmetic only (no device needed). */
 int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, double* dos);
 
+/* ---- autotuning ----
+ * Times idos_sample_levels(n_samples) on this model for every candidate
+ * configuration and installs the fastest: the SMs reserved for the finest
+ * level (sm_split: 0, 24, 32, 40, 48, 56, 64 where the device allows) and the
+ * largest n the shared-memory kernel takes before the two-stage path (64, or
+ * whatever fits: 160 float32 / 112 float64).  Each candidate runs once
+ * untimed and `reps` times timed (best kept), on sample indices from 2^40 on;
+ * the level statistics are restored afterwards.  Results do not depend on the
+ * choice beyond float rounding of the path choice; out: the choice and every
+ * candidate's best step time. */
+#define IDOS_TUNE_MAX 32
+typedef struct idos_tuning {
+  int32_t sm_split;      /* chosen SMs reserved for the finest level (0 = shared) */
+  int32_t small_max_n;   /* chosen limit of the shared-memory kernel (-1 = what fits) */
+  double best_ms;        /* step time of the chosen configuration */
+  int32_t n_tried;
+  int32_t tried_split[IDOS_TUNE_MAX];
+  int32_t tried_small[IDOS_TUNE_MAX];
+  double tried_ms[IDOS_TUNE_MAX];
+} idos_tuning;
+int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
+
 /* ---- serving ----
  * A request loop over the level sampler (a scheduler thread inside the
  * library).  Requests arrive from any host thread; they are admitted in

@@ -41,6 +41,15 @@ class MlmcOpts(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+TUNE_MAX = 32
+
+
+class Tuning(C.Structure):
+    _fields_ = [("sm_split", C.c_int32), ("small_max_n", C.c_int32), ("best_ms", C.c_double),
+                ("n_tried", C.c_int32), ("tried_split", C.c_int32 * TUNE_MAX), ("tried_small", C.c_int32 * TUNE_MAX),
+                ("tried_ms", C.c_double * TUNE_MAX)]
+
+
 class Estimate(C.Structure):
     _fields_ = [("mean", C.POINTER(C.c_double)), ("var", C.POINTER(C.c_double)),
                 ("M", C.POINTER(C.c_int64)), ("V", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
@@ -84,6 +93,7 @@ _SYMBOLS = {
                                    C.POINTER(C.c_int64)]),
     "idos_server_destroy": (None, [C.c_void_p]),
     "idos_dos_from_idos": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p]),
+    "idos_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Tuning)]),
     "idos_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "idos_profile_count": (C.c_int, []),
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -215,6 +225,16 @@ class Model:
                                                        _ptr(Y), _ptr(Qf), _ptr(Qc)),
                "idos_sample_level_detail")
         return Y, Qf, Qc
+
+    def autotune(self, n_samples, reps: int = 1):
+        """idos_autotune: time every candidate configuration on this allocation
+        and install the fastest; returns the choice and the timings."""
+        n = np.ascontiguousarray(list(n_samples) + [0] * (self.n_levels - len(n_samples)), dtype=np.int64)
+        t = Tuning()
+        _check(load_library().idos_autotune(self._h, _ptr(n), reps, C.byref(t)), "idos_autotune")
+        tried = [{"sm_split": t.tried_split[i], "small_max_n": t.tried_small[i], "ms": round(t.tried_ms[i], 3)}
+                 for i in range(t.n_tried)]
+        return {"sm_split": t.sm_split, "small_max_n": t.small_max_n, "best_ms": round(t.best_ms, 3), "tried": tried}
 
     def get_partition(self):
         """(SMs of the finest level, SMs of the others, reason when unsplit)."""

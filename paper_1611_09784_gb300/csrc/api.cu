@@ -102,6 +102,12 @@ EnergyGrid grid_of(const idos_model_desc& d) {
   return EnergyGrid{d.e_min, d.e_max, d.delta, d.n_E, d.smoothing, d.precision == IDOS_FP32_REFINE64 ? 1 : 0};
 }
 
+// The shared-memory kernel takes graphene matrices up to what fits (or up to
+// the model's tuned limit); everything else goes through the two-stage path.
+bool use_small_path(const Model* M, int n) {
+  return M->d.kind == IDOS_GRAPHENE && small_path_fits(M->d.precision, n) && (M->small_max_n < 0 || n <= M->small_max_n);
+}
+
 // Eigen-solve + IDoS of every cell of `cells` on a Kside grid: Q[count][n_E].
 // `eigs_keep` (optional) receives the device eigenvalue buffer pointer.
 int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double** eigs_keep, cudaStream_t st,
@@ -135,7 +141,7 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.tmdc_p = M->tmdc_p;
   a.sm_avail = sm_avail;
   a.max_cluster = sm_avail ? 8 : 16;
-  if (M->d.kind == IDOS_GRAPHENE && small_path_fits(M->d.precision, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
+  if (use_small_path(M, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
   IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
   if (M->d.overlap_s != 0.0)
@@ -174,7 +180,7 @@ size_t solve_bytes(int precision, int N, int Kside, int64_t count, int n_E, int 
 // Room the large-matrix path wants for its dense batch (0 if the small path runs).
 size_t large_room(const Model* M, int N, int Kside, int64_t count) {
   const int n = orb_per_cell(M->d.kind) * N * N;
-  if (M->d.kind == IDOS_GRAPHENE && small_path_fits(M->d.precision, n)) return 0;
+  if (use_small_path(M, n)) return 0;
   const size_t one = large_path_bytes(M->d.precision, n, 1);
   const size_t cap = M->d.workspace_bytes > 0 ? (size_t)M->d.workspace_bytes : kDefaultWorkspace;
   const size_t want = large_path_bytes(M->d.precision, n, count * (int64_t)Kside * Kside);
@@ -264,6 +270,41 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     M->M[level] += n_samples;
     M->seconds[level] += ms * 1e-3;
   }
+  return IDOS_OK;
+}
+
+// (Re)builds the partitioned level streams for `split` SMs reserved for the
+// finest level (0: none).  A partition the driver cannot make leaves every
+// level on all SMs and records why.
+int apply_partition(Model* m, int split) {
+  const int L = m->d.n_levels;
+  for (int l = 0; l < L; ++l) {
+    if (m->pstream[l]) {
+      IDOS_CUDA_TRY(cudaStreamSynchronize(m->pstream[l]));
+      IDOS_CUDA_TRY(cudaStreamDestroy(m->pstream[l]));
+      m->pstream[l] = nullptr;
+    }
+    m->lsms[l] = 0;
+  }
+  partition_destroy(m->part);
+  m->sm_split_now = 0;
+  m->part_note.clear();
+  if (split <= 0 || L < 2 || split >= m->sm_count) return IDOS_OK;
+  if (partition_create(split, m->part) != IDOS_OK) {
+    m->part_note = get_error();
+    set_error("");
+    return IDOS_OK;
+  }
+  int prio_least = 0, prio_greatest = 0;
+  IDOS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+  for (int l = 0; l < L; ++l) {
+    int prio = prio_greatest + (L - 1 - l);
+    if (prio > prio_least) prio = prio_least;
+    const int which = l == L - 1 ? 0 : 1;
+    IDOS_TRY(partition_stream(m->part, which, prio, &m->pstream[l]));
+    m->lsms[l] = m->part.sms[which];
+  }
+  m->sm_split_now = m->part.sms[0];
   return IDOS_OK;
 }
 
@@ -371,32 +412,17 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
   // whenever the many-matrix levels release an SM.
   int prio_least = 0, prio_greatest = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
-  // SM partition: the finest level on a reserved set of SMs, the others on
-  // the rest (a failure to create it leaves every level on all SMs)
-  const int split = d->sm_split == -1 ? kDefaultSmSplit : d->sm_split;
-  bool parted = false;
-  if (e == cudaSuccess && split > 0 && d->n_levels >= 2 && split < sms) {
-    parted = partition_create(split, m->part) == IDOS_OK;
-    if (!parted) {
-      m->part_note = get_error();
-      set_error("");
-    }
-  }
   for (int l = 0; l < d->n_levels && e == cudaSuccess; ++l) {
     int prio = prio_greatest + (d->n_levels - 1 - l);   // greatest priority is the lowest number
     if (prio > prio_least) prio = prio_least;
-    if (parted) {
-      const int which = l == d->n_levels - 1 ? 0 : 1;
-      if (partition_stream(m->part, which, prio, &m->pstream[l]) != IDOS_OK) {
-        e = cudaErrorUnknown;
-        break;
-      }
-      m->lsms[l] = m->part.sms[which];
-    }
     e = cudaStreamCreateWithPriority(&m->lstream[l], cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev0[l]);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev1[l]);
   }
+  // SM partition: the finest level on a reserved set of SMs, the others on
+  // the rest (a failure to create it leaves every level on all SMs)
+  if (e == cudaSuccess && apply_partition(m, d->sm_split == -1 ? kDefaultSmSplit : d->sm_split) != IDOS_OK)
+    e = cudaErrorUnknown;
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) {
     set_error(std::string("model allocation: ") + cudaGetErrorString(e));
@@ -785,5 +811,77 @@ int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, dou
   dos[0] = (Q[1] - Q[0]) / h;
   dos[n_E - 1] = (Q[n_E - 1] - Q[n_E - 2]) / h;
   return IDOS_OK;
+}
+
+int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out) {
+  if (!m || !n_samples || !out || reps < 1 || reps > 100) {
+    set_error("null argument or reps outside 1..100");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  const int L = m->d.n_levels, n_E = m->d.n_E;
+  // keep the caller's statistics
+  std::vector<double> acc_saved((size_t)2 * n_E * L);
+  IDOS_CUDA_TRY(cudaMemcpyAsync(acc_saved.data(), m->acc, sizeof(double) * acc_saved.size(), cudaMemcpyDeviceToHost,
+                                m->stream));
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  int64_t M_saved[IDOS_MAX_LEVELS];
+  double sec_saved[IDOS_MAX_LEVELS];
+  std::copy(m->M, m->M + IDOS_MAX_LEVELS, M_saved);
+  std::copy(m->seconds, m->seconds + IDOS_MAX_LEVELS, sec_saved);
+  const int splits[] = {0, 24, 32, 40, 48, 56, 64};
+  bool has_mid = false;   // a level (or corner) size where the two kernels compete
+  for (int l = 0; l < L; ++l) {
+    const int nf = orb_per_cell(m->d.kind) * m->d.N[l] * m->d.N[l];
+    const int nc = l > 0 ? nf / 4 : 0;
+    for (int n : {nf, nc})
+      if (n > 64 && m->d.kind == IDOS_GRAPHENE && small_path_fits(m->d.precision, n)) has_mid = true;
+  }
+  const int smalls[] = {-1, 64};
+  out->n_tried = 0;
+  out->best_ms = 1e300;
+  int best_split = m->sm_split_now, best_small = m->small_max_n;
+  int64_t first[IDOS_MAX_LEVELS];
+  int64_t round = 0;
+  int rc = IDOS_OK;
+  for (int sm : smalls) {
+    if (sm == 64 && !has_mid) continue;
+    for (int sp : splits) {
+      if (sp >= m->sm_count || (sp > 0 && L < 2) || out->n_tried >= IDOS_TUNE_MAX) continue;
+      m->small_max_n = sm;
+      rc = apply_partition(m, sp);
+      if (rc != IDOS_OK) break;
+      if (sp > 0 && m->sm_split_now == 0) continue;   // the driver could not make this split
+      double best = 1e300;
+      for (int r = 0; r <= reps && rc == IDOS_OK; ++r) {
+        for (int l = 0; l < L; ++l) first[l] = (int64_t(1) << 40) + (round++) * (n_samples[l] + 1);
+        const auto t0 = std::chrono::steady_clock::now();
+        rc = idos_sample_levels(m, n_samples, 0x5eedull, first);
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (r > 0) best = std::min(best, ms);   // r = 0 warms the configuration up
+      }
+      if (rc != IDOS_OK) break;
+      const int i = out->n_tried++;
+      out->tried_split[i] = m->sm_split_now;
+      out->tried_small[i] = sm;
+      out->tried_ms[i] = best;
+      if (best < out->best_ms) {
+        out->best_ms = best;
+        best_split = sp;
+        best_small = sm;
+      }
+    }
+    if (rc != IDOS_OK) break;
+  }
+  // install the winner and restore the caller's statistics
+  m->small_max_n = best_small;
+  const int rc2 = apply_partition(m, best_split);
+  IDOS_CUDA_TRY(cudaMemcpyAsync(m->acc, acc_saved.data(), sizeof(double) * acc_saved.size(), cudaMemcpyHostToDevice,
+                                m->stream));
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  std::copy(M_saved, M_saved + IDOS_MAX_LEVELS, m->M);
+  std::copy(sec_saved, sec_saved + IDOS_MAX_LEVELS, m->seconds);
+  out->sm_split = m->sm_split_now;
+  out->small_max_n = m->small_max_n;
+  return rc != IDOS_OK ? rc : rc2;
 }
 

@@ -112,6 +112,8 @@ struct Model {
   SmPartition part;               // SM split of idos_sample_levels (ctx null: shared SMs)
   std::string part_note;          // why there is no split (empty when there is one or none was asked)
   int lsms[IDOS_MAX_LEVELS] = {};  // SMs of each level stream's partition (0: whole device)
+  int sm_split_now = 0;           // SMs reserved for the finest level now (0: no partition)
+  int small_max_n = -1;           // largest n on the shared-memory kernel (-1: whatever fits)
   double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream

@@ -210,3 +210,30 @@ def test_sm_partition_is_default_and_does_not_change_results():
     for a, b in zip(stats[0], stats[-1]):
         assert a[0] == b[0]
         assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_autotune_picks_the_fastest_and_restores_statistics():
+    import paper_1611_09784_gb300 as pkg
+    w, cfg, prm = cfg_and_prm(precision="fp32")
+    m = pkg.create_model(cfg)
+    m.sample_level(0, 7, w["seed"], 0)
+    before = m.get_level_stats(0)
+    tune = m.autotune([40, 4, 2, 1], reps=1)
+    after = m.get_level_stats(0)
+    assert after[0] == before[0] and np.array_equal(after[1], before[1]) and np.array_equal(after[2], before[2])
+    assert tune["tried"]
+    assert abs(tune["best_ms"] - min(t["ms"] for t in tune["tried"])) < 1e-3
+    fin, rest, _ = m.get_partition()
+    assert fin == tune["sm_split"]
+    # the tuned model still gives the per-level results (same or path-rounding close)
+    counts, firsts = [5, 3, 2, 1], [70, 71, 72, 73]
+    m.reset_level_stats(-1)
+    m.sample_levels(counts, w["seed"], firsts)
+    tuned = [m.get_level_stats(l)[1] for l in range(4)]
+    m.close()
+    ref = pkg.create_model(dict(cfg, sm_split=0))
+    ref.sample_levels(counts, w["seed"], firsts)
+    for l in range(4):
+        s1 = ref.get_level_stats(l)[1]
+        assert np.max(np.abs(tuned[l] - s1)) <= 1e-9 * max(1.0, np.max(np.abs(s1)))
+    ref.close()
