@@ -424,7 +424,7 @@ def run_gpu(args):
 
     # the project's autotuner picks the SM partition and the small/two-stage
     # cutoff for this allocation (timed on sample indices outside the run's)
-    tuning = model.autotune(M, reps=1)
+    tuning = model.autotune(M, reps=1) if args.sm_split < 0 else {"fixed_sm_split": args.sm_split}
 
     def step(idx):
         # every level of the allocation at once (concurrent level streams)

@@ -203,7 +203,8 @@ int check_status_word(const int* err) {
 // otherwise the caller does that after synchronising ev1.
 int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh, double* Qfh,
               double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, bool blocking,
-              int sm_avail = 0, double* acc_out = nullptr) {
+              int sm_avail = 0, double* acc_out = nullptr, cudaStream_t st2 = nullptr, cudaEvent_t fork2 = nullptr,
+              cudaEvent_t join2 = nullptr) {
   const idos_model_desc& d = M->d;
   const int Nf = d.N[level], Kf = d.Kside[level];
   const bool coarse = level > 0;
@@ -219,8 +220,14 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
   IDOS_CUDA_TRY(cudaEventRecord(ev0, st));
   for (int64_t s0 = 0; s0 < n_samples; s0 += chunk) {
     const int64_t S = std::min(chunk, n_samples - s0);
+    // With a second stream the corners' solve runs beside the fine one, from
+    // a slice of the workspace of its own (both large rooms are needed).
+    const bool two = coarse && st2 && fork2 && join2;
+    const size_t coarse_slice =
+        two ? solve_bytes(d.precision, Nc, Kc, 4 * S, n_E, d.kind) + large_room(M, Nc, Kc, 4 * S) + 64 * 1024 : 0;
     const size_t need = S * per_sample + 64 * 1024 + ((S + 63) / 64) * 2 * n_E * 8 +
-                        std::max(large_room(M, Nf, Kf, S), coarse ? large_room(M, Nc, Kc, 4 * S) : 0);
+                        (two ? large_room(M, Nf, Kf, S) + coarse_slice
+                             : std::max(large_room(M, Nf, Kf, S), coarse ? large_room(M, Nc, Kc, 4 * S) : 0));
     IDOS_TRY(ws.reserve(need, st));
     ws.reset();
     CellSet fine, crs;
@@ -247,12 +254,26 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     // the large path takes its dense batch from whatever is left, so the
     // bigger solve goes last
     const size_t mark = ws.used;
-    if (coarse) {
-      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st, ws, err, sm_avail));
+    if (two) {
+      Arena sub;   // a view of part of ws, never reserved or released itself
+      sub.base = ws.take<char>(coarse_slice);
+      sub.cap = sub.base ? coarse_slice : 0;
+      if (!sub.base) { set_error("workspace (corner solve)"); return IDOS_ERR_OUT_OF_MEMORY; }
+      IDOS_CUDA_TRY(cudaEventRecord(fork2, st));
+      IDOS_CUDA_TRY(cudaStreamWaitEvent(st2, fork2, 0));
+      IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st2, sub, err, sm_avail));
+      IDOS_CUDA_TRY(cudaEventRecord(join2, st2));
+      IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err, sm_avail));
+      IDOS_CUDA_TRY(cudaStreamWaitEvent(st, join2, 0));
+      ws.used = mark;
+    } else {
+      if (coarse) {
+        IDOS_TRY(solve_and_idos(M, crs, Kc, Qc, nullptr, st, ws, err, sm_avail));
+        ws.used = mark;
+      }
+      IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err, sm_avail));
       ws.used = mark;
     }
-    IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err, sm_avail));
-    ws.used = mark;
     double* acc = acc_out ? acc_out : M->acc + (size_t)level * 2 * n_E;
     IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, ws, st));
     if (Yh) IDOS_CUDA_TRY(cudaMemcpyAsync(Yh + s0 * n_E, Y, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, st));
@@ -279,10 +300,12 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
 int apply_partition(Model* m, int split) {
   const int L = m->d.n_levels;
   for (int l = 0; l < L; ++l) {
-    if (m->pstream[l]) {
-      IDOS_CUDA_TRY(cudaStreamSynchronize(m->pstream[l]));
-      IDOS_CUDA_TRY(cudaStreamDestroy(m->pstream[l]));
-      m->pstream[l] = nullptr;
+    for (cudaStream_t* sp : {&m->pstream[l], &m->pstream2[l]}) {
+      if (*sp) {
+        IDOS_CUDA_TRY(cudaStreamSynchronize(*sp));
+        IDOS_CUDA_TRY(cudaStreamDestroy(*sp));
+        *sp = nullptr;
+      }
     }
     m->lsms[l] = 0;
   }
@@ -302,6 +325,7 @@ int apply_partition(Model* m, int split) {
     if (prio > prio_least) prio = prio_least;
     const int which = l == L - 1 ? 0 : 1;
     IDOS_TRY(partition_stream(m->part, which, prio, &m->pstream[l]));
+    IDOS_TRY(partition_stream(m->part, which, prio, &m->pstream2[l]));
     m->lsms[l] = m->part.sms[which];
   }
   m->sm_split_now = m->part.sms[0];
@@ -406,6 +430,9 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->stream2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join2, cudaEventDisableTiming);
   // Level streams get scheduling priorities by cost: the finest level's few
   // large matrices form the critical path of a concurrent step (long chains
   // of small, latency-bound launches), so its blocks are dispatched first
@@ -416,8 +443,11 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
     int prio = prio_greatest + (d->n_levels - 1 - l);   // greatest priority is the lowest number
     if (prio > prio_least) prio = prio_least;
     e = cudaStreamCreateWithPriority(&m->lstream[l], cudaStreamNonBlocking, prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&m->lstream2[l], cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev0[l]);
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev1[l]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->lfork2[l], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ljoin2[l], cudaEventDisableTiming);
   }
   // SM partition: the finest level on a reserved set of SMs, the others on
   // the rest (a failure to create it leaves every level on all SMs)
@@ -442,15 +472,25 @@ void idos_destroy_model(idos_model* m) {
   if (m->ev0) cudaEventDestroy(m->ev0);
   if (m->ev1) cudaEventDestroy(m->ev1);
   if (m->fork) cudaEventDestroy(m->fork);
+  if (m->stream2) {
+    cudaStreamSynchronize(m->stream2);
+    cudaStreamDestroy(m->stream2);
+  }
+  if (m->fork2) cudaEventDestroy(m->fork2);
+  if (m->join2) cudaEventDestroy(m->join2);
   for (int l = 0; l < IDOS_MAX_LEVELS; ++l) {
     if (m->lstream[l]) {
       cudaStreamSynchronize(m->lstream[l]);
       cudaStreamDestroy(m->lstream[l]);
     }
-    if (m->pstream[l]) {
-      cudaStreamSynchronize(m->pstream[l]);
-      cudaStreamDestroy(m->pstream[l]);
+    for (cudaStream_t* sp : {&m->pstream[l], &m->lstream2[l], &m->pstream2[l]}) {
+      if (*sp) {
+        cudaStreamSynchronize(*sp);
+        cudaStreamDestroy(*sp);
+      }
     }
+    if (m->lfork2[l]) cudaEventDestroy(m->lfork2[l]);
+    if (m->ljoin2[l]) cudaEventDestroy(m->ljoin2[l]);
     if (m->lev0[l]) cudaEventDestroy(m->lev0[l]);
     if (m->lev1[l]) cudaEventDestroy(m->lev1[l]);
     m->lws[l].release();
@@ -468,7 +508,7 @@ int idos_sample_level_detail(idos_model* m, int level, int64_t n_samples, uint64
   if (n_samples == 0) return IDOS_OK;
   ProfGuard pg(m);
   return run_level(m, level, n_samples, seed, first_sample, per_sample_Y, Q_fine, Q_coarse, m->stream, m->ws, m->ev0,
-                   m->ev1, m->err + IDOS_MAX_LEVELS, true);
+                   m->ev1, m->err + IDOS_MAX_LEVELS, true, 0, nullptr, m->stream2, m->fork2, m->join2);
 }
 
 int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed, int64_t first_sample,
@@ -494,6 +534,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
   for (int l = 0; l < L; ++l) (l == L - 1 ? w_fin : w_rest) += (double)n_samples[l] * flop_model(m->d, l);
   const bool parted = m->pstream[L - 1] != nullptr && w_fin > 0.0 && w_rest >= 0.5 * w_fin;
   cudaStream_t* streams = parted ? m->pstream : m->lstream;
+  cudaStream_t* streams2 = parted ? m->pstream2 : m->lstream2;
   // every level stream starts after the work already queued on the model's stream
   IDOS_CUDA_TRY(cudaEventRecord(m->fork, m->stream));
   for (int l = 0; l < L; ++l) IDOS_CUDA_TRY(cudaStreamWaitEvent(streams[l], m->fork, 0));
@@ -504,7 +545,8 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     const int l = order[q];
     if (n_samples[l] == 0) continue;
     IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr, nullptr,
-                       streams[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false, parted ? m->lsms[l] : 0));
+                       streams[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false, parted ? m->lsms[l] : 0,
+                       nullptr, streams2[l], m->lfork2[l], m->ljoin2[l]));
   }
   for (int l = 0; l < L; ++l) {
     if (n_samples[l] == 0) continue;

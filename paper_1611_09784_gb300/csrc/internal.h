@@ -106,6 +106,11 @@ struct Model {
   // one stream, workspace and event pair per level for idos_sample_levels
   cudaStream_t lstream[IDOS_MAX_LEVELS] = {};   // shared SMs, priorities by cost
   cudaStream_t pstream[IDOS_MAX_LEVELS] = {};   // the same on the SM partition (null without one)
+  // second stream per level for the corners' solve beside the fine one
+  cudaStream_t lstream2[IDOS_MAX_LEVELS] = {}, pstream2[IDOS_MAX_LEVELS] = {};
+  cudaEvent_t lfork2[IDOS_MAX_LEVELS] = {}, ljoin2[IDOS_MAX_LEVELS] = {};
+  cudaStream_t stream2 = nullptr;                // the same for calls on the model's stream
+  cudaEvent_t fork2 = nullptr, join2 = nullptr;
   Arena lws[IDOS_MAX_LEVELS];
   cudaEvent_t lev0[IDOS_MAX_LEVELS] = {}, lev1[IDOS_MAX_LEVELS] = {};
   cudaEvent_t fork = nullptr;
