@@ -16,11 +16,14 @@
 // their x-derivatives, rescaled by exact powers of two: no division.  One
 // pass gives the count at x and the Newton step -p_n/p_n', used inside the
 // current bracket (safeguarded Newton: bisect when the step leaves it).
-//   IDOS_FP32_REFINE64: float32 bisection to 2 ulp, then refine64_iters
-//     float64 passes starting at the bracket midpoint;
+// Every matrix is first scaled by an exact power of two so that its
+// Gershgorin interval lies within [-1, 1] (results scaled back exactly).
+//   IDOS_FP32_REFINE64: float32 bisection to 2 ulp or 2 eps |T|, whichever is
+//     wider, then refine64_iters passes starting at the bracket midpoint, with
+//     count and p_n in float64 and p_n' in float32;
 //   IDOS_FP64: float32 bisection on the rounded tridiagonal gives a bracket,
-//     checked and widened in float64, then safeguarded Newton to float64
-//     resolution.
+//     checked and widened in float64, then safeguarded Newton, all in float64,
+//     to float64 resolution.
 #include <cfloat>
 
 #include "internal.h"
@@ -83,13 +86,69 @@ __device__ __forceinline__ int sturm_newton64(const double* __restrict__ d, cons
   return cnt;
 }
 
+__device__ __forceinline__ int fexp(float v) { return (__float_as_int(v) >> 23) & 0xff; }
+
+// The same pass with the derivative carried in float32: the count and p_n(x)
+// (the residual, where the cancellation is) stay float64 - three float64
+// operations per row - while p' only sets the Newton step length, for which
+// float32 accuracy is ample (a relative error r in p' leaves an error r times
+// the step; a wild value is caught by the bracket safeguard).  The float32
+// recurrence runs on a float32 copy of p (d32, e32: the same normalised
+// tridiagonal rounded to float32), so no per-row float64 -> float32
+// conversion is needed.  With |T| <= 1 (the caller normalises) a value grows
+// by at most 3x per row, so an exponent check every 8 rows that rescales all
+// values by 2^-e once the largest binary exponent e leaves [-60, 60] keeps
+// the float32 values far from overflow.
+__device__ __forceinline__ int sturm_newton_mixed(const double* __restrict__ d, const double* __restrict__ e2,
+                                                  const float* __restrict__ d32, const float* __restrict__ e32, int n,
+                                                  double x, double& step) {
+  const float x32 = (float)x;
+  double p0 = 1.0, p1 = d[0] - x;
+  float r0 = 1.0f, r1 = d32[0] - x32;           // float32 copy of p
+  float q0 = 0.0f, q1 = -1.0f;                  // p', float32
+  if (dzero(p1)) p1 = -0x1p-1000;
+  int cnt = dneg(p1);
+  bool lost = false;
+  for (int i = 1; i < n; ++i) {
+    const double t = d[i] - x;
+    double p2 = fma(t, p1, -(e2[i - 1] * p0));
+    const float t32 = d32[i] - x32, b32 = e32[i - 1];
+    const float r2 = fmaf(t32, r1, -(b32 * r0));
+    const float q2 = fmaf(t32, q1, -fmaf(b32, q0, r1));
+    // an exact zero becomes +-2^-1000 of the sign opposite to p1 (a negative
+    // pivot), chosen on the bit patterns so that no float64 work is issued
+    if (dzero(p2)) p2 = dneg(p1) ? 0x1p-1000 : -0x1p-1000;
+    cnt += dneg(p2) != dneg(p1);
+    p0 = p1; p1 = p2; r0 = r1; r1 = r2; q0 = q1; q1 = q2;
+    if ((i & 7) == 0) {
+      // unbiased exponents; a zero (field 0) does not take part
+      const int ep = max(dexp(p0), dexp(p1));
+      const int eq = max(fexp(q0), fexp(q1));
+      const int e = max(ep > 0 ? ep - 1023 : -2000, eq > 0 ? eq - 127 : -2000);
+      if (e > 60 || (e < -60 && e > -2000)) {
+        const int ed = min(max(e, -1000), 1000), ef = min(max(e, -126), 126);
+        const double sd = __hiloint2double((1023 - ed) << 20, 0);   // 2^-ed
+        const float sf = __int_as_float((127 - ef) << 23);           // 2^-ef
+        p0 *= sd; p1 *= sd;
+        r0 *= sf; r1 *= sf; q0 *= sf; q1 *= sf;
+        lost |= ed != ef;   // float32 values out of range: no Newton step
+      }
+    }
+  }
+  // p and (r, q) carry the same scale; a zero step ends the polish at the
+  // bracket midpoint
+  step = (!lost && q1 != 0.0f) ? -p1 * (double)(1.0f / q1) : 0.0;
+  return cnt;
+}
+
 // Safeguarded Newton for eigenvalue k inside [lo, hi] (count(lo) <= k < count(hi)).
-__device__ __forceinline__ double newton_polish(const double* d, const double* e2, int n, int k, double lo, double hi,
-                                                int passes) {
+// Pass(x, step) returns count(x) and sets the Newton step.
+template <typename Pass>
+__device__ __forceinline__ double newton_polish(Pass pass, int k, double lo, double hi, int passes) {
   double x = 0.5 * (lo + hi);
   for (int it = 0; it < passes; ++it) {
     double step;
-    const int c = sturm_newton64(d, e2, n, x, step);
+    const int c = pass(x, step);
     if (c >= k + 1) hi = x; else lo = x;
     const double xn = x + step;
     const bool inside = xn > lo && xn < hi;
@@ -107,14 +166,19 @@ __device__ __forceinline__ T ulp_of(T x) {
   else return fabs(x) * DBL_EPSILON + DBL_MIN;
 }
 
-// Bisect [lo, hi] for eigenvalue index k: count(lo) <= k < count(hi).
+// Bisect [lo, hi] for eigenvalue index k: count(lo) <= k < count(hi).  The
+// bracket stops shrinking at 2 ulp of the eigenvalue or at atol, whichever is
+// larger: the float32 count itself is only backward stable to a perturbation
+// of order ulp * |T| of the matrix, so narrowing a bracket around an
+// eigenvalue near zero (a zero mode) below that scale buys no accuracy, and it
+// would hold the whole warp for up to ~100 iterations instead of ~24.
 template <typename T, typename S>
 __device__ __forceinline__ void bisect_index(const S* d, const S* e2, int n, int k, T pivmin, T& lo,
-                                             T& hi, int max_iter) {
+                                             T& hi, int max_iter, T atol) {
   for (int it = 0; it < max_iter; ++it) {
     const T mid = T(0.5) * (lo + hi);
     if (!(mid > lo && mid < hi)) break;                     // no representable midpoint left
-    if (hi - lo <= T(2) * ulp_of<T>(fabs(lo) > fabs(hi) ? lo : hi)) break;
+    if (hi - lo <= fmax(T(2) * ulp_of<T>(fabs(lo) > fabs(hi) ? lo : hi), atol)) break;
     if (sturm_count<T, S>(d, e2, n, mid, pivmin) >= k + 1) hi = mid;
     else lo = mid;
   }
@@ -149,29 +213,27 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
     if (i >= n) out[i] = __longlong_as_double(0x7ff8000000000000ll);   // NaN padding
   }
   if (n <= 0 || c_lo >= n) return;
-  // Gershgorin bounds and the largest e^2, in double for safety
-  double glo = 1e300, ghi = -1e300, emax = 0.0;
+  // Gershgorin bounds and the largest e^2 in the storage precision (widened
+  // below by far more than their rounding)
+  S glo_s = S(1e30), ghi_s = S(-1e30), emax_s = S(0);
   for (int i = tid; i < n; i += G) {
     const S di = d_in[mat * n_max + i];
     const S ei = (i < n - 1) ? e2_in[mat * n_max + i] : S(0);
     d[i] = di;
     e2[i] = ei;
-    if constexpr (sizeof(S) == 4) {
-      dd[i] = (double)di;
-      ee[i] = (double)ei;
-    }
-    const double el = (i > 0) ? sqrt((double)e2_in[mat * n_max + i - 1]) : 0.0;
-    const double er = sqrt((double)ei);
-    glo = fmin(glo, (double)di - el - er);
-    ghi = fmax(ghi, (double)di + el + er);
-    emax = fmax(emax, (double)ei);
+    const S el = (i > 0) ? sqrt(e2_in[mat * n_max + i - 1]) : S(0);
+    const S er = sqrt(ei);
+    glo_s = fmin(glo_s, di - el - er);
+    ghi_s = fmax(ghi_s, di + el + er);
+    emax_s = fmax(emax_s, ei);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
-    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
-    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    glo_s = fmin(glo_s, __shfl_xor_sync(0xffffffffu, glo_s, o));
+    ghi_s = fmax(ghi_s, __shfl_xor_sync(0xffffffffu, ghi_s, o));
+    emax_s = fmax(emax_s, __shfl_xor_sync(0xffffffffu, emax_s, o));
   }
+  double glo = (double)glo_s, ghi = (double)ghi_s, emax = (double)emax_s;
   if constexpr (G > 32) {
     const int w = tid >> 5;
     if ((tid & 31) == 0) { red_lo[gid][w] = glo; red_hi[gid][w] = ghi; red_e[gid][w] = emax; }
@@ -182,28 +244,55 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
       emax = fmax(emax, red_e[gid][q]);
     }
   }
+  // Normalise by an exact power of two, sc = 2^-e with max(|glo|, |ghi|) =
+  // m 2^e, m in [0.5, 1): every pass below works on T' = sc T (eigenvalues
+  // sc lambda, counts unchanged), so the float32 values of the mixed pass
+  // stay in range whatever the scale of the input; results are scaled back
+  // exactly.
+  int ex = 0;
+  const double tn = fmax(fabs(glo), fabs(ghi));
+  if (tn > 0.0 && tn < 1e300) frexp(tn, &ex);
+  ex = sizeof(S) == 4 ? min(max(ex, -60), 60) : min(max(ex, -900), 900);
+  const double sc = ldexp(1.0, -ex), isc = ldexp(1.0, ex);
   group_sync<G, MPB>(gid);
+  const S sc_s = (S)sc;   // 2^-ex, |ex| <= 900: exact in float64; float32 uses |ex| <= 126
+  for (int i = tid; i < n; i += G) {
+    const S di = d[i] * sc_s, ei = e2[i] * sc_s * sc_s;
+    d[i] = di;
+    e2[i] = ei;
+    if constexpr (sizeof(S) == 4) {
+      dd[i] = (double)di;
+      ee[i] = (double)ei;
+    }
+  }
+  group_sync<G, MPB>(gid);
+  glo *= sc;
+  ghi *= sc;
+  emax *= sc * sc;
   const double span = fmax(ghi - glo, 1e-30);
   glo -= 1e-6 * span + 1e-12;   // float rounding of the reduced bounds
   ghi += 1e-6 * span + 1e-12;
   const float piv32 = 1e-30f * fmaxf(1.0f, (float)emax);
+  const float atol32 = 2.0f * FLT_EPSILON * (float)fmax(fabs(glo), fabs(ghi));
   for (int k = c_lo + tid; k < min(n, c_hi); k += G) {
     if constexpr (sizeof(S) == 8) {
       // float32 bracket on the rounded tridiagonal (float64 data read and
       // rounded on the fly), widened, checked in float64, then polished
       float lo32 = (float)glo, hi32 = (float)ghi;
-      bisect_index<float, S>(d, e2, n, k, piv32, lo32, hi32, 100);
+      bisect_index<float, S>(d, e2, n, k, piv32, lo32, hi32, 100, atol32);
       const double w = 64.0 * (double)FLT_EPSILON * fmax(fabs(glo), fabs(ghi)) + 1e-12;
       double lo = fmax(glo, (double)lo32 - w), hi = fmin(ghi, (double)hi32 + w);
       double st;
       if (sturm_newton64(dd, ee, n, lo, st) > k) lo = glo;      // bracket lost: fall back
       if (sturm_newton64(dd, ee, n, hi, st) < k + 1) hi = ghi;
-      out[k] = newton_polish(dd, ee, n, k, lo, hi, 60);
+      const auto pass = [&](double x, double& step) { return sturm_newton64(dd, ee, n, x, step); };
+      out[k] = isc * newton_polish(pass, k, lo, hi, 60);
     } else {
       float lo = (float)glo, hi = (float)ghi;
-      bisect_index<float, S>(d, e2, n, k, piv32, lo, hi, 100);
-      out[k] = refine > 0 ? newton_polish(dd, ee, n, k, (double)lo, (double)hi, refine)
-                          : 0.5 * ((double)lo + (double)hi);
+      bisect_index<float, S>(d, e2, n, k, piv32, lo, hi, 100, atol32);
+      const auto pass = [&](double x, double& step) { return sturm_newton_mixed(dd, ee, d, e2, n, x, step); };
+      out[k] = isc * (refine > 0 ? newton_polish(pass, k, (double)lo, (double)hi, refine)
+                                 : 0.5 * ((double)lo + (double)hi));
     }
   }
 }

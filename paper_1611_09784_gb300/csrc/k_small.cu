@@ -21,12 +21,21 @@ namespace idos {
 
 namespace {
 
+// The reflector v and update vector w of one step, side by side, so the
+// fused pass reads the pending pair of a row with one 16-byte (float) load.
+template <typename T>
+struct __align__(2 * sizeof(c2<T>)) VW {
+  c2<T> v, w;
+};
+
 template <typename T>
 struct SmallLayout {
-  // per group: A[n_max * n_max], v[2][n_max], w[2][n_max] (complex), scratch
+  // per group: vw[2][n_max] (pending and next pair, first: 16-byte aligned),
+  // A[n_max * n_max] (complex), 3 bond phases, scratch
   __host__ __device__ static size_t bytes(int n_max) {
-    const size_t b = sizeof(c2<T>) * ((size_t)n_max * n_max + 4 * (size_t)n_max + 3) + sizeof(T) * 64;
-    return (b + 15) & ~size_t(15);
+    const size_t b = sizeof(VW<T>) * 2 * (size_t)n_max + sizeof(c2<T>) * ((size_t)n_max * n_max + 3) +
+                     sizeof(T) * 64;
+    return (b + 31) & ~size_t(31);
   }
 };
 
@@ -44,12 +53,10 @@ k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
   if (mat >= n_mat) return;   // whole group leaves together
 
   unsigned char* base = smem_raw + (size_t)gid * SmallLayout<T>::bytes(n_max);
-  C* A = reinterpret_cast<C*>(base);
-  C* vb0 = A + (size_t)n_max * n_max;
-  C* vb1 = vb0 + n_max;
-  C* wb0 = vb1 + n_max;
-  C* wb1 = wb0 + n_max;
-  C* ph = wb1 + n_max;
+  VW<T>* vwb0 = reinterpret_cast<VW<T>*>(base);
+  VW<T>* vwb1 = vwb0 + n_max;
+  C* A = reinterpret_cast<C*>(vwb1 + n_max);
+  C* ph = A + (size_t)n_max * n_max;
   T* scratch = reinterpret_cast<T*>(ph + 3);
 
   const int K2 = K * K;
@@ -97,17 +104,18 @@ k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
   group_sync<NT, MPB>(gid);
 
   // ------------------------------------------------------ tridiagonalise ---
-  C* v = vb0; C* w = wb0;       // pending update (v, w) of the previous step
-  C* nv = vb1; C* nw = wb1;     // this step's reflector and update vector
+  VW<T>* vw = vwb0;     // pending update (v, w) of the previous step
+  VW<T>* nvw = vwb1;    // this step's reflector and update vector
   bool pend = false;
   for (int j = 0; j < n - 1; ++j) {
     // (a) bring row j up to date (columns c >= j): it is conj of column j.
     if (pend) {
-      const C vj = v[j], wj = w[j];
+      const VW<T> q = vw[j];
       for (int c = j + tid; c < n; c += NT) {
+        const VW<T> qc = vw[c];
         C a = A[(size_t)j * n + c];
-        a = csub<T>(a, cmulc<T>(vj, w[c]));
-        a = csub<T>(a, cmulc<T>(wj, v[c]));
+        a = csub<T>(a, cmulc<T>(q.v, qc.w));
+        a = csub<T>(a, cmulc<T>(q.w, qc.v));
         A[(size_t)j * n + c] = a;
       }
     }
@@ -132,45 +140,68 @@ k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
       const C phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
       tau = T(1) / (sigma * (sigma + aa));
       for (int c = j + 1 + tid; c < n; c += NT)
-        nv[c] = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * n + c]);
+        nvw[c].v = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * n + c]);
     }
     group_sync<NT, MPB>(gid);
     // (c) fused pass: apply the pending update to the trailing block and
     //     accumulate p = tau A22 v with the updated entries.
     T kpart = T(0);
-    for (int c = j + 1 + tid; c < n; c += NT) {
-      C p = mk<T>(T(0), T(0));
-      const C wc = pend ? w[c] : mk<T>(T(0), T(0));
-      const C vc = pend ? v[c] : mk<T>(T(0), T(0));
-      for (int r = j + 1; r < n; ++r) {
-        C a = A[(size_t)r * n + c];
-        if (pend) {
-          a = csub<T>(a, cmulc<T>(v[r], wc));
-          a = csub<T>(a, cmulc<T>(w[r], vc));
-          A[(size_t)r * n + c] = a;
+    if (pend && tr) {
+      // the common case, without branches in the row loop
+      for (int c = j + 1 + tid; c < n; c += NT) {
+        const VW<T> qc = vw[c];
+        C p = mk<T>(T(0), T(0));
+        C* ac = A + (size_t)(j + 1) * n + c;
+#pragma unroll 4
+        for (int r = j + 1; r < n; ++r, ac += n) {
+          const VW<T> qr = vw[r];
+          C a = *ac;
+          a = csub<T>(a, cmulc<T>(qr.v, qc.w));
+          a = csub<T>(a, cmulc<T>(qr.w, qc.v));
+          *ac = a;
+          p = cadd<T>(p, cjmul<T>(a, nvw[r].v));   // (A22 v)_c = sum_r conj(A[r][c]) v_r
         }
-        if (tr) p = cadd<T>(p, cjmul<T>(a, nv[r]));   // (A22 v)_c = sum_r conj(A[r][c]) v_r
-      }
-      if (tr) {
         p = cscale<T>(p, tau);
-        nw[c] = p;
-        kpart += nv[c].x * p.x + nv[c].y * p.y;   // Re(conj(v_c) p_c)
+        nvw[c].w = p;
+        const C nc = nvw[c].v;
+        kpart += nc.x * p.x + nc.y * p.y;   // Re(conj(v_c) p_c)
+      }
+    } else if (pend || tr) {
+      for (int c = j + 1 + tid; c < n; c += NT) {
+        C p = mk<T>(T(0), T(0));
+        const VW<T> qc = pend ? vw[c] : VW<T>{mk<T>(T(0), T(0)), mk<T>(T(0), T(0))};
+        for (int r = j + 1; r < n; ++r) {
+          C a = A[(size_t)r * n + c];
+          if (pend) {
+            const VW<T> qr = vw[r];
+            a = csub<T>(a, cmulc<T>(qr.v, qc.w));
+            a = csub<T>(a, cmulc<T>(qr.w, qc.v));
+            A[(size_t)r * n + c] = a;
+          }
+          if (tr) p = cadd<T>(p, cjmul<T>(a, nvw[r].v));
+        }
+        if (tr) {
+          p = cscale<T>(p, tau);
+          nvw[c].w = p;
+          const C nc = nvw[c].v;
+          kpart += nc.x * p.x + nc.y * p.y;
+        }
       }
     }
     if (tr) {
       const T Kc = T(0.5) * tau * group_sum<NT, MPB, T>(kpart, scratch, gid);
-      for (int c = j + 1 + tid; c < n; c += NT) nw[c] = csub<T>(nw[c], cscale<T>(nv[c], Kc));
+      for (int c = j + 1 + tid; c < n; c += NT) nvw[c].w = csub<T>(nvw[c].w, cscale<T>(nvw[c].v, Kc));
     }
     pend = tr;
-    C* tv = v; v = nv; nv = tv;
-    C* tw = w; w = nw; nw = tw;
+    VW<T>* t = vw; vw = nvw; nvw = t;
     group_sync<NT, MPB>(gid);
   }
   if (tid == 0) {
     C a = A[(size_t)(n - 1) * n + (n - 1)];
     if (pend) {
-      a = csub<T>(a, cmulc<T>(v[n - 1], w[n - 1]));
-      a = csub<T>(a, cmulc<T>(w[n - 1], v[n - 1]));
+      const VW<T> q = vw[n - 1];
+      a = csub<T>(a, cmulc<T>(q.v, q.w));
+      a = csub<T>(a, cmulc<T>(q.w, q.v));
     }
     dO[n - 1] = a.x;
   }
@@ -187,9 +218,11 @@ template <typename T>
 struct RgLayout {
   // row stride: n_max rounded up to 16, plus 8 (rows 16 banks apart)
   __host__ __device__ static int ld(int n_max) { return ((n_max + 15) & ~15) + 8; }
+  // vw[2][nc] first, then A[n_max][ld], 3 bond phases, scratch
   __host__ __device__ static size_t bytes(int n_max, int nc) {
-    const size_t b = sizeof(c2<T>) * ((size_t)n_max * ld(n_max) + 4 * (size_t)nc + 3) + sizeof(T) * 64;
-    return (b + 15) & ~size_t(15);
+    const size_t b = sizeof(VW<T>) * 2 * (size_t)nc + sizeof(c2<T>) * ((size_t)n_max * ld(n_max) + 3) +
+                     sizeof(T) * 64;
+    return (b + 31) & ~size_t(31);
   }
 };
 
@@ -205,12 +238,10 @@ k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ a
   const int tid = threadIdx.x;
   const int64_t mat = blockIdx.x;
   if (mat >= n_mat) return;
-  C* A = reinterpret_cast<C*>(smem_raw);
-  C* vb0 = A + (size_t)n_max * LD;
-  C* vb1 = vb0 + NC;
-  C* wb0 = vb1 + NC;
-  C* wb1 = wb0 + NC;
-  C* ph = wb1 + NC;
+  VW<T>* vwb0 = reinterpret_cast<VW<T>*>(smem_raw);
+  VW<T>* vwb1 = vwb0 + NC;
+  C* A = reinterpret_cast<C*>(vwb1 + NC);
+  C* ph = A + (size_t)n_max * LD;
   T* scratch = reinterpret_cast<T*>(ph + 3);
 
   const int K2 = K * K;
@@ -259,17 +290,18 @@ k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ a
 
   // ------------------------------------------------------ tridiagonalise ---
   const int c_own = tid / RG, rg = tid % RG;
-  C* v = vb0; C* w = wb0;
-  C* nv = vb1; C* nw = wb1;
+  VW<T>* vw = vwb0;
+  VW<T>* nvw = vwb1;
   bool pend = false;
   for (int j = 0; j < n - 1; ++j) {
     // (a) row j of the trailing block, columns c >= j
     if (pend) {
-      const C vj = v[j], wj = w[j];
+      const VW<T> q = vw[j];
       for (int c = j + tid; c < n; c += NT) {
+        const VW<T> qc = vw[c];
         C a = A[(size_t)j * LD + c];
-        a = csub<T>(a, cmulc<T>(vj, w[c]));
-        a = csub<T>(a, cmulc<T>(wj, v[c]));
+        a = csub<T>(a, cmulc<T>(q.v, qc.w));
+        a = csub<T>(a, cmulc<T>(q.w, qc.v));
         A[(size_t)j * LD + c] = a;
       }
     }
@@ -292,7 +324,7 @@ k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ a
       const C phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
       tau = T(1) / (sigma * (sigma + aa));
       for (int c = j + 1 + tid; c < n; c += NT)
-        nv[c] = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * LD + c]);
+        nvw[c].v = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * LD + c]);
     }
     __syncthreads();
     // (c) fused pass over the trailing block: this thread's column, every
@@ -302,17 +334,30 @@ k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ a
       const int c = c_own;
       const bool act_c = c > j && c < n;
       C p = mk<T>(T(0), T(0));
-      if (act_c) {
-        const C wc = pend ? w[c] : mk<T>(T(0), T(0));
-        const C vc = pend ? v[c] : mk<T>(T(0), T(0));
+      if (act_c && pend && tr) {
+        // the common case, without branches in the row loop
+        const VW<T> qc = vw[c];
+        C* ac = A + (size_t)(j + 1 + rg) * LD + c;
+#pragma unroll 2
+        for (int r = j + 1 + rg; r < n; r += RG, ac += RG * LD) {
+          const VW<T> qr = vw[r];
+          C a = *ac;
+          a = csub<T>(a, cmulc<T>(qr.v, qc.w));
+          a = csub<T>(a, cmulc<T>(qr.w, qc.v));
+          *ac = a;
+          p = cadd<T>(p, cjmul<T>(a, nvw[r].v));
+        }
+      } else if (act_c && (pend || tr)) {
+        const VW<T> qc = pend ? vw[c] : VW<T>{mk<T>(T(0), T(0)), mk<T>(T(0), T(0))};
         for (int r = j + 1 + rg; r < n; r += RG) {
           C a = A[(size_t)r * LD + c];
           if (pend) {
-            a = csub<T>(a, cmulc<T>(v[r], wc));
-            a = csub<T>(a, cmulc<T>(w[r], vc));
+            const VW<T> qr = vw[r];
+            a = csub<T>(a, cmulc<T>(qr.v, qc.w));
+            a = csub<T>(a, cmulc<T>(qr.w, qc.v));
             A[(size_t)r * LD + c] = a;
           }
-          if (tr) p = cadd<T>(p, cjmul<T>(a, nv[r]));
+          if (tr) p = cadd<T>(p, cjmul<T>(a, nvw[r].v));
         }
       }
 #pragma unroll
@@ -322,24 +367,25 @@ k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ a
       }
       if (tr && act_c && rg == 0) {
         p = cscale<T>(p, tau);
-        nw[c] = p;
-        kpart = nv[c].x * p.x + nv[c].y * p.y;
+        nvw[c].w = p;
+        const C nc = nvw[c].v;
+        kpart = nc.x * p.x + nc.y * p.y;
       }
     }
     if (tr) {
       const T Kc = T(0.5) * tau * group_sum<NT, 1, T>(kpart, scratch, 0);
-      for (int c = j + 1 + tid; c < n; c += NT) nw[c] = csub<T>(nw[c], cscale<T>(nv[c], Kc));
+      for (int c = j + 1 + tid; c < n; c += NT) nvw[c].w = csub<T>(nvw[c].w, cscale<T>(nvw[c].v, Kc));
     }
     pend = tr;
-    C* tv = v; v = nv; nv = tv;
-    C* tw = w; w = nw; nw = tw;
+    VW<T>* t = vw; vw = nvw; nvw = t;
     __syncthreads();
   }
   if (tid == 0) {
     C a = A[(size_t)(n - 1) * LD + (n - 1)];
     if (pend) {
-      a = csub<T>(a, cmulc<T>(v[n - 1], w[n - 1]));
-      a = csub<T>(a, cmulc<T>(w[n - 1], v[n - 1]));
+      const VW<T> q = vw[n - 1];
+      a = csub<T>(a, cmulc<T>(q.v, q.w));
+      a = csub<T>(a, cmulc<T>(q.w, q.v));
     }
     dO[n - 1] = a.x;
   }
