@@ -458,6 +458,9 @@ def run_gpu(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
+    g_replays, g_captures, g_note = model.graph_info()
+    graph_line = {"replays": g_replays, "captures": g_captures, "note": g_note,
+                  "what": "idos_sample_levels captured once as a CUDA graph (all level streams), replayed per step"}
     # combine (eq. (2.6)) from the device accumulators, summed over replicas
     from paper_1611_09784_gb300 import replicas
     counts, sums = replicas.model_stats(model)
@@ -469,14 +472,13 @@ def run_gpu(args):
     # Per-kernel CUDA-event times: the timed steps run the levels on
     # concurrent streams, where one kernel's event span includes time spent
     # waiting for SMs held by kernels of other levels.  So the kernels are
-    # timed on the same work (the timed steps' samples) replayed level by
-    # level, events on the launching stream around every launch.
+    # timed on the same work (the timed steps' samples, the same launches)
+    # replayed with profiling on, which issues them in order on one stream,
+    # events on that stream around every launch.
     model.reset_profile()
     model.set_profiling(True)
     for k in range(args.steps):
-        for l, Ml in enumerate(M):
-            if Ml:
-                model.sample_level(l, Ml, seed, first_sample=(args.warmup + k) * Ml)
+        model.sample_levels(M, seed, [(args.warmup + k) * Ml for Ml in M])
     torch.cuda.synchronize()
     model.set_profiling(False)
     prof = model.get_profile()
@@ -503,7 +505,8 @@ def run_gpu(args):
                               "partial": "timed steps only (--skip-extras)", "samples_per_level": M,
                               "level_span_ms_per_step": level_span_ms,
                               "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
-                              "roofline": roof, "clocks": clk}), flush=True)
+                              "roofline": roof, "clocks": clk, "graph": graph_line, "autotune": tuning}),
+                  flush=True)
         model.close()
         if pool is not None:
             pool.close()
@@ -569,12 +572,13 @@ def run_gpu(args):
             "gpu_launches": int(sum(v[1] for v in prof.values()) // args.steps),
             "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in sorted(prof.items(), key=lambda x: -x[1][0])},
             "level_span_ms_per_step": level_span_ms,
-            "kernels_timing": "CUDA events per launch, the timed steps' samples replayed level by level (unprofiled timed steps run the levels concurrently)",
+            "kernels_timing": "CUDA events per launch, the timed steps' launches replayed in order on one stream (unprofiled timed steps run the levels concurrently)",
             "roofline": roof,
             "rooflines": roofs,
             "clocks": clk,
             "cpu_baseline": cpu,
             "autotune": tuning,
+            "graph": graph_line,
             "serving": serve,
             "tmdc_sweep": sweep,
             "stress": stress_line,

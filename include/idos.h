@@ -121,6 +121,21 @@ typedef struct idos_model_desc {
                           phase matrix on the kept sites) the generalized
                           eigenvalues of eq. (3.1) are E = (eps_onsite + l) /
                           (1 + (s/t) l), l the eigenvalues of t B.           */
+  int32_t persistent;  /* idos_sample_levels, graphene, IDOS_FP32_REFINE64:
+                          1 = the shared-memory reductions (n <= 160) of
+                          every level, fine and corner cells, in one
+                          persistent launch over a size-sorted work list
+                          (larger matrices first, one per CTA; n <= 32 one
+                          per warp, taken by whichever warp is free); 0 = one
+                          launch per cell set on its level's stream; -1 =
+                          library default (1).  Results are bit-identical.  */
+  int32_t graph;       /* idos_sample_levels: 1 = the call's launches (all
+                          level streams) are captured once as a CUDA graph
+                          and replayed by later calls with the same sample
+                          counts and settings, the seed and first sample
+                          indices read by the mask kernels from a device
+                          buffer; 0 = direct launches; -1 = library default
+                          (1).  Results are bit-identical.                   */
 } idos_model_desc;
 
 typedef struct idos_model idos_model;
@@ -138,6 +153,11 @@ void idos_destroy_model(idos_model* m);
  * SMs (sm_split = 0, one level, or no green-context support in the driver;
  * *why then holds the reason, a static string, "" when none). */
 int idos_get_partition(const idos_model* m, int* sms_finest, int* sms_rest, const char** why);
+
+/* Graph replay of idos_sample_levels: how many calls replayed a graph and
+ * how many captures were made; *why: "" while graph mode is on, else the
+ * reason it was given up (a static string valid until the next call on m). */
+int idos_get_graph_info(const idos_model* m, int64_t* replays, int64_t* captures, const char** why);
 
 /* Static text for a status code. */
 const char* idos_status_string(int status);
@@ -292,7 +312,10 @@ int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, dou
  * configuration and installs the fastest: the SMs reserved for the finest
  * level (sm_split: 0, 24, 32, 40, 48, 56, 64 where the device allows) and the
  * largest n the shared-memory kernel takes before the two-stage path (64, or
- * whatever fits: 160 float32 / 112 float64).  Each candidate runs once
+ * whatever fits: 160 float32 / 112 float64) and, with the latter, the
+ * persistent launch on or off (graphene, IDOS_FP32_REFINE64; on with graph
+ * replay, off without), then the winner with graph replay switched (unless
+ * the model gave graphs up).  Each candidate runs once
  * untimed and `reps` times timed (best kept), on sample indices from 2^40 on;
  * the level statistics are restored afterwards.  Results do not depend on the
  * choice beyond float rounding of the path choice; out: the choice and every
@@ -306,6 +329,10 @@ typedef struct idos_tuning {
   int32_t tried_split[IDOS_TUNE_MAX];
   int32_t tried_small[IDOS_TUNE_MAX];
   double tried_ms[IDOS_TUNE_MAX];
+  int32_t persistent;    /* chosen persistent setting (idos_model_desc.persistent) */
+  int32_t tried_persistent[IDOS_TUNE_MAX];
+  int32_t graph;         /* chosen graph setting (idos_model_desc.graph) */
+  int32_t tried_graph[IDOS_TUNE_MAX];
 } idos_tuning;
 int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
 

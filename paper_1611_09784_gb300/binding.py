@@ -32,6 +32,7 @@ class ModelDesc(C.Structure):
         ("sentinel", C.c_double), ("e_min", C.c_double), ("e_max", C.c_double), ("delta", C.c_double),
         ("n_E", C.c_int32), ("refine64_iters", C.c_int32), ("model_seed", C.c_uint64),
         ("workspace_bytes", C.c_int64), ("tc_products", C.c_int32), ("sm_split", C.c_int32), ("overlap_s", C.c_double),
+        ("persistent", C.c_int32), ("graph", C.c_int32),
     ]
 
 
@@ -47,7 +48,9 @@ TUNE_MAX = 32
 class Tuning(C.Structure):
     _fields_ = [("sm_split", C.c_int32), ("small_max_n", C.c_int32), ("best_ms", C.c_double),
                 ("n_tried", C.c_int32), ("tried_split", C.c_int32 * TUNE_MAX), ("tried_small", C.c_int32 * TUNE_MAX),
-                ("tried_ms", C.c_double * TUNE_MAX)]
+                ("tried_ms", C.c_double * TUNE_MAX), ("persistent", C.c_int32),
+                ("tried_persistent", C.c_int32 * TUNE_MAX), ("graph", C.c_int32),
+                ("tried_graph", C.c_int32 * TUNE_MAX)]
 
 
 class Estimate(C.Structure):
@@ -85,6 +88,8 @@ _SYMBOLS = {
     "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_her2k": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_get_partition": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_char_p)]),
+    "idos_get_graph_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_char_p)]),
     "idos_server_create": (C.c_int, [C.POINTER(ModelDesc), C.c_int, C.c_int64, C.POINTER(C.c_void_p)]),
     "idos_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_int64, C.POINTER(C.c_int64)]),
     "idos_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
@@ -166,6 +171,8 @@ def make_desc(cfg: dict) -> ModelDesc:
     d.tc_products = int(cfg.get("tc_products", DEFAULT_TC_PRODUCTS))
     d.sm_split = int(cfg.get("sm_split", -1))
     d.overlap_s = float(cfg.get("s", 0.0))
+    d.persistent = int(cfg.get("persistent", -1))
+    d.graph = int(cfg.get("graph", -1))
     return d
 
 
@@ -232,9 +239,19 @@ class Model:
         n = np.ascontiguousarray(list(n_samples) + [0] * (self.n_levels - len(n_samples)), dtype=np.int64)
         t = Tuning()
         _check(load_library().idos_autotune(self._h, _ptr(n), reps, C.byref(t)), "idos_autotune")
-        tried = [{"sm_split": t.tried_split[i], "small_max_n": t.tried_small[i], "ms": round(t.tried_ms[i], 3)}
+        tried = [{"sm_split": t.tried_split[i], "small_max_n": t.tried_small[i],
+                  "persistent": t.tried_persistent[i], "graph": t.tried_graph[i], "ms": round(t.tried_ms[i], 3)}
                  for i in range(t.n_tried)]
-        return {"sm_split": t.sm_split, "small_max_n": t.small_max_n, "best_ms": round(t.best_ms, 3), "tried": tried}
+        return {"sm_split": t.sm_split, "small_max_n": t.small_max_n, "persistent": t.persistent,
+                "graph": t.graph, "best_ms": round(t.best_ms, 3), "tried": tried}
+
+    def graph_info(self):
+        """(calls that replayed a graph, captures made, reason graph mode was
+        given up or "")."""
+        r, c, why = C.c_int64(), C.c_int64(), C.c_char_p()
+        _check(load_library().idos_get_graph_info(self._h, C.byref(r), C.byref(c), C.byref(why)),
+               "idos_get_graph_info")
+        return r.value, c.value, (why.value or b"").decode()
 
     def get_partition(self):
         """(SMs of the finest level, SMs of the others, reason when unsplit)."""

@@ -23,6 +23,12 @@ double cell_area(double a) { return 0.5 * std::sqrt(3.0) * a * a; }
 
 int Arena::reserve(size_t bytes, cudaStream_t s) {
   if (bytes <= cap) return IDOS_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  IDOS_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    set_error("workspace growth during graph capture");
+    return kErrGrowDuringCapture;
+  }
   IDOS_CUDA_TRY(cudaStreamSynchronize(s));
   if (base) IDOS_CUDA_TRY(cudaFree(base));
   base = nullptr;
@@ -31,6 +37,7 @@ int Arena::reserve(size_t bytes, cudaStream_t s) {
   IDOS_CUDA_TRY(cudaMalloc(&base, want));
   cap = want;
   used = 0;
+  ++gen;
   return IDOS_OK;
 }
 
@@ -64,6 +71,8 @@ namespace {
 constexpr size_t kDefaultWorkspace = size_t(3) << 30;   // 3 GiB
 constexpr size_t kSmallBudget = size_t(768) << 20;      // per-chunk small buffers
 constexpr int kDefaultSmSplit = 48;                      // SMs reserved for the finest level
+constexpr int kDefaultPersistent = 1;                    // persistent launch of the small matrices
+constexpr int kDefaultGraph = 1;                         // idos_sample_levels replayed as a CUDA graph
 // TMDC-shaped model: parameter range (uniform on [lo, hi) eV)
 constexpr double kTmdcParamLo = -2.0, kTmdcParamHi = 2.0;
 
@@ -93,6 +102,8 @@ int validate(const idos_model_desc* d) {
   if (!(std::fabs(d->overlap_s) < 1.0 / 3.0)) return bad("overlap_s must satisfy |s| < 1/3 (S positive definite)");
   if (d->overlap_s != 0.0 && d->kind != IDOS_GRAPHENE) return bad("overlap_s applies to the graphene model only");
   if (d->overlap_s != 0.0 && d->t == 0.0) return bad("overlap_s needs a nonzero hopping t");
+  if (d->persistent < -1 || d->persistent > 1) return bad("persistent must be -1, 0 or 1");
+  if (d->graph < -1 || d->graph > 1) return bad("graph must be -1, 0 or 1");
   return IDOS_OK;
 }
 
@@ -106,6 +117,20 @@ EnergyGrid grid_of(const idos_model_desc& d) {
 // the model's tuned limit); everything else goes through the two-stage path.
 bool use_small_path(const Model* M, int n) {
   return M->d.kind == IDOS_GRAPHENE && small_path_fits(M->d.precision, n) && (M->small_max_n < 0 || n <= M->small_max_n);
+}
+
+// Eigenvalues of the reduced (d, e^2) of every matrix of `cells` and the IDoS
+// of every cell: Q[count][n_E].
+int eigs_and_idos(Model* M, const CellSet& cells, int Kside, const void* d, const void* e2, double* eigs, double* Q,
+                  cudaStream_t st) {
+  const int n_max = cells.n_sites;
+  const int K2 = Kside * Kside;
+  const int64_t n_mat = cells.count * (int64_t)K2;
+  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
+  if (M->d.overlap_s != 0.0)
+    IDOS_TRY(launch_overlap_map(eigs, cells.n_act, K2, n_max, n_mat, M->d.eps_onsite, M->d.overlap_s / M->d.t, st));
+  const double area = (double)cells.N * cells.N * cell_area(M->d.a);
+  return launch_idos(eigs, cells.n_act, K2, n_max, cells.count, area, grid_of(M->d), Q, st);
 }
 
 // Eigen-solve + IDoS of every cell of `cells` on a Kside grid: Q[count][n_E].
@@ -143,13 +168,27 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.max_cluster = sm_avail ? 8 : 16;
   if (use_small_path(M, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
-  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
-  if (M->d.overlap_s != 0.0)
-    IDOS_TRY(launch_overlap_map(eigs, cells.n_act, K2, n_max, n_mat, M->d.eps_onsite, M->d.overlap_s / M->d.t, st));
-  const double area = (double)cells.N * cells.N * cell_area(M->d.a);
-  IDOS_TRY(launch_idos(eigs, cells.n_act, K2, n_max, cells.count, area, grid_of(M->d), Q, st));
+  IDOS_TRY(eigs_and_idos(M, cells, Kside, d, e2, eigs, Q, st));
   if (eigs_keep) *eigs_keep = eigs;
   return IDOS_OK;
+}
+
+// The (d, e^2) of every matrix of a small cell set (graphene, float32) as a
+// segment of the persistent launch, with its solve buffers taken from ws.
+bool take_small_segment(Arena& ws, const CellSet& cells, int Kside, SmallSeg& sg, double*& eigs) {
+  const int n_max = cells.n_sites;
+  const int64_t n_mat = cells.count * (int64_t)Kside * Kside;
+  sg.n_act = cells.n_act;
+  sg.act = cells.act;
+  sg.inv = cells.inv;
+  sg.N = cells.N;
+  sg.Kside = Kside;
+  sg.n_max = n_max;
+  sg.n_mat = n_mat;
+  sg.d = ws.take<float>((size_t)n_mat * n_max);
+  sg.e2 = ws.take<float>((size_t)n_mat * n_max);
+  eigs = ws.take<double>((size_t)n_mat * n_max);
+  return sg.d && sg.e2 && eigs;
 }
 
 bool take_cells(Arena& ws, CellSet& c, int N, int64_t count, int kind) {
@@ -201,10 +240,20 @@ int check_status_word(const int* err) {
 // Samples of one level on stream st with workspace ws.  blocking: wait for
 // the level to finish and add its time and count to the accumulators;
 // otherwise the caller does that after synchronising ev1.
+// A timing event: an external event node when the stream is being captured
+// (so that a replay records it), a plain record otherwise.
+cudaError_t record_timing(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, st);
+}
+
 int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, double* Yh, double* Qfh,
               double* Qch, cudaStream_t st, Arena& ws, cudaEvent_t ev0, cudaEvent_t ev1, int* err, bool blocking,
               int sm_avail = 0, double* acc_out = nullptr, cudaStream_t st2 = nullptr, cudaEvent_t fork2 = nullptr,
-              cudaEvent_t join2 = nullptr) {
+              cudaEvent_t join2 = nullptr, const uint64_t* dyn = nullptr) {
   const idos_model_desc& d = M->d;
   const int Nf = d.N[level], Kf = d.Kside[level];
   const bool coarse = level > 0;
@@ -217,7 +266,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
   int64_t chunk = std::max<int64_t>(1, (int64_t)(kSmallBudget / per_sample));
   chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_samples, 1));
   IDOS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-  IDOS_CUDA_TRY(cudaEventRecord(ev0, st));
+  IDOS_CUDA_TRY(record_timing(ev0, st));
   for (int64_t s0 = 0; s0 < n_samples; s0 += chunk) {
     const int64_t S = std::min(chunk, n_samples - s0);
     // With a second stream the corners' solve runs beside the fine one, from
@@ -243,7 +292,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
       Qc = ws.take<double>((size_t)4 * S * n_E);
     }
     if (!Qf || !Y || (coarse && !Qc)) { set_error("workspace (IDoS buffers)"); return IDOS_ERR_OUT_OF_MEMORY; }
-    IDOS_TRY(launch_fine_masks(fine.vmask, fine.n_vac, S, seed, level, first + s0, d.p, st));
+    IDOS_TRY(launch_fine_masks(fine.vmask, fine.n_vac, S, seed, level, dyn ? s0 : first + s0, d.p, st, dyn));
     if (d.kind == IDOS_TMDC) IDOS_TRY(launch_orbital_masks(fine.vmask, Nf, S, fine.mask, st));
     IDOS_TRY(launch_cell_maps(fine, st));
     if (coarse) {
@@ -282,7 +331,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
       IDOS_CUDA_TRY(cudaMemcpyAsync(Qch + s0 * 4 * n_E, Qc, sizeof(double) * 4 * S * n_E, cudaMemcpyDeviceToHost, st));
     if (Yh || Qfh || Qch) IDOS_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  IDOS_CUDA_TRY(cudaEventRecord(ev1, st));
+  IDOS_CUDA_TRY(record_timing(ev1, st));
   if (blocking) {
     IDOS_CUDA_TRY(cudaEventSynchronize(ev1));
     IDOS_TRY(check_status_word(err));
@@ -294,11 +343,183 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
   return IDOS_OK;
 }
 
+// ------------------------------------------------- persistent-mode step ---
+// All levels of one idos_sample_levels call with the shared-memory matrices
+// of every level (fine and corner cells) reduced by one persistent launch:
+//   (A) per level, on its stream: masks, cell maps, solve buffers (one chunk
+//       per level); an event when its inputs are ready;
+//   (B) on the stream of the lowest such level: wait for the other levels'
+//       inputs, one persistent launch over all small segments, an event;
+//   (C) per level, finest first: the two-stage solves of its large sets, then
+//       (after the launch) bisection and IDoS of its small sets, level stats.
+struct LevelPlan {
+  int64_t S = 0;
+  CellSet fine, crs;
+  double *Qf = nullptr, *Y = nullptr, *Qc = nullptr;
+  bool fine_small = false, crs_small = false;
+  SmallSeg fseg, cseg;
+  double *feig = nullptr, *ceig = nullptr;
+  size_t mark = 0;
+};
+
+size_t level_per_sample(const Model* M, int level) {
+  const idos_model_desc& d = M->d;
+  const int Nf = d.N[level], Kf = d.Kside[level];
+  const bool coarse = level > 0;
+  const int Nc = coarse ? Nf / 2 : 0, Kc = coarse ? d.Kside[level - 1] : 0;
+  return cells_bytes(Nf, 1, d.kind) + solve_bytes(d.precision, Nf, Kf, 1, d.n_E, d.kind) +
+         (coarse ? cells_bytes(Nc, 4, d.kind) + solve_bytes(d.precision, Nc, Kc, 4, d.n_E, d.kind) : 0) +
+         3 * d.n_E * sizeof(double);
+}
+
+// Whether this call can take the persistent route: graphene, float32, every
+// level in one chunk, 1 .. kMaxSmallSegs small sets.
+bool persistent_route(const Model* M, const int64_t* n_samples) {
+  const idos_model_desc& d = M->d;
+  if (!M->persistent || d.precision != IDOS_FP32_REFINE64 || d.kind != IDOS_GRAPHENE) return false;
+  int segs = 0;
+  for (int l = 0; l < d.n_levels; ++l) {
+    if (n_samples[l] == 0) continue;
+    if (n_samples[l] > std::max<int64_t>(1, (int64_t)(kSmallBudget / level_per_sample(M, l)))) return false;
+    const int nf = 2 * d.N[l] * d.N[l];
+    const int nc = l > 0 ? nf / 4 : 0;
+    for (int n : {nf, nc})
+      if (n > 0 && use_small_path(M, n)) {
+        if (n > kPersistMaxN) return false;
+        ++segs;
+      }
+  }
+  return segs >= 1 && segs <= kMaxSmallSegs;
+}
+
+int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, const int64_t* first_sample,
+                             cudaStream_t* streams, cudaStream_t* streams2, bool parted, const uint64_t* dyn) {
+  const idos_model_desc& d = m->d;
+  const int L = d.n_levels, n_E = d.n_E;
+  LevelPlan P[IDOS_MAX_LEVELS];
+  SmallSeg segs[kMaxSmallSegs];
+  int n_seg = 0, lp = -1;
+  // (A) inputs of every level
+  for (int l = 0; l < L; ++l) {
+    LevelPlan& p = P[l];
+    p.S = n_samples[l];
+    if (p.S == 0) continue;
+    const int Nf = d.N[l], Kf = d.Kside[l];
+    const bool coarse = l > 0;
+    const int Nc = coarse ? Nf / 2 : 0, Kc = coarse ? d.Kside[l - 1] : 0;
+    const int64_t S = p.S;
+    cudaStream_t st = streams[l];
+    Arena& ws = m->lws[l];
+    const bool two = coarse && streams2[l];
+    const size_t coarse_slice =
+        two ? solve_bytes(d.precision, Nc, Kc, 4 * S, n_E, d.kind) + large_room(m, Nc, Kc, 4 * S) + 64 * 1024 : 0;
+    const size_t need = S * level_per_sample(m, l) + 64 * 1024 + ((S + 63) / 64) * 2 * n_E * 8 +
+                        (two ? large_room(m, Nf, Kf, S) + coarse_slice
+                             : std::max(large_room(m, Nf, Kf, S), coarse ? large_room(m, Nc, Kc, 4 * S) : 0));
+    IDOS_TRY(ws.reserve(need, st));
+    ws.reset();
+    if (!take_cells(ws, p.fine, Nf, S, d.kind)) { set_error("workspace (fine cells)"); return IDOS_ERR_OUT_OF_MEMORY; }
+    p.Qf = ws.take<double>((size_t)S * n_E);
+    p.Y = ws.take<double>((size_t)S * n_E);
+    if (coarse) {
+      if (!take_cells(ws, p.crs, Nc, 4 * S, d.kind)) {
+        set_error("workspace (corner cells)");
+        return IDOS_ERR_OUT_OF_MEMORY;
+      }
+      p.Qc = ws.take<double>((size_t)4 * S * n_E);
+    }
+    if (!p.Qf || !p.Y || (coarse && !p.Qc)) { set_error("workspace (IDoS buffers)"); return IDOS_ERR_OUT_OF_MEMORY; }
+    p.fine_small = use_small_path(m, p.fine.n_sites);
+    p.crs_small = coarse && use_small_path(m, p.crs.n_sites);
+    if (p.fine_small && !take_small_segment(ws, p.fine, Kf, p.fseg, p.feig)) {
+      set_error("workspace (fine solve buffers)");
+      return IDOS_ERR_OUT_OF_MEMORY;
+    }
+    if (p.crs_small && !take_small_segment(ws, p.crs, Kc, p.cseg, p.ceig)) {
+      set_error("workspace (corner solve buffers)");
+      return IDOS_ERR_OUT_OF_MEMORY;
+    }
+    p.mark = ws.used;
+    IDOS_CUDA_TRY(cudaMemsetAsync(m->err + l, 0, sizeof(int), st));
+    IDOS_CUDA_TRY(record_timing(m->lev0[l], st));
+    const int64_t first = first_sample ? first_sample[l] : m->M[l];
+    IDOS_TRY(launch_fine_masks(p.fine.vmask, p.fine.n_vac, S, seed, l, dyn ? 0 : first, d.p, st, dyn));
+    IDOS_TRY(launch_cell_maps(p.fine, st));
+    if (coarse) {
+      IDOS_TRY(launch_corner_masks(p.fine.vmask, Nf, vac_per_cell(d.kind), S, p.crs.vmask, st));
+      IDOS_TRY(launch_cell_maps(p.crs, st));
+    }
+    if (p.fine_small || p.crs_small) {
+      if (lp < 0) lp = l;
+      if (p.fine_small) segs[n_seg++] = p.fseg;
+      if (p.crs_small) segs[n_seg++] = p.cseg;
+      IDOS_CUDA_TRY(cudaEventRecord(m->lprep[l], st));
+    }
+  }
+  // (B) one launch over the small matrices of all levels
+  if (lp >= 0) {
+    cudaStream_t ps = streams[lp];
+    for (int l = lp + 1; l < L; ++l)
+      if (P[l].S > 0 && (P[l].fine_small || P[l].crs_small)) IDOS_CUDA_TRY(cudaStreamWaitEvent(ps, m->lprep[l], 0));
+    const double eps = d.overlap_s != 0.0 ? 0.0 : d.eps_onsite;
+    IDOS_TRY(solve_small_persistent(segs, n_seg, d.t, eps, m->small_ctr, parted ? m->lsms[lp] : 0, ps));
+    IDOS_CUDA_TRY(cudaEventRecord(m->small_done, ps));
+  }
+  // (C) large sets, then the rest of every level, finest first
+  for (int l = L - 1; l >= 0; --l) {
+    LevelPlan& p = P[l];
+    if (p.S == 0) continue;
+    const int Kf = d.Kside[l], Kc = l > 0 ? d.Kside[l - 1] : 0;
+    cudaStream_t st = streams[l];
+    Arena& ws = m->lws[l];
+    int* err = m->err + l;
+    const int sm_avail = parted ? m->lsms[l] : 0;
+    const bool coarse = l > 0;
+    if (coarse && !p.crs_small && !p.fine_small && streams2[l]) {
+      // both large: the corners' solve beside the fine one (own workspace slice)
+      const size_t coarse_slice = solve_bytes(d.precision, p.crs.N, Kc, p.crs.count, n_E, d.kind) +
+                                  large_room(m, p.crs.N, Kc, p.crs.count) + 64 * 1024;
+      Arena sub;
+      sub.base = ws.take<char>(coarse_slice);
+      sub.cap = sub.base ? coarse_slice : 0;
+      if (!sub.base) { set_error("workspace (corner solve)"); return IDOS_ERR_OUT_OF_MEMORY; }
+      IDOS_CUDA_TRY(cudaEventRecord(m->lfork2[l], st));
+      IDOS_CUDA_TRY(cudaStreamWaitEvent(streams2[l], m->lfork2[l], 0));
+      IDOS_TRY(solve_and_idos(m, p.crs, Kc, p.Qc, nullptr, streams2[l], sub, err, sm_avail));
+      IDOS_CUDA_TRY(cudaEventRecord(m->ljoin2[l], streams2[l]));
+      IDOS_TRY(solve_and_idos(m, p.fine, Kf, p.Qf, nullptr, st, ws, err, sm_avail));
+      IDOS_CUDA_TRY(cudaStreamWaitEvent(st, m->ljoin2[l], 0));
+    } else {
+      if (coarse && !p.crs_small) {
+        IDOS_TRY(solve_and_idos(m, p.crs, Kc, p.Qc, nullptr, st, ws, err, sm_avail));
+        ws.used = p.mark;
+      }
+      if (!p.fine_small) IDOS_TRY(solve_and_idos(m, p.fine, Kf, p.Qf, nullptr, st, ws, err, sm_avail));
+    }
+    ws.used = p.mark;
+    if (p.fine_small || p.crs_small) {
+      if (l != lp) IDOS_CUDA_TRY(cudaStreamWaitEvent(st, m->small_done, 0));
+      if (p.crs_small) IDOS_TRY(eigs_and_idos(m, p.crs, Kc, p.cseg.d, p.cseg.e2, p.ceig, p.Qc, st));
+      if (p.fine_small) IDOS_TRY(eigs_and_idos(m, p.fine, Kf, p.fseg.d, p.fseg.e2, p.feig, p.Qf, st));
+    }
+    IDOS_TRY(launch_level_stats(p.Qf, p.Qc, p.S, n_E, p.Y, m->acc + (size_t)l * 2 * n_E, ws, st));
+    IDOS_CUDA_TRY(record_timing(m->lev1[l], st));
+  }
+  return IDOS_OK;
+}
+
 // (Re)builds the partitioned level streams for `split` SMs reserved for the
 // finest level (0: none).  A partition the driver cannot make leaves every
 // level on all SMs and records why.
 int apply_partition(Model* m, int split) {
   const int L = m->d.n_levels;
+  // a captured graph refers to the streams and contexts rebuilt here
+  if (m->gexec) {
+    IDOS_CUDA_TRY(cudaGraphExecDestroy(m->gexec));
+    m->gexec = nullptr;
+    m->gkey.clear();
+  }
+  ++m->part_gen;
   for (int l = 0; l < L; ++l) {
     for (cudaStream_t* sp : {&m->pstream[l], &m->pstream2[l]}) {
       if (*sp) {
@@ -448,7 +669,18 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
     if (e == cudaSuccess) e = cudaEventCreate(&m->lev1[l]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->lfork2[l], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ljoin2[l], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->lprep[l], cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->small_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&m->small_ctr, 2 * sizeof(unsigned long long));
+  for (int l = 0; l < d->n_levels && e == cudaSuccess; ++l)
+    e = cudaEventCreateWithFlags(&m->ljoin[l], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork0, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&m->dyn_dev, sizeof(uint64_t) * (1 + IDOS_MAX_LEVELS));
+  if (e == cudaSuccess) e = cudaMallocHost(&m->dyn_host, sizeof(uint64_t) * (1 + IDOS_MAX_LEVELS));
+  m->persistent = d->persistent == -1 ? kDefaultPersistent : d->persistent;
+  m->graph = d->graph == -1 ? kDefaultGraph : d->graph;
   // SM partition: the finest level on a reserved set of SMs, the others on
   // the rest (a failure to create it leaves every level on all SMs)
   if (e == cudaSuccess && apply_partition(m, d->sm_split == -1 ? kDefaultSmSplit : d->sm_split) != IDOS_OK)
@@ -478,6 +710,16 @@ void idos_destroy_model(idos_model* m) {
   }
   if (m->fork2) cudaEventDestroy(m->fork2);
   if (m->join2) cudaEventDestroy(m->join2);
+  if (m->small_done) cudaEventDestroy(m->small_done);
+  if (m->small_ctr) cudaFree(m->small_ctr);
+  if (m->gexec) cudaGraphExecDestroy(m->gexec);
+  if (m->gstream) {
+    cudaStreamSynchronize(m->gstream);
+    cudaStreamDestroy(m->gstream);
+  }
+  if (m->fork0) cudaEventDestroy(m->fork0);
+  if (m->dyn_dev) cudaFree(m->dyn_dev);
+  if (m->dyn_host) cudaFreeHost(m->dyn_host);
   for (int l = 0; l < IDOS_MAX_LEVELS; ++l) {
     if (m->lstream[l]) {
       cudaStreamSynchronize(m->lstream[l]);
@@ -491,6 +733,8 @@ void idos_destroy_model(idos_model* m) {
     }
     if (m->lfork2[l]) cudaEventDestroy(m->lfork2[l]);
     if (m->ljoin2[l]) cudaEventDestroy(m->ljoin2[l]);
+    if (m->lprep[l]) cudaEventDestroy(m->lprep[l]);
+    if (m->ljoin[l]) cudaEventDestroy(m->ljoin[l]);
     if (m->lev0[l]) cudaEventDestroy(m->lev0[l]);
     if (m->lev1[l]) cudaEventDestroy(m->lev1[l]);
     m->lws[l].release();
@@ -516,6 +760,35 @@ int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed
   return idos_sample_level_detail(m, level, n_samples, seed, first_sample, per_sample_Y, nullptr, nullptr);
 }
 
+// Issues every level of one idos_sample_levels call: the level streams fork
+// from the model's stream and join it again at the end (so the call can be
+// captured as one graph from that stream).
+int enqueue_levels(Model* m, cudaStream_t origin, const int64_t* n_samples, uint64_t seed,
+                   const int64_t* first_sample, cudaStream_t* streams, cudaStream_t* streams2, bool parted,
+                   bool route_p, const uint64_t* dyn) {
+  const int L = m->d.n_levels;
+  IDOS_CUDA_TRY(cudaEventRecord(m->fork, origin));
+  for (int l = 0; l < L; ++l)
+    if (n_samples[l] > 0) IDOS_CUDA_TRY(cudaStreamWaitEvent(streams[l], m->fork, 0));
+  if (route_p) {
+    IDOS_TRY(sample_levels_persistent(m, n_samples, seed, first_sample, streams, streams2, parted, dyn));
+  } else {
+    // costliest level first, so its long latency-bound phases overlap the rest
+    for (int l = L - 1; l >= 0; --l) {
+      if (n_samples[l] == 0) continue;
+      IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr,
+                         nullptr, streams[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false,
+                         parted ? m->lsms[l] : 0, nullptr, streams2[l], m->lfork2[l], m->ljoin2[l], dyn));
+    }
+  }
+  for (int l = 0; l < L; ++l) {
+    if (n_samples[l] == 0) continue;
+    IDOS_CUDA_TRY(cudaEventRecord(m->ljoin[l], streams[l]));
+    IDOS_CUDA_TRY(cudaStreamWaitEvent(origin, m->ljoin[l], 0));
+  }
+  return IDOS_OK;
+}
+
 int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, const int64_t* first_sample) {
   if (!m || !n_samples) { set_error("null model or sample counts"); return IDOS_ERR_INVALID_ARG; }
   const int L = m->d.n_levels;
@@ -532,31 +805,100 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
   // level shares all SMs.
   double w_fin = 0.0, w_rest = 0.0;
   for (int l = 0; l < L; ++l) (l == L - 1 ? w_fin : w_rest) += (double)n_samples[l] * flop_model(m->d, l);
-  const bool parted = m->pstream[L - 1] != nullptr && w_fin > 0.0 && w_rest >= 0.5 * w_fin;
+  bool parted = m->pstream[L - 1] != nullptr && w_fin > 0.0 && w_rest >= 0.5 * w_fin;
   cudaStream_t* streams = parted ? m->pstream : m->lstream;
   cudaStream_t* streams2 = parted ? m->pstream2 : m->lstream2;
-  // every level stream starts after the work already queued on the model's stream
-  IDOS_CUDA_TRY(cudaEventRecord(m->fork, m->stream));
-  for (int l = 0; l < L; ++l) IDOS_CUDA_TRY(cudaStreamWaitEvent(streams[l], m->fork, 0));
-  // costliest level first, so its long latency-bound phases overlap the rest
-  int order[IDOS_MAX_LEVELS];
-  for (int l = 0; l < L; ++l) order[l] = L - 1 - l;
-  for (int q = 0; q < L; ++q) {
-    const int l = order[q];
-    if (n_samples[l] == 0) continue;
-    IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr, nullptr,
-                       streams[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false, parted ? m->lsms[l] : 0,
-                       nullptr, streams2[l], m->lfork2[l], m->ljoin2[l]));
+  // A profiled call issues the same launches in order on the model's stream,
+  // so that each kernel's event span is its own (on concurrent streams it
+  // would include time spent waiting for SMs held by other levels).
+  // The call is issued from the model's own non-blocking origin stream (a
+  // graph cannot be captured from the legacy default stream), after the work
+  // already queued on the caller's stream.
+  cudaStream_t origin = m->gstream;
+  IDOS_CUDA_TRY(cudaEventRecord(m->fork0, m->stream));
+  IDOS_CUDA_TRY(cudaStreamWaitEvent(origin, m->fork0, 0));
+  cudaStream_t ser[IDOS_MAX_LEVELS], ser2[IDOS_MAX_LEVELS] = {};
+  if (m->prof.enabled) {
+    for (int l = 0; l < L; ++l) ser[l] = origin;
+    streams = ser;
+    streams2 = ser2;
+    parted = false;
   }
+  const bool route_p = persistent_route(m, n_samples);
+  // per-call values of the mask kernels (a replayed graph reads them here)
+  m->dyn_host[0] = seed;
+  for (int l = 0; l < L; ++l) m->dyn_host[1 + l] = (uint64_t)(first_sample ? first_sample[l] : m->M[l]);
+  IDOS_CUDA_TRY(cudaMemcpyAsync(m->dyn_dev, m->dyn_host, sizeof(uint64_t) * (1 + L), cudaMemcpyHostToDevice,
+                                origin));
+  auto enqueue = [&]() -> int {
+    return enqueue_levels(m, origin, n_samples, seed, first_sample, streams, streams2, parted, route_p, m->dyn_dev);
+  };
+  bool issued = false;
+  if (m->graph && !m->prof.enabled) {
+    // the graph of the last call is replayed while nothing it was captured
+    // from has changed: sample counts, route, settings, partition, arenas
+    std::vector<int64_t> key(n_samples, n_samples + L);
+    for (int64_t v : {(int64_t)parted, (int64_t)route_p, (int64_t)m->small_max_n, (int64_t)m->persistent,
+                      (int64_t)m->part_gen})
+      key.push_back(v);
+    for (int l = 0; l < L; ++l) key.push_back((int64_t)m->lws[l].gen);
+    if (m->gexec && key == m->gkey) {
+      IDOS_CUDA_TRY(cudaGraphLaunch(m->gexec, origin));
+      ++m->graph_replays;
+      issued = true;
+    } else {
+      if (m->gexec) {
+        IDOS_CUDA_TRY(cudaGraphExecDestroy(m->gexec));
+        m->gexec = nullptr;
+        m->gkey.clear();
+      }
+      IDOS_CUDA_TRY(cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed));
+      const int rc = enqueue();
+      cudaGraph_t g = nullptr;
+      cudaError_t ec = cudaStreamEndCapture(origin, &g);
+      cudaGraphExec_t ex = nullptr;
+      // the kernel nodes keep the priorities of the level streams they were
+      // captured from (finest level first), not the origin stream's
+      if (rc == IDOS_OK && ec == cudaSuccess && g)
+        ec = cudaGraphInstantiateWithFlags(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
+      if (g) cudaGraphDestroy(g);
+      if (rc == IDOS_OK && ec == cudaSuccess && ex) {
+        m->gexec = ex;
+        m->gkey = key;
+        ++m->graph_captures;
+        IDOS_CUDA_TRY(cudaGraphLaunch(ex, origin));
+        ++m->graph_replays;
+        issued = true;
+      } else {
+        (void)cudaGetLastError();   // capture errors are not sticky
+        if (rc != kErrGrowDuringCapture) {
+          // the launches cannot be captured here: run without graphs from now on
+          m->graph = 0;
+          m->graph_note = rc != IDOS_OK ? std::string(get_error())
+                                        : std::string("capture/instantiate: ") + cudaGetErrorString(ec);
+        }
+        // (a workspace had to grow: this call runs directly, the next one captures)
+      }
+    }
+  }
+  if (!issued) IDOS_TRY(enqueue());
+  IDOS_CUDA_TRY(cudaStreamSynchronize(origin));
   for (int l = 0; l < L; ++l) {
     if (n_samples[l] == 0) continue;
-    IDOS_CUDA_TRY(cudaEventSynchronize(m->lev1[l]));
     IDOS_TRY(check_status_word(m->err + l));
     float ms = 0.f;
     IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, m->lev0[l], m->lev1[l]));
     m->M[l] += n_samples[l];
     m->seconds[l] += ms * 1e-3;
   }
+  return IDOS_OK;
+}
+
+int idos_get_graph_info(const idos_model* m, int64_t* replays, int64_t* captures, const char** why) {
+  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  if (replays) *replays = m->graph_replays;
+  if (captures) *captures = m->graph_captures;
+  if (why) *why = m->graph_note.c_str();
   return IDOS_OK;
 }
 
@@ -878,44 +1220,67 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     for (int n : {nf, nc})
       if (n > 64 && m->d.kind == IDOS_GRAPHENE && small_path_fits(m->d.precision, n)) has_mid = true;
   }
-  const int smalls[] = {-1, 64};
+  // (small-kernel limit, persistent launch): the persistent launch only
+  // with the default limit, and only where it applies
+  const bool can_persist = m->d.kind == IDOS_GRAPHENE && m->d.precision == IDOS_FP32_REFINE64;
+  // (small-kernel limit, persistent launch, graph replay)
+  const int variants[][3] = {{-1, 1, 1}, {-1, 0, 0}, {64, 0, 0}};
   out->n_tried = 0;
   out->best_ms = 1e300;
-  int best_split = m->sm_split_now, best_small = m->small_max_n;
+  int best_split = m->sm_split_now, best_small = m->small_max_n, best_persist = m->persistent, best_graph = m->graph;
+  const int graph_saved = m->graph;
   int64_t first[IDOS_MAX_LEVELS];
   int64_t round = 0;
   int rc = IDOS_OK;
-  for (int sm : smalls) {
+  auto time_config = [&](int sp, int sm, int pers, int gr) -> int {
+    m->small_max_n = sm;
+    m->persistent = pers;
+    m->graph = graph_saved ? gr : 0;   // a model that gave up graphs stays without
+    int r = apply_partition(m, sp);
+    if (r != IDOS_OK) return r;
+    if (sp > 0 && m->sm_split_now == 0) return IDOS_OK;   // the driver could not make this split
+    double best = 1e300;
+    for (int k = 0; k <= reps && r == IDOS_OK; ++k) {
+      for (int l = 0; l < L; ++l) first[l] = (int64_t(1) << 40) + (round++) * (n_samples[l] + 1);
+      const auto t0 = std::chrono::steady_clock::now();
+      r = idos_sample_levels(m, n_samples, 0x5eedull, first);
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (k > 0) best = std::min(best, ms);   // k = 0 warms the configuration up (and captures)
+    }
+    if (r != IDOS_OK || out->n_tried >= IDOS_TUNE_MAX) return r;
+    const int i = out->n_tried++;
+    out->tried_split[i] = m->sm_split_now;
+    out->tried_small[i] = sm;
+    out->tried_persistent[i] = pers;
+    out->tried_graph[i] = m->graph;
+    out->tried_ms[i] = best;
+    if (best < out->best_ms) {
+      out->best_ms = best;
+      best_split = sp;
+      best_small = sm;
+      best_persist = pers;
+      best_graph = m->graph;
+    }
+    return IDOS_OK;
+  };
+  for (const auto& var : variants) {
+    const int sm = var[0], pers = var[1], gr = var[2];
     if (sm == 64 && !has_mid) continue;
+    if (pers == 1 && !can_persist) continue;
     for (int sp : splits) {
       if (sp >= m->sm_count || (sp > 0 && L < 2) || out->n_tried >= IDOS_TUNE_MAX) continue;
-      m->small_max_n = sm;
-      rc = apply_partition(m, sp);
+      rc = time_config(sp, sm, pers, gr);
       if (rc != IDOS_OK) break;
-      if (sp > 0 && m->sm_split_now == 0) continue;   // the driver could not make this split
-      double best = 1e300;
-      for (int r = 0; r <= reps && rc == IDOS_OK; ++r) {
-        for (int l = 0; l < L; ++l) first[l] = (int64_t(1) << 40) + (round++) * (n_samples[l] + 1);
-        const auto t0 = std::chrono::steady_clock::now();
-        rc = idos_sample_levels(m, n_samples, 0x5eedull, first);
-        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        if (r > 0) best = std::min(best, ms);   // r = 0 warms the configuration up
-      }
-      if (rc != IDOS_OK) break;
-      const int i = out->n_tried++;
-      out->tried_split[i] = m->sm_split_now;
-      out->tried_small[i] = sm;
-      out->tried_ms[i] = best;
-      if (best < out->best_ms) {
-        out->best_ms = best;
-        best_split = sp;
-        best_small = sm;
-      }
     }
     if (rc != IDOS_OK) break;
   }
+  // second stage: the winner with graph replay switched
+  if (rc == IDOS_OK && graph_saved && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
+    rc = time_config(best_split, best_small, best_persist, best_graph ? 0 : 1);
   // install the winner and restore the caller's statistics
   m->small_max_n = best_small;
+  m->persistent = best_persist;
+  m->graph = best_graph;
   const int rc2 = apply_partition(m, best_split);
   IDOS_CUDA_TRY(cudaMemcpyAsync(m->acc, acc_saved.data(), sizeof(double) * acc_saved.size(), cudaMemcpyHostToDevice,
                                 m->stream));
@@ -924,6 +1289,8 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   std::copy(sec_saved, sec_saved + IDOS_MAX_LEVELS, m->seconds);
   out->sm_split = m->sm_split_now;
   out->small_max_n = m->small_max_n;
+  out->persistent = m->persistent;
+  out->graph = m->graph;
   return rc != IDOS_OK ? rc : rc2;
 }
 

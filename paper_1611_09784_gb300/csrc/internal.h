@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/idos.h"
 #include "common.cuh"
@@ -16,11 +17,16 @@ namespace idos {
 
 // Bump allocator over one device buffer.  reset() at the start of every API
 // call; grow() reallocates (after a stream sync) when a call needs more.
+// Returned by Arena::reserve when the arena would have to grow while its
+// stream is being captured into a graph (never leaves the library).
+constexpr int kErrGrowDuringCapture = -1000;
+
 struct Arena {
   char* base = nullptr;
   size_t cap = 0;
   size_t used = 0;
   size_t peak = 0;
+  uint64_t gen = 0;   // bumped on every (re)allocation: graphs hold pointers into it
   int reserve(size_t bytes, cudaStream_t s);   // ensure capacity >= bytes
   void reset() { used = 0; }
   template <typename T>
@@ -114,11 +120,32 @@ struct Model {
   Arena lws[IDOS_MAX_LEVELS];
   cudaEvent_t lev0[IDOS_MAX_LEVELS] = {}, lev1[IDOS_MAX_LEVELS] = {};
   cudaEvent_t fork = nullptr;
+  // persistent launch over the levels' shared-memory matrices: per-level
+  // "inputs ready" events, the launch's completion, its work counters
+  cudaEvent_t lprep[IDOS_MAX_LEVELS] = {};
+  cudaEvent_t small_done = nullptr;
+  unsigned long long* small_ctr = nullptr;
+  // graph replay of idos_sample_levels: per-call values (seed, first sample
+  // of every level) read by the mask kernels from dyn_dev; the executable
+  // graph of the last key (sample counts, route, partition, arena
+  // generations) and how often it was captured / replayed
+  int graph = 1;
+  cudaStream_t gstream = nullptr;   // origin stream of idos_sample_levels (non-blocking)
+  cudaEvent_t fork0 = nullptr;      // caller's stream -> origin stream
+  uint64_t* dyn_dev = nullptr;
+  uint64_t* dyn_host = nullptr;   // pinned
+  cudaEvent_t ljoin[IDOS_MAX_LEVELS] = {};
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int64_t> gkey;
+  int64_t graph_replays = 0, graph_captures = 0;
+  std::string graph_note;         // why graph mode was given up ("" while it works)
+  uint64_t part_gen = 0;          // bumped by every partition rebuild
   SmPartition part;               // SM split of idos_sample_levels (ctx null: shared SMs)
   std::string part_note;          // why there is no split (empty when there is one or none was asked)
   int lsms[IDOS_MAX_LEVELS] = {};  // SMs of each level stream's partition (0: whole device)
   int sm_split_now = 0;           // SMs reserved for the finest level now (0: no partition)
   int small_max_n = -1;           // largest n on the shared-memory kernel (-1: whatever fits)
+  int persistent = 1;             // one persistent launch for the levels' shared-memory matrices
   double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream
@@ -131,8 +158,10 @@ struct Model {
 };
 
 // ---- stage launchers (return idos_status) ----
+// dyn (optional, device): [0] seed, read in place of `seed`; [1 + level]
+// first sample, to which `first_sample` is added as an offset.
 int launch_fine_masks(uint8_t* out, int n_sites, int64_t count, uint64_t seed, int level,
-                      int64_t first_sample, double p, cudaStream_t s);
+                      int64_t first_sample, double p, cudaStream_t s, const uint64_t* dyn = nullptr);
 int launch_corner_masks(const uint8_t* fine, int N, int per_cell, int64_t count, uint8_t* out, cudaStream_t s);
 // TMDC-shaped model: orbital masks [count][11 N^2] from pair masks [count][N^2]
 int launch_orbital_masks(const uint8_t* pairs, int N, int64_t count, uint8_t* out, cudaStream_t s);
@@ -146,6 +175,28 @@ void tmdc_draw_params(uint64_t model_seed, double lo, double hi, double* out);
 // Householder reduction to real symmetric tridiagonal (d, e^2).
 bool small_path_fits(int precision, int n_max);
 int solve_small(int precision, const SolveArgs& a);
+
+// One segment of the persistent shared-memory launch: every matrix (cell x
+// k-point) of one graphene cell set, reduced to float32 (d, e^2).
+constexpr int kMaxSmallSegs = 8;
+struct SmallSeg {
+  const int* n_act = nullptr;
+  const int* act = nullptr;
+  const int* inv = nullptr;
+  int N = 0, Kside = 0, n_max = 0;
+  int64_t n_mat = 0;
+  float* d = nullptr;
+  float* e2 = nullptr;
+};
+// Largest n_max the persistent launch takes (float32).
+constexpr int kPersistMaxN = 160;
+// Reduces the matrices of all segments (n_max <= kPersistMaxN each) in one
+// launch of at most `ctas` CTAs (0: one per SM of the device): matrices with
+// n_max > 32 are CTA work items, handed out largest first; the n_max <= 32
+// ones are warp work items taken one at a time by any warp that is free.
+// counters: device [2] uint64 scratch, zeroed here on the stream.
+int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double eps, unsigned long long* counters,
+                           int ctas, cudaStream_t s);
 int solve_large(int precision, const SolveArgs& a);
 // Workspace the large-matrix path needs to hold n_mat matrices in one batch.
 size_t large_path_bytes(int precision, int n_max, int64_t n_mat);

@@ -11,8 +11,16 @@ namespace idos {
 // Site `site` of sample `sample` on `level` is removed iff word 0 of
 // Philox4x64-10(counter = (site, sample, level, 0), key = (seed, 1)) is below
 // floor(p 2^64); all_removed handles p = 1 (threshold 2^64).
+// dyn (optional, device): [0] the seed, used in place of `seed`, and
+// [1 + level] the first sample index, to which `first_sample` is then added
+// as an offset (a replayed graph takes its per-call values from there).
 __global__ void k_fine_masks(uint8_t* __restrict__ out, int n_sites, int64_t total, uint64_t seed,
-                             int level, int64_t first_sample, uint64_t thr, int all_removed) {
+                             int level, int64_t first_sample, uint64_t thr, int all_removed,
+                             const uint64_t* __restrict__ dyn) {
+  if (dyn) {
+    seed = dyn[0];
+    first_sample += (int64_t)dyn[1 + level];
+  }
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = idx / n_sites;
@@ -24,7 +32,7 @@ __global__ void k_fine_masks(uint8_t* __restrict__ out, int n_sites, int64_t tot
 }
 
 int launch_fine_masks(uint8_t* out, int n_sites, int64_t count, uint64_t seed, int level,
-                      int64_t first_sample, double p, cudaStream_t s) {
+                      int64_t first_sample, double p, cudaStream_t s, const uint64_t* dyn) {
   const int all_removed = p >= 1.0 ? 1 : 0;
   const uint64_t thr = all_removed ? 0ull : (uint64_t)std::ldexp(p, 64);
   const int64_t total = count * (int64_t)n_sites;
@@ -33,7 +41,7 @@ int launch_fine_masks(uint8_t* out, int n_sites, int64_t count, uint64_t seed, i
   const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
   ProfScope ps(KID_MASKS, s);
   k_fine_masks<<<(unsigned)blocks, threads, 0, s>>>(out, n_sites, total, seed, level, first_sample,
-                                                   thr, all_removed);
+                                                   thr, all_removed, dyn);
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
 }

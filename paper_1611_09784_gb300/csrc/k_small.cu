@@ -12,6 +12,7 @@
 // update uses p = tau A22 v, K = tau/2 Re(v^H p), w = p - K v,
 // A22 <- A22 - v w^H - w v^H, fused with the next step's product: each step
 // reads and writes the trailing block once.
+#include <algorithm>
 #include <cfloat>
 
 #include "graphene.cuh"
@@ -39,20 +40,15 @@ struct SmallLayout {
   }
 };
 
+// One matrix `mat` reduced by the NT threads of group gid (tid = rank in the
+// group) in the shared-memory slot `base` of SmallLayout<T>::bytes(n_max).
 template <typename T, int NT, int MPB>
-__global__ void __launch_bounds__(NT* MPB)
-k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
-                const int* __restrict__ inv, int N, int K, int n_max, int64_t n_mat, double t_hop,
-                double eps, const double2* __restrict__ Hin, T* __restrict__ d_out,
-                T* __restrict__ e2_out) {
+__device__ __forceinline__ void small_tridiag_group(unsigned char* base, int gid, int tid,
+                                                    const int* __restrict__ n_act_cell, const int* __restrict__ act,
+                                                    const int* __restrict__ inv, int N, int K, int n_max, int64_t mat,
+                                                    double t_hop, double eps, const double2* __restrict__ Hin,
+                                                    T* __restrict__ d_out, T* __restrict__ e2_out) {
   using C = c2<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int gid = threadIdx.x / NT;
-  const int tid = threadIdx.x % NT;
-  const int64_t mat = (int64_t)blockIdx.x * MPB + gid;
-  if (mat >= n_mat) return;   // whole group leaves together
-
-  unsigned char* base = smem_raw + (size_t)gid * SmallLayout<T>::bytes(n_max);
   VW<T>* vwb0 = reinterpret_cast<VW<T>*>(base);
   VW<T>* vwb1 = vwb0 + n_max;
   C* A = reinterpret_cast<C*>(vwb1 + n_max);
@@ -207,6 +203,21 @@ k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
   }
 }
 
+template <typename T, int NT, int MPB>
+__global__ void __launch_bounds__(NT* MPB)
+k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
+                const int* __restrict__ inv, int N, int K, int n_max, int64_t n_mat, double t_hop,
+                double eps, const double2* __restrict__ Hin, T* __restrict__ d_out,
+                T* __restrict__ e2_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int gid = threadIdx.x / NT;
+  const int tid = threadIdx.x % NT;
+  const int64_t mat = (int64_t)blockIdx.x * MPB + gid;
+  if (mat >= n_mat) return;   // whole group leaves together
+  small_tridiag_group<T, NT, MPB>(smem_raw + (size_t)gid * SmallLayout<T>::bytes(n_max), gid, tid, n_act_cell, act,
+                                  inv, N, K, n_max, mat, t_hop, eps, Hin, d_out, e2_out);
+}
+
 // Row-group variant for 32 < n <= NC: thread t works on column c = t / RG
 // and on the rows r = j + 1 + (t % RG) (mod RG) of the trailing block, so NC
 // columns keep NC * RG threads busy and every step's column loops are RG times
@@ -226,18 +237,18 @@ struct RgLayout {
   }
 };
 
+// One matrix `mat` reduced by the whole CTA (NC * RG threads) in the
+// shared-memory region smem_raw of RgLayout<T>::bytes(n_max, NC).
 template <typename T, int NC, int RG>
-__global__ void __launch_bounds__(NC* RG)
-k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv,
-                   int N, int K, int n_max, int64_t n_mat, double t_hop, double eps, const double2* __restrict__ Hin,
-                   T* __restrict__ d_out, T* __restrict__ e2_out) {
+__device__ __forceinline__ void small_tridiag_rg_cta(unsigned char* smem_raw, const int* __restrict__ n_act_cell,
+                                                     const int* __restrict__ act, const int* __restrict__ inv, int N,
+                                                     int K, int n_max, int64_t mat, double t_hop, double eps,
+                                                     const double2* __restrict__ Hin, T* __restrict__ d_out,
+                                                     T* __restrict__ e2_out) {
   using C = c2<T>;
   constexpr int NT = NC * RG;
   const int LD = RgLayout<T>::ld(n_max);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
-  const int64_t mat = blockIdx.x;
-  if (mat >= n_mat) return;
   VW<T>* vwb0 = reinterpret_cast<VW<T>*>(smem_raw);
   VW<T>* vwb1 = vwb0 + NC;
   C* A = reinterpret_cast<C*>(vwb1 + NC);
@@ -392,6 +403,17 @@ k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ a
 }
 
 template <typename T, int NC, int RG>
+__global__ void __launch_bounds__(NC* RG)
+k_small_tridiag_rg(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv,
+                   int N, int K, int n_max, int64_t n_mat, double t_hop, double eps, const double2* __restrict__ Hin,
+                   T* __restrict__ d_out, T* __restrict__ e2_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t mat = blockIdx.x;
+  if (mat >= n_mat) return;
+  small_tridiag_rg_cta<T, NC, RG>(smem_raw, n_act_cell, act, inv, N, K, n_max, mat, t_hop, eps, Hin, d_out, e2_out);
+}
+
+template <typename T, int NC, int RG>
 int run_small_rg(const SolveArgs& a) {
   const size_t smem = RgLayout<T>::bytes(a.n_max, NC);
   auto kern = k_small_tridiag_rg<T, NC, RG>;
@@ -422,7 +444,113 @@ int run_small(const SolveArgs& a) {
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
+// ---------------------------------------------------- persistent launch ---
+// 640 threads: one matrix of n <= 160 per CTA item (160 columns x 4 row
+// groups) or one matrix of n <= 32 per warp item (20 warps).
+constexpr int kPNC = kPersistMaxN, kPRG = 4, kPThreads = kPNC * kPRG, kPWarps = kPThreads / 32;
+
+struct PersistWork {
+  SmallSeg seg[kMaxSmallSegs];
+  int64_t end[kMaxSmallSegs];   // cumulative matrix counts, per phase
+  int n_cta;                    // segments [0, n_cta): CTA items; [n_cta, n_seg): warp items
+  int n_seg;
+  int64_t total_cta, total_warp;
+};
+
+__global__ void __launch_bounds__(kPThreads, 1)
+k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_item;
+  // phase 1: the larger matrices, one per CTA item, segments in descending n
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[0], 1ull);
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= w.total_cta) break;   // uniform over the CTA
+    int g = 0;
+    while (g + 1 < w.n_cta && it >= w.end[g]) ++g;
+    const SmallSeg& sg = w.seg[g];
+    const int64_t mat = it - (g > 0 ? w.end[g - 1] : 0);
+    small_tridiag_rg_cta<float, kPNC, kPRG>(smem_raw, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat,
+                                            t_hop, eps, nullptr, sg.d, sg.e2);
+    __syncthreads();   // s_item and the shared region are reused
+  }
+  // phase 2: the n <= 32 matrices, one per warp item, each warp in its slot
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* slot = smem_raw + (size_t)warp * SmallLayout<float>::bytes(32);
+  for (;;) {
+    long long it = 0;
+    if (lane == 0) it = (long long)atomicAdd(&ctr[1], 1ull);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= w.total_warp) break;
+    int g = w.n_cta;
+    while (g + 1 < w.n_seg && it >= w.end[g]) ++g;
+    const SmallSeg& sg = w.seg[g];
+    const int64_t mat = it - (g > w.n_cta ? w.end[g - 1] : 0);
+    small_tridiag_group<float, 32, 1>(slot, warp, lane, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat,
+                                      t_hop, eps, nullptr, sg.d, sg.e2);
+    __syncwarp();
+  }
+}
+
 }  // namespace
+
+int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double eps, unsigned long long* counters,
+                           int ctas, cudaStream_t s) {
+  if (n_segs <= 0) return IDOS_OK;
+  if (n_segs > kMaxSmallSegs || !counters) {
+    set_error("persistent launch: too many segments or no counters");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  // CTA segments first, in descending n_max; then the warp segments
+  PersistWork w{};
+  int order[kMaxSmallSegs], no = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < n_segs; ++i)
+      if ((segs[i].n_max > 32) == (pass == 0) && segs[i].n_mat > 0) order[no++] = i;
+  std::sort(order, order + no, [&](int a, int b) {
+    const bool ca = segs[a].n_max > 32, cb = segs[b].n_max > 32;
+    if (ca != cb) return ca;
+    return segs[a].n_max > segs[b].n_max;
+  });
+  size_t smem = 0;
+  for (int q = 0; q < no; ++q) {
+    const SmallSeg& sg = segs[order[q]];
+    if (sg.n_max < 1 || sg.n_max > kPersistMaxN || !sg.n_act || !sg.act || !sg.inv || !sg.d || !sg.e2) {
+      set_error("persistent launch: segment with n_max outside 1..160 or a null buffer");
+      return IDOS_ERR_INVALID_ARG;
+    }
+    w.seg[q] = sg;
+    if (sg.n_max > 32) {
+      w.total_cta += sg.n_mat;
+      w.end[q] = w.total_cta;
+      w.n_cta = q + 1;
+      smem = std::max(smem, RgLayout<float>::bytes(sg.n_max, kPNC));
+    } else {
+      w.total_warp += sg.n_mat;
+      w.end[q] = w.total_warp;
+      smem = std::max(smem, SmallLayout<float>::bytes(32) * kPWarps);
+    }
+  }
+  w.n_seg = no;
+  if (no == 0) return IDOS_OK;
+  if (smem > kSmemLimit) {
+    set_error("persistent launch: shared memory above the per-CTA limit");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  int dev = 0, sms = 0;
+  IDOS_CUDA_TRY(cudaGetDevice(&dev));
+  IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int grid = ctas > 0 ? std::min(ctas, sms) : sms;
+  const int64_t items = w.total_cta + (w.total_warp + kPWarps - 1) / kPWarps;
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, items));
+  IDOS_CUDA_TRY(cudaFuncSetAttribute(k_small_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  IDOS_CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s));
+  ProfScope ps(KID_SMALL_TRIDIAG, s);
+  k_small_persistent<<<grid, kPThreads, smem, s>>>(w, t, eps, counters);
+  IDOS_CHECK_LAUNCH();
+  return IDOS_OK;
+}
 
 bool small_path_fits(int precision, int n_max) {
   if (n_max <= 32) {
