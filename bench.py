@@ -416,7 +416,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     cfg = dict(w["model"], p=w["p"], levels=levels, e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
                delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64,
-               tc_products=TC_PRODUCTS, sm_split=args.sm_split)
+               tc_products=TC_PRODUCTS, sm_split=args.sm_split, graph=args.graph)
     model = pkg.create_model(cfg, stream=stream.cuda_stream)
     seed = w["seed"] + 1000 * rank
     eig_step = sum(Ml * eigsolves_per_sample(levels, l) for l, Ml in enumerate(M))
@@ -439,10 +439,11 @@ def run_gpu(args):
         step(i)
     torch.cuda.synchronize()
     model.reset_level_stats(-1)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local) if not args.no_clocks else None
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    if clocks:
+        clocks.start()
     evs = []
     for k in range(args.steps):
         with torch.cuda.stream(stream):
@@ -455,7 +456,7 @@ def run_gpu(args):
         evs.append((e0, e1))
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     g_replays, g_captures, g_note = model.graph_info()
@@ -631,6 +632,11 @@ def main():
                     help="comma list of level indices to run (profiling a part of the workload)")
     ap.add_argument("--sm-split", type=int, default=-1,
                     help="SMs reserved for the finest level (0: shared SMs, -1: library default)")
+    ap.add_argument("--graph", type=int, default=-1, choices=[-1, 0, 1],
+                    help="graph replay of idos_sample_levels (-1: library default / autotuner; 0 for ncu runs, "
+                         "which cannot follow a stream capture)")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="do not sample nvidia-smi clocks (profiler runs)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the timed steps: no e2e / plain-MC / CPU-baseline measurements")
     args = ap.parse_args()
