@@ -491,6 +491,89 @@ k_ts_w(Batch bt, int k, const c2<T>* __restrict__ A, const c2<T>* __restrict__ Y
   }
 }
 
+// Float32 W = A22 (Y T) with register tiles: 128 rows x 16 columns per CTA,
+// each thread 4 rows x 2 columns; A22 tiles read as 16-byte pairs of
+// complex entries (row-major, rows 34 complex apart: the 4 rows a warp reads
+// at once fall on distinct banks), (Y T) tiles stored x-major so a thread
+// reads its column pair with one 16-byte load; the next tile is fetched into
+// registers while the current one is used.  Needs an even n_max (16-byte
+// alignment of every row pair); same sums as k_ts_w in a different order.
+constexpr int W4R = 128, W4K = 32, W4LD = W4K + 2;
+
+__device__ __forceinline__ float4 ld_pair(const float2* __restrict__ row, int x, int x_hi, bool row_ok) {
+  if (!row_ok || x >= x_hi) return make_float4(0.f, 0.f, 0.f, 0.f);
+  if (x + 1 < x_hi) return *reinterpret_cast<const float4*>(row + x);
+  const float2 a = row[x];
+  return make_float4(a.x, a.y, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256)
+k_ts_w4(Batch bt, int k, const float2* __restrict__ A, const float2* __restrict__ YT, float2* __restrict__ Wp,
+        int nsplit) {
+  __shared__ __align__(16) float2 sA[W4R * W4LD];
+  __shared__ __align__(16) float2 sY[W4K * BW];
+  const int b = blockIdx.z / nsplit, sp = blockIdx.z % nsplit;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int m = n - k - BW;
+  const int r0 = blockIdx.x * W4R;
+  if (m <= 0 || r0 >= m) return;
+  const int chunk = ((m + nsplit - 1) / nsplit + W4K - 1) / W4K * W4K;
+  const int x_lo = sp * chunk, x_hi = min(m, x_lo + chunk);
+  const float2* A22 = A + (size_t)b * nm * nm + (size_t)(k + BW) * nm + (k + BW);
+  const float2* YTb = YT + (size_t)b * BW * nm;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cp = lane >> 2, rg = lane & 3;   // column pair (2 cp, 2 cp + 1), row group
+  // tile loads: A rows tid / 16 + 16 i (i < 8), pair tid % 16; Y column tid / 16, pair tid % 16
+  const int la_r = tid >> 4, la_p = tid & 15;
+  float4 ra[8], ry;
+  auto fetch = [&](int x0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + la_r + 16 * i;
+      ra[i] = ld_pair(A22 + (size_t)r * nm, x0 + 2 * la_p, x_hi, r < m);
+    }
+    ry = ld_pair(YTb + (size_t)la_r * nm, x0 + 2 * la_p, x_hi, true);
+  };
+  float2 acc[4][2];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = make_float2(0.f, 0.f);
+  if (x_lo < x_hi) fetch(x_lo);
+  for (int x0 = x_lo; x0 < x_hi; x0 += W4K) {
+    __syncthreads();   // the previous tile is no longer read
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      *reinterpret_cast<float4*>(&sA[(la_r + 16 * i) * W4LD + 2 * la_p]) = ra[i];
+    sY[(2 * la_p) * BW + la_r] = make_float2(ry.x, ry.y);
+    sY[(2 * la_p + 1) * BW + la_r] = make_float2(ry.z, ry.w);
+    __syncthreads();
+    if (x0 + W4K < x_hi) fetch(x0 + W4K);
+#pragma unroll 4
+    for (int xx = 0; xx < W4K; xx += 2) {
+      const float4 y0 = *reinterpret_cast<const float4*>(&sY[xx * BW + 2 * cp]);         // Y[xx][2cp], Y[xx][2cp+1]
+      const float4 y1 = *reinterpret_cast<const float4*>(&sY[(xx + 1) * BW + 2 * cp]);   // Y[xx+1][..]
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 a = *reinterpret_cast<const float4*>(&sA[(warp * 16 + rg + 4 * u) * W4LD + xx]);
+        // acc[u][j] += A[xx] Y[xx][j] + A[xx+1] Y[xx+1][j]
+        acc[u][0].x += a.x * y0.x - a.y * y0.y + a.z * y1.x - a.w * y1.y;
+        acc[u][0].y += a.x * y0.y + a.y * y0.x + a.z * y1.y + a.w * y1.x;
+        acc[u][1].x += a.x * y0.z - a.y * y0.w + a.z * y1.z - a.w * y1.w;
+        acc[u][1].y += a.x * y0.w + a.y * y0.z + a.z * y1.w + a.w * y1.z;
+      }
+    }
+  }
+  float2* W = Wp + ((size_t)b * nsplit + sp) * BW * nm;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = r0 + warp * 16 + rg + 4 * u;
+    if (r < m) {
+      W[(size_t)(2 * cp) * nm + r] = acc[u][0];
+      W[(size_t)(2 * cp + 1) * nm + r] = acc[u][1];
+    }
+  }
+}
+
 // ----------------------------------------------- Z = W - 1/2 Y (T^H M) --
 // Two wide launches over row chunks of ZR rows: k_ts_wm sums the split
 // partials of W (kept in Z) and forms the chunk's share of M = Y^H W;
@@ -771,12 +854,24 @@ int solve_large_t(const SolveArgs& a) {
                                                                                               use_smem);
           }
         }
-        const int rt = (m + Tiles<T>::WR - 1) / Tiles<T>::WR;
+        // float32 with an even n_max: the register-tiled W (16-byte pairs)
+        const bool w4 = sizeof(T) == 4 && (nm % 2) == 0;
+        const int wr = w4 ? W4R : Tiles<T>::WR;
+        const int rt = (m + wr - 1) / wr;
         const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (2 * sms + rt * nb_mat - 1) / (rt * nb_mat)));
         {
           {
             ProfScope p2(KID_LG_W, a.stream);
-            k_ts_w<T><<<dim3(rt, 1, (unsigned)(nb_mat * nsplit)), 256, 0, a.stream>>>(bt, k, A, YT, Wp, nsplit);
+            if constexpr (sizeof(T) == 4) {
+              if (w4)
+                k_ts_w4<<<dim3(rt, 1, (unsigned)(nb_mat * nsplit)), 256, 0, a.stream>>>(
+                    bt, k, reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(YT),
+                    reinterpret_cast<float2*>(Wp), nsplit);
+              else
+                k_ts_w<T><<<dim3(rt, 1, (unsigned)(nb_mat * nsplit)), 256, 0, a.stream>>>(bt, k, A, YT, Wp, nsplit);
+            } else {
+              k_ts_w<T><<<dim3(rt, 1, (unsigned)(nb_mat * nsplit)), 256, 0, a.stream>>>(bt, k, A, YT, Wp, nsplit);
+            }
           }
           ProfScope p2z(KID_LG_Z, a.stream, 2);
           const int nchunk = (m + ZR - 1) / ZR;
