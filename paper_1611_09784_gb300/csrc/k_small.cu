@@ -29,6 +29,27 @@ struct __align__(2 * sizeof(c2<T>)) VW {
   c2<T> v, w;
 };
 
+// sigma = sqrt(sigma2), |alpha| = sqrt(aa2), the phase alpha / |alpha| and
+// tau = 1 / (sigma (sigma + |alpha|)) of a reflector (sigma2 > 0).  Float32
+// takes the hardware reciprocal square root and the fast divide (a relative
+// error of a few 1e-7, the size of the reduction's own rounding); float64 the
+// correctly rounded operations.
+template <typename T>
+__device__ __forceinline__ void reflector_scalars(c2<T> alpha, T aa2, T sigma2, T& sigma, T& aa, c2<T>& phs, T& tau) {
+  if constexpr (sizeof(T) == 4) {
+    sigma = sigma2 * rsqrtf(sigma2);
+    const float ra = aa2 > 0.f ? rsqrtf(aa2) : 0.f;
+    aa = aa2 * ra;
+    phs = aa2 > 0.f ? cscale<T>(alpha, ra) : mk<T>(T(1), T(0));
+    tau = __fdividef(1.f, sigma * (sigma + aa));
+  } else {
+    sigma = sqrt(sigma2);
+    aa = sqrt(aa2);
+    phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+    tau = T(1) / (sigma * (sigma + aa));
+  }
+}
+
 template <typename T>
 struct SmallLayout {
   // per group: vw[2][n_max] (pending and next pair, first: 16-byte aligned),
@@ -132,9 +153,9 @@ __device__ __forceinline__ void small_tridiag_group(unsigned char* base, int gid
     const bool tr = rest > (sizeof(T) == 4 ? T(1e-30f) : T(1e-290));
     T tau = T(0);
     if (tr) {
-      const T sigma = sqrt(sigma2), aa = sqrt(aa2);
-      const C phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
-      tau = T(1) / (sigma * (sigma + aa));
+      T sigma, aa;
+      C phs;
+      reflector_scalars<T>(alpha, aa2, sigma2, sigma, aa, phs, tau);
       for (int c = j + 1 + tid; c < n; c += NT)
         nvw[c].v = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * n + c]);
     }
@@ -146,17 +167,33 @@ __device__ __forceinline__ void small_tridiag_group(unsigned char* base, int gid
       // the common case, without branches in the row loop
       for (int c = j + 1 + tid; c < n; c += NT) {
         const VW<T> qc = vw[c];
-        C p = mk<T>(T(0), T(0));
+        // two partial sums (rows j+1, j+3, ... and j+2, j+4, ...) halve the
+        // dependent accumulation chain
+        C p0 = mk<T>(T(0), T(0)), p1 = mk<T>(T(0), T(0));
         C* ac = A + (size_t)(j + 1) * n + c;
-#pragma unroll 4
-        for (int r = j + 1; r < n; ++r, ac += n) {
-          const VW<T> qr = vw[r];
-          C a = *ac;
-          a = csub<T>(a, cmulc<T>(qr.v, qc.w));
-          a = csub<T>(a, cmulc<T>(qr.w, qc.v));
-          *ac = a;
-          p = cadd<T>(p, cjmul<T>(a, nvw[r].v));   // (A22 v)_c = sum_r conj(A[r][c]) v_r
+        int r = j + 1;
+#pragma unroll 2
+        for (; r + 1 < n; r += 2, ac += 2 * n) {
+          const VW<T> q0 = vw[r], q1 = vw[r + 1];
+          C a0 = ac[0], a1 = ac[n];
+          a0 = csub<T>(a0, cmulc<T>(q0.v, qc.w));
+          a1 = csub<T>(a1, cmulc<T>(q1.v, qc.w));
+          a0 = csub<T>(a0, cmulc<T>(q0.w, qc.v));
+          a1 = csub<T>(a1, cmulc<T>(q1.w, qc.v));
+          ac[0] = a0;
+          ac[n] = a1;
+          p0 = cadd<T>(p0, cjmul<T>(a0, nvw[r].v));   // (A22 v)_c = sum_r conj(A[r][c]) v_r
+          p1 = cadd<T>(p1, cjmul<T>(a1, nvw[r + 1].v));
         }
+        if (r < n) {
+          const VW<T> q0 = vw[r];
+          C a0 = ac[0];
+          a0 = csub<T>(a0, cmulc<T>(q0.v, qc.w));
+          a0 = csub<T>(a0, cmulc<T>(q0.w, qc.v));
+          ac[0] = a0;
+          p0 = cadd<T>(p0, cjmul<T>(a0, nvw[r].v));
+        }
+        C p = cadd<T>(p0, p1);
         p = cscale<T>(p, tau);
         nvw[c].w = p;
         const C nc = nvw[c].v;
@@ -331,9 +368,9 @@ __device__ __forceinline__ void small_tridiag_rg_cta(unsigned char* smem_raw, co
     const bool tr = rest > (sizeof(T) == 4 ? T(1e-30f) : T(1e-290));
     T tau = T(0);
     if (tr) {
-      const T sigma = sqrt(sigma2), aa = sqrt(aa2);
-      const C phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
-      tau = T(1) / (sigma * (sigma + aa));
+      T sigma, aa;
+      C phs;
+      reflector_scalars<T>(alpha, aa2, sigma2, sigma, aa, phs, tau);
       for (int c = j + 1 + tid; c < n; c += NT)
         nvw[c].v = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * LD + c]);
     }
