@@ -57,3 +57,26 @@ def test_graph_replay_fp64_model():
     for a, b in zip(got, ref):
         for x, y in zip(a, b):
             assert np.array_equal(x[1], y[1]) and np.array_equal(x[2], y[2])
+
+
+def test_graph_replay_tmdc_model():
+    """The TMDC-shaped model (two-stage path at every size, per-level launches)
+    replays with the same sums as direct launches."""
+    from synthetic import model_params, workload
+    w = workload("tmdc_sweep")
+    cfg = dict(w["model"])
+    cfg.update(p=w["p"], levels=[(4, 2), (8, 1)], e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
+               delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=1)
+    calls = [([3, 1], 5, [0, 0]), ([3, 1], 6, [3, 1]), ([3, 1], 6, [10, 20])]
+    out = {}
+    for graph in (1, 0):
+        with pkg.create_model(dict(cfg, graph=graph)) as m:
+            res = []
+            for counts, seed, firsts in calls:
+                m.sample_levels(counts, seed, firsts)
+                res.append([m.get_level_stats(l)[:3] for l in range(2)])
+            out[graph] = (res, m.graph_info())
+    assert out[1][1][2] == "" and out[1][1][0] >= 1
+    for a, b in zip(out[1][0], out[0][0]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x[1], y[1]) and np.array_equal(x[2], y[2])

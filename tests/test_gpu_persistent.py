@@ -62,3 +62,18 @@ def test_persistent_field_validated():
     w, cfg, prm = cfg_and_prm(precision="fp32")
     with pytest.raises(Exception):
         pkg.create_model(dict(cfg, persistent=2))
+
+
+@pytest.mark.parametrize("levels", [[(4, 6), (8, 3)], [(4, 6)], [(2, 4), (4, 3), (8, 2)]])
+def test_persistent_other_level_sets(levels):
+    """Two levels (the finest level's own small sets on the persistent launch,
+    partition on), one level, and three small levels (up to 5 segments)."""
+    w, cfg, prm = cfg_and_prm(precision="fp32")
+    cfg = dict(cfg, levels=levels)
+    counts = [7, 3, 2][:len(levels)]
+    firsts = [300, 301, 302][:len(levels)]
+    a = _stats(dict(cfg, persistent=1), counts, w["seed"], firsts)
+    b = _stats(dict(cfg, persistent=0, sm_split=0), counts, w["seed"], firsts)
+    for x, y in zip(a, b):
+        assert x[0] == y[0]
+        assert np.array_equal(x[1], y[1]) and np.array_equal(x[2], y[2])
