@@ -129,13 +129,14 @@ typedef struct idos_model_desc {
                           per warp, taken by whichever warp is free); 0 = one
                           launch per cell set on its level's stream; -1 =
                           library default (1).  Results are bit-identical.  */
-  int32_t graph;       /* idos_sample_levels: 1 = the call's launches (all
-                          level streams) are captured once as a CUDA graph
-                          and replayed by later calls with the same sample
-                          counts and settings, the seed and first sample
-                          indices read by the mask kernels from a device
-                          buffer; 0 = direct launches; -1 = library default
-                          (1).  Results are bit-identical.                   */
+  int32_t graph;       /* idos_sample_levels: 1 = a call that repeats the
+                          previous call's sample counts and settings is
+                          captured as a CUDA graph (all level streams) and
+                          later such calls replay it, the seed and first
+                          sample indices read by the mask kernels from a
+                          device buffer (a first call with new counts runs
+                          directly); 0 = direct launches; -1 = library
+                          default (1).  Results are bit-identical.           */
 } idos_model_desc;
 
 typedef struct idos_model idos_model;
@@ -315,8 +316,9 @@ int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, dou
  * whatever fits: 160 float32 / 112 float64) and, with the latter, the
  * persistent launch on or off (graphene, IDOS_FP32_REFINE64; on with graph
  * replay, off without), then the winner with graph replay switched (unless
- * the model gave graphs up).  Each candidate runs once
- * untimed and `reps` times timed (best kept), on sample indices from 2^40 on;
+ * the model gave graphs up).  Each candidate runs twice untimed (a direct
+ * call, then the graph capture) and `reps` times timed (best kept), on
+ * sample indices from 2^40 on;
  * the level statistics are restored afterwards.  Results do not depend on the
  * choice beyond float rounding of the path choice; out: the choice and every
  * candidate's best step time. */

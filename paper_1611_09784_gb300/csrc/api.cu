@@ -837,15 +837,21 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
   if (m->graph && !m->prof.enabled) {
     // the graph of the last call is replayed while nothing it was captured
     // from has changed: sample counts, route, settings, partition, arenas
-    std::vector<int64_t> key(n_samples, n_samples + L);
+    std::vector<int64_t> core(n_samples, n_samples + L);
     for (int64_t v : {(int64_t)parted, (int64_t)route_p, (int64_t)m->small_max_n, (int64_t)m->persistent,
                       (int64_t)m->part_gen})
-      key.push_back(v);
+      core.push_back(v);
+    std::vector<int64_t> key = core;
     for (int l = 0; l < L; ++l) key.push_back((int64_t)m->lws[l].gen);
     if (m->gexec && key == m->gkey) {
       IDOS_CUDA_TRY(cudaGraphLaunch(m->gexec, origin));
       ++m->graph_replays;
       issued = true;
+    } else if (core != m->glast) {
+      // counts and settings seen for the first time run directly: capturing
+      // pays only for calls that repeat (a fixed allocation), not for one-off
+      // calls such as the rounds of the adaptive estimator
+      m->glast = core;
     } else {
       if (m->gexec) {
         IDOS_CUDA_TRY(cudaGraphExecDestroy(m->gexec));
@@ -1232,6 +1238,8 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   int64_t first[IDOS_MAX_LEVELS];
   int64_t round = 0;
   int rc = IDOS_OK;
+  // two untimed calls per candidate: the first runs directly (and sizes the
+  // workspaces), the second captures the graph; the timed calls replay it
   auto time_config = [&](int sp, int sm, int pers, int gr) -> int {
     m->small_max_n = sm;
     m->persistent = pers;
@@ -1240,12 +1248,12 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     if (r != IDOS_OK) return r;
     if (sp > 0 && m->sm_split_now == 0) return IDOS_OK;   // the driver could not make this split
     double best = 1e300;
-    for (int k = 0; k <= reps && r == IDOS_OK; ++k) {
+    for (int k = 0; k < reps + 2 && r == IDOS_OK; ++k) {
       for (int l = 0; l < L; ++l) first[l] = (int64_t(1) << 40) + (round++) * (n_samples[l] + 1);
       const auto t0 = std::chrono::steady_clock::now();
       r = idos_sample_levels(m, n_samples, 0x5eedull, first);
       const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      if (k > 0) best = std::min(best, ms);   // k = 0 warms the configuration up (and captures)
+      if (k >= 2) best = std::min(best, ms);
     }
     if (r != IDOS_OK || out->n_tried >= IDOS_TUNE_MAX) return r;
     const int i = out->n_tried++;

@@ -137,6 +137,7 @@ struct Model {
   cudaEvent_t ljoin[IDOS_MAX_LEVELS] = {};
   cudaGraphExec_t gexec = nullptr;
   std::vector<int64_t> gkey;
+  std::vector<int64_t> glast;     // key of the previous call (a repeat is captured)
   int64_t graph_replays = 0, graph_captures = 0;
   std::string graph_note;         // why graph mode was given up ("" while it works)
   uint64_t part_gen = 0;          // bumped by every partition rebuild
