@@ -240,8 +240,13 @@ typedef struct idos_estimate {
 
 /* Adaptive MLMC (Sec. 2.2): pilot round (see pilot_samples), V_l and
  * W_l, M_l from eq. (2.7) with target variance (theta tol / c_alpha)^2, extra
- * samples, combine by eq. (2.6).  Starts from zeroed accumulators.  Sample
- * indices continue from 0 on every level. */
+ * samples, combine by eq. (2.6).  With three or more levels the pilots of
+ * all but the finest level run first, and the finest level's pilot runs in
+ * one concurrent call with a provisional top-up of the other levels sized by
+ * eq. (2.7) with the finest level's term estimated from the variance decay
+ * of the two levels below it (half of it counted); the rounds then top up
+ * every level to eq. (2.7) with all pilots.  Starts from zeroed
+ * accumulators.  Sample indices continue from 0 on every level. */
 int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* out);
 
 /* ---- kernel timing (tracing) ----

@@ -1112,38 +1112,67 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   for (int l = 0; l < L; ++l)
     target[l] = std::max<int64_t>(4, (int64_t)std::ceil(o->pilot_samples *
                                                         std::sqrt(flop_model(m->d, 0) / flop_model(m->d, l))));
-  int64_t d2h = 0;
+  int64_t d2h = 0, h2d = 0;
   int rounds = 0;
+  // V_l (max over the grid of the unbiased sample variance) and W_l of level l
+  auto estimate_vw = [&](int l) -> int {
+    int64_t M = 0;
+    double secs = 0;
+    IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
+    d2h += 2 * (int64_t)sizeof(double) * n_E;
+    double vmax = 0.0;
+    for (int j = 0; j < n_E; ++j) {
+      const double mean = sum[j] / M;
+      const double v = std::max(0.0, (sq[j] - M * mean * mean) / (M - 1));
+      vmax = std::max(vmax, v);
+    }
+    V[l] = std::max(vmax, 1e-300);
+    W[l] = o->work_model == 1 ? std::max(secs / M, 1e-12) : flop_model(m->d, l);
+    return IDOS_OK;
+  };
+  const double f = (o->c_alpha / (o->theta * o->tol)) * (o->c_alpha / (o->theta * o->tol));
+  auto sample = [&](const int64_t* extra) -> int {
+    int64_t first[IDOS_MAX_LEVELS] = {};
+    for (int l = 0; l < L; ++l) first[l] = m->M[l];
+    h2d += (int64_t)sizeof(uint64_t) * (1 + L);   // the call's seed and first sample indices
+    return idos_sample_levels(m, extra, o->seed, first);
+  };
+  if (L >= 3) {
+    // The finest level's pilot is the longest part of the pilot round, so it
+    // runs beside a provisional top-up of the other levels: their pilots come
+    // first, then eq. (2.7) with the finest level's term estimated from the
+    // rate at which the variance decays over the two levels below it
+    // (V_{L-1} ~ V_{L-2}^2 / V_{L-3}, W_{L-1} from the flop model relative to
+    // W_{L-2}), counted at half its size so that the provisional targets stay
+    // below the final ones; round 0 below issues both at once.
+    int64_t extra[IDOS_MAX_LEVELS] = {};
+    for (int l = 0; l + 1 < L; ++l) extra[l] = target[l];
+    IDOS_TRY(sample(extra));
+    double s0 = 0.0;
+    for (int l = 0; l + 1 < L; ++l) {
+      IDOS_TRY(estimate_vw(l));
+      s0 += std::sqrt(W[l] * V[l]);
+    }
+    const double v_fin = V[L - 2] * std::min(1.0, V[L - 2] / V[L - 3]);
+    const double w_fin = W[L - 2] * flop_model(m->d, L - 1) / flop_model(m->d, L - 2);
+    s0 += 0.5 * std::sqrt(w_fin * v_fin);
+    for (int l = 0; l + 1 < L; ++l)
+      target[l] = std::max(target[l], std::max<int64_t>(2, (int64_t)std::ceil(f * std::sqrt(V[l] / W[l]) * s0)));
+  }
   for (int round = 0; round <= o->max_rounds; ++round) {
     // every level's extra samples in one concurrent call (level streams)
-    int64_t extra[IDOS_MAX_LEVELS] = {}, first[IDOS_MAX_LEVELS] = {};
+    int64_t extra[IDOS_MAX_LEVELS] = {};
     bool any = false;
     for (int l = 0; l < L; ++l) {
       extra[l] = std::max<int64_t>(0, target[l] - m->M[l]);
-      first[l] = m->M[l];
       any = any || extra[l] > 0;
     }
-    if (any) IDOS_TRY(idos_sample_levels(m, extra, o->seed, first));
+    if (any) IDOS_TRY(sample(extra));
     if (round == o->max_rounds) break;
-    // V_l (max over the grid of the unbiased sample variance), W_l
-    for (int l = 0; l < L; ++l) {
-      int64_t M = 0;
-      double secs = 0;
-      IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
-      d2h += 2 * (int64_t)sizeof(double) * n_E;
-      double vmax = 0.0;
-      for (int j = 0; j < n_E; ++j) {
-        const double mean = sum[j] / M;
-        const double v = std::max(0.0, (sq[j] - M * mean * mean) / (M - 1));
-        vmax = std::max(vmax, v);
-      }
-      V[l] = std::max(vmax, 1e-300);
-      W[l] = o->work_model == 1 ? std::max(secs / M, 1e-12) : flop_model(m->d, l);
-    }
+    for (int l = 0; l < L; ++l) IDOS_TRY(estimate_vw(l));
     // eq. (2.7)
     double s = 0.0;
     for (int l = 0; l < L; ++l) s += std::sqrt(W[l] * V[l]);
-    const double f = (o->c_alpha / (o->theta * o->tol)) * (o->c_alpha / (o->theta * o->tol));
     bool more = false;
     for (int l = 0; l < L; ++l) {
       const int64_t Ml = std::max<int64_t>(2, (int64_t)std::ceil(f * std::sqrt(V[l] / W[l]) * s));
@@ -1175,7 +1204,7 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   }
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   out->rounds = rounds;
-  out->h2d_bytes = 0;   // every input (model, seeds, sizes) travels as kernel arguments
+  out->h2d_bytes = h2d;   // per call: seed and first sample indices (model and sizes travel as kernel arguments)
   out->d2h_bytes = d2h;
   return IDOS_OK;
 }

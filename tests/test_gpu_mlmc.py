@@ -1,0 +1,56 @@
+"""The adaptive MLMC estimator (idos_mlmc_estimate, eq. (2.6)-(2.7)) against
+the oracle: the same estimator recomputed by the oracle on the same samples,
+and a one-level estimate against the exact expectation over every vacancy
+outcome of a 2 x 2 cell."""
+import numpy as np
+import pytest
+
+from oracle import mlmc as omlmc
+
+from gpu_common import IDOS_TOL, cfg_and_prm
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_1611_09784_gb300")
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_estimate_equals_oracle_on_the_same_samples(persistent):
+    """Level l uses samples 0 .. M_l - 1 of the seed: the oracle's level
+    differences over those samples give the same mean (eq. (2.6)) within the
+    per-sample IDoS tolerance, and the same level variances."""
+    levels = [(2, 4), (4, 3), (8, 2)]
+    w, cfg, prm = cfg_and_prm(precision="fp32", p=0.1)
+    cfg = dict(cfg, levels=levels, persistent=persistent)
+    seed = 4242
+    with pkg.create_model(cfg) as m:
+        est = m.mlmc_estimate(8e-3, theta=0.5, c_alpha=1.96, pilot_samples=8, max_rounds=3, seed=seed)
+    M = [int(x) for x in est["M"]]
+    assert all(x >= 2 for x in M) and est["rounds"] >= 1
+    assert est["h2d_bytes"] > 0 and est["d2h_bytes"] > 0
+    mean = np.zeros_like(est["mean"])
+    var = np.zeros_like(est["var"])
+    for l, Ml in enumerate(M):
+        Y = np.array([omlmc.level_sample(prm, levels, l, s, seed)["Y"] for s in range(Ml)])
+        mean += Y.mean(0)
+        var += Y.var(0, ddof=1) / Ml
+        # per-sample differences below IDOS_TOL move a variance by at most
+        # about 2 IDOS_TOL max|Y - mean| + IDOS_TOL^2
+        assert abs(est["V"][l] - Y.var(0, ddof=1).max()) <= 4 * IDOS_TOL * np.abs(Y).max() + 2 * IDOS_TOL ** 2
+    assert np.max(np.abs(est["mean"] - mean)) < len(levels) * IDOS_TOL
+    assert np.max(np.abs(np.sqrt(est["var"]) - np.sqrt(var))) < len(levels) * IDOS_TOL
+
+
+def test_one_level_estimate_matches_exhaustive_expectation():
+    """Plain MC on a 2 x 2 cell (eq. (2.6) with one level): within four
+    standard errors of E[Q] summed over all 2^8 vacancy outcomes."""
+    w, cfg, prm = cfg_and_prm(precision="fp32", p=0.3)
+    K = 3
+    cfg = dict(cfg, levels=[(2, K)])
+    prm = dict(prm, p=0.3)
+    exact = omlmc.exhaustive_expectation(prm, 2, K)
+    with pkg.create_model(cfg) as m:
+        est = m.mlmc_estimate(2e-3, theta=0.5, c_alpha=1.96, pilot_samples=64, max_rounds=3, seed=77)
+    se = np.sqrt(est["var"])
+    assert int(est["M"][0]) >= 64
+    assert np.all(np.abs(est["mean"] - exact) <= 4.0 * se + IDOS_TOL)
