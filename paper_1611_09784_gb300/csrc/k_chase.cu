@@ -609,6 +609,229 @@ k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
   if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while others may still read its shared memory
 }
 
+// ------------------------------------------------------ warp-pair chase --
+// The clustered dataflow chase with two warps per sweep.  A step's work
+// splits at its reflector: the E warp waits for the step's inputs, applies
+// the previous reflector to the block below the previous diagonal block (or,
+// at step 0, takes column i), forms the new reflector and applies it to that
+// block from the left; the D warp loads the next diagonal block meanwhile and,
+// once the reflector is in shared memory, applies it two-sided.  The two
+// halves write disjoint entries (E: columns [j0, j0 + BW) below row
+// j0 + BW - 1; D: rows and columns from j0 + BW), and the next step of the
+// sweep touches neither half's block except through the reflector, so they
+// run side by side.  Both warps pass the same three pair barriers per step
+// (inputs ready / reflector ready / step done) in the same order on every
+// path; only the E warp polls (bounded) and hands its outcome to the D warp
+// through shared memory before the first barrier, so a wait that gives up
+// ends both warps' loops at the same point.
+__device__ __forceinline__ void pair_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// E half of step k of sweep i; wsd: the D warp's scratch, which receives the
+// reflector (v in wsd->v, tau in wsd->tau_prev) before the reflector barrier.
+template <typename T, typename BandT>
+__device__ __forceinline__ void pair_step_e(const BandT& bd, int n, int i, int k, DScratch<T>* ws, DScratch<T>* wsd,
+                                            int bar) {
+  using C = c2<T>;
+  const int lane = threadIdx.x & 31, l = lane & 15, h = lane >> 4;
+  if (k == 0) {
+    const int L = min(BW, n - 1 - i);
+    const C x = (h == 0 && l < L) ? bd.get(i + 1 + l, i) : mk<T>(T(0), T(0));
+    T tau;
+    C v, beta;
+    const bool tr = dreflector<T>(x, L, tau, v, beta);
+    if (tr && h == 0 && l < L) bd.set(i + 1 + l, i, l == 0 ? beta : mk<T>(T(0), T(0)));
+    if (h == 0) wsd->v[l] = (tr && l < L) ? v : mk<T>(T(0), T(0));
+    if (lane == 0) wsd->tau_prev = tr ? tau : T(0);
+    pair_bar(bar);   // reflector ready
+    if (h == 0) ws->vp[l] = (tr && l < L) ? v : mk<T>(T(0), T(0));
+    if (lane == 0) ws->tau_prev = tr ? tau : T(0);
+    return;
+  }
+  const int j0 = i + 1 + (k - 1) * BW;
+  const int Lp = min(BW, n - j0);
+  const int r0 = j0 + BW;
+  const int Lr = min(BW, n - r0);
+  C e[HB];
+  dload<T>(bd, r0, j0, Lr, Lp, e);
+  __syncwarp();
+  const T tprev = ws->tau_prev;
+  if (tprev != T(0)) {
+    C u = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int q = 0; q < HB; ++q) u = cadd<T>(u, cmul<T>(e[q], ws->vp[h * HB + q]));
+    u.x += __shfl_xor_sync(0xffffffffu, u.x, 16);
+    u.y += __shfl_xor_sync(0xffffffffu, u.y, 16);
+    u = cscale<T>(u, tprev);
+#pragma unroll
+    for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cmulc<T>(u, ws->vp[h * HB + q]));
+  }
+  T tau;
+  C v, beta;
+  const bool tr = dreflector<T>(e[0], Lr, tau, v, beta);
+  if (h == 0) wsd->v[l] = (tr && l < Lr) ? v : mk<T>(T(0), T(0));
+  if (lane == 0) wsd->tau_prev = tr ? tau : T(0);
+  pair_bar(bar);   // reflector ready
+  if (tr) {
+#pragma unroll
+    for (int q = 0; q < HB; ++q) ws->m[l][h * HB + q] = l < Lr ? cjmul<T>(v, e[q]) : mk<T>(T(0), T(0));
+    __syncwarp();
+    {
+      const int c = l;
+      C acc = mk<T>(T(0), T(0));
+#pragma unroll
+      for (int rr = 0; rr < HB; ++rr) acc = cadd<T>(acc, ws->m[h * HB + rr][c]);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+      __syncwarp();
+      if (h == 0) ws->w[c] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < HB; ++q) e[q] = csub<T>(e[q], cscale<T>(cmul<T>(v, ws->w[h * HB + q]), tau));
+    if (h == 0) e[0] = l == 0 ? beta : mk<T>(T(0), T(0));
+  }
+  if (l < Lr) {
+#pragma unroll
+    for (int q = 0; q < HB; ++q)
+      if (h * HB + q < Lp) bd.set(r0 + l, j0 + h * HB + q, e[q]);
+  }
+  __syncwarp();
+  if (h == 0) ws->vp[l] = (tr && l < Lr) ? v : mk<T>(T(0), T(0));
+  if (lane == 0) ws->tau_prev = tr ? tau : T(0);
+}
+
+// D half of step k of sweep i: the two-sided update of the diagonal block
+// with the reflector the E warp left in ws (this warp's scratch).
+template <typename T, typename BandT>
+__device__ __forceinline__ void pair_step_d(const BandT& bd, int n, int i, int k, DScratch<T>* ws, int bar) {
+  using C = c2<T>;
+  const int l = threadIdx.x & 15;
+  const int r0 = k == 0 ? i + 1 : i + 1 + k * BW;
+  const int L = k == 0 ? min(BW, n - 1 - i) : min(BW, n - r0);
+  C dr[HB];
+  dload<T>(bd, r0, r0, L, L, dr);
+  pair_bar(bar);   // reflector ready
+  const T tau = ws->tau_prev;
+  if (tau != T(0)) dtwo_sided<T>(bd, r0, L, tau, ws->v[l], ws, dr);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * Chase<T>::WARPS)
+k_ts_chase_pair(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T* __restrict__ e2_out, int cwl,
+                int* __restrict__ err) {
+  using C = c2<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int CSZ = (int)cg::this_cluster().num_blocks();
+  const int rank = (int)cg::this_cluster().block_rank();
+  const int nwarps = blockDim.x >> 5, npairs = nwarps >> 1;
+  const int cw = 1 << cwl;
+  const int NSL = chase_ring(cw);
+  const int b = blockIdx.x / CSZ;
+  const int n = batch_n(bt, b);
+  const int nm = bt.n_max;
+  const int lo = rank * cw, hi = lo + cw;
+  DScratch<T>* wsc = reinterpret_cast<DScratch<T>*>(smem_raw);
+  Mailbox<T>* mbox = reinterpret_cast<Mailbox<T>*>(wsc + nwarps);   // [NMB]
+  int* prog = reinterpret_cast<int*>(mbox + NMB);                  // [NSL]
+  int* pok = prog + NSL;                                           // [16] per pair: inputs ready
+  const size_t head =
+      sizeof(DScratch<T>) * nwarps + sizeof(Mailbox<T>) * NMB + sizeof(int) * ((size_t)NSL + 16);
+  C* local = reinterpret_cast<C*>(smem_raw + ((head + 255) & ~size_t(255)));
+  const C* gband = Bd + (size_t)b * ND * nm;
+  for (int idx = threadIdx.x; idx < ND * cw; idx += blockDim.x) {
+    const int d = idx >> cwl, c = lo + (idx & (cw - 1));
+    local[idx] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
+  }
+  for (int idx = threadIdx.x; idx < NSL; idx += blockDim.x) prog[idx] = 0;
+  cg::this_cluster().sync();
+  const DBand<T, true> bd{local, cwl, rank};
+  const LBand<T> lb{local, cwl, lo};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, l = lane & 15, h = lane >> 4;
+  const int pair = warp >> 1, role = warp & 1;   // role 0: E half, 1: D half
+  const int bar = 1 + pair;                      // named barrier of the pair (0 is the CTA's)
+  DScratch<T>* ws = wsc + warp;
+  DScratch<T>* wsd = wsc + (warp | 1);           // the pair's D scratch (receives the reflector)
+  auto wait_for = [&](int slot, int want) -> bool {
+    bool ok = true;
+    int spins = 0;
+    while (ld_acquire<true>(prog + slot) < want) {
+      ++spins;
+      if ((spins & 1023) == 0 && (spins >= (1 << 25) || *(volatile int*)err)) {
+        atomicExch(err, 1);
+        ok = false;
+        break;
+      }
+      if (spins > 256) __nanosleep(20);
+    }
+    return __all_sync(0xffffffffu, ok);
+  };
+  bool ok = true;
+  for (int i = pair; ok && i <= n - 3 && i < hi; i += npairs) {
+    const int nsteps = (n - 2 - i) / BW + 1;
+    const int klo = i >= lo ? 0 : (lo - i - 1 + BW - 1) / BW + 1;
+    const int khi = min(nsteps, (hi - i - 1 + BW - 1) / BW + 1);
+    if (klo >= khi) continue;
+    const int dep_steps = i > 0 ? (n - 1 - i) / BW + 1 : 0;
+    for (int k = klo; k < khi; ++k) {
+      // inputs: the E warp waits (bounded) and hands the outcome over
+      if (role == 0) {
+        bool in_ok = true;
+        if (k == klo && klo > 0) {
+          in_ok = wait_for(i % NSL, i * 1024 + k);
+          if (in_ok) {
+            const Mailbox<T>* mb = mbox + (i % NMB);
+            if (h == 0) ws->vp[l] = mb->v[l];
+            if (lane == 0) ws->tau_prev = mb->tau;
+          }
+        }
+        if (in_ok && i > 0) in_ok = wait_for((i - 1) % NSL, (i - 1) * 1024 + min(k + 2, dep_steps));
+        if (lane == 0) pok[pair] = in_ok ? 1 : 0;
+      }
+      pair_bar(bar);   // inputs ready
+      ok = pok[pair] != 0;
+      if (!ok) break;
+      const int anchor = k == 0 ? i : i + 1 + (k - 1) * BW;
+      const bool here = anchor + 2 * BW <= hi;
+      if (role == 0) {
+        if (here) pair_step_e<T>(lb, n, i, k, ws, wsd, bar);
+        else pair_step_e<T>(bd, n, i, k, ws, wsd, bar);
+      } else {
+        if (here) pair_step_d<T>(lb, n, i, k, ws, bar);
+        else pair_step_d<T>(bd, n, i, k, ws, bar);
+      }
+      const bool handover = k == khi - 1 && k + 1 < nsteps;
+      if (role == 0 && handover) {
+        Mailbox<T>* mb = cg::this_cluster().map_shared_rank(mbox + (i % NMB), rank + 1);
+        __syncwarp();
+        if (h == 0) mb->v[l] = ws->vp[l];
+        if (lane == 0) mb->tau = ws->tau_prev;
+      }
+      pair_bar(bar);   // step done (both halves' writes before the release below)
+      if (role == 0 && lane == 0) {
+        const int tagv = i * 1024 + k + 1;
+        int* own = prog + (i % NSL);
+        fence_acq_rel<true>();
+        if (rank > 0) st_relaxed<true>(cg::this_cluster().map_shared_rank(own, rank - 1), tagv);
+        st_relaxed<true>(own, tagv);
+        if (rank + 1 < CSZ) {
+          int* right = cg::this_cluster().map_shared_rank(own, rank + 1);
+          if (handover) st_release<true>(right, tagv);
+          else st_relaxed<true>(right, tagv);
+        }
+      }
+    }
+  }
+  cg::this_cluster().sync();
+  for (int c_ = threadIdx.x; c_ < cw; c_ += blockDim.x) {
+    const int c = lo + c_;
+    if (c < n) {
+      d_out[(size_t)b * nm + c] = bd.get(c, c).x;
+      if (c < n - 1) e2_out[(size_t)b * nm + c] = cabs2<T>(bd.get(c + 1, c));
+    }
+  }
+  cg::this_cluster().sync();   // no CTA leaves while others may still read its shared memory
+}
+
 template <typename T>
 int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p) {
   using C = c2<T>;
@@ -651,6 +874,27 @@ int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p) 
       break;
     }
   }
+  // Two warps per sweep when the cluster splits the band into CTAs narrow
+  // enough that the pairs still cover a CTA's active sweeps (a pair leaves a
+  // sweep after cw / BW steps, the next sweep starts 2 steps later).
+  if (p.csz > 1) {
+    const int cw = 1 << p.ccwl;
+    const int pairs = std::min(Chase<T>::WARPS / 2, cw / (2 * BW) + 2);
+    if (pairs >= cw / (2 * BW) && pairs >= 1) {
+      const size_t hb = (sizeof(DScratch<T>) * 2 * pairs + sizeof(Mailbox<T>) * NMB +
+                         sizeof(int) * ((size_t)chase_ring(cw) + 16) + 255) & ~size_t(255);
+      const size_t need = hb + sizeof(C) * (size_t)ND * cw + 64;
+      if (need <= 200 * 1024) {
+        p.pair = 1;
+        p.cwarps = 2 * pairs;
+        p.csmem = need;
+        IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_pair<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.csmem));
+        if (p.csz > 8)
+          IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_pair<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        return IDOS_OK;
+      }
+    }
+  }
   if (p.csz == 1) {
     IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_chase_flow<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.csmem));
   } else if (p.csz > 1) {
@@ -681,7 +925,10 @@ int chase_run_t(const ChasePlan& p, const Batch& bt, const c2<T>* A, c2<T>* Bd, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    IDOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ts_chase_flow<T, true>, bt, (const C*)Bd, d, e2, p.ccwl, err));
+    if (p.pair)
+      IDOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ts_chase_pair<T>, bt, (const C*)Bd, d, e2, p.ccwl, err));
+    else
+      IDOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_ts_chase_flow<T, true>, bt, (const C*)Bd, d, e2, p.ccwl, err));
   } else {
     k_ts_chase<T><<<nb, p.threads, p.smem, s>>>(bt, Bd, d, e2, p.slots, p.band_in_smem);
   }

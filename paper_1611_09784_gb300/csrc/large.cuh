@@ -46,6 +46,7 @@ __device__ __forceinline__ int batch_n(const Batch& b, int m) {
 // kernel (bands too large for 16 CTAs).
 struct ChasePlan {
   int csz = 0, cwarps = 0, ccwl = 0;
+  int pair = 0;   // clustered chase with two warps per sweep (k_ts_chase_pair)
   size_t csmem = 0;
   int threads = 0, slots = 0, band_in_smem = 0;
   size_t smem = 0;
