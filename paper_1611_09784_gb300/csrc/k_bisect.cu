@@ -88,55 +88,67 @@ __device__ __forceinline__ int sturm_newton64(const double* __restrict__ d, cons
 
 __device__ __forceinline__ int fexp(float v) { return (__float_as_int(v) >> 23) & 0xff; }
 
-// The same pass with the derivative carried in float32: the count and p_n(x)
-// (the residual, where the cancellation is) stay float64 - three float64
-// operations per row - while p' only sets the Newton step length, for which
-// float32 accuracy is ample (a relative error r in p' leaves an error r times
-// the step; a wild value is caught by the bracket safeguard).  The float32
-// recurrence runs on a float32 copy of p (d32, e32: the same normalised
-// tridiagonal rounded to float32), so no per-row float64 -> float32
-// conversion is needed.  With |T| <= 1 (the caller normalises) a value grows
-// by at most 3x per row, so an exponent check every 8 rows that rescales all
-// values by 2^-e once the largest binary exponent e leaves [-60, 60] keeps
-// the float32 values far from overflow.
-__device__ __forceinline__ int sturm_newton_mixed(const double* __restrict__ d, const double* __restrict__ e2,
-                                                  const float* __restrict__ d32, const float* __restrict__ e32, int n,
-                                                  double x, double& step) {
+// The float32 path keeps its rows interleaved: de[i] = (d_i, e^2_{i-1}) in
+// float32 and dde[i] the same pair in float64, so a row is one 8-byte
+// (16-byte) shared-memory load.  sturm_count_pairs is sturm_count on de.
+// sturm_newton_mixed_pairs is the float64 pass above with the derivative
+// carried in float32: the count and p_n(x) (the residual, where the
+// cancellation is) stay float64 - three float64 operations per row - while p'
+// only sets the Newton step length, for which float32 accuracy is ample (a
+// relative error r in p' leaves an error r times the step; a wild value is
+// caught by the bracket safeguard).  The float32 recurrence runs on a float32
+// copy of p (from de, the same normalised tridiagonal rounded to float32), so
+// no per-row float64 -> float32 conversion is needed.  With |T| <= 1 (the
+// caller normalises) a value grows by at most 3x per row, so an exponent
+// check every 8 rows that rescales all values by 2^-e once the largest binary
+// exponent e leaves [-60, 60] keeps the float32 values far from overflow.
+__device__ __forceinline__ int sturm_count_pairs(const float2* __restrict__ de, int n, float x, float pivmin) {
+  float q = de[0].x - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.f;
+  for (int i = 1; i < n; ++i) {
+    const float2 r = de[i];
+    q = (r.x - x) - __fdividef(r.y, q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
+__device__ __forceinline__ int sturm_newton_mixed_pairs(const double2* __restrict__ dde, const float2* __restrict__ de,
+                                                        int n, double x, double& step) {
   const float x32 = (float)x;
-  double p0 = 1.0, p1 = d[0] - x;
-  float r0 = 1.0f, r1 = d32[0] - x32;           // float32 copy of p
-  float q0 = 0.0f, q1 = -1.0f;                  // p', float32
+  double p0 = 1.0, p1 = dde[0].x - x;
+  float r0 = 1.0f, r1 = de[0].x - x32;
+  float q0 = 0.0f, q1 = -1.0f;
   if (dzero(p1)) p1 = -0x1p-1000;
   int cnt = dneg(p1);
   bool lost = false;
   for (int i = 1; i < n; ++i) {
-    const double t = d[i] - x;
-    double p2 = fma(t, p1, -(e2[i - 1] * p0));
-    const float t32 = d32[i] - x32, b32 = e32[i - 1];
+    const double2 rd = dde[i];
+    const float2 rf = de[i];
+    const double t = rd.x - x;
+    double p2 = fma(t, p1, -(rd.y * p0));
+    const float t32 = rf.x - x32, b32 = rf.y;
     const float r2 = fmaf(t32, r1, -(b32 * r0));
     const float q2 = fmaf(t32, q1, -fmaf(b32, q0, r1));
-    // an exact zero becomes +-2^-1000 of the sign opposite to p1 (a negative
-    // pivot), chosen on the bit patterns so that no float64 work is issued
     if (dzero(p2)) p2 = dneg(p1) ? 0x1p-1000 : -0x1p-1000;
     cnt += dneg(p2) != dneg(p1);
     p0 = p1; p1 = p2; r0 = r1; r1 = r2; q0 = q1; q1 = q2;
     if ((i & 7) == 0) {
-      // unbiased exponents; a zero (field 0) does not take part
       const int ep = max(dexp(p0), dexp(p1));
       const int eq = max(fexp(q0), fexp(q1));
       const int e = max(ep > 0 ? ep - 1023 : -2000, eq > 0 ? eq - 127 : -2000);
       if (e > 60 || (e < -60 && e > -2000)) {
         const int ed = min(max(e, -1000), 1000), ef = min(max(e, -126), 126);
-        const double sd = __hiloint2double((1023 - ed) << 20, 0);   // 2^-ed
-        const float sf = __int_as_float((127 - ef) << 23);           // 2^-ef
+        const double sd = __hiloint2double((1023 - ed) << 20, 0);
+        const float sf = __int_as_float((127 - ef) << 23);
         p0 *= sd; p1 *= sd;
         r0 *= sf; r1 *= sf; q0 *= sf; q1 *= sf;
-        lost |= ed != ef;   // float32 values out of range: no Newton step
+        lost |= ed != ef;
       }
     }
   }
-  // p and (r, q) carry the same scale; a zero step ends the polish at the
-  // bracket midpoint
   step = (!lost && q1 != 0.0f) ? -p1 * (double)(1.0f / q1) : 0.0;
   return cnt;
 }
@@ -184,6 +196,22 @@ __device__ __forceinline__ void bisect_index(const S* d, const S* e2, int n, int
   }
 }
 
+__device__ __forceinline__ void bisect_index_pairs(const float2* de, int n, int k, float pivmin, float& lo, float& hi,
+                                                   int max_iter, float atol) {
+  for (int it = 0; it < max_iter; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (hi - lo <= fmaxf(2.0f * ulp_of<float>(fabsf(lo) > fabsf(hi) ? lo : hi), atol)) break;
+    if (sturm_count_pairs(de, n, mid, pivmin) >= k + 1) hi = mid;
+    else lo = mid;
+  }
+}
+
+// Byte offset of the float64 pair copies in the float32 layout (16-byte aligned).
+__host__ __device__ __forceinline__ size_t bisect_pair_offset(int n_max, int mpb) {
+  return (sizeof(float) * 2 * (size_t)n_max * mpb + 15) & ~size_t(15);
+}
+
 // One group of G threads per (matrix, chunk of `chunk` eigenvalue indices),
 // MPB groups per CTA; every group holds its matrix's whole (d, e^2) in shared
 // memory.  S = storage type of (d, e^2).
@@ -199,12 +227,14 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   const int c_lo = (int)(gidx - mat * n_chunks) * chunk;
   const int c_hi = min(n_max, c_lo + chunk);
   if (mat >= n_mat) return;
+  // float64 storage: d[n_max], e2[n_max] per group.  float32 storage: the
+  // same bytes hold de[n_max] = (d_i, e^2_{i-1}) pairs, then (16-byte
+  // aligned) their float64 copies dde[n_max].
   S* d = reinterpret_cast<S*>(smem_raw) + (size_t)gid * 2 * n_max;
   S* e2 = d + n_max;
-  // float64 copy for the float64 passes (the same arrays when S is double)
-  double* dd;
-  if constexpr (sizeof(S) == 8) dd = reinterpret_cast<double*>(d);
-  else dd = reinterpret_cast<double*>(smem_raw + sizeof(S) * 2 * (size_t)n_max * MPB) + (size_t)gid * 2 * n_max;
+  float2* de = reinterpret_cast<float2*>(smem_raw) + (size_t)gid * n_max;
+  double2* dde = reinterpret_cast<double2*>(smem_raw + bisect_pair_offset(n_max, MPB)) + (size_t)gid * n_max;
+  double* dd = reinterpret_cast<double*>(d);   // float64 path: the same arrays
   double* ee = dd + n_max;
   __shared__ double red_lo[MPB][G / 32], red_hi[MPB][G / 32], red_e[MPB][G / 32];
   const int n = n_act_cell ? n_act_cell[mat / K2] : n_max;
@@ -219,8 +249,15 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   for (int i = tid; i < n; i += G) {
     const S di = d_in[mat * n_max + i];
     const S ei = (i < n - 1) ? e2_in[mat * n_max + i] : S(0);
-    d[i] = di;
-    e2[i] = ei;
+    if constexpr (sizeof(S) == 4) {
+      float* def = reinterpret_cast<float*>(de);
+      def[2 * i] = di;
+      if (i + 1 < n) def[2 * (i + 1) + 1] = ei;
+      if (i == 0) def[1] = 0.0f;
+    } else {
+      d[i] = di;
+      e2[i] = ei;
+    }
     const S el = (i > 0) ? sqrt(e2_in[mat * n_max + i - 1]) : S(0);
     const S er = sqrt(ei);
     glo_s = fmin(glo_s, di - el - er);
@@ -255,14 +292,17 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   ex = sizeof(S) == 4 ? min(max(ex, -60), 60) : min(max(ex, -900), 900);
   const double sc = ldexp(1.0, -ex), isc = ldexp(1.0, ex);
   group_sync<G, MPB>(gid);
-  const S sc_s = (S)sc;   // 2^-ex, |ex| <= 900: exact in float64; float32 uses |ex| <= 126
+  const S sc_s = (S)sc;   // 2^-ex, |ex| <= 900: exact in float64; float32 uses |ex| <= 60
   for (int i = tid; i < n; i += G) {
-    const S di = d[i] * sc_s, ei = e2[i] * sc_s * sc_s;
-    d[i] = di;
-    e2[i] = ei;
     if constexpr (sizeof(S) == 4) {
-      dd[i] = (double)di;
-      ee[i] = (double)ei;
+      float2 r = de[i];
+      r.x = r.x * sc_s;
+      r.y = r.y * sc_s * sc_s;
+      de[i] = r;
+      dde[i] = make_double2((double)r.x, (double)r.y);
+    } else {
+      d[i] = d[i] * sc_s;
+      e2[i] = e2[i] * sc_s * sc_s;
     }
   }
   group_sync<G, MPB>(gid);
@@ -289,8 +329,8 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
       out[k] = isc * newton_polish(pass, k, lo, hi, 60);
     } else {
       float lo = (float)glo, hi = (float)ghi;
-      bisect_index<float, S>(d, e2, n, k, piv32, lo, hi, 100, atol32);
-      const auto pass = [&](double x, double& step) { return sturm_newton_mixed(dd, ee, d, e2, n, x, step); };
+      bisect_index_pairs(de, n, k, piv32, lo, hi, 100, atol32);
+      const auto pass = [&](double x, double& step) { return sturm_newton_mixed_pairs(dde, de, n, x, step); };
       out[k] = isc * (refine > 0 ? newton_polish(pass, k, (double)lo, (double)hi, refine)
                                  : 0.5 * ((double)lo + (double)hi));
     }
@@ -300,7 +340,8 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
 template <typename S, int G, int MPB>
 int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int n_max, int64_t n_mat,
                int refine, double* eigs, cudaStream_t s, int chunk) {
-  const size_t smem = (sizeof(S) + (sizeof(S) == 4 ? 8 : 0)) * 2 * (size_t)n_max * MPB;
+  const size_t smem = sizeof(S) == 4 ? bisect_pair_offset(n_max, MPB) + sizeof(double) * 2 * (size_t)n_max * MPB
+                                     : sizeof(S) * 2 * (size_t)n_max * MPB;
   auto kern = k_bisect<S, G, MPB>;
   IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t groups = n_mat * ((n_max + chunk - 1) / chunk);
