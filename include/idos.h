@@ -321,7 +321,9 @@ int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, dou
  * whatever fits: 160 float32 / 112 float64) and, with the latter, the
  * persistent launch on or off (graphene, IDOS_FP32_REFINE64; on with graph
  * replay, off without), then the winner with graph replay switched (unless
- * the model gave graphs up).  Each candidate runs twice untimed (a direct
+ * the model gave graphs up), then the two-stage kernel shapes (the W tile
+ * and one or two warps per sweep in clustered band chases).  Each candidate
+ * runs twice untimed (a direct
  * call, then the graph capture) and `reps` times timed (best kept), on
  * sample indices from 2^40 on;
  * the level statistics are restored afterwards.  Results do not depend on the
@@ -340,6 +342,10 @@ typedef struct idos_tuning {
   int32_t tried_persistent[IDOS_TUNE_MAX];
   int32_t graph;         /* chosen graph setting (idos_model_desc.graph) */
   int32_t tried_graph[IDOS_TUNE_MAX];
+  int32_t w_tile;        /* stage-1 W kernel: 1 = 128-row register tiles, 0 = 64-row tiles */
+  int32_t chase_pair;    /* clustered band chases: 1 = two warps per sweep, 0 = one */
+  int32_t tried_w_tile[IDOS_TUNE_MAX];
+  int32_t tried_chase_pair[IDOS_TUNE_MAX];
 } idos_tuning;
 int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
 

@@ -93,6 +93,11 @@ struct SolveArgs {
   // for every cluster size, the panel QR never exceeds 8)
   int sm_avail = 0;
   int max_cluster = 16;
+  // kernel shapes of the two-stage path (set by the autotuner): the float32
+  // W = A22 (Y T) kernel with 128-row register tiles (1) or 64-row tiles (0);
+  // clustered band chases with two warps per sweep (1) or one (0)
+  int w_tile = 1;
+  int chase_pair = 1;
 };
 
 // Two green contexts splitting the device's SMs (partition.cu): ctx[0] has
@@ -147,6 +152,7 @@ struct Model {
   int sm_split_now = 0;           // SMs reserved for the finest level now (0: no partition)
   int small_max_n = -1;           // largest n on the shared-memory kernel (-1: whatever fits)
   int persistent = 1;             // one persistent launch for the levels' shared-memory matrices
+  int w_tile = 1, chase_pair = 1;  // two-stage kernel shapes (SolveArgs)
   double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream

@@ -833,7 +833,7 @@ k_ts_chase_pair(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
 }
 
 template <typename T>
-int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p) {
+int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p, bool allow_pair) {
   using C = c2<T>;
   p = ChasePlan{};
   // barrier kernel: one warp per concurrently active sweep (at most n/(2 BW) + 2)
@@ -877,7 +877,7 @@ int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p) 
   // Two warps per sweep when the cluster splits the band into CTAs narrow
   // enough that the pairs still cover a CTA's active sweeps (a pair leaves a
   // sweep after cw / BW steps, the next sweep starts 2 steps later).
-  if (p.csz > 1) {
+  if (p.csz > 1 && allow_pair) {
     const int cw = 1 << p.ccwl;
     const int pairs = std::min(Chase<T>::WARPS / 2, cw / (2 * BW) + 2);
     if (pairs >= cw / (2 * BW) && pairs >= 1) {
@@ -939,15 +939,15 @@ int chase_run_t(const ChasePlan& p, const Batch& bt, const c2<T>* A, c2<T>* Bd, 
 }  // namespace
 
 template <typename T>
-int chase_plan(int n_max, int64_t batch, int sms, int max_cluster, ChasePlan& p) {
-  return chase_plan_t<T>(n_max, batch, sms, max_cluster, p);
+int chase_plan(int n_max, int64_t batch, int sms, int max_cluster, ChasePlan& p, bool allow_pair) {
+  return chase_plan_t<T>(n_max, batch, sms, max_cluster, p, allow_pair);
 }
 template <typename T>
 int chase_run(const ChasePlan& p, const Batch& bt, const c2<T>* A, c2<T>* Bd, T* d, T* e2, int* err, cudaStream_t s) {
   return chase_run_t<T>(p, bt, A, Bd, d, e2, err, s);
 }
-template int chase_plan<float>(int, int64_t, int, int, ChasePlan&);
-template int chase_plan<double>(int, int64_t, int, int, ChasePlan&);
+template int chase_plan<float>(int, int64_t, int, int, ChasePlan&, bool);
+template int chase_plan<double>(int, int64_t, int, int, ChasePlan&, bool);
 template int chase_run<float>(const ChasePlan&, const Batch&, const c2<float>*, c2<float>*, float*, float*, int*,
                               cudaStream_t);
 template int chase_run<double>(const ChasePlan&, const Batch&, const c2<double>*, c2<double>*, double*, double*, int*,

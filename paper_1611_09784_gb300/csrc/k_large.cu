@@ -799,7 +799,7 @@ int solve_large_t(const SolveArgs& a) {
     IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel_cl<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
   }
   ChasePlan cp;
-  IDOS_TRY(chase_plan<T>(nm, batch, sms, a.max_cluster, cp));
+  IDOS_TRY(chase_plan<T>(nm, batch, sms, a.max_cluster, cp, a.chase_pair != 0));
   const bool own_err = a.err == nullptr;
   int* d_err = own_err ? a.ws->take<int>(1) : a.err;
   if (!d_err) {
@@ -855,7 +855,7 @@ int solve_large_t(const SolveArgs& a) {
           }
         }
         // float32 with an even n_max: the register-tiled W (16-byte pairs)
-        const bool w4 = sizeof(T) == 4 && (nm % 2) == 0;
+        const bool w4 = sizeof(T) == 4 && (nm % 2) == 0 && a.w_tile != 0;
         const int wr = w4 ? W4R : Tiles<T>::WR;
         const int rt = (m + wr - 1) / wr;
         const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (2 * sms + rt * nb_mat - 1) / (rt * nb_mat)));

@@ -55,7 +55,7 @@ struct ChasePlan {
 // Picks the plan for `batch` matrices per launch on `sms` SMs with clusters of
 // at most max_cluster CTAs and sets the kernels' shared-memory attributes.
 template <typename T>
-int chase_plan(int n_max, int64_t batch, int sms, int max_cluster, ChasePlan& p);
+int chase_plan(int n_max, int64_t batch, int sms, int max_cluster, ChasePlan& p, bool allow_pair = true);
 
 // Copies the band of the dense matrices A (the stage-1 output) into Bd and
 // reduces it: d = diagonal, e2 = squared subdiagonal of each tridiagonal.

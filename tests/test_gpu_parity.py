@@ -233,7 +233,12 @@ def test_autotune_picks_the_fastest_and_restores_statistics():
     m.close()
     ref = pkg.create_model(dict(cfg, sm_split=0))
     ref.sample_levels(counts, w["seed"], firsts)
+    # a tuned choice may change the float32 path (the small / two-stage cutoff,
+    # the W tile): both sums then stay within the per-sample IDoS tolerance of
+    # the oracle's, so within twice it of each other per sample
     for l in range(4):
         s1 = ref.get_level_stats(l)[1]
-        assert np.max(np.abs(tuned[l] - s1)) <= 1e-9 * max(1.0, np.max(np.abs(s1)))
+        assert np.max(np.abs(tuned[l] - s1)) <= counts[l] * 2 * IDOS_TOL
+    assert {"w_tile", "chase_pair", "persistent", "graph"} <= set(tune)
+    assert any(t["w_tile"] == 0 for t in tune["tried"]) and any(t["chase_pair"] == 0 for t in tune["tried"])
     ref.close()
