@@ -320,7 +320,8 @@ int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, dou
  * largest n the shared-memory kernel takes before the two-stage path (64, or
  * whatever fits: 160 float32 / 112 float64) and, with the latter, the
  * persistent launch on or off (graphene, IDOS_FP32_REFINE64; on with graph
- * replay, off without), then the winner with graph replay switched (unless
+ * replay, with the two-stage levels below the finest on either partition;
+ * off without graph replay), then the winner with graph replay switched (unless
  * the model gave graphs up), then the two-stage kernel shapes (the W tile
  * and one or two warps per sweep in clustered band chases).  Each candidate
  * runs twice untimed (a direct
@@ -346,6 +347,9 @@ typedef struct idos_tuning {
   int32_t chase_pair;    /* clustered band chases: 1 = two warps per sweep, 0 = one */
   int32_t tried_w_tile[IDOS_TUNE_MAX];
   int32_t tried_chase_pair[IDOS_TUNE_MAX];
+  int32_t large_to_finest; /* persistent route on the partition: 1 = a level below the finest whose
+                              fine cells take the two-stage path runs on the finest level's SMs */
+  int32_t tried_large_to_finest[IDOS_TUNE_MAX];
 } idos_tuning;
 int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
 

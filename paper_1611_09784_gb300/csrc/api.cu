@@ -395,7 +395,7 @@ bool persistent_route(const Model* M, const int64_t* n_samples) {
 }
 
 int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, const int64_t* first_sample,
-                             cudaStream_t* streams, cudaStream_t* streams2, bool parted, const uint64_t* dyn) {
+                             cudaStream_t* streams, cudaStream_t* streams2, const int* lsms, const uint64_t* dyn) {
   const idos_model_desc& d = m->d;
   const int L = d.n_levels, n_E = d.n_E;
   LevelPlan P[IDOS_MAX_LEVELS];
@@ -464,7 +464,7 @@ int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, 
     for (int l = lp + 1; l < L; ++l)
       if (P[l].S > 0 && (P[l].fine_small || P[l].crs_small)) IDOS_CUDA_TRY(cudaStreamWaitEvent(ps, m->lprep[l], 0));
     const double eps = d.overlap_s != 0.0 ? 0.0 : d.eps_onsite;
-    IDOS_TRY(solve_small_persistent(segs, n_seg, d.t, eps, m->small_ctr, parted ? m->lsms[lp] : 0, ps));
+    IDOS_TRY(solve_small_persistent(segs, n_seg, d.t, eps, m->small_ctr, lsms[lp], ps));
     IDOS_CUDA_TRY(cudaEventRecord(m->small_done, ps));
   }
   // (C) large sets, then the rest of every level, finest first
@@ -475,7 +475,7 @@ int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, 
     cudaStream_t st = streams[l];
     Arena& ws = m->lws[l];
     int* err = m->err + l;
-    const int sm_avail = parted ? m->lsms[l] : 0;
+    const int sm_avail = lsms[l];
     const bool coarse = l > 0;
     if (coarse && !p.crs_small && !p.fine_small && streams2[l]) {
       // both large: the corners' solve beside the fine one (own workspace slice)
@@ -523,7 +523,7 @@ int apply_partition(Model* m, int split) {
   }
   ++m->part_gen;
   for (int l = 0; l < L; ++l) {
-    for (cudaStream_t* sp : {&m->pstream[l], &m->pstream2[l]}) {
+    for (cudaStream_t* sp : {&m->pstream[l], &m->pstream2[l], &m->pstreamF[l]}) {
       if (*sp) {
         IDOS_CUDA_TRY(cudaStreamSynchronize(*sp));
         IDOS_CUDA_TRY(cudaStreamDestroy(*sp));
@@ -549,6 +549,7 @@ int apply_partition(Model* m, int split) {
     const int which = l == L - 1 ? 0 : 1;
     IDOS_TRY(partition_stream(m->part, which, prio, &m->pstream[l]));
     IDOS_TRY(partition_stream(m->part, which, prio, &m->pstream2[l]));
+    if (l < L - 1) IDOS_TRY(partition_stream(m->part, 0, prio, &m->pstreamF[l]));
     m->lsms[l] = m->part.sms[which];
   }
   m->sm_split_now = m->part.sms[0];
@@ -727,7 +728,7 @@ void idos_destroy_model(idos_model* m) {
       cudaStreamSynchronize(m->lstream[l]);
       cudaStreamDestroy(m->lstream[l]);
     }
-    for (cudaStream_t* sp : {&m->pstream[l], &m->lstream2[l], &m->pstream2[l]}) {
+    for (cudaStream_t* sp : {&m->pstream[l], &m->lstream2[l], &m->pstream2[l], &m->pstreamF[l]}) {
       if (*sp) {
         cudaStreamSynchronize(*sp);
         cudaStreamDestroy(*sp);
@@ -766,21 +767,21 @@ int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed
 // from the model's stream and join it again at the end (so the call can be
 // captured as one graph from that stream).
 int enqueue_levels(Model* m, cudaStream_t origin, const int64_t* n_samples, uint64_t seed,
-                   const int64_t* first_sample, cudaStream_t* streams, cudaStream_t* streams2, bool parted,
+                   const int64_t* first_sample, cudaStream_t* streams, cudaStream_t* streams2, const int* lsms,
                    bool route_p, const uint64_t* dyn) {
   const int L = m->d.n_levels;
   IDOS_CUDA_TRY(cudaEventRecord(m->fork, origin));
   for (int l = 0; l < L; ++l)
     if (n_samples[l] > 0) IDOS_CUDA_TRY(cudaStreamWaitEvent(streams[l], m->fork, 0));
   if (route_p) {
-    IDOS_TRY(sample_levels_persistent(m, n_samples, seed, first_sample, streams, streams2, parted, dyn));
+    IDOS_TRY(sample_levels_persistent(m, n_samples, seed, first_sample, streams, streams2, lsms, dyn));
   } else {
     // costliest level first, so its long latency-bound phases overlap the rest
     for (int l = L - 1; l >= 0; --l) {
       if (n_samples[l] == 0) continue;
       IDOS_TRY(run_level(m, l, n_samples[l], seed, first_sample ? first_sample[l] : m->M[l], nullptr, nullptr,
                          nullptr, streams[l], m->lws[l], m->lev0[l], m->lev1[l], m->err + l, false,
-                         parted ? m->lsms[l] : 0, nullptr, streams2[l], m->lfork2[l], m->ljoin2[l], dyn));
+                         lsms[l], nullptr, streams2[l], m->lfork2[l], m->ljoin2[l], dyn));
     }
   }
   for (int l = 0; l < L; ++l) {
@@ -827,13 +828,30 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     parted = false;
   }
   const bool route_p = persistent_route(m, n_samples);
+  // per-level streams and SM counts of this call; with the partition and the
+  // persistent route, a level below the finest whose fine cells take the
+  // two-stage path may run on the finest level's partition
+  cudaStream_t lst[IDOS_MAX_LEVELS], lst2[IDOS_MAX_LEVELS];
+  int lsm[IDOS_MAX_LEVELS];
+  for (int l = 0; l < L; ++l) {
+    lst[l] = streams[l];
+    lst2[l] = streams2[l];
+    lsm[l] = parted ? m->lsms[l] : 0;
+    if (parted && route_p && m->large_to_finest && l < L - 1 && m->pstreamF[l] &&
+        !use_small_path(m, orb_per_cell(m->d.kind) * m->d.N[l] * m->d.N[l])) {
+      lst[l] = m->pstreamF[l];
+      lsm[l] = m->lsms[L - 1];
+    }
+  }
+  streams = lst;
+  streams2 = lst2;
   // per-call values of the mask kernels (a replayed graph reads them here)
   m->dyn_host[0] = seed;
   for (int l = 0; l < L; ++l) m->dyn_host[1 + l] = (uint64_t)(first_sample ? first_sample[l] : m->M[l]);
   IDOS_CUDA_TRY(cudaMemcpyAsync(m->dyn_dev, m->dyn_host, sizeof(uint64_t) * (1 + L), cudaMemcpyHostToDevice,
                                 origin));
   auto enqueue = [&]() -> int {
-    return enqueue_levels(m, origin, n_samples, seed, first_sample, streams, streams2, parted, route_p, m->dyn_dev);
+    return enqueue_levels(m, origin, n_samples, seed, first_sample, streams, streams2, lsm, route_p, m->dyn_dev);
   };
   bool issued = false;
   if (m->graph && !m->prof.enabled) {
@@ -841,7 +859,8 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     // from has changed: sample counts, route, settings, partition, arenas
     std::vector<int64_t> core(n_samples, n_samples + L);
     for (int64_t v : {(int64_t)parted, (int64_t)route_p, (int64_t)m->small_max_n, (int64_t)m->persistent,
-                      (int64_t)m->part_gen, (int64_t)m->w_tile, (int64_t)m->chase_pair})
+                      (int64_t)m->part_gen, (int64_t)m->w_tile, (int64_t)m->chase_pair,
+                      (int64_t)m->large_to_finest})
       core.push_back(v);
     std::vector<int64_t> key = core;
     for (int l = 0; l < L; ++l) key.push_back((int64_t)m->lws[l].gen);
@@ -1260,21 +1279,23 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   // (small-kernel limit, persistent launch): the persistent launch only
   // with the default limit, and only where it applies
   const bool can_persist = m->d.kind == IDOS_GRAPHENE && m->d.precision == IDOS_FP32_REFINE64;
-  // (small-kernel limit, persistent launch, graph replay)
-  const int variants[][3] = {{-1, 1, 1}, {-1, 0, 0}, {64, 0, 0}};
+  // (small-kernel limit, persistent launch, graph replay, two-stage levels on
+  // the finest level's partition)
+  const int variants[][4] = {{-1, 1, 1, 0}, {-1, 1, 1, 1}, {-1, 0, 0, 0}, {64, 0, 0, 0}};
   out->n_tried = 0;
   out->best_ms = 1e300;
   int best_split = m->sm_split_now, best_small = m->small_max_n, best_persist = m->persistent, best_graph = m->graph;
-  int best_w = m->w_tile, best_cp = m->chase_pair;
+  int best_w = m->w_tile, best_cp = m->chase_pair, best_ltf = m->large_to_finest;
   const int graph_saved = m->graph;
   int64_t first[IDOS_MAX_LEVELS];
   int64_t round = 0;
   int rc = IDOS_OK;
   // two untimed calls per candidate: the first runs directly (and sizes the
   // workspaces), the second captures the graph; the timed calls replay it
-  auto time_config = [&](int sp, int sm, int pers, int gr, int wt, int cp) -> int {
+  auto time_config = [&](int sp, int sm, int pers, int gr, int wt, int cp, int ltf) -> int {
     m->small_max_n = sm;
     m->persistent = pers;
+    m->large_to_finest = ltf;
     m->graph = graph_saved ? gr : 0;   // a model that gave up graphs stays without
     m->w_tile = wt;
     m->chase_pair = cp;
@@ -1297,6 +1318,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     out->tried_graph[i] = m->graph;
     out->tried_w_tile[i] = wt;
     out->tried_chase_pair[i] = cp;
+    out->tried_large_to_finest[i] = ltf;
     out->tried_ms[i] = best;
     if (best < out->best_ms) {
       out->best_ms = best;
@@ -1306,16 +1328,17 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
       best_graph = m->graph;
       best_w = wt;
       best_cp = cp;
+      best_ltf = ltf;
     }
     return IDOS_OK;
   };
   for (const auto& var : variants) {
-    const int sm = var[0], pers = var[1], gr = var[2];
+    const int sm = var[0], pers = var[1], gr = var[2], ltf = var[3];
     if (sm == 64 && !has_mid) continue;
     if (pers == 1 && !can_persist) continue;
     for (int sp : splits) {
       if (sp >= m->sm_count || (sp > 0 && L < 2) || out->n_tried >= IDOS_TUNE_MAX) continue;
-      rc = time_config(sp, sm, pers, gr, 1, 1);
+      rc = time_config(sp, sm, pers, gr, 1, 1, ltf);
       if (rc != IDOS_OK) break;
     }
     if (rc != IDOS_OK) break;
@@ -1323,17 +1346,18 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   // second stage, at the winner: graph replay switched, then the two-stage
   // kernel shapes (64-row W tiles; one warp per sweep in clustered chases)
   if (rc == IDOS_OK && graph_saved && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
-    rc = time_config(best_split, best_small, best_persist, best_graph ? 0 : 1, best_w, best_cp);
+    rc = time_config(best_split, best_small, best_persist, best_graph ? 0 : 1, best_w, best_cp, best_ltf);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
-    rc = time_config(best_split, best_small, best_persist, best_graph, best_w ? 0 : 1, best_cp);
+    rc = time_config(best_split, best_small, best_persist, best_graph, best_w ? 0 : 1, best_cp, best_ltf);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
-    rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp ? 0 : 1);
+    rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp ? 0 : 1, best_ltf);
   // install the winner and restore the caller's statistics
   m->small_max_n = best_small;
   m->persistent = best_persist;
   m->graph = best_graph;
   m->w_tile = best_w;
   m->chase_pair = best_cp;
+  m->large_to_finest = best_ltf;
   const int rc2 = apply_partition(m, best_split);
   IDOS_CUDA_TRY(cudaMemcpyAsync(m->acc, acc_saved.data(), sizeof(double) * acc_saved.size(), cudaMemcpyHostToDevice,
                                 m->stream));
@@ -1346,6 +1370,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   out->graph = m->graph;
   out->w_tile = m->w_tile;
   out->chase_pair = m->chase_pair;
+  out->large_to_finest = m->large_to_finest;
   return rc != IDOS_OK ? rc : rc2;
 }
 

@@ -119,6 +119,12 @@ struct Model {
   cudaStream_t pstream[IDOS_MAX_LEVELS] = {};   // the same on the SM partition (null without one)
   // second stream per level for the corners' solve beside the fine one
   cudaStream_t lstream2[IDOS_MAX_LEVELS] = {}, pstream2[IDOS_MAX_LEVELS] = {};
+  // streams of the levels below the finest on the finest level's partition:
+  // with large_to_finest a level whose fine cells take the two-stage path runs
+  // there (its latency-bound chain beside the finest level's) instead of
+  // waiting for the persistent launch to free the other partition's SMs
+  cudaStream_t pstreamF[IDOS_MAX_LEVELS] = {};
+  int large_to_finest = 0;        // off by default (the autotuner may switch it on)
   cudaEvent_t lfork2[IDOS_MAX_LEVELS] = {}, ljoin2[IDOS_MAX_LEVELS] = {};
   cudaStream_t stream2 = nullptr;                // the same for calls on the model's stream
   cudaEvent_t fork2 = nullptr, join2 = nullptr;
