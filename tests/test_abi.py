@@ -77,3 +77,32 @@ def test_dos_from_idos_matches_oracle():
     assert np.allclose(got, ref, rtol=1e-14, atol=0)
     with pytest.raises(pkg.IdosError):
         pkg.dos_from_idos(Q[:1], -9.0, 9.0)
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """Every public struct of include/idos.h has the binding's field names,
+    offsets and size (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    from paper_1611_09784_gb300 import binding as b
+    structs = {"idos_model_desc": b.ModelDesc, "idos_mlmc_opts": b.MlmcOpts, "idos_estimate": b.Estimate,
+               "idos_tuning": b.Tuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "idos.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} . %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.splitlines():
+        cname, fname, value = line.split()
+        cls = structs[cname]
+        want = ctypes.sizeof(cls) if fname == "." else getattr(cls, fname).offset
+        assert int(value) == want, (cname, fname, int(value), want)
