@@ -23,8 +23,10 @@ Sec. 2, in float64.
   small cell weighted by p^|v| (1-p)^(n-|v|).
 
 Pinned: telescoping with p = 0, corner tiling, CV unbiasedness (statistical),
-exhaustive N = 2 expectation vs Monte Carlo, and the optimality conditions of
-eq. (2.7) (tests/test_oracle_mlmc.py).
+exhaustive N = 2 expectation vs Monte Carlo, the optimality conditions of
+eq. (2.7), the eq. (2.6) mean and variance on a hand-worked two-level case, and
+the reported variance against the spread of independent two-level estimates
+around the exact expectation (tests/test_oracle_mlmc.py).
 """
 from __future__ import annotations
 
