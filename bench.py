@@ -61,10 +61,11 @@ def eigsolves_per_sample(levels, level):
     return n
 
 
-def workload_config(alloc, w):
+def workload_config(alloc, w, precision=None):
     return {"workload": WORKLOAD, "model": "graphene pz NN tight-binding, t=-2.7 eV, a=2.46 A",
             "p": w["p"], "levels_N_K": w["levels"], "samples_per_level": alloc["M"], "tol": w["tol"],
-            "n_E": w["n_E"], "delta": w["delta"], "precision": f"fp32 reduction + {REFINE64} fp64 bisection step",
+            "n_E": w["n_E"], "delta": w["delta"],
+            "precision": precision or f"fp32 reduction + {REFINE64} fp64 Newton/Sturm pass, fp64 sums",
             "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"}
 
 
@@ -175,20 +176,35 @@ def n_act_of(masks, N):
     return fine, np.stack(corners, 1)
 
 
-def algorithmic_work(m, levels, M, seed, firsts, bw=16):
+# Kernel families of the library's profiler and what bounds each one:
+# "alu" (float32 FMA issue), "alu64" (float64 FMA issue), "tensor" (bf16 MMA),
+# "hbm" (DRAM bytes).
+FAMILIES = {"k_small_tridiag": "alu", "k_ts_panel": "alu", "k_ts_w": "alu", "k_ts_z": "hbm", "k_ts_her2k": "tensor",
+            "k_ts_chase": "alu", "k_bisect": "alu64", "k_idos": "hbm"}
+
+
+def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16):
     """Exact algorithmic work of one step from the samples' kept-site counts,
-    in real flops per kernel: the small-matrix Householder kernel (16/3 n^3
-    per matrix); per stage-1 panel of bw columns with m rows below it,
-    W = A22 (Y T) (m^2 bw complex multiply-adds, 8 m^2 bw) and the
-    full-storage rank-2bw update (16 m^2 bw); the bulge chase, per sweep step
-    the right and left reflector applications to the bw x bw bulge block
-    (2 x 8 bw^2) and the two-sided update of the bw x bw diagonal block
-    (3 x 8 bw^2)."""
+    per kernel family (flops, or bytes for the HBM-bound families):
+    - k_small_tridiag: Householder reduction, 16/3 n^3 real flops per matrix;
+    - per stage-1 panel of bw columns with m rows below it (float32 complex,
+      8 bytes per entry): panel QR 8 m bw^2 flops, W = A22 (Y T) 8 m^2 bw
+      flops, Z = W - 1/2 Y (T^H M) 4 bw m x 8 bytes (W and Y twice read, Z
+      written once), the rank-2bw update 16 m^2 bw flops;
+    - k_ts_chase: per sweep step the right and left reflector applications to
+      the bw x bw bulge block (2 x 8 bw^2) and the two-sided update of the
+      bw x bw diagonal block (3 x 8 bw^2);
+    - k_bisect: the float64 refinement passes, 4 flops per row of the
+      characteristic-polynomial recurrence, refine x n^2 rows per matrix;
+    - k_idos: the eigenvalues read (8 bytes each) and Q written (8 n_E bytes
+      per cell)."""
     import numpy as np
-    work = {"k_small_tridiag": 0.0, "k_ts_w": 0.0, "k_ts_her2k": 0.0, "k_ts_chase": 0.0}
+    work = {k: 0.0 for k in FAMILIES}
 
     def add(n_arr, K2, big):
         n = n_arr.astype(np.float64)
+        work["k_bisect"] += K2 * float(np.sum(4.0 * refine * n ** 2))
+        work["k_idos"] += float(np.sum(8.0 * K2 * n + 8.0 * n_E))
         if not big:
             work["k_small_tridiag"] += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
             return
@@ -196,7 +212,9 @@ def algorithmic_work(m, levels, M, seed, firsts, bw=16):
             nn = int(nn)
             for k in range(0, nn - bw, bw):
                 mm = nn - k - bw
+                work["k_ts_panel"] += K2 * 8.0 * mm * bw * bw
                 work["k_ts_w"] += K2 * 8.0 * bw * mm * mm
+                work["k_ts_z"] += K2 * 4.0 * bw * mm * 8.0
                 work["k_ts_her2k"] += K2 * 16.0 * bw * mm * mm
             steps = sum((nn - 2 - i) // bw + 1 for i in range(0, nn - 2))
             work["k_ts_chase"] += K2 * 40.0 * bw * bw * steps
@@ -215,35 +233,45 @@ def algorithmic_work(m, levels, M, seed, firsts, bw=16):
 AGGREGATE_SCOPES = ("k_lg_band (stage 1, all)",)
 
 
-def roofline(prof, work, steps, pk, pk_kind, clocks, tc_products=6):
-    """Roofline objects of the modelled kernels; the first is the single kernel
-    (not an aggregate scope) with the largest event time."""
+def roofline(prof, work, steps, pk, pk_kind, fma, tc_products=6):
+    """Roofline objects of the kernel families; the first is the single kernel
+    family (not an aggregate scope) with the largest event time.  fma: the
+    FMA peaks measured in this run (TFLOP/s, float32 and float64)."""
     singles = sorted(((k, v) for k, v in prof.items() if k not in AGGREGATE_SCOPES), key=lambda kv: -kv[1][0])
-    # the trailing update runs on the tensor cores: tc_products bf16 MMA flops
-    # per algorithmic flop, against the measured bf16 GEMM rate (sustained: the
-    # kernels are timed inside a long replay)
-    models = {"k_small_tridiag": "alu", "k_ts_w": "alu", "k_ts_her2k": "tensor" if tc_products else "alu",
-              "k_ts_chase": "alu"}
-    mhz = pk.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     out = []
     for name, (ms, launches) in singles:
-        if name not in models or not launches or not ms:
+        bound = FAMILIES.get(name)
+        if bound is None or not launches or not ms:
             continue
+        if bound == "tensor" and not tc_products:
+            bound = "alu"
         per_launch_s = ms * 1e-3 / launches
         units_per_launch = work[name] * steps / launches
-        if models[name] == "tensor":
+        executed = units_per_launch
+        if bound == "tensor":
+            # the trailing update runs on the tensor cores: tc_products bf16 MMA
+            # flops per algorithmic flop, against the measured bf16 GEMM rate
+            # (sustained: the kernels are timed inside a long replay)
             executed = units_per_launch * tc_products
-            achieved = executed / per_launch_s / 1e12
+            achieved, unit = executed / per_launch_s / 1e12, "TFLOP/s"
             peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
             src = f"{pk_kind} bf16 GEMM, sustained; achieved counts the {tc_products} split-bf16 products per algorithmic flop"
+        elif bound == "hbm":
+            achieved, unit = units_per_launch / per_launch_s / 1e9, "GB/s"
+            peak = pk.get("hbm_gbs", 6800.0)
+            src = f"{pk_kind} HBM copy bandwidth"
+        elif bound == "alu64":
+            achieved, unit = units_per_launch / per_launch_s / 1e12, "TFLOP/s"
+            peak = fma["fp64_tflops"]
+            src = "measured in this run: float64 FMA microbenchmark (idos_measure_fma_peak)"
         else:
-            executed = units_per_launch
-            achieved = units_per_launch / per_launch_s / 1e12
-            peak = alu_peak
-            src = f"{pk_kind} SM clock x 152 SMs x 128 FP32 lanes x 2 (FP32 FMA issue rate)"
-        out.append({"kernel": name, "bound": models[name], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": ncu_traffic(name, units_per_launch),
+            achieved, unit = units_per_launch / per_launch_s / 1e12, "TFLOP/s"
+            peak = fma["fp32_tflops"]
+            src = "measured in this run: float32 FMA microbenchmark (idos_measure_fma_peak)"
+        out.append({"kernel": name, "bound": "alu" if bound == "alu64" else bound,
+                    "pipe": {"alu": "fp32", "alu64": "fp64", "tensor": "bf16 mma", "hbm": "dram"}[bound],
+                    "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                    "traffic": ncu_traffic(name, units_per_launch),
                     "algorithmic_per_launch": units_per_launch, "executed_per_launch": executed,
                     "launches": launches, "avg_launch_ms": per_launch_s * 1e3, "peak_source": src})
     dominant = singles[0][0] if singles else None
@@ -251,6 +279,22 @@ def roofline(prof, work, steps, pk, pk_kind, clocks, tc_products=6):
     if first is not None:
         first = dict(first, dominant_by_event_time=dominant)
     return first, out
+
+
+def measure_fma_peaks(pkg, stream, clock_gpu=0):
+    """FMA issue rates of this GPU (float32, float64) with the SM clock
+    sampled meanwhile; each launch runs for a few hundred milliseconds."""
+    clocks = ClockSampler(clock_gpu)
+    clocks.start()
+    f32, ms32 = pkg.measure_fma_peak("fp32", 1 << 21, stream)
+    f64, ms64 = pkg.measure_fma_peak("fp64", 1 << 15, stream)
+    clk = clocks.stop()
+    out = {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12, "fp32_ms": ms32, "fp64_ms": ms64,
+           "kernel": "k_fma_peak: 8 CTAs x 256 threads per SM, 8 independent FMA chains per thread",
+           "clocks": clk}
+    if clk:
+        out["fp32_tflops_per_ghz"] = out["fp32_tflops"] / (clk["sm_mhz"] / 1e3)
+    return out
 
 
 # ------------------------------------------------------------- oracle (CPU) --
@@ -267,34 +311,118 @@ def _oracle_job(args):
     return level, time.perf_counter() - t0
 
 
+def _oracle_check_job(args):
+    """The oracle's level sample (Y, Q_fine, Q_coarse) and, when asked, the
+    fine cell's band energies, for the GPU-vs-oracle check of the bench line."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle import idos as oidos
+    from oracle import mlmc as omlmc
+    from synthetic import model_params, workload
+    level, sample, seed, want_bands = args
+    w = workload(WORKLOAD)
+    prm = model_params(w)
+    r = omlmc.level_sample(prm, w["levels"], level, sample, seed)
+    out = {"level": level, "sample": sample, "Y": r["Y"], "Q_fine": r["Q_fine"], "Q_coarse": r["Q_coarse"]}
+    if want_bands:
+        N, K = w["levels"][level]
+        out["E"] = oidos.band_energies(N, K, r["mask"], prm)
+    return out
+
+
 def oracle_pool():
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return mp.get_context("spawn").Pool(cores), cores
 
 
+def oracle_sample_counts(alloc, frac=1.0 / 16):
+    return [max(1, int(math.ceil(Ml * frac))) for Ml in alloc["M"]]
+
+
 def oracle_measure(pool, cores, alloc, levels, frac=1.0 / 16, first=50_000_000, seed=161109784):
-    """Run a bounded, workload-shaped sample of level samples on all host cores
-    (one process per core, BLAS single-threaded) and extrapolate the oracle's
-    eigen-solves/s over the full allocation."""
-    M = alloc["M"]
-    counts = [max(1, int(math.ceil(Ml * frac))) for Ml in M]
-    jobs = [(l, first + s, seed) for l in range(len(M)) for s in range(counts[l])]
+    """Time the oracle (float64, LAPACK eigvalsh) on a bounded, workload-shaped
+    sample: ceil(M_l / 16) level samples of every level (at least one), run on
+    all host cores (one process per core, BLAS single-threaded).  value =
+    eigen-solves of the sample / its wall time; nothing is extrapolated."""
+    counts = oracle_sample_counts(alloc, frac)
+    jobs = [(l, first + s, seed) for l in range(len(counts)) for s in range(counts[l])]
     jobs.sort(key=lambda j: -j[0])
     t0 = time.perf_counter()
     res = pool.map(_oracle_job, jobs, chunksize=1)
     wall = time.perf_counter() - t0
-    per = [[] for _ in M]
+    per = [[] for _ in counts]
     for l, t in res:
         per[l].append(t)
     mean = [sum(x) / len(x) for x in per]
-    core_seconds = sum(Ml * t for Ml, t in zip(M, mean))
-    full_wall = core_seconds / cores
-    eig = sum(Ml * eigsolves_per_sample(levels, l) for l, Ml in enumerate(M))
-    return {"value": eig / full_wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"{counts} level samples (levels 0..3) of the allocation {M}, run on {cores} host "
-                       f"processes (1 BLAS thread each) in {wall:.1f} s; per-level mean seconds {[round(x, 4) for x in mean]} "
-                       f"extrapolated to the full allocation assuming all cores busy"),
-            "seconds_per_step_extrapolated": full_wall}
+    eig = sum(c * eigsolves_per_sample(levels, l) for l, c in enumerate(counts))
+    return {"value": eig / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{counts} level samples of levels 0..3 (1/16 of the allocation {alloc['M']}, at least one "
+                       f"per level; {eig} eigen-solves) on {cores} host processes, 1 BLAS thread each, "
+                       f"{wall:.1f} s wall; value = those eigen-solves / that wall time (measured, not extrapolated)"),
+            "wall_s": wall, "eigsolves": eig, "per_level_mean_core_s": [round(x, 4) for x in mean]}
+
+
+def gpu_oracle_check(model, levels, seed, counts=(4, 2, 2, 1), first=90_000_000):
+    """GPU side of the oracle check at the bench's settings: per level the
+    level samples (Y, Q_fine, Q_coarse) and the first sample's fine-cell
+    eigenvalues (NaN-padded rows)."""
+    out = []
+    for l, c in enumerate(counts):
+        Y, Qf, Qc = model.sample_level_detail(l, c, seed, first)
+        N, K = levels[l]
+        _, E = model.eval_idos(N, K, seed=seed, level=l, sample=first, want_eigs=True)
+        out.append({"Y": Y, "Q_fine": Qf, "Q_coarse": Qc, "E": E})
+    return out
+
+
+def oracle_check_jobs(seed, counts=(4, 2, 2, 1), first=90_000_000):
+    return [(l, first + s, seed, s == 0) for l in range(len(counts)) for s in range(counts[l])]
+
+
+def compare_oracle_check(gpu, oracle_res, counts=(4, 2, 2, 1), first=90_000_000):
+    """Max absolute differences GPU - oracle per level: Y, Q_fine, Q_coarse
+    (states/A^2) and eigenvalues (eV, the first sample's fine cell, as sorted
+    multisets per grid point)."""
+    import numpy as np
+    by = {(r["level"], r["sample"]): r for r in oracle_res}
+    per_level = []
+    for l, c in enumerate(counts):
+        g = gpu[l]
+        dY = dQ = dC = 0.0
+        for s in range(c):
+            r = by[(l, first + s)]
+            dY = max(dY, float(np.max(np.abs(g["Y"][s] - r["Y"]))))
+            dQ = max(dQ, float(np.max(np.abs(g["Q_fine"][s] - r["Q_fine"]))))
+            if l > 0:
+                dC = max(dC, float(np.max(np.abs(g["Q_coarse"][s] - np.stack(r["Q_coarse"])))))
+        Eo = by[(l, first)]["E"]
+        dE = 0.0
+        for row, ref in zip(g["E"], Eo):
+            act = np.sort(row[~np.isnan(row)])
+            if act.shape != ref.shape:
+                dE = float("inf")
+                break
+            dE = max(dE, float(np.max(np.abs(act - ref))) if ref.size else 0.0)
+        per_level.append({"level": l, "samples": c, "max_abs_dY": dY, "max_abs_dQ_fine": dQ,
+                          "max_abs_dQ_coarse": dC, "max_abs_dE_eV": dE})
+    worst_q = max(max(p["max_abs_dY"], p["max_abs_dQ_fine"], p["max_abs_dQ_coarse"]) for p in per_level)
+    worst_e = max(p["max_abs_dE_eV"] for p in per_level)
+    return {"per_level": per_level, "max_abs_dQ": worst_q, "max_abs_dE_eV": worst_e,
+            "tolerance": {"Q": 1e-5, "E_eV": 1e-4}, "pass": bool(worst_q < 1e-5 and worst_e < 1e-4),
+            "what": ("GPU (bench settings: float32 reduction, tensor-core update with 6 split-bf16 products, "
+                     f"{REFINE64} float64 pass) against the float64 oracle on the same seeded samples "
+                     f"{first}.. of every level, computed outside the timed region")}
+
+
+def level_cost_model(levels, l):
+    """Flop-model work of one level-l sample: sum of n^3 over its eigen-solves
+    (fine cell at K_l^2 points, the four corners at K_{l-1}^2 points)."""
+    N, K = levels[l]
+    c = K * K * float(2 * N * N) ** 3
+    if l > 0:
+        Nc, Kc = levels[l - 1]
+        c += 4 * Kc * Kc * float(2 * Nc * Nc) ** 3
+    return c
 
 
 # ------------------------------------------------ other workloads (extras) --
@@ -396,7 +524,7 @@ def run_gpu(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pool = cores = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.skip_extras:
+    if rank == 0 and world == 1 and not args.skip_extras:
         pool, cores = oracle_pool()     # spawn pool before the first GPU call
     if world > 1:
         dist.init_process_group("nccl", rank=rank, world_size=world)
@@ -462,14 +590,15 @@ def run_gpu(args):
     g_replays, g_captures, g_note = model.graph_info()
     graph_line = {"replays": g_replays, "captures": g_captures, "note": g_note,
                   "what": "idos_sample_levels captured once as a CUDA graph (all level streams), replayed per step"}
-    # combine (eq. (2.6)) from the device accumulators, summed over replicas
+    # combine (eq. (2.6), idos_combine_level_stats) from the device
+    # accumulators, summed over replicas
     from paper_1611_09784_gb300 import replicas
     counts, sums = replicas.model_stats(model)
     level_span_ms = [round(model.get_level_stats(l)[3] * 1e3 / args.steps, 3) for l in range(len(M))]
+    moments = np.stack([model.get_level_moments(l)[1] for l in range(len(M))])
     if world > 1:
         counts, sums = replicas.merge(counts, sums, device=dev)
-    used = [l for l in range(len(M)) if M[l]]
-    mean, var = replicas.combine(counts[used], sums[used])
+    mean, var = replicas.combine(counts, sums)
     # Per-kernel CUDA-event times: the timed steps run the levels on
     # concurrent streams, where one kernel's event span includes time spent
     # waiting for SMs held by kernels of other levels.  So the kernels are
@@ -493,11 +622,36 @@ def run_gpu(args):
     firsts_steps = [[(args.warmup + k) * Ml for Ml in M] for k in range(args.steps)]
     work = {}
     for firsts in firsts_steps:
-        wk = algorithmic_work(model, levels, M, seed, firsts)
+        wk = algorithmic_work(model, levels, M, seed, firsts, n_E=w["n_E"])
         for k2 in wk:
             work[k2] = work.get(k2, 0.0) + wk[k2] / args.steps
     pk, pk_kind = peaks()
-    roof, roofs = roofline(prof, work, args.steps, pk, pk_kind, clk, tc_products=TC_PRODUCTS)
+    fma = measure_fma_peaks(pkg, stream.cuda_stream, local)
+    roof, roofs = roofline(prof, work, args.steps, pk, pk_kind, fma, tc_products=TC_PRODUCTS)
+
+    # rates W, S, D, C (Sec. 2.1-2.2, fitted as Sec. 4.4 does) from the timed
+    # steps' level accumulators; cost per sample: each level alone on the
+    # model stream (CUDA events), and the flop model sum n^3
+    rates = None
+    if all(M):
+        Ns = [N for N, _ in levels]
+        cnt = [model.get_level_stats(l)[0] for l in range(len(M))]
+        cost_s = []
+        for l in range(len(M)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            model.sample_level(l, M[l], seed + 7, 1 << 41)
+            b.record(stream)
+            torch.cuda.synchronize()
+            cost_s.append(a.elapsed_time(b) * 1e-3 / M[l])
+        flop = [level_cost_model(levels, l) for l in range(len(M))]
+        rates = {"measured_gpu_cost": pkg.fit_rates(Ns, cnt, moments, cost_s),
+                 "flop_model_cost": pkg.fit_rates(Ns, cnt, moments, flop),
+                 "C_last_two_levels_gpu": math.log(cost_s[-1] / cost_s[-2]) / math.log(Ns[-1] / Ns[-2]),
+                 "gpu_seconds_per_sample": cost_s, "samples_per_level": cnt,
+                 "norm": "arithmetic mean over the energy grid",
+                 "paper_printed": {"W": 1.5, "S": 2, "D": 3, "C": 4, "work_mc": 10 / 3, "work_mlmc": 8 / 3}}
 
     if args.skip_extras:
         if rank == 0:
@@ -506,7 +660,8 @@ def run_gpu(args):
                               "partial": "timed steps only (--skip-extras)", "samples_per_level": M,
                               "level_span_ms_per_step": level_span_ms,
                               "kernels_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
-                              "roofline": roof, "clocks": clk, "graph": graph_line, "autotune": tuning}),
+                              "roofline": roof, "rooflines": roofs, "fma_peaks": fma, "rates": rates,
+                              "clocks": clk, "graph": graph_line, "autotune": tuning}),
                   flush=True)
         model.close()
         if pool is not None:
@@ -552,9 +707,17 @@ def run_gpu(args):
     stress_line = stress(pkg, torch, stream)
     serve = serving(pkg, cfg, levels, seed)
 
+    # GPU against the oracle at the bench's settings, outside the timed region
+    chk = None
+    if pool is not None and not args.no_oracle_check:
+        chk_async = pool.map_async(_oracle_check_job, oracle_check_jobs(seed), chunksize=1)
+        gpu_chk = gpu_oracle_check(model, levels, seed)
+        chk = compare_oracle_check(gpu_chk, chk_async.get())
+
     cpu = None
     if pool is not None:
-        cpu = oracle_measure(pool, cores, alloc, levels)
+        if not args.no_cpu_baseline:
+            cpu = oracle_measure(pool, cores, alloc, levels)
         pool.close()
 
     if rank == 0:
@@ -584,6 +747,9 @@ def run_gpu(args):
             "tmdc_sweep": sweep,
             "stress": stress_line,
             "estimate_check": {"Q_at_e_max": float(mean[-1]), "max_std": float(np.sqrt(np.max(var)))},
+            "oracle_check": chk,
+            "rates": rates,
+            "fma_peaks": fma,
         }
         print(json.dumps(line), flush=True)
     model.close()
@@ -593,6 +759,9 @@ def run_gpu(args):
 
 # -------------------------------------------------------------- reference arm --
 def run_reference(args):
+    """The oracle as it stands (float64, LAPACK eigvalsh) on the host cores:
+    each step is one bounded, workload-shaped sample (oracle_measure), timed
+    for real; value and ms_per_step are medians over the timed steps."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -607,14 +776,16 @@ def run_reference(args):
         r = oracle_measure(pool, cores, alloc, levels, first=60_000_000 + 10_000 * i)
         if i >= args.warmup:
             vals.append(r["value"])
-            secs.append(r["seconds_per_step_extrapolated"])
+            secs.append(r["wall_s"])
     pool.close()
     value = statistics.median(vals)
+    cfg = workload_config(alloc, w, precision="fp64 throughout (the oracle: numpy / LAPACK eigvalsh, float64 sums)")
+    cfg["step"] = "one bounded sample of the allocation per step: " + r["sample"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Philox vacancy masks)", "config": workload_config(alloc, w),
+        "data": "synthetic (seeded Philox vacancy masks)", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": r["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -639,6 +810,8 @@ def main():
                     help="do not sample nvidia-smi clocks (profiler runs)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the timed steps: no e2e / plain-MC / CPU-baseline measurements")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the GPU-vs-oracle check at the bench settings")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -141,12 +141,18 @@ typedef struct idos_model_desc {
 
 typedef struct idos_model idos_model;
 
-/* Create a model on the current CUDA device.  Validates d, allocates the
- * level accumulators and a workspace.  *out receives the handle (NULL on
- * error).  cuda_stream: cudaStream_t as void*, or NULL. */
+/* Create a model on the current CUDA device: the tight-binding model of
+ * Sec. 3.1 (graphene, eq. (3.2a)-(3.2d), or the TMDC-shaped model), its
+ * vacancy law (Sec. 3.2), the MLMC level hierarchy N_l = 2 N_{l-1} with the
+ * control variates of Sec. 3.3, and the Brillouin-zone grid and smoothed IDoS
+ * of Sec. 4.2-4.3.  Validates d (IDOS_ERR_INVALID_ARG before any device call),
+ * allocates the level accumulators and a workspace.  *out receives the handle
+ * (NULL on error).  cuda_stream: cudaStream_t as void*, or NULL. */
 int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** out);
 
-/* Free every device buffer of the model (synchronises its stream). NULL ok. */
+/* Free every device buffer of the model created by idos_create_model (the
+ * model of Sec. 3.1-3.3 and the grids of Sec. 4.2-4.3); synchronises its
+ * stream first.  NULL ok. */
 void idos_destroy_model(idos_model* m);
 
 /* The SM partition idos_sample_levels uses: *sms_finest SMs for the finest
@@ -200,6 +206,52 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
  * (host, may be NULL), *seconds of GPU time spent on the level (may be NULL). */
 int idos_get_level_stats(const idos_model* m, int level, int64_t* M, double* sum,
                          double* sumsq, double* seconds);
+
+/* All four float64 accumulators of one level: moments host float64[4 * n_E],
+ * rows sum Y, sum Y^2 (the level term of eq. (2.6), as idos_get_level_stats),
+ * sum Q_l, sum Q_l^2 (the fine IDoS Q_l of the same outcomes alone, whose
+ * variance decay is the rate S of eq. (Q_variance)); *M samples, *seconds
+ * GPU time (both may be NULL). */
+int idos_get_level_moments(const idos_model* m, int level, int64_t* M, double* moments, double* seconds);
+
+/* Eq. (2.6) and the variance display after it, from level accumulators (host
+ * arithmetic, no device needed): mean[j] = sum_l S1_l[j] / M_l and
+ * var[j] = sum_l V_l[j] / M_l with V_l[j] = (S2_l[j] - M_l mean_l[j]^2) /
+ * (M_l - 1) the unbiased sample variance.  M: int64[n_levels]; a level with
+ * M_l = 0 is left out.  sums: float64[n_levels * 2 * n_E], per level the rows
+ * S1 = sum Y, S2 = sum Y^2.  mean, var: host float64[n_E].  INVALID_ARG for a
+ * level with M_l = 1 or M_l < 0, no level with samples, or bad sizes. */
+int idos_combine_level_stats(int n_levels, const int64_t* M, const double* sums, int n_E, double* mean,
+                             double* var);
+
+/* Rates of the complexity models of Sec. 2.1-2.2 (eq. (compl_model):
+ * Q - E[Q_N] ~ N^-W, Var(Q_N) ~ N^-S, cost per sample ~ N^C; eq.
+ * (compl_model2): Var(Q_l - Q_l^CV) ~ N^-D), fitted as Sec. 4.4 does
+ * (eq. (param_est)), and the asymptotic work exponents they imply. */
+typedef struct idos_rates {
+  double W, S, D, C;              /* fitted exponents (NaN with < 2 usable levels)      */
+  double W_se, S_se, D_se, C_se;  /* standard errors of the slopes (0 with 2 points)   */
+  int32_t n_W, n_S, n_D, n_C;     /* levels each fit used                              */
+  double work_mc;    /* eq. (Work_SLMC): Work_MC ~ TOL^-(2 + (C - S)/W)                 */
+  double work_mlmc;  /* eq. (Work_MLMC): Work_MLMC ~ TOL^-(2 + (C - D)/W) (for D < C)   */
+  double work_fs;    /* eq. (Work_FS): one sample on a large cell, TOL^-(2 C / S)      */
+  double theta_mc;   /* the MC bias/statistics split 1 / (1 + (C - S)/W) of Sec. 2.1   */
+} idos_rates;
+
+/* Fit the rates from level accumulators (host arithmetic, no device needed).
+ * N: int32[n_levels] supercell sides (doubling); M: int64[n_levels]; moments:
+ * float64[n_levels * 4 * n_E] as idos_get_level_moments returns them; cost:
+ * float64[n_levels] work per sample (seconds or a flop model), or NULL (C is
+ * then NaN); a level with cost <= 0 is left out of C.  Norm: the arithmetic
+ * mean over the energy grid, as the paper's convergence plots use.  Each rate
+ * is minus (C: plus) the least-squares slope of log(value) against log N_l:
+ * S from the grid-mean sample variance of Q_l over levels with M_l >= 2; D
+ * from that of Y_l over levels l >= 1 (0-based) with M_l >= 2; W from the
+ * grid mean of |sum Y_l / M_l| over levels l >= 1 with M_l >= 1 (E[Y_l] =
+ * E[Q_l] - E[Q_{l-1}] is proportional to N_l^-W when N doubles); C from cost.
+ * INVALID_ARG for bad sizes or pointers. */
+int idos_fit_rates(int n_levels, const int32_t* N, const int64_t* M, const double* moments, const double* cost,
+                   int n_E, idos_rates* out);
 
 /* Zero the accumulators of one level, or of all levels when level == -1. */
 int idos_reset_level_stats(idos_model* m, int level);
@@ -313,6 +365,15 @@ int idos_her2k(int tc_products, int n, int64_t batch, const double* A, const dou
  * host float64[n_E].  Host arithmetic only (no device needed). */
 int idos_dos_from_idos(const double* Q, int n_E, double e_min, double e_max, double* dos);
 
+/* FMA throughput of the current device, the denominator of the ALU
+ * rooflines (the paper has no counterpart; it times one CPU core): a grid of
+ * 8 CTAs x 256 threads per SM, each thread running 8 independent dependent
+ * FMA chains for `iters` iterations, timed with CUDA events on cuda_stream
+ * after one untimed launch.  precision: IDOS_FP32_REFINE64 (float32 FMA) or
+ * IDOS_FP64 (float64 FMA).  *flops_per_s: 2 flops per FMA; *ms (nullable):
+ * the timed launch.  Blocking.  INVALID_ARG for iters outside 1 .. 2^30. */
+int idos_measure_fma_peak(int precision, int64_t iters, void* cuda_stream, double* flops_per_s, double* ms);
+
 /* ---- autotuning ----
  * Times idos_sample_levels(n_samples) on this model for every candidate
  * configuration and installs the fastest: the SMs reserved for the finest
@@ -401,8 +462,8 @@ void idos_server_destroy(idos_server* s);
  * NULL) lives in one file-scope static device array of 1 MiB that every GPU
  * which loads libidos.so holds until the process exits.
  *  - d: model description (only the single-configuration fields are used:
- *    kind, precision, smoothing, t, eps_onsite, a, p, e_min, e_max, delta,
- *    n_E, refine64_iters).
+ *    kind (graphene only), precision, smoothing, t, eps_onsite, a, p, e_min,
+ *    e_max, delta, n_E, refine64_iters, overlap_s (|s| < 1/3, nonzero t)).
  *  - N, Kside: supercell side and k-grid side.  Only matrices of the
  *    shared-memory path are accepted (2N^2 <= 160 in float32, <= 112 in
  *    float64), and the scratch must fit 1 MiB (about 2 K^2 2N^2 (2 s + 8)
@@ -414,12 +475,19 @@ void idos_server_destroy(idos_server* s);
  *    float64[Kside^2 * 2N^2] (layout as in idos_eval_idos).  Caller-owned.
  *  - cuda_stream: cudaStream_t as void* (NULL = legacy default stream).  The
  *    call enqueues its kernels and returns without synchronising.
- * The first call on a device looks up the static array's device address
- * (cudaGetSymbolAddress, once per device); make that first call before any
- * stream capture.  All calls share the array and every call overwrites all
- * of the scratch it reads, so nothing needs clearing between calls; calls
- * whose kernels overlap on the GPU (other streams, other host threads) race
- * on the array and must be serialised by the caller. */
+ * Set-up: every call whose stream is not being captured looks up the static
+ * array's device address (cudaGetSymbolAddress, no allocation), so the
+ * address stays valid across a cudaDeviceReset; a call on a capturing stream
+ * reuses the address of the last uncaptured call on that device, so make the
+ * first call on a device before any stream capture.  The first call on a
+ * device may also load the library's kernel modules (CUDA loads modules
+ * lazily by default), which takes device memory once: make it outside the
+ * region that must not allocate, as a warm-up.  After that no call allocates.
+ * All calls share the array and every call overwrites all of the scratch it
+ * reads, so nothing needs clearing between calls (a call after a larger one
+ * sees none of its contents); calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race on the array and must be serialised by
+ * the caller. */
 int idos_eval_idos_noalloc(const idos_model_desc* d, int N, int Kside, const uint8_t* mask_dev,
                            uint64_t seed, int level, int64_t sample, double* idos_dev_out,
                            double* eigs_dev_out, void* cuda_stream);

@@ -21,6 +21,12 @@ Sec. 2, in float64.
   the pointwise variance over the energy grid.
 * ``exhaustive_expectation``: Sec. 1 / Sec. 4.4: all 2^n vacancy outcomes of a
   small cell weighted by p^|v| (1-p)^(n-|v|).
+* ``fit_rates``: the rates of the complexity models eq. (compl_model) and
+  eq. (compl_model2) fitted as Sec. 4.4 does (eq. (param_est)): log-log least
+  squares against N of the grid-mean sample variance of Q_l (S), of
+  Y_l = Q_l - Q_l^CV (D), the grid mean of |E[Y_l]| = |E[Q_l] - E[Q_{l-1}]|
+  (W: proportional to N_l^-W when N doubles) and the cost per sample (C);
+  then the work exponents of eq. (Work_SLMC), eq. (Work_MLMC), eq. (Work_FS).
 
 Pinned: telescoping with p = 0, corner tiling, CV unbiasedness (statistical),
 exhaustive N = 2 expectation vs Monte Carlo, the optimality conditions of
@@ -92,6 +98,41 @@ def optimal_samples(V, W, tol: float, theta: float = 0.5, c_alpha: float = 1.96)
     s = np.sum(np.sqrt(W * V))
     M = (c_alpha / (theta * tol)) ** 2 * np.sqrt(V / W) * s
     return np.maximum(1, np.ceil(M)).astype(np.int64), M
+
+
+def fit_rates(N, Y_levels, Q_levels, cost=None):
+    """Rates W, S, D, C from per-level sample arrays (Y_levels[l], Q_levels[l]:
+    (M_l, n_E); level 0 is the coarsest) and an optional cost per sample per
+    level.  Norm: the arithmetic mean over the energy grid."""
+    N = np.asarray(N, dtype=np.float64)
+
+    def slope(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        ok = (x > 0) & (y > 0)
+        if ok.sum() < 2:
+            return float("nan")
+        return float(np.polyfit(np.log(x[ok]), np.log(y[ok]), 1)[0])
+
+    xs, vq, xd, vy, xw, bias = [], [], [], [], [], []
+    for l in range(len(N)):
+        Y = np.asarray(Y_levels[l], dtype=np.float64)
+        Q = np.asarray(Q_levels[l], dtype=np.float64)
+        if Y.shape[0] >= 2:
+            xs.append(N[l])
+            vq.append(np.mean(Q.var(axis=0, ddof=1)))
+            if l > 0:
+                xd.append(N[l])
+                vy.append(np.mean(Y.var(axis=0, ddof=1)))
+        if Y.shape[0] >= 1 and l > 0:
+            xw.append(N[l])
+            bias.append(np.mean(np.abs(Y.mean(axis=0))))
+    S = -slope(xs, vq)
+    D = -slope(xd, vy)
+    W = -slope(xw, bias)
+    C = slope(N, cost) if cost is not None else float("nan")
+    return {"W": W, "S": S, "D": D, "C": C, "work_mc": 2 + (C - S) / W, "work_mlmc": 2 + (C - D) / W,
+            "work_fs": 2 * C / S, "theta_mc": 1 / (1 + (C - S) / W)}
 
 
 def exhaustive_expectation(prm, N: int, K: int):

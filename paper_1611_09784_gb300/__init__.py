@@ -7,6 +7,7 @@ entry-point names.  Importing it loads the library and fails loudly when the
 library has not been built: there is no CPU fallback.
 """
 from .binding import (  # noqa: F401
-    FP32_REFINE64, FP64, GRAPHENE, SMOOTH_GAUSS, SMOOTH_POLY, TMDC, IdosError, Model, Server, create_model,
-    dos_from_idos, eigvalsh, her2k, lib_path, load_library, status_string,
+    FP32_REFINE64, FP64, GRAPHENE, SMOOTH_GAUSS, SMOOTH_POLY, TMDC, IdosError, Model, Server, combine_level_stats,
+    create_model, dos_from_idos, eigvalsh, fit_rates, her2k, lib_path, load_library, measure_fma_peak,
+    status_string,
 )

@@ -62,6 +62,14 @@ class Estimate(C.Structure):
                 ("d2h_bytes", C.c_int64)]
 
 
+class Rates(C.Structure):
+    _fields_ = [("W", C.c_double), ("S", C.c_double), ("D", C.c_double), ("C", C.c_double),
+                ("W_se", C.c_double), ("S_se", C.c_double), ("D_se", C.c_double), ("C_se", C.c_double),
+                ("n_W", C.c_int32), ("n_S", C.c_int32), ("n_D", C.c_int32), ("n_C", C.c_int32),
+                ("work_mc", C.c_double), ("work_mlmc", C.c_double), ("work_fs", C.c_double),
+                ("theta_mc", C.c_double)]
+
+
 class IdosError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: {status_string(status)} ({status}): {detail}")
@@ -81,6 +89,11 @@ _SYMBOLS = {
     "idos_get_level_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p,
                                        C.POINTER(C.c_double)]),
     "idos_reset_level_stats": (C.c_int, [C.c_void_p, C.c_int]),
+    "idos_get_level_moments": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.c_void_p,
+                                         C.POINTER(C.c_double)]),
+    "idos_combine_level_stats": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "idos_fit_rates": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                 C.POINTER(Rates)]),
     "idos_eval_idos": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_uint64, C.c_int, C.c_int64,
                                  C.c_void_p, C.c_void_p]),
     "idos_mlmc_estimate": (C.c_int, [C.c_void_p, C.POINTER(MlmcOpts), C.POINTER(Estimate)]),
@@ -101,6 +114,8 @@ _SYMBOLS = {
     "idos_server_destroy": (None, [C.c_void_p]),
     "idos_dos_from_idos": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p]),
     "idos_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Tuning)]),
+    "idos_measure_fma_peak": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
     "idos_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "idos_profile_count": (C.c_int, []),
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -272,6 +287,15 @@ class Model:
                                                    C.byref(secs)), "idos_get_level_stats")
         return int(M.value), s1, s2, float(secs.value)
 
+    def get_level_moments(self, level: int):
+        """(M, moments[4, n_E]: sum Y, sum Y^2, sum Q_l, sum Q_l^2, GPU seconds)."""
+        mo = np.empty((4, self.n_E))
+        M = C.c_int64()
+        secs = C.c_double()
+        _check(load_library().idos_get_level_moments(self._h, level, C.byref(M), _ptr(mo), C.byref(secs)),
+               "idos_get_level_moments")
+        return int(M.value), mo, float(secs.value)
+
     def reset_level_stats(self, level: int = -1):
         _check(load_library().idos_reset_level_stats(self._h, level), "idos_reset_level_stats")
 
@@ -383,6 +407,47 @@ def dos_from_idos(Q, e_min: float, e_max: float):
     out = np.empty_like(Q)
     _check(load_library().idos_dos_from_idos(_ptr(Q), Q.shape[-1], e_min, e_max, _ptr(out)), "idos_dos_from_idos")
     return out
+
+
+def combine_level_stats(counts, sums):
+    """Eq. (2.6) estimate and its variance (idos_combine_level_stats) from
+    per-level sample counts (int64[L]) and sums (float64[L, 2, n_E]: sum Y,
+    sum Y^2); levels with count 0 are left out."""
+    M = np.ascontiguousarray(counts, dtype=np.int64)
+    S = np.ascontiguousarray(sums, dtype=np.float64)
+    if S.ndim != 3 or S.shape[0] != M.shape[0] or S.shape[1] != 2:
+        raise ValueError("sums must have shape (levels, 2, n_E)")
+    n_E = S.shape[2]
+    mean = np.empty(n_E)
+    var = np.empty(n_E)
+    _check(load_library().idos_combine_level_stats(M.shape[0], _ptr(M), _ptr(S), n_E, _ptr(mean), _ptr(var)),
+           "idos_combine_level_stats")
+    return mean, var
+
+
+def fit_rates(Ns, counts, moments, cost=None) -> dict:
+    """Rates W, S, D, C of the complexity models and the work exponents they
+    imply (idos_fit_rates).  Ns: supercell sides; counts: int64[L];
+    moments: float64[L, 4, n_E] as Model.get_level_moments; cost: per-sample
+    work per level or None."""
+    N = np.ascontiguousarray(Ns, dtype=np.int32)
+    M = np.ascontiguousarray(counts, dtype=np.int64)
+    mo = np.ascontiguousarray(moments, dtype=np.float64)
+    if mo.ndim != 3 or mo.shape[:2] != (M.shape[0], 4) or N.shape[0] != M.shape[0]:
+        raise ValueError("moments must have shape (levels, 4, n_E)")
+    c = None if cost is None else np.ascontiguousarray(cost, dtype=np.float64)
+    r = Rates()
+    _check(load_library().idos_fit_rates(M.shape[0], _ptr(N), _ptr(M), _ptr(mo), _ptr(c), mo.shape[2], C.byref(r)),
+           "idos_fit_rates")
+    return {name: getattr(r, name) for name, _ in Rates._fields_}
+
+
+def measure_fma_peak(precision="fp32", iters: int = 1 << 16, stream: int | None = None):
+    """(flop/s, ms) of the FMA microbenchmark (idos_measure_fma_peak)."""
+    f, ms = C.c_double(0), C.c_double(0)
+    _check(load_library().idos_measure_fma_peak(_PRECISION[precision], iters, C.c_void_p(stream or 0), C.byref(f),
+                                                C.byref(ms)), "idos_measure_fma_peak")
+    return f.value, ms.value
 
 
 def create_model(cfg: dict, stream: int | None = None) -> Model:

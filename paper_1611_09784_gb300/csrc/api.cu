@@ -4,6 +4,7 @@
 // eq. (2.7)) and the parity entry points.  Host code only; every arithmetic
 // step of the path runs in the kernels of k_*.cu.
 #include <algorithm>
+#include <limits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -276,7 +277,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
     const bool two = coarse && st2 && fork2 && join2;
     const size_t coarse_slice =
         two ? solve_bytes(d.precision, Nc, Kc, 4 * S, n_E, d.kind) + large_room(M, Nc, Kc, 4 * S) + 64 * 1024 : 0;
-    const size_t need = S * per_sample + 64 * 1024 + ((S + 63) / 64) * 2 * n_E * 8 +
+    const size_t need = S * per_sample + 64 * 1024 + ((S + 63) / 64) * kAccRows * n_E * 8 +
                         (two ? large_room(M, Nf, Kf, S) + coarse_slice
                              : std::max(large_room(M, Nf, Kf, S), coarse ? large_room(M, Nc, Kc, 4 * S) : 0));
     IDOS_TRY(ws.reserve(need, st));
@@ -325,7 +326,7 @@ int run_level(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t fir
       IDOS_TRY(solve_and_idos(M, fine, Kf, Qf, nullptr, st, ws, err, sm_avail));
       ws.used = mark;
     }
-    double* acc = acc_out ? acc_out : M->acc + (size_t)level * 2 * n_E;
+    double* acc = acc_out ? acc_out : M->acc + (size_t)level * kAccRows * n_E;
     IDOS_TRY(launch_level_stats(Qf, Qc, S, n_E, Y, acc, ws, st));
     if (Yh) IDOS_CUDA_TRY(cudaMemcpyAsync(Yh + s0 * n_E, Y, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, st));
     if (Qfh) IDOS_CUDA_TRY(cudaMemcpyAsync(Qfh + s0 * n_E, Qf, sizeof(double) * S * n_E, cudaMemcpyDeviceToHost, st));
@@ -415,7 +416,7 @@ int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, 
     const bool two = coarse && streams2[l];
     const size_t coarse_slice =
         two ? solve_bytes(d.precision, Nc, Kc, 4 * S, n_E, d.kind) + large_room(m, Nc, Kc, 4 * S) + 64 * 1024 : 0;
-    const size_t need = S * level_per_sample(m, l) + 64 * 1024 + ((S + 63) / 64) * 2 * n_E * 8 +
+    const size_t need = S * level_per_sample(m, l) + 64 * 1024 + ((S + 63) / 64) * kAccRows * n_E * 8 +
                         (two ? large_room(m, Nf, Kf, S) + coarse_slice
                              : std::max(large_room(m, Nf, Kf, S), coarse ? large_room(m, Nc, Kc, 4 * S) : 0));
     IDOS_TRY(ws.reserve(need, st));
@@ -504,7 +505,7 @@ int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, 
       if (p.crs_small) IDOS_TRY(eigs_and_idos(m, p.crs, Kc, p.cseg.d, p.cseg.e2, p.ceig, p.Qc, st));
       if (p.fine_small) IDOS_TRY(eigs_and_idos(m, p.fine, Kf, p.fseg.d, p.fseg.e2, p.feig, p.Qf, st));
     }
-    IDOS_TRY(launch_level_stats(p.Qf, p.Qc, p.S, n_E, p.Y, m->acc + (size_t)l * 2 * n_E, ws, st));
+    IDOS_TRY(launch_level_stats(p.Qf, p.Qc, p.S, n_E, p.Y, m->acc + (size_t)l * kAccRows * n_E, ws, st));
     IDOS_CUDA_TRY(record_timing(m->lev1[l], st));
   }
   return IDOS_OK;
@@ -569,7 +570,7 @@ size_t level_workspace(const Model* M, int level, int64_t n_samples) {
                             3 * n_E * sizeof(double);
   int64_t chunk = std::max<int64_t>(1, (int64_t)(kSmallBudget / per_sample));
   chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_samples, 1));
-  return chunk * per_sample + 64 * 1024 + ((chunk + 63) / 64) * 2 * n_E * 8 +
+  return chunk * per_sample + 64 * 1024 + ((chunk + 63) / 64) * kAccRows * n_E * 8 +
          std::max(large_room(M, Nf, Kf, chunk), coarse ? large_room(M, Nc, Kc, 4 * chunk) : 0);
 }
 
@@ -612,6 +613,57 @@ int read_status_word(const int* err) { return check_status_word(err); }
 
 using namespace idos;
 
+namespace {
+
+// Unbiased sample variance of the level term at grid point j from the sums
+// s[0][j] = sum Y, s[1][j] = sum Y^2 over M >= 2 samples (the V_l of eq. (2.6)).
+double level_var(int64_t M, const double* s, int n_E, int j) {
+  const double mean = s[j] / (double)M;
+  return std::max(0.0, (s[n_E + j] - (double)M * mean * mean) / (double)(M - 1));
+}
+
+// max over the grid of level_var: the scalar V_l of eq. (2.7) (reading: a
+// pointwise bound over the energy grid).
+double level_vmax(int64_t M, const double* s, int n_E) {
+  double v = 0.0;
+  for (int j = 0; j < n_E; ++j) v = std::max(v, level_var(M, s, n_E, j));
+  return v;
+}
+
+// Least-squares slope of log y against log x over the points with y > 0 and
+// x > 0; se: standard error of the slope (0 with two points); false with
+// fewer than two points.
+bool loglog_slope(const std::vector<double>& x, const std::vector<double>& y, double& slope, double& se, int& used) {
+  std::vector<double> lx, ly;
+  for (size_t i = 0; i < x.size(); ++i)
+    if (x[i] > 0 && y[i] > 0 && std::isfinite(y[i])) {
+      lx.push_back(std::log(x[i]));
+      ly.push_back(std::log(y[i]));
+    }
+  used = (int)lx.size();
+  if (used < 2) return false;
+  double mx = 0, my = 0;
+  for (int i = 0; i < used; ++i) { mx += lx[i]; my += ly[i]; }
+  mx /= used;
+  my /= used;
+  double sxx = 0, sxy = 0;
+  for (int i = 0; i < used; ++i) { sxx += (lx[i] - mx) * (lx[i] - mx); sxy += (lx[i] - mx) * (ly[i] - my); }
+  if (!(sxx > 0)) return false;
+  slope = sxy / sxx;
+  se = 0.0;
+  if (used > 2) {
+    double rss = 0;
+    for (int i = 0; i < used; ++i) {
+      const double r = ly[i] - (my + slope * (lx[i] - mx));
+      rss += r * r;
+    }
+    se = std::sqrt(rss / (used - 2) / sxx);
+  }
+  return true;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* idos_status_string(int status) {
@@ -640,7 +692,7 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
   m->d = *d;
   m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   m->sm_count = sms;
-  const size_t acc_bytes = sizeof(double) * 2 * d->n_E * d->n_levels;
+  const size_t acc_bytes = sizeof(double) * kAccRows * d->n_E * d->n_levels;
   cudaError_t e = cudaMalloc(&m->acc, acc_bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->acc, 0, acc_bytes, m->stream);
   if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int) * (IDOS_MAX_LEVELS + 1));
@@ -934,12 +986,108 @@ int idos_get_level_stats(const idos_model* m, int level, int64_t* M, double* sum
   if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
   if (level < 0 || level >= m->d.n_levels) { set_error("level out of range"); return IDOS_ERR_INVALID_ARG; }
   const int n_E = m->d.n_E;
-  const double* acc = m->acc + (size_t)level * 2 * n_E;
+  const double* acc = m->acc + (size_t)level * kAccRows * n_E;
   if (sum) IDOS_CUDA_TRY(cudaMemcpyAsync(sum, acc, sizeof(double) * n_E, cudaMemcpyDeviceToHost, m->stream));
   if (sumsq) IDOS_CUDA_TRY(cudaMemcpyAsync(sumsq, acc + n_E, sizeof(double) * n_E, cudaMemcpyDeviceToHost, m->stream));
   IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
   if (M) *M = m->M[level];
   if (seconds) *seconds = m->seconds[level];
+  return IDOS_OK;
+}
+
+int idos_get_level_moments(const idos_model* m, int level, int64_t* M, double* moments, double* seconds) {
+  if (!m || !moments) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
+  if (level < 0 || level >= m->d.n_levels) { set_error("level out of range"); return IDOS_ERR_INVALID_ARG; }
+  const int n_E = m->d.n_E;
+  IDOS_CUDA_TRY(cudaMemcpyAsync(moments, m->acc + (size_t)level * kAccRows * n_E, sizeof(double) * kAccRows * n_E,
+                                cudaMemcpyDeviceToHost, m->stream));
+  IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (M) *M = m->M[level];
+  if (seconds) *seconds = m->seconds[level];
+  return IDOS_OK;
+}
+
+int idos_combine_level_stats(int n_levels, const int64_t* M, const double* sums, int n_E, double* mean,
+                             double* var) {
+  if (!M || !sums || !mean || !var || n_levels < 1 || n_levels > IDOS_MAX_LEVELS || n_E < 1) {
+    set_error("null array, n_levels outside 1..IDOS_MAX_LEVELS or n_E < 1");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  int used = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    if (M[l] < 0 || M[l] == 1) {
+      set_error("level " + std::to_string(l) + ": M = " + std::to_string(M[l]) +
+                " (a level term needs M >= 2 for its variance, or M = 0 to leave it out)");
+      return IDOS_ERR_INVALID_ARG;
+    }
+    used += M[l] > 0;
+  }
+  if (!used) { set_error("no level has samples"); return IDOS_ERR_INVALID_ARG; }
+  std::fill(mean, mean + n_E, 0.0);
+  std::fill(var, var + n_E, 0.0);
+  for (int l = 0; l < n_levels; ++l) {
+    if (!M[l]) continue;
+    const double* s = sums + (size_t)l * 2 * n_E;
+    for (int j = 0; j < n_E; ++j) {
+      mean[j] += s[j] / (double)M[l];
+      var[j] += level_var(M[l], s, n_E, j) / (double)M[l];
+    }
+  }
+  return IDOS_OK;
+}
+
+int idos_fit_rates(int n_levels, const int32_t* N, const int64_t* M, const double* moments, const double* cost,
+                   int n_E, idos_rates* out) {
+  if (!N || !M || !moments || !out || n_levels < 1 || n_levels > IDOS_MAX_LEVELS || n_E < 1) {
+    set_error("null array, n_levels outside 1..IDOS_MAX_LEVELS or n_E < 1");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  for (int l = 0; l < n_levels; ++l)
+    if (N[l] < 1 || M[l] < 0) { set_error("N[l] < 1 or M[l] < 0"); return IDOS_ERR_INVALID_ARG; }
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  std::vector<double> xs, vq, xd, vy, xw, bias, xc, cs;
+  for (int l = 0; l < n_levels; ++l) {
+    const double* mo = moments + (size_t)l * kAccRows * n_E;
+    const double Nl = (double)N[l];
+    if (M[l] >= 2) {
+      // grid means of the pointwise sample variances of Q_l and of Y_l
+      double a = 0, b = 0;
+      for (int j = 0; j < n_E; ++j) {
+        a += level_var(M[l], mo + 2 * n_E, n_E, j);
+        b += level_var(M[l], mo, n_E, j);
+      }
+      xs.push_back(Nl);
+      vq.push_back(a / n_E);
+      if (l > 0) {
+        xd.push_back(Nl);
+        vy.push_back(b / n_E);
+      }
+    }
+    if (M[l] >= 1 && l > 0) {
+      // |E[Y_l]| = |E[Q_l] - E[Q_{l-1}]|, proportional to N_l^-W for doubling sizes
+      double c = 0;
+      for (int j = 0; j < n_E; ++j) c += std::fabs(mo[j] / (double)M[l]);
+      xw.push_back(Nl);
+      bias.push_back(c / n_E);
+    }
+    if (cost && cost[l] > 0) {
+      xc.push_back(Nl);
+      cs.push_back(cost[l]);
+    }
+  }
+  double sl, se;
+  out->S = loglog_slope(xs, vq, sl, se, out->n_S) ? -sl : nan;
+  out->S_se = out->n_S >= 2 ? se : nan;
+  out->D = loglog_slope(xd, vy, sl, se, out->n_D) ? -sl : nan;
+  out->D_se = out->n_D >= 2 ? se : nan;
+  out->W = loglog_slope(xw, bias, sl, se, out->n_W) ? -sl : nan;
+  out->W_se = out->n_W >= 2 ? se : nan;
+  out->C = loglog_slope(xc, cs, sl, se, out->n_C) ? sl : nan;
+  out->C_se = out->n_C >= 2 ? se : nan;
+  out->work_mc = 2.0 + (out->C - out->S) / out->W;
+  out->work_mlmc = 2.0 + (out->C - out->D) / out->W;
+  out->work_fs = 2.0 * out->C / out->S;
+  out->theta_mc = 1.0 / (1.0 + (out->C - out->S) / out->W);
   return IDOS_OK;
 }
 
@@ -949,7 +1097,7 @@ int idos_reset_level_stats(idos_model* m, int level) {
   const int n_E = m->d.n_E;
   const int l0 = level < 0 ? 0 : level, l1 = level < 0 ? m->d.n_levels : level + 1;
   for (int l = l0; l < l1; ++l) {
-    IDOS_CUDA_TRY(cudaMemsetAsync(m->acc + (size_t)l * 2 * n_E, 0, sizeof(double) * 2 * n_E, m->stream));
+    IDOS_CUDA_TRY(cudaMemsetAsync(m->acc + (size_t)l * kAccRows * n_E, 0, sizeof(double) * kAccRows * n_E, m->stream));
     m->M[l] = 0;
     m->seconds[l] = 0.0;
   }
@@ -1126,7 +1274,7 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   const auto t0 = std::chrono::steady_clock::now();
   const int L = m->d.n_levels, n_E = m->d.n_E;
   IDOS_TRY(idos_reset_level_stats(m, -1));
-  std::vector<double> sum(n_E), sq(n_E);
+  std::vector<double> sum(2 * (size_t)n_E);
   std::vector<double> V(L), W(L);
   // pilot: pilot_samples on level 0, fewer on costlier levels
   std::vector<int64_t> target(L);
@@ -1139,15 +1287,9 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   auto estimate_vw = [&](int l) -> int {
     int64_t M = 0;
     double secs = 0;
-    IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
+    IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sum.data() + n_E, &secs));
     d2h += 2 * (int64_t)sizeof(double) * n_E;
-    double vmax = 0.0;
-    for (int j = 0; j < n_E; ++j) {
-      const double mean = sum[j] / M;
-      const double v = std::max(0.0, (sq[j] - M * mean * mean) / (M - 1));
-      vmax = std::max(vmax, v);
-    }
-    V[l] = std::max(vmax, 1e-300);
+    V[l] = std::max(level_vmax(M, sum.data(), n_E), 1e-300);
     W[l] = o->work_model == 1 ? std::max(secs / M, 1e-12) : flop_model(m->d, l);
     return IDOS_OK;
   };
@@ -1204,25 +1346,18 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
     if (!more) break;
   }
   // combine, eq. (2.6)
-  std::fill(out->mean, out->mean + n_E, 0.0);
-  std::fill(out->var, out->var + n_E, 0.0);
+  std::vector<int64_t> Ms(L);
+  std::vector<double> sums((size_t)L * 2 * n_E);
   for (int l = 0; l < L; ++l) {
-    int64_t M = 0;
     double secs = 0;
-    IDOS_TRY(idos_get_level_stats(m, l, &M, sum.data(), sq.data(), &secs));
+    IDOS_TRY(idos_get_level_stats(m, l, &Ms[l], sums.data() + (size_t)l * 2 * n_E,
+                                  sums.data() + (size_t)l * 2 * n_E + n_E, &secs));
     d2h += 2 * (int64_t)sizeof(double) * n_E;
-    double vmax = 0.0;
-    for (int j = 0; j < n_E; ++j) {
-      const double mean = sum[j] / M;
-      const double v = std::max(0.0, (sq[j] - M * mean * mean) / (M - 1));
-      out->mean[j] += mean;
-      out->var[j] += v / M;
-      vmax = std::max(vmax, v);
-    }
-    if (out->M) out->M[l] = M;
-    if (out->V) out->V[l] = vmax;
-    if (out->W) out->W[l] = o->work_model == 1 ? secs / M : flop_model(m->d, l);
+    if (out->M) out->M[l] = Ms[l];
+    if (out->V) out->V[l] = level_vmax(Ms[l], sums.data() + (size_t)l * 2 * n_E, n_E);
+    if (out->W) out->W[l] = o->work_model == 1 ? secs / Ms[l] : flop_model(m->d, l);
   }
+  IDOS_TRY(idos_combine_level_stats(L, Ms.data(), sums.data(), n_E, out->mean, out->var));
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   out->rounds = rounds;
   out->h2d_bytes = h2d;   // per call: seed and first sample indices (model and sizes travel as kernel arguments)
@@ -1260,7 +1395,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   }
   const int L = m->d.n_levels, n_E = m->d.n_E;
   // keep the caller's statistics
-  std::vector<double> acc_saved((size_t)2 * n_E * L);
+  std::vector<double> acc_saved((size_t)kAccRows * n_E * L);
   IDOS_CUDA_TRY(cudaMemcpyAsync(acc_saved.data(), m->acc, sizeof(double) * acc_saved.size(), cudaMemcpyDeviceToHost,
                                 m->stream));
   IDOS_CUDA_TRY(cudaStreamSynchronize(m->stream));

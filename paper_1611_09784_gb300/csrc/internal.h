@@ -159,7 +159,7 @@ struct Model {
   int small_max_n = -1;           // largest n on the shared-memory kernel (-1: whatever fits)
   int persistent = 1;             // one persistent launch for the levels' shared-memory matrices
   int w_tile = 1, chase_pair = 1;  // two-stage kernel shapes (SolveArgs)
-  double* acc = nullptr;          // device [n_levels][2][n_E]: sum Y, sum Y^2
+  double* acc = nullptr;          // device [n_levels][kAccRows][n_E]: sum Y, Y^2, Q_fine, Q_fine^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream
   int64_t M[IDOS_MAX_LEVELS] = {};
@@ -229,15 +229,21 @@ struct EnergyGrid { double e_min, e_max, delta; int n_E; int smoothing; int fp32
 int launch_idos(const double* eigs, const int* n_act_cell, int K2, int n_max, int64_t n_cells,
                 double area, const EnergyGrid& g, double* Q, cudaStream_t s);
 
+// Rows of a level accumulator (float64 [kAccRows][n_E]): sum Y, sum Y^2 (the
+// level term of eq. (2.6)), sum Q_fine, sum Q_fine^2 (the fine IDoS alone,
+// whose variance decay is the rate S of Sec. 2.1).
+constexpr int kAccRows = 4;
+
 // Level difference and float64 statistics: Y = Qf - (1/4) sum_r Qc[r] (or Qf),
-// acc[0][j] += sum_s Y, acc[1][j] += sum_s Y^2, optional Y export.
+// acc[0][j] += sum_s Y, acc[1][j] += sum_s Y^2, acc[2][j] += sum_s Qf,
+// acc[3][j] += sum_s Qf^2, optional Y export.
 int launch_level_stats(const double* Qf, const double* Qc, int64_t S, int n_E, double* Y,
                        double* acc, Arena& ws, cudaStream_t s);
 
 double cell_area(double a);   // |a1 x a2| = sqrt(3)/2 a^2
 
 // Level sampling for other drivers (api.cu): n_samples of `level` on stream st
-// with workspace ws, float64 sums Y, Y^2 added to acc [2][n_E] (device, zeroed
+// with workspace ws, float64 sums added to acc [kAccRows][n_E] (device, zeroed
 // by the caller), err (device status word) zeroed first; ev0 / ev1 recorded
 // around the work; returns without waiting.
 int level_run_async(Model* M, int level, int64_t n_samples, uint64_t seed, int64_t first, cudaStream_t st,

@@ -87,16 +87,18 @@ k_idos(const double* __restrict__ eigs, const int* __restrict__ n_act_cell, int 
 
 constexpr int STAT_CHUNK = 64;
 
-// partial[chunk][0|1][j] over STAT_CHUNK samples, fixed order.
+// partial[chunk][r][j] over STAT_CHUNK samples in a fixed order, rows r of
+// the level accumulator: sum Y, sum Y^2, sum Q_fine, sum Q_fine^2.
 __global__ void k_level_partial(const double* __restrict__ Qf, const double* __restrict__ Qc, int64_t S,
                                 int n_E, double* __restrict__ Y, double* __restrict__ partial) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t chunk = blockIdx.y;
   if (j >= n_E) return;
-  double s1 = 0.0, s2 = 0.0;
+  double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
   const int64_t s0 = chunk * STAT_CHUNK, s_end = min(S, s0 + STAT_CHUNK);
   for (int64_t smp = s0; smp < s_end; ++smp) {
-    double y = Qf[smp * n_E + j];
+    const double qf = Qf[smp * n_E + j];
+    double y = qf;
     if (Qc) {
       const double* q = Qc + smp * 4 * (int64_t)n_E + j;
       y -= 0.25 * (q[0] + q[n_E] + q[2 * n_E] + q[3 * n_E]);
@@ -104,22 +106,26 @@ __global__ void k_level_partial(const double* __restrict__ Qf, const double* __r
     if (Y) Y[smp * n_E + j] = y;
     s1 += y;
     s2 += y * y;
+    s3 += qf;
+    s4 += qf * qf;
   }
-  partial[(chunk * 2 + 0) * n_E + j] = s1;
-  partial[(chunk * 2 + 1) * n_E + j] = s2;
+  double* pc = partial + chunk * kAccRows * n_E + j;
+  pc[0] = s1;
+  pc[n_E] = s2;
+  pc[2 * n_E] = s3;
+  pc[3 * n_E] = s4;
 }
 
 __global__ void k_level_final(const double* __restrict__ partial, int64_t n_chunks, int n_E,
                               double* __restrict__ acc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_E) return;
-  double s1 = 0.0, s2 = 0.0;
-  for (int64_t c = 0; c < n_chunks; ++c) {
-    s1 += partial[(c * 2 + 0) * n_E + j];
-    s2 += partial[(c * 2 + 1) * n_E + j];
-  }
-  acc[j] += s1;
-  acc[n_E + j] += s2;
+  double s[kAccRows] = {};
+  for (int64_t c = 0; c < n_chunks; ++c)
+#pragma unroll
+    for (int r = 0; r < kAccRows; ++r) s[r] += partial[(c * kAccRows + r) * n_E + j];
+#pragma unroll
+  for (int r = 0; r < kAccRows; ++r) acc[r * n_E + j] += s[r];
 }
 
 }  // namespace
@@ -157,7 +163,7 @@ int launch_level_stats(const double* Qf, const double* Qc, int64_t S, int n_E, d
                        Arena& ws, cudaStream_t s) {
   if (S == 0) return IDOS_OK;
   const int64_t n_chunks = (S + STAT_CHUNK - 1) / STAT_CHUNK;
-  double* partial = ws.take<double>((size_t)n_chunks * 2 * n_E);
+  double* partial = ws.take<double>((size_t)n_chunks * kAccRows * n_E);
   if (!partial) {
     set_error("workspace too small for level statistics");
     return IDOS_ERR_OUT_OF_MEMORY;

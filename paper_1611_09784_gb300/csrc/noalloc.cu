@@ -21,9 +21,13 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 std::mutex g_setup_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device (host code may not use the symbol's host-side stand-in).
-int scratch_address(void** out) {
+// Device address of g_noalloc_scratch on the current device (host code may
+// not use the symbol's host-side stand-in).  It is looked up again on every
+// call whose stream is not being captured, so an address cached before a
+// cudaDeviceReset (which unloads the module and may place the array
+// elsewhere when it is loaded again) is never reused; a call on a capturing
+// stream uses the address of the last uncaptured call on that device.
+int scratch_address(cudaStream_t s, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -34,8 +38,14 @@ int scratch_address(void** out) {
     set_error("device ordinal above the supported count");
     return IDOS_ERR_NO_DEVICE;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+    return IDOS_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -43,6 +53,9 @@ int scratch_address(void** out) {
       return IDOS_ERR_CUDA;
     }
     g_scratch_ptr[dev] = p;
+  } else if (!g_scratch_ptr[dev]) {
+    set_error("idos_eval_idos_noalloc: the first call on a device must come before any stream capture");
+    return IDOS_ERR_INVALID_ARG;
   }
   *out = g_scratch_ptr[dev];
   return IDOS_OK;
@@ -119,9 +132,9 @@ extern "C" int idos_eval_idos_noalloc(const idos_model_desc* d, int N, int Kside
               std::to_string(kNoAllocScratchBytes));
     return IDOS_ERR_INVALID_ARG;
   }
-  void* base = nullptr;
-  IDOS_TRY(scratch_address(&base));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  void* base = nullptr;
+  IDOS_TRY(scratch_address(s, &base));
   Carve c{reinterpret_cast<char*>(base)};
   CellSet cells;
   cells.N = N;

@@ -45,7 +45,7 @@ struct Worker {
   Arena ws;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int* err = nullptr;
-  double* acc = nullptr;   // device [2][n_E]
+  double* acc = nullptr;   // device [kAccRows][n_E]
   int64_t ticket = -1;     // request in flight, -1 = free
 };
 
@@ -105,7 +105,7 @@ void start(Server* S, Worker& w, int64_t t) {
   w.ticket = t;
   S->in_flight_bytes += r.footprint;
   S->peak_bytes = std::max(S->peak_bytes, S->in_flight_bytes);
-  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * 2 * S->n_E, w.stream);
+  cudaError_t e = cudaMemsetAsync(w.acc, 0, sizeof(double) * kAccRows * S->n_E, w.stream);
   int st = e == cudaSuccess ? IDOS_OK : IDOS_ERR_CUDA;
   if (st == IDOS_OK)
     st = level_run_async(S->model, r.level, r.n, r.seed, r.first, w.stream, w.ws, w.ev0, w.ev1, w.err, w.acc);
@@ -188,7 +188,7 @@ extern "C" int idos_server_create(const idos_model_desc* d, int n_workers, int64
     if (e == cudaSuccess) e = cudaEventCreate(&w.ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&w.ev1);
     if (e == cudaSuccess) e = cudaMalloc(&w.err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&w.acc, sizeof(double) * 2 * S->n_E);
+    if (e == cudaSuccess) e = cudaMalloc(&w.acc, sizeof(double) * kAccRows * S->n_E);
   }
   if (e != cudaSuccess) {
     set_error(std::string("server resources: ") + cudaGetErrorString(e));

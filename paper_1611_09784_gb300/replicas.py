@@ -2,10 +2,9 @@
 
 The samples of different ranks are independent (disjoint seeds or sample
 ranges), so replicas exchange only the per-level float64 accumulators
-(M_l, sum Y, sum Y^2) once, with a sum over ranks, and combine them by
-eq. (2.6): mean = sum_l sum_l / M_l, Var = sum_l V_l / M_l with V_l the
-unbiased sample variance.  Works with any torch.distributed backend (gloo on
-CPU, NCCL on GPU).
+(M_l, sum Y, sum Y^2) once, with a sum over ranks; the eq. (2.6) combine of
+the merged sums is the library's idos_combine_level_stats.  Works with any
+torch.distributed backend (gloo on CPU, NCCL on GPU).
 """
 from __future__ import annotations
 
@@ -37,17 +36,7 @@ def merge(counts, sums, group=None, device=None):
 
 
 def combine(counts, sums):
-    """Eq. (2.6) estimate and its variance from merged accumulators."""
-    counts = np.asarray(counts, dtype=np.int64)
-    sums = np.asarray(sums, dtype=np.float64)
-    mean = np.zeros(sums.shape[-1])
-    var = np.zeros(sums.shape[-1])
-    for l in range(len(counts)):
-        M = counts[l]
-        if M < 2:
-            raise ValueError("every level needs at least two samples")
-        mu = sums[l, 0] / M
-        v = np.maximum(sums[l, 1] - M * mu * mu, 0.0) / (M - 1)
-        mean += mu
-        var += v / M
-    return mean, var
+    """Eq. (2.6) estimate and its variance from merged accumulators
+    (idos_combine_level_stats)."""
+    from .binding import combine_level_stats
+    return combine_level_stats(counts, sums)

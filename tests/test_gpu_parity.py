@@ -19,11 +19,21 @@ pytestmark = pytest.mark.gpu
 pkg = pytest.importorskip("paper_1611_09784_gb300")
 
 
-@pytest.fixture(scope="module", params=["fp64", "fp32"])
+# (precision, float64 refinement passes): the float64 path, the float32 path
+# with two passes, and the benchmark's exact setting (float32, one pass, the
+# tensor-core trailing update with 6 split-bfloat16 products and the library's
+# default kernel shapes: 128-row W tiles, two warps per sweep in clustered
+# chases, the persistent launch and graph replay in idos_sample_levels).
+BENCH_SETTING = ("fp32", 1)
+
+
+@pytest.fixture(scope="module", params=[("fp64", 2), ("fp32", 2), BENCH_SETTING], ids=["fp64", "fp32r2", "fp32r1"])
 def model(request):
-    w, cfg, prm = cfg_and_prm(precision=request.param)
+    prec, refine = request.param
+    w, cfg, prm = cfg_and_prm(precision=prec, refine=refine)
+    cfg.update(tc_products=6)
     m = pkg.create_model(cfg)
-    yield m, w, prm, request.param
+    yield m, w, prm, prec
     m.close()
 
 
@@ -242,3 +252,31 @@ def test_autotune_picks_the_fastest_and_restores_statistics():
     assert {"w_tile", "chase_pair", "persistent", "graph"} <= set(tune)
     assert any(t["w_tile"] == 0 for t in tune["tried"]) and any(t["chase_pair"] == 0 for t in tune["tried"])
     ref.close()
+
+
+def test_bench_route_graph_replay_matches_oracle_sums():
+    """The benchmark's route at its exact settings (float32, one float64
+    refinement pass, 6 split-bfloat16 products, default SM split, persistent
+    launch, graph capture then replay): three idos_sample_levels calls with the
+    same counts and new sample indices (direct, captured, replayed); each
+    call's level sums against the oracle's sums over the same samples, within
+    the per-sample IDoS tolerance times the sample count."""
+    prec, refine = BENCH_SETTING
+    w, cfg, prm = cfg_and_prm(precision=prec, refine=refine)
+    counts = [6, 3, 2, 1]
+    m = pkg.create_model(dict(cfg, tc_products=6))
+    try:
+        for call in range(3):
+            firsts = [500 + 10 * call + l for l in range(4)]
+            m.reset_level_stats(-1)
+            m.sample_levels(counts, w["seed"], firsts)
+            for l in range(4):
+                M, s1, s2, _ = m.get_level_stats(l)
+                assert M == counts[l]
+                Ys = np.array([omlmc.level_sample(prm, w["levels"], l, firsts[l] + s, w["seed"])["Y"]
+                               for s in range(counts[l])])
+                assert np.max(np.abs(s1 - Ys.sum(0))) < counts[l] * IDOS_TOL, (call, l)
+        replays, captures, why = m.graph_info()
+        assert why == "" and captures >= 1 and replays >= 1, (replays, captures, why)
+    finally:
+        m.close()

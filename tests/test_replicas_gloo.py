@@ -1,7 +1,8 @@
 """Replica path on CPU: two gloo ranks with disjoint sample ranges merge their
 level accumulators and reproduce the single-process MLMC estimate.  The level
 samples come from the oracle (no GPU); what is tested is the replica logic
-(the exchange and the eq. (2.6) combine)."""
+(the exchange, and the library's host-arithmetic eq. (2.6) combine of the
+merged sums)."""
 import os
 import socket
 
@@ -53,9 +54,14 @@ def _free_port():
         return s.getsockname()[1]
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_1611_09784_gb300 import build
+    build.build()
+
+
 def test_two_gloo_ranks_reproduce_single_process():
     from oracle import mlmc
-    from paper_1611_09784_gb300 import replicas
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -78,6 +84,6 @@ def test_two_gloo_ranks_reproduce_single_process():
 
 
 def test_combine_rejects_single_sample_levels():
-    from paper_1611_09784_gb300 import replicas
-    with pytest.raises(ValueError):
+    from paper_1611_09784_gb300 import IdosError, replicas
+    with pytest.raises(IdosError):
         replicas.combine([1, 3], np.zeros((2, 2, 4)))

@@ -63,3 +63,29 @@ def test_noalloc_given_mask_and_limits():
     with pytest.raises(pkg.IdosError) as ei:
         binding.eval_idos_noalloc(cfg, 8, 40, q.data_ptr())
     assert ei.value.status == -1 and "static scratch" in str(ei.value)
+
+
+def test_noalloc_allocates_nothing_and_carries_no_state():
+    """After a warm-up call (which may load the library's kernel modules), the
+    device's free memory is the same before and after a series of calls,
+    including a large call followed by a small one on the same scratch; the
+    small call's result after the large one equals its result before it."""
+    w, cfg, prm = cfg_and_prm(precision="fp32")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    small = torch.empty(w["n_E"], dtype=torch.float64, device=dev)
+    large = torch.empty(w["n_E"], dtype=torch.float64, device=dev)
+    again = torch.empty(w["n_E"], dtype=torch.float64, device=dev)
+    e_small = torch.empty((4, 32), dtype=torch.float64, device=dev)
+    binding.eval_idos_noalloc(cfg, 4, 2, small.data_ptr(), seed=w["seed"], level=0, sample=9, stream=stream)
+    binding.eval_idos_noalloc(cfg, 8, 6, large.data_ptr(), seed=w["seed"], level=1, sample=9, stream=stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(3):
+        binding.eval_idos_noalloc(cfg, 8, 6, large.data_ptr(), seed=w["seed"], level=1, sample=9, stream=stream)
+        binding.eval_idos_noalloc(cfg, 4, 2, again.data_ptr(), eigs_dev_ptr=e_small.data_ptr(), seed=w["seed"],
+                                  level=0, sample=9, stream=stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0, (free0, free1)
+    assert torch.equal(small, again)
