@@ -595,7 +595,11 @@ def run_gpu(args):
     from paper_1611_09784_gb300 import replicas
     counts, sums = replicas.model_stats(model)
     level_span_ms = [round(model.get_level_stats(l)[3] * 1e3 / args.steps, 3) for l in range(len(M))]
-    moments = np.stack([model.get_level_moments(l)[1] for l in range(len(M))])
+    # the four accumulator rows and their sample counts, read together (the
+    # profiled replay below adds to the accumulators)
+    mom = [model.get_level_moments(l) for l in range(len(M))]
+    moments = np.stack([x[1] for x in mom])
+    mom_counts = [x[0] for x in mom]
     if world > 1:
         counts, sums = replicas.merge(counts, sums, device=dev)
     mean, var = replicas.combine(counts, sums)
@@ -635,7 +639,7 @@ def run_gpu(args):
     rates = None
     if all(M):
         Ns = [N for N, _ in levels]
-        cnt = [model.get_level_stats(l)[0] for l in range(len(M))]
+        cnt = mom_counts
         cost_s = []
         for l in range(len(M)):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

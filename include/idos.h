@@ -345,6 +345,16 @@ int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t
 int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int64_t batch,
                   const double* H, double* eigs_out, void* cuda_stream);
 
+/* The real symmetric tridiagonal (d, e^2) that the hot path's Householder
+ * reduction (Sec. 4.2's dense eigensolver; shared-memory path or two-stage
+ * path by size, tc_products as in idos_model_desc) makes of `batch` dense
+ * Hermitian n x n matrices (H as in idos_eigvalsh): d_out, e2_out: host
+ * float64[batch * n]; e2_out[b n + i] = |e_i|^2 couples rows i and i + 1
+ * (the last entry of every matrix is 0).  Its eigenvalues are those of H.
+ * Parity entry point (checks the reduction apart from the bisection). */
+int idos_tridiagonalize(int precision, int tc_products, int n, int64_t batch, const double* H, double* d_out,
+                        double* e2_out, void* cuda_stream);
+
 /* The trailing update of one stage-1 panel of the two-stage reduction
  * (compact-WY form of the two-sided Householder update, Sec. 4.2's dense
  * eigensolver): A_out = A - (Y Z^H + Z Y^H) for `batch` complex n x n

@@ -101,6 +101,8 @@ _SYMBOLS = {
                                      C.c_void_p]),
     "idos_hamiltonian": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "idos_eigvalsh": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_tridiagonalize": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "idos_her2k": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_get_partition": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_char_p)]),
     "idos_get_graph_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -466,6 +468,21 @@ def eigvalsh(H, precision="fp32", refine64_iters: int = 0, stream: int | None = 
     _check(load_library().idos_eigvalsh(_PRECISION[precision], refine64_iters, tc, n, batch, _ptr(H), _ptr(out),
                                         C.c_void_p(stream or 0)), "idos_eigvalsh")
     return out
+
+
+def tridiagonalize(H, precision="fp32", stream: int | None = None, tc_products: int | None = None):
+    """(d, e^2) of the hot path's reduction of a batch of Hermitian matrices
+    (idos_tridiagonalize); e^2[:, i] couples rows i and i + 1."""
+    H = np.ascontiguousarray(H, dtype=np.complex128)
+    if H.ndim == 2:
+        H = H[None]
+    batch, n, _ = H.shape
+    d = np.empty((batch, n))
+    e2 = np.empty((batch, n))
+    tc = DEFAULT_TC_PRODUCTS if tc_products is None else int(tc_products)
+    _check(load_library().idos_tridiagonalize(_PRECISION[precision], tc, n, batch, _ptr(H), _ptr(d), _ptr(e2),
+                                              C.c_void_p(stream or 0)), "idos_tridiagonalize")
+    return d, e2
 
 
 def her2k(A, Y, Z, tc_products: int = DEFAULT_TC_PRODUCTS):

@@ -1184,9 +1184,15 @@ int idos_hamiltonian(idos_model* m, int N, int Kside, int k_index, const uint8_t
   return IDOS_OK;
 }
 
-int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int64_t batch, const double* H,
-                  double* eigs_out, void* cuda_stream) {
-  if (!H || !eigs_out) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
+namespace {
+
+// The batched eigen-solve of explicit Hermitian matrices behind idos_eigvalsh
+// and idos_tridiagonalize: reduction to (d, e^2) by the hot path's kernels,
+// then (eigs_out != NULL) Sturm bisection; d_out / e2_out (nullable) receive
+// the tridiagonal as float64.
+int solve_explicit(int precision, int refine64_iters, int tc_products, int n, int64_t batch, const double* H,
+                   double* eigs_out, double* d_out, double* e2_out, void* cuda_stream) {
+  if (!H || (!eigs_out && !d_out && !e2_out)) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
   if (precision != IDOS_FP64 && precision != IDOS_FP32_REFINE64) { set_error("precision"); return IDOS_ERR_INVALID_ARG; }
   if (tc_products != 0 && tc_products != 3 && tc_products != 6) {
     set_error("tc_products must be 0, 3 or 6");
@@ -1231,15 +1237,54 @@ int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int
     a.tc_np = tc_products;
     rc = small ? solve_small(precision, a) : solve_large(precision, a);
   }
-  if (rc == IDOS_OK) rc = launch_bisect(precision, refine64_iters, d, e2, nullptr, 1, n, batch, eigs, s);
+  if (rc == IDOS_OK && eigs_out) rc = launch_bisect(precision, refine64_iters, d, e2, nullptr, 1, n, batch, eigs, s);
   if (rc == IDOS_OK) {
-    cudaError_t e = cudaMemcpyAsync(eigs_out, eigs, sizeof(double) * batch * n, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaSuccess;
+    if (eigs_out) e = cudaMemcpyAsync(eigs_out, eigs, sizeof(double) * batch * n, cudaMemcpyDeviceToHost, s);
+    std::vector<char> hd, he;
+    if (e == cudaSuccess && d_out) {
+      hd.resize(ts * batch * n);
+      e = cudaMemcpyAsync(hd.data(), d, hd.size(), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess && e2_out) {
+      he.resize(ts * batch * n);
+      e = cudaMemcpyAsync(he.data(), e2, he.size(), cudaMemcpyDeviceToHost, s);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = IDOS_ERR_CUDA; }
+    if (e != cudaSuccess) {
+      set_error(cudaGetErrorString(e));
+      rc = IDOS_ERR_CUDA;
+    } else {
+      const size_t cnt = (size_t)batch * n;
+      auto widen = [&](const std::vector<char>& src, double* dst) {
+        for (size_t i = 0; i < cnt; ++i)
+          dst[i] = ts == 4 ? (double)reinterpret_cast<const float*>(src.data())[i]
+                           : reinterpret_cast<const double*>(src.data())[i];
+      };
+      if (d_out) widen(hd, d_out);
+      if (e2_out) {
+        widen(he, e2_out);
+        for (int64_t b = 0; b < batch; ++b) e2_out[b * n + n - 1] = 0.0;   // no coupling past the last row
+      }
+    }
   }
   cudaStreamSynchronize(s);
   ws.release();
   return rc;
+}
+
+}  // namespace
+
+int idos_eigvalsh(int precision, int refine64_iters, int tc_products, int n, int64_t batch, const double* H,
+                  double* eigs_out, void* cuda_stream) {
+  if (!eigs_out) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
+  return solve_explicit(precision, refine64_iters, tc_products, n, batch, H, eigs_out, nullptr, nullptr, cuda_stream);
+}
+
+int idos_tridiagonalize(int precision, int tc_products, int n, int64_t batch, const double* H, double* d_out,
+                        double* e2_out, void* cuda_stream) {
+  if (!d_out || !e2_out) { set_error("null argument"); return IDOS_ERR_INVALID_ARG; }
+  return solve_explicit(precision, 0, tc_products, n, batch, H, nullptr, d_out, e2_out, cuda_stream);
 }
 
 int idos_set_profiling(idos_model* m, int enable) {

@@ -58,6 +58,26 @@ template <typename T> __device__ __forceinline__ c2<T> cjmul(c2<T> a, c2<T> b) {
   return mk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 template <typename T> __device__ __forceinline__ c2<T> cscale(c2<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+
+// |a| and the phase a / |a| (1 for a = 0) of a reflector's leading entry,
+// computed on a scaled by its larger component.  Forming |a|^2 first loses
+// the phase when a is tiny: below about 1e-19 in float32 (1e-154 in float64)
+// the square is subnormal and keeps only a few bits, so a / sqrt(|a|^2) is
+// not of unit modulus and I - tau v v^H is not unitary.  Such entries are
+// rounding noise where the exact value is 0 (the bipartite lattice makes
+// many), so they do occur.
+template <typename T>
+__device__ __forceinline__ T cabs_phase(c2<T> a, c2<T>& ph) {
+  const T s = fmax(fabs(a.x), fabs(a.y));
+  if (!(s > T(0))) {
+    ph = mk<T>(T(1), T(0));
+    return T(0);
+  }
+  const T ax = a.x / s, ay = a.y / s;
+  const T r = sqrt(ax * ax + ay * ay);
+  ph = mk<T>(ax / r, ay / r);
+  return s * r;
+}
 template <typename T> __device__ __forceinline__ T cabs2(c2<T> a) { return a.x * a.x + a.y * a.y; }
 template <typename T> __device__ __forceinline__ c2<T> conjg(c2<T> a) { return mk<T>(a.x, -a.y); }
 

@@ -70,8 +70,8 @@ __device__ __forceinline__ bool warp_reflector(c2<T> x, int L, T& tau, c2<T>& v,
   v = x;
   beta = alpha;
   if (!(rest > tiny_rest<T>())) return false;
-  const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
-  const c2<T> ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+  c2<T> ph;
+  const T aa = cabs_phase<T>(alpha, ph), sigma = sqrt(cabs2<T>(alpha) + rest);
   tau = T(1) / (sigma * (sigma + aa));
   if (lane == 0) v = cadd<T>(alpha, cscale<T>(ph, sigma));
   beta = cscale<T>(ph, -sigma);
@@ -337,8 +337,8 @@ __device__ __forceinline__ bool dreflector(c2<T> x, int L, T& tau, c2<T>& v, c2<
   v = xl;
   beta = alpha;
   if (!(rest > tiny_rest<T>())) return false;
-  const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
-  const c2<T> ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+  c2<T> ph;
+  const T aa = cabs_phase<T>(alpha, ph), sigma = sqrt(cabs2<T>(alpha) + rest);
   tau = T(1) / (sigma * (sigma + aa));
   if (l == 0) v = cadd<T>(alpha, cscale<T>(ph, sigma));
   beta = cscale<T>(ph, -sigma);

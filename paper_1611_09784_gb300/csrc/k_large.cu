@@ -168,8 +168,8 @@ k_ts_panel(Batch bt, int k, c2<T>* __restrict__ A, c2<T>* __restrict__ Y, c2<T>*
     T tau = T(0);
     C v0 = alpha, beta = alpha;
     if (tr) {
-      const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
-      const C ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+      C ph;
+      const T aa = cabs_phase<T>(alpha, ph), sigma = sqrt(cabs2<T>(alpha) + rest);
       tau = T(1) / (sigma * (sigma + aa));
       v0 = cadd<T>(alpha, cscale<T>(ph, sigma));
       beta = cscale<T>(ph, -sigma);
@@ -350,8 +350,8 @@ k_ts_panel_cl(Batch bt, int k, c2<T>* __restrict__ A, c2<T>* __restrict__ Y, c2<
     T tau = T(0);
     C vc = alpha, beta = alpha;
     if (tr) {
-      const T aa = sqrt(cabs2<T>(alpha)), sigma = sqrt(cabs2<T>(alpha) + rest);
-      const C ph = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
+      C ph;
+      const T aa = cabs_phase<T>(alpha, ph), sigma = sqrt(cabs2<T>(alpha) + rest);
       tau = T(1) / (sigma * (sigma + aa));
       vc = cadd<T>(alpha, cscale<T>(ph, sigma));
       beta = cscale<T>(ph, -sigma);

@@ -29,23 +29,20 @@ struct __align__(2 * sizeof(c2<T>)) VW {
   c2<T> v, w;
 };
 
-// sigma = sqrt(sigma2), |alpha| = sqrt(aa2), the phase alpha / |alpha| and
-// tau = 1 / (sigma (sigma + |alpha|)) of a reflector (sigma2 > 0).  Float32
-// takes the hardware reciprocal square root and the fast divide (a relative
-// error of a few 1e-7, the size of the reduction's own rounding); float64 the
-// correctly rounded operations.
+// sigma = sqrt(sigma2), |alpha|, the phase alpha / |alpha| (by cabs_phase,
+// exact for tiny alpha) and tau = 1 / (sigma (sigma + |alpha|)) of a
+// reflector (sigma2 > 0).  Float32 takes the hardware reciprocal square root
+// and the fast divide for sigma and tau (a relative error of a few 1e-7, the
+// size of the reduction's own rounding); float64 the correctly rounded
+// operations.
 template <typename T>
-__device__ __forceinline__ void reflector_scalars(c2<T> alpha, T aa2, T sigma2, T& sigma, T& aa, c2<T>& phs, T& tau) {
+__device__ __forceinline__ void reflector_scalars(c2<T> alpha, T sigma2, T& sigma, T& aa, c2<T>& phs, T& tau) {
+  aa = cabs_phase<T>(alpha, phs);
   if constexpr (sizeof(T) == 4) {
     sigma = sigma2 * rsqrtf(sigma2);
-    const float ra = aa2 > 0.f ? rsqrtf(aa2) : 0.f;
-    aa = aa2 * ra;
-    phs = aa2 > 0.f ? cscale<T>(alpha, ra) : mk<T>(T(1), T(0));
     tau = __fdividef(1.f, sigma * (sigma + aa));
   } else {
     sigma = sqrt(sigma2);
-    aa = sqrt(aa2);
-    phs = aa > T(0) ? cscale<T>(alpha, T(1) / aa) : mk<T>(T(1), T(0));
     tau = T(1) / (sigma * (sigma + aa));
   }
 }
@@ -155,7 +152,7 @@ __device__ __forceinline__ void small_tridiag_group(unsigned char* base, int gid
     if (tr) {
       T sigma, aa;
       C phs;
-      reflector_scalars<T>(alpha, aa2, sigma2, sigma, aa, phs, tau);
+      reflector_scalars<T>(alpha, sigma2, sigma, aa, phs, tau);
       for (int c = j + 1 + tid; c < n; c += NT)
         nvw[c].v = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * n + c]);
     }
@@ -370,7 +367,7 @@ __device__ __forceinline__ void small_tridiag_rg_cta(unsigned char* smem_raw, co
     if (tr) {
       T sigma, aa;
       C phs;
-      reflector_scalars<T>(alpha, aa2, sigma2, sigma, aa, phs, tau);
+      reflector_scalars<T>(alpha, sigma2, sigma, aa, phs, tau);
       for (int c = j + 1 + tid; c < n; c += NT)
         nvw[c].v = (c == j + 1) ? cadd<T>(alpha, cscale<T>(phs, sigma)) : conjg<T>(A[(size_t)j * LD + c]);
     }

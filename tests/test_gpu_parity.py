@@ -280,3 +280,64 @@ def test_bench_route_graph_replay_matches_oracle_sums():
         assert why == "" and captures >= 1 and replays >= 1, (replays, captures, why)
     finally:
         m.close()
+
+
+def _tiny_lead(n, seed, pos, value, band=None):
+    """Random Hermitian matrix (scale 3) whose entries (r, c) in `pos` (and
+    their mirror) are set to the tiny complex `value`; with `band`, entries
+    more than `band` below or above the diagonal are zero."""
+    H = synth.hermitian(n, seed, scale=3.0)
+    if band is not None:
+        i, j = np.indices(H.shape)
+        H[np.abs(i - j) > band] = 0.0
+    for r, c in pos:
+        H[r, c] = value
+        H[c, r] = np.conj(value)
+    return H
+
+
+@pytest.mark.parametrize("mag", [2e-22, 3e-23, 1e-20])
+@pytest.mark.parametrize("n,pos,band,tc", [
+    (32, [(0, 1)], None, 6),          # warp path: the first reflector's leading entry is conj(A[0][1])
+    (100, [(0, 1)], None, 6),         # CTA row-group path
+    (300, [(16, 0)], None, 6),        # two-stage: the first panel column's leading entry is A[16][0]
+    (300, [(16, 0)], None, 0),
+    (300, [(1, 0)], 16, 6),           # a band matrix: stage 1 leaves it, the chase's first sweep starts at A[1][0]
+])
+def test_reflector_with_tiny_leading_entry_fp32(mag, n, pos, band, tc):
+    """A reflector whose leading entry alpha is tiny but nonzero (rounding
+    noise where the exact value is 0, as the bipartite lattice produces):
+    |alpha|^2 is subnormal in float32 for |alpha| below ~1e-19, so its phase
+    must not come from sqrt(|alpha|^2).  Eigenvalues against LAPACK."""
+    value = mag * (0.6 + 0.8j)
+    H = np.stack([_tiny_lead(n, 4000 + b, pos, value, band) for b in range(2)])
+    ref = np.linalg.eigvalsh(H)
+    got = np.sort(pkg.eigvalsh(H, precision="fp32", refine64_iters=1, tc_products=tc), axis=1)
+    assert np.max(np.abs(got - ref)) < EIG_TOL
+
+
+@pytest.mark.parametrize("n,pos,band", [(32, [(0, 1)], None), (100, [(0, 1)], None), (300, [(16, 0)], None),
+                                        (300, [(1, 0)], 16)])
+def test_reflector_with_tiny_leading_entry_fp64(n, pos, band):
+    """The same in float64, where |alpha|^2 is subnormal below ~1e-154."""
+    value = 3e-162 * (0.6 + 0.8j)
+    H = np.stack([_tiny_lead(n, 5000 + b, pos, value, band) for b in range(2)])
+    ref = np.linalg.eigvalsh(H)
+    got = np.sort(pkg.eigvalsh(H, precision="fp64", refine64_iters=2), axis=1)
+    assert np.max(np.abs(got - ref)) < 1e-9
+
+
+def test_level3_sample_with_noise_level_reflector_entry():
+    """Level-3 sample 90 000 000 of the MLMC workload: one corner (n = 492,
+    N = 16, K = 2) meets a panel column whose leading entry is ~6e-23 (zero in
+    exact arithmetic); at the benchmark's settings its IDoS was 3.2e-4 off
+    before the phase fix.  Y, Q_fine and the four Q_coarse against the
+    oracle."""
+    w, cfg, prm = cfg_and_prm(precision="fp32", refine=1)
+    with pkg.create_model(dict(cfg, tc_products=6)) as m:
+        Y, Qf, Qc = m.sample_level_detail(3, 1, w["seed"], 90_000_000)
+    ref = omlmc.level_sample(prm, w["levels"], 3, 90_000_000, w["seed"])
+    assert np.max(np.abs(Qf[0] - ref["Q_fine"])) < IDOS_TOL
+    for r in range(4):
+        assert np.max(np.abs(Qc[0, r] - ref["Q_coarse"][r])) < IDOS_TOL, r
+    assert np.max(np.abs(Y[0] - ref["Y"])) < IDOS_TOL
