@@ -261,7 +261,8 @@ int idos_reset_level_stats(idos_model* m, int level);
  * idos_kind), or NULL to draw it from (seed, level, sample) exactly as
  * idos_sample_level does.  idos_out: host float64[n_E].  eigs_out: NULL or
  * host float64[Kside^2 * n]: per k the ascending eigenvalues of the active
- * block, then NaN padding to n. */
+ * block (equal eigenvalues may come out in either order within their
+ * rounding), then NaN padding to n. */
 int idos_eval_idos(idos_model* m, int N, int Kside, const uint8_t* mask, uint64_t seed,
                    int level, int64_t sample, double* idos_out, double* eigs_out);
 

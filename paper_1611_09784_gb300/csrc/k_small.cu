@@ -237,6 +237,188 @@ __device__ __forceinline__ void small_tridiag_group(unsigned char* base, int gid
   }
 }
 
+// Register-resident variant for float32 and n <= 32, one warp per matrix:
+// lane c holds column c of A in registers (a[r] = A[r][c]).  Same method and
+// step order as small_tridiag_group: row j is brought up to date with the
+// pending update (v', w') of step j - 1 (by symmetry conj(row j) is the
+// column below the diagonal), the reflector is formed from it, then one
+// pass over rows r > j applies the pending update to a[r] and accumulates
+// p = tau A22 v.  Only the vectors v and (v', w') travel through shared
+// memory (a 768-byte slot per warp, read as broadcasts); no matrix entry
+// does.  Lanes c >= n carry zero columns that stay zero.
+struct WarpRegSlot {
+  float4 vw[32];   // pending (v', w') of every row
+  float2 v[32];    // this step's reflector
+};
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+// a - x conj(y) - z conj(u)
+__device__ __forceinline__ float2 rank2_sub(float2 a, float2 x, float2 y, float2 z, float2 u) {
+  a.x -= x.x * y.x + x.y * y.y;
+  a.y -= x.y * y.x - x.x * y.y;
+  a.x -= z.x * u.x + z.y * u.y;
+  a.y -= z.y * u.x - z.x * u.y;
+  return a;
+}
+// p + conj(a) v
+__device__ __forceinline__ float2 cj_fma(float2 p, float2 a, float2 v) {
+  p.x += a.x * v.x + a.y * v.y;
+  p.y += a.x * v.y - a.y * v.x;
+  return p;
+}
+
+__device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane, const int* __restrict__ n_act_cell,
+                                                       const int* __restrict__ act, const int* __restrict__ inv,
+                                                       int N, int K, int n_max, int64_t mat, double t_hop,
+                                                       double eps, const double2* __restrict__ Hin,
+                                                       float* __restrict__ d_out, float* __restrict__ e2_out) {
+  const int K2 = K * K;
+  const int64_t cell = mat / K2;
+  const int kidx = (int)(mat - cell * K2);
+  const int n = Hin ? n_max : n_act_cell[cell];
+  float* dO = d_out + mat * n_max;
+  float* eO = e2_out + mat * n_max;
+  if (n <= 0) return;
+  const int c = lane;
+  float2 a[32];
+  if (Hin) {
+    const double2* src = Hin + mat * (int64_t)n * n;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      a[r] = f2(0.f, 0.f);
+      if (r < n && c < n) a[r] = f2((float)src[(size_t)r * n + c].x, (float)src[(size_t)r * n + c].y);
+    }
+  } else {
+    // column c of H(k): A[col_b][c] = conj(H[c][col_b]) for the three bonds of
+    // kept site c (bonds to removed sites dropped; N = 1 sums on one entry)
+    int col[3] = {-1, -1, -1};
+    float2 hv[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
+    if (c < n) {
+      const int n_sites = 2 * N * N;
+      int nb[3];
+      bool fromB;
+      graphene_neighbours(N, act[cell * n_sites + c], nb, fromB);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float2 ph = graphene_phase_f(N, K, kidx, b);
+        const float hx = (float)t_hop * ph.x, hy = (float)t_hop * ph.y;
+        col[b] = inv[cell * n_sites + nb[b]];
+        hv[b] = fromB ? f2(hx, hy) : f2(hx, -hy);   // conj of the row entry
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      float2 s2 = f2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        if (col[b] == r) {
+          s2.x += hv[b].x;
+          s2.y += hv[b].y;
+        }
+      if (r == c && c < n) s2.x += (float)eps;
+      a[r] = s2;
+    }
+  }
+  float2 vp = f2(0.f, 0.f), wp = f2(0.f, 0.f);   // this lane's entries of the pending (v', w')
+  bool pend = false;
+  float2 rowj = a[0];
+  for (int j = 0; j < n - 1; ++j) {
+    // (a) A[j][c] up to date
+    if (pend) {
+      const float4 q = sl->vw[j];
+      rowj = rank2_sub(rowj, f2(q.x, q.y), wp, f2(q.z, q.w), vp);
+    }
+    // (b) x_c = conj(A[j][c]) for c > j; sigma^2 = |x_{j+1}|^2 + rest
+    const float2 x = f2(rowj.x, -rowj.y);
+    float rest = (c > j + 1 && c < n) ? x.x * x.x + x.y * x.y : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+    const float2 alpha = f2(__shfl_sync(0xffffffffu, x.x, j + 1), __shfl_sync(0xffffffffu, x.y, j + 1));
+    const float sigma2 = alpha.x * alpha.x + alpha.y * alpha.y + rest;
+    if (c == j) dO[j] = rowj.x;
+    if (c == 0) eO[j] = sigma2;
+    const bool tr = rest > 1e-30f;
+    float tau = 0.f;
+    float2 v = f2(0.f, 0.f);
+    if (tr) {
+      float sigma, aa;
+      float2 phs;
+      reflector_scalars<float>(alpha, sigma2, sigma, aa, phs, tau);
+      if (c == j + 1) v = f2(alpha.x + phs.x * sigma, alpha.y + phs.y * sigma);
+      else if (c > j + 1 && c < n) v = x;
+    }
+    sl->v[c] = v;
+    __syncwarp();
+    // (c) pending update of rows r > j and p = A22 v (two partial sums)
+    float2 p0 = f2(0.f, 0.f), p1 = f2(0.f, 0.f), rown = f2(0.f, 0.f);
+    if (pend && tr) {
+#pragma unroll
+      for (int r = 1; r < 32; ++r) {
+        if (r > j && r < n) {
+          const float4 q = sl->vw[r];
+          const float2 ar = rank2_sub(a[r], f2(q.x, q.y), wp, f2(q.z, q.w), vp);
+          a[r] = ar;
+          if (r & 1) p1 = cj_fma(p1, ar, sl->v[r]);
+          else p0 = cj_fma(p0, ar, sl->v[r]);
+          if (r == j + 1) rown = ar;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 1; r < 32; ++r) {
+        if (r > j && r < n) {
+          float2 ar = a[r];
+          if (pend) {
+            const float4 q = sl->vw[r];
+            ar = rank2_sub(ar, f2(q.x, q.y), wp, f2(q.z, q.w), vp);
+            a[r] = ar;
+          }
+          if (tr) p0 = cj_fma(p0, ar, sl->v[r]);
+          if (r == j + 1) rown = ar;
+        }
+      }
+    }
+    // (d) w = p - K v with p = tau A22 v, K = tau/2 Re(v^H p)
+    float2 w = f2(0.f, 0.f);
+    if (tr) {
+      const float2 p = f2((p0.x + p1.x) * tau, (p0.y + p1.y) * tau);
+      float kp = (c > j && c < n) ? v.x * p.x + v.y * p.y : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+      const float Kc = 0.5f * tau * kp;
+      w = f2(p.x - Kc * v.x, p.y - Kc * v.y);
+    }
+    __syncwarp();   // every lane has read the previous pending pair and v
+    sl->vw[c] = make_float4(v.x, v.y, w.x, w.y);
+    __syncwarp();
+    vp = v;
+    wp = w;
+    pend = tr;
+    rowj = rown;
+  }
+  if (c == n - 1) {
+    float2 dl = rowj;
+    if (pend) {
+      const float4 q = sl->vw[n - 1];
+      dl = rank2_sub(dl, f2(q.x, q.y), wp, f2(q.z, q.w), vp);
+    }
+    dO[n - 1] = dl.x;
+  }
+}
+
+constexpr int kRegWarps = 4;   // warps (matrices) per CTA of k_small_tridiag_reg (5 CTAs per SM at 102 registers)
+
+__global__ void __launch_bounds__(32 * kRegWarps)
+k_small_tridiag_reg(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv,
+                    int N, int K, int n_max, int64_t n_mat, double t_hop, double eps, const double2* __restrict__ Hin,
+                    float* __restrict__ d_out, float* __restrict__ e2_out) {
+  __shared__ WarpRegSlot slots[kRegWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t mat = (int64_t)blockIdx.x * kRegWarps + warp;
+  if (mat >= n_mat) return;   // whole warp leaves together
+  small_tridiag_warp_reg(&slots[warp], lane, n_act_cell, act, inv, N, K, n_max, mat, t_hop, eps, Hin, d_out, e2_out);
+}
+
 template <typename T, int NT, int MPB>
 __global__ void __launch_bounds__(NT* MPB)
 k_small_tridiag(const int* __restrict__ n_act_cell, const int* __restrict__ act,
@@ -511,7 +693,7 @@ k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long 
   }
   // phase 2: the n <= 32 matrices, one per warp item, each warp in its slot
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* slot = smem_raw + (size_t)warp * SmallLayout<float>::bytes(32);
+  WarpRegSlot* slot = reinterpret_cast<WarpRegSlot*>(smem_raw) + warp;
   for (;;) {
     long long it = 0;
     if (lane == 0) it = (long long)atomicAdd(&ctr[1], 1ull);
@@ -521,8 +703,8 @@ k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long 
     while (g + 1 < w.n_seg && it >= w.end[g]) ++g;
     const SmallSeg& sg = w.seg[g];
     const int64_t mat = it - (g > w.n_cta ? w.end[g - 1] : 0);
-    small_tridiag_group<float, 32, 1>(slot, warp, lane, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat,
-                                      t_hop, eps, nullptr, sg.d, sg.e2);
+    small_tridiag_warp_reg(slot, lane, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps, nullptr,
+                           sg.d, sg.e2);
     __syncwarp();
   }
 }
@@ -563,7 +745,7 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
     } else {
       w.total_warp += sg.n_mat;
       w.end[q] = w.total_warp;
-      smem = std::max(smem, SmallLayout<float>::bytes(32) * kPWarps);
+      smem = std::max(smem, sizeof(WarpRegSlot) * kPWarps);
     }
   }
   w.n_seg = no;
@@ -597,8 +779,22 @@ bool small_path_fits(int precision, int n_max) {
   return b <= kSmemLimit;
 }
 
+int run_small_reg(const SolveArgs& a) {
+  const CellSet* c = a.cells;
+  const int64_t blocks = (a.n_mat + kRegWarps - 1) / kRegWarps;
+  ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
+  k_small_tridiag_reg<<<(unsigned)blocks, 32 * kRegWarps, 0, a.stream>>>(
+      c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside, a.n_max, a.n_mat,
+      a.t, a.eps, a.H, reinterpret_cast<float*>(a.d), reinterpret_cast<float*>(a.e2));
+  IDOS_CHECK_LAUNCH();
+  return IDOS_OK;
+}
+
 template <typename T>
 static int solve_small_t(const SolveArgs& a) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.n_max <= 32) return run_small_reg(a);
+  }
   if (a.n_max <= 32) {
     // up to 4 matrices per CTA while they fit
     if (SmallLayout<T>::bytes(a.n_max) * 4 <= kSmemLimit) return run_small<T, 32, 4>(a);
