@@ -78,6 +78,23 @@ __device__ __forceinline__ T cabs_phase(c2<T> a, c2<T>& ph) {
   ph = mk<T>(ax / r, ay / r);
   return s * r;
 }
+// float32: one correctly rounded reciprocal and one hardware reciprocal
+// square root (|ph| = 1 to a few float32 ulp), short on the latency path of
+// the band chase's reflectors.
+template <>
+__device__ __forceinline__ float cabs_phase<float>(float2 a, float2& ph) {
+  const float s = fmaxf(fabsf(a.x), fabsf(a.y));
+  if (!(s > 0.f)) {
+    ph = make_float2(1.f, 0.f);
+    return 0.f;
+  }
+  const float rs = __frcp_rn(s);
+  const float ax = a.x * rs, ay = a.y * rs;
+  const float q = ax * ax + ay * ay;   // in [1, 2]
+  const float rq = rsqrtf(q);
+  ph = make_float2(ax * rq, ay * rq);
+  return s * (q * rq);
+}
 template <typename T> __device__ __forceinline__ T cabs2(c2<T> a) { return a.x * a.x + a.y * a.y; }
 template <typename T> __device__ __forceinline__ c2<T> conjg(c2<T> a) { return mk<T>(a.x, -a.y); }
 

@@ -242,29 +242,51 @@ __device__ __forceinline__ void small_tridiag_group(unsigned char* base, int gid
 // step order as small_tridiag_group: row j is brought up to date with the
 // pending update (v', w') of step j - 1 (by symmetry conj(row j) is the
 // column below the diagonal), the reflector is formed from it, then one
-// pass over rows r > j applies the pending update to a[r] and accumulates
-// p = tau A22 v.  Only the vectors v and (v', w') travel through shared
-// memory (a 768-byte slot per warp, read as broadcasts); no matrix entry
-// does.  Lanes c >= n carry zero columns that stay zero.
+// pass over the rows applies the pending update to a[r] and accumulates
+// p = A22 v.  Only the vectors travel through shared memory (a 1.5 KB slot
+// per warp, read as broadcasts), pre-arranged so that the pass is six packed
+// float32 FMAs per row (fma.rn.f32x2):
+//   a <- a - (v'_r.x, v'_r.y) w'_c.x - (v'_r.y, -v'_r.x) w'_c.y
+//          - (w'_r.x, w'_r.y) v'_c.x - (w'_r.y, -w'_r.x) v'_c.y
+//      = a - v'_r conj(w'_c) - w'_r conj(v'_c),
+//   P1 += a (v_r.x, v_r.x),  P2 += a (v_r.y, v_r.y),
+//   conj(a) v_r summed = (P1.x + P2.y, P2.x - P1.y).
+// The reflector and update entries of rows <= j (reduced) and of rows >= n
+// (lanes without a column) are exactly zero, so those rows are no-ops and
+// the pass runs over 4-row chunks that intersect (j, n), skipping the others
+// with a warp-uniform branch.
 struct WarpRegSlot {
-  float4 vw[32];   // pending (v', w') of every row
-  float2 v[32];    // this step's reflector
+  float4 pv[32];   // pending: (v'.x, v'.y, v'.y, -v'.x) of every row
+  float4 pw[32];   //          (w'.x, w'.y, w'.y, -w'.x)
+  float4 vv[32];   // this step's reflector: (v.x, v.x, v.y, v.y)
 };
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-// a - x conj(y) - z conj(u)
-__device__ __forceinline__ float2 rank2_sub(float2 a, float2 x, float2 y, float2 z, float2 u) {
-  a.x -= x.x * y.x + x.y * y.y;
-  a.y -= x.y * y.x - x.x * y.y;
-  a.x -= z.x * u.x + z.y * u.y;
-  a.y -= z.y * u.x - z.x * u.y;
-  return a;
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
 }
-// p + conj(a) v
-__device__ __forceinline__ float2 cj_fma(float2 p, float2 a, float2 v) {
-  p.x += a.x * v.x + a.y * v.y;
-  p.y += a.x * v.y - a.y * v.x;
-  return p;
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+// packed a b + c on (x, y) pairs
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(d);
+}
+// the pending rank-2 update of one entry; nw*, nv*: this lane's negated
+// (w'_c.x, w'_c.x), (w'_c.y, w'_c.y), (v'_c.x, v'_c.x), (v'_c.y, v'_c.y)
+__device__ __forceinline__ float2 pend_update(float2 a, float4 pv, float4 pw, float2 nwx, float2 nwy, float2 nvx,
+                                              float2 nvy) {
+  a = fma2(f2(pv.x, pv.y), nwx, a);
+  a = fma2(f2(pv.z, pv.w), nwy, a);
+  a = fma2(f2(pw.x, pw.y), nvx, a);
+  a = fma2(f2(pw.z, pw.w), nvy, a);
+  return a;
 }
 
 __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane, const int* __restrict__ n_act_cell,
@@ -319,15 +341,13 @@ __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane
       a[r] = s2;
     }
   }
-  float2 vp = f2(0.f, 0.f), wp = f2(0.f, 0.f);   // this lane's entries of the pending (v', w')
+  // this lane's negated pending entries, packed: (-w'.x, -w'.x) ...
+  float2 nwx = f2(0.f, 0.f), nwy = nwx, nvx = nwx, nvy = nwx;
   bool pend = false;
   float2 rowj = a[0];
   for (int j = 0; j < n - 1; ++j) {
     // (a) A[j][c] up to date
-    if (pend) {
-      const float4 q = sl->vw[j];
-      rowj = rank2_sub(rowj, f2(q.x, q.y), wp, f2(q.z, q.w), vp);
-    }
+    if (pend) rowj = pend_update(rowj, sl->pv[j], sl->pw[j], nwx, nwy, nvx, nvy);
     // (b) x_c = conj(A[j][c]) for c > j; sigma^2 = |x_{j+1}|^2 + rest
     const float2 x = f2(rowj.x, -rowj.y);
     float rest = (c > j + 1 && c < n) ? x.x * x.x + x.y * x.y : 0.f;
@@ -347,66 +367,66 @@ __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane
       if (c == j + 1) v = f2(alpha.x + phs.x * sigma, alpha.y + phs.y * sigma);
       else if (c > j + 1 && c < n) v = x;
     }
-    sl->v[c] = v;
+    sl->vv[c] = make_float4(v.x, v.x, v.y, v.y);
     __syncwarp();
-    // (c) pending update of rows r > j and p = A22 v (two partial sums)
-    float2 p0 = f2(0.f, 0.f), p1 = f2(0.f, 0.f), rown = f2(0.f, 0.f);
-    if (pend && tr) {
+    // (c) one pass over the 4-row chunks meeting (j, n)
+    float2 p1a = f2(0.f, 0.f), p2a = p1a, p1b = p1a, p2b = p1a, rown = p1a;
 #pragma unroll
-      for (int r = 1; r < 32; ++r) {
-        if (r > j && r < n) {
-          const float4 q = sl->vw[r];
-          const float2 ar = rank2_sub(a[r], f2(q.x, q.y), wp, f2(q.z, q.w), vp);
-          a[r] = ar;
-          if (r & 1) p1 = cj_fma(p1, ar, sl->v[r]);
-          else p0 = cj_fma(p0, ar, sl->v[r]);
-          if (r == j + 1) rown = ar;
-        }
-      }
-    } else {
+    for (int rb = 0; rb < 8; ++rb) {
+      if (4 * rb + 3 > j && 4 * rb < n) {   // warp-uniform
+        const bool has_next = (j + 1) >> 2 == rb;
 #pragma unroll
-      for (int r = 1; r < 32; ++r) {
-        if (r > j && r < n) {
+        for (int q = 0; q < 4; ++q) {
+          const int r = 4 * rb + q;
           float2 ar = a[r];
-          if (pend) {
-            const float4 q = sl->vw[r];
-            ar = rank2_sub(ar, f2(q.x, q.y), wp, f2(q.z, q.w), vp);
-            a[r] = ar;
+          if (pend) ar = pend_update(ar, sl->pv[r], sl->pw[r], nwx, nwy, nvx, nvy);
+          a[r] = ar;
+          if (tr) {
+            const float4 vr = sl->vv[r];
+            if (q & 1) {
+              p1b = fma2(ar, f2(vr.x, vr.y), p1b);
+              p2b = fma2(ar, f2(vr.z, vr.w), p2b);
+            } else {
+              p1a = fma2(ar, f2(vr.x, vr.y), p1a);
+              p2a = fma2(ar, f2(vr.z, vr.w), p2a);
+            }
           }
-          if (tr) p0 = cj_fma(p0, ar, sl->v[r]);
-          if (r == j + 1) rown = ar;
+          if (has_next && r == j + 1) rown = ar;
         }
       }
     }
-    // (d) w = p - K v with p = tau A22 v, K = tau/2 Re(v^H p)
+    // (d) w = p - K v with p = tau A22 v, K = tau/2 Re(v^H p); zero on the
+    //     reduced rows and on lanes without a column
     float2 w = f2(0.f, 0.f);
     if (tr) {
-      const float2 p = f2((p0.x + p1.x) * tau, (p0.y + p1.y) * tau);
-      float kp = (c > j && c < n) ? v.x * p.x + v.y * p.y : 0.f;
+      const float px = (p1a.x + p1b.x) + (p2a.y + p2b.y), py = (p2a.x + p2b.x) - (p1a.y + p1b.y);
+      const float2 p = f2(px * tau, py * tau);
+      const bool live = c > j && c < n;
+      float kp = live ? v.x * p.x + v.y * p.y : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
       const float Kc = 0.5f * tau * kp;
-      w = f2(p.x - Kc * v.x, p.y - Kc * v.y);
+      if (live) w = f2(p.x - Kc * v.x, p.y - Kc * v.y);
     }
     __syncwarp();   // every lane has read the previous pending pair and v
-    sl->vw[c] = make_float4(v.x, v.y, w.x, w.y);
+    sl->pv[c] = make_float4(v.x, v.y, v.y, -v.x);
+    sl->pw[c] = make_float4(w.x, w.y, w.y, -w.x);
     __syncwarp();
-    vp = v;
-    wp = w;
+    nwx = f2(-w.x, -w.x);
+    nwy = f2(-w.y, -w.y);
+    nvx = f2(-v.x, -v.x);
+    nvy = f2(-v.y, -v.y);
     pend = tr;
     rowj = rown;
   }
   if (c == n - 1) {
     float2 dl = rowj;
-    if (pend) {
-      const float4 q = sl->vw[n - 1];
-      dl = rank2_sub(dl, f2(q.x, q.y), wp, f2(q.z, q.w), vp);
-    }
+    if (pend) dl = pend_update(dl, sl->pv[n - 1], sl->pw[n - 1], nwx, nwy, nvx, nvy);
     dO[n - 1] = dl.x;
   }
 }
 
-constexpr int kRegWarps = 4;   // warps (matrices) per CTA of k_small_tridiag_reg (5 CTAs per SM at 102 registers)
+constexpr int kRegWarps = 4;   // warps (matrices) per CTA of k_small_tridiag_reg
 
 __global__ void __launch_bounds__(32 * kRegWarps)
 k_small_tridiag_reg(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv,
@@ -677,7 +697,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
 k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_item;
-  // phase 1: the larger matrices, one per CTA item, segments in descending n
+  // the larger matrices, one per CTA item, segments in descending n
   for (;;) {
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[0], 1ull);
     __syncthreads();
@@ -691,9 +711,18 @@ k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long 
                                             t_hop, eps, nullptr, sg.d, sg.e2);
     __syncthreads();   // s_item and the shared region are reused
   }
-  // phase 2: the n <= 32 matrices, one per warp item, each warp in its slot
+}
+
+// The n <= 32 matrices of every warp segment, one per warp item, taken by
+// whichever warp is free (a second persistent launch after the CTA items:
+// the register-resident reduction needs more registers per thread than the
+// 640-thread CTA items leave).
+constexpr int kPWarpCta = 4;   // warps per CTA of the warp-item launch
+
+__global__ void __launch_bounds__(32 * kPWarpCta)
+k_small_persistent_warps(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
+  __shared__ WarpRegSlot slots[kPWarpCta];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpRegSlot* slot = reinterpret_cast<WarpRegSlot*>(smem_raw) + warp;
   for (;;) {
     long long it = 0;
     if (lane == 0) it = (long long)atomicAdd(&ctr[1], 1ull);
@@ -703,8 +732,8 @@ k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long 
     while (g + 1 < w.n_seg && it >= w.end[g]) ++g;
     const SmallSeg& sg = w.seg[g];
     const int64_t mat = it - (g > w.n_cta ? w.end[g - 1] : 0);
-    small_tridiag_warp_reg(slot, lane, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps, nullptr,
-                           sg.d, sg.e2);
+    small_tridiag_warp_reg(&slots[warp], lane, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps,
+                           nullptr, sg.d, sg.e2);
     __syncwarp();
   }
 }
@@ -745,7 +774,6 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
     } else {
       w.total_warp += sg.n_mat;
       w.end[q] = w.total_warp;
-      smem = std::max(smem, sizeof(WarpRegSlot) * kPWarps);
     }
   }
   w.n_seg = no;
@@ -757,14 +785,23 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
   int dev = 0, sms = 0;
   IDOS_CUDA_TRY(cudaGetDevice(&dev));
   IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int grid = ctas > 0 ? std::min(ctas, sms) : sms;
-  const int64_t items = w.total_cta + (w.total_warp + kPWarps - 1) / kPWarps;
-  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, items));
-  IDOS_CUDA_TRY(cudaFuncSetAttribute(k_small_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int sm_grid = ctas > 0 ? std::min(ctas, sms) : sms;
   IDOS_CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s));
-  ProfScope ps(KID_SMALL_TRIDIAG, s);
-  k_small_persistent<<<grid, kPThreads, smem, s>>>(w, t, eps, counters);
-  IDOS_CHECK_LAUNCH();
+  if (w.total_cta > 0) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_grid, w.total_cta));
+    IDOS_CUDA_TRY(cudaFuncSetAttribute(k_small_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(KID_SMALL_TRIDIAG, s);
+    k_small_persistent<<<grid, kPThreads, smem, s>>>(w, t, eps, counters);
+    IDOS_CHECK_LAUNCH();
+  }
+  if (w.total_warp > 0) {
+    // four 4-warp CTAs per SM (the register-resident reduction's occupancy)
+    const int64_t ctas_w = (w.total_warp + kPWarpCta - 1) / kPWarpCta;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_grid * 4, ctas_w));
+    ProfScope ps(KID_SMALL_TRIDIAG, s);
+    k_small_persistent_warps<<<grid, 32 * kPWarpCta, 0, s>>>(w, t, eps, counters);
+    IDOS_CHECK_LAUNCH();
+  }
   return IDOS_OK;
 }
 

@@ -36,7 +36,7 @@ def test_generalized_eigenvalues_and_idos(N, K, precision):
             got = E[k][~np.isnan(E[k])]
             # still ascending after the map (equal eigenvalues, e.g. a pair of
             # zero modes, may come out in either order within rounding)
-            assert np.all(np.diff(got) >= -1e-12)
+            assert np.all(np.diff(got) >= -1e-9)
             assert np.max(np.abs(got - E_ref[k])) < EIG_TOL
         assert np.max(np.abs(Q - oidos.sample_idos(N, K, mask, prm))) < IDOS_TOL
     m.close()
