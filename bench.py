@@ -452,65 +452,162 @@ def tmdc_sweep(pkg, torch, stream, samples=(32, 32, 32, 8)):
     return out
 
 
-def stress(pkg, torch, stream):
-    """Graphene N = 64 (n = 8192), p = 0.02, 2 x 2 grid: one sample (4 solves)
-    on the float32 path with the tensor-core trailing update."""
+def stress(pkg, torch, stream, samples=2, fp64_check=True):
+    """Graphene N = 64 (n = 8192), p = 0.02, 2 x 2 grid: `samples` samples
+    (4 solves each) on the float32 path with the tensor-core trailing update
+    (CUDA events), the tensor-core update's achieved MMA rate from a profiled
+    replay of the same call, and the eigenvalue difference to the float64 GPU
+    path on one grid point of sample 0 (K = 1 model, same mask)."""
+    import numpy as np
     from synthetic import workload
     w = workload("graphene_stress")
-    cfg = dict(w["model"], p=w["p"], levels=w["levels"], e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
-               delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64,
-               tc_products=TC_PRODUCTS)
-    m = pkg.create_model(cfg, stream=stream.cuda_stream)
+    base = dict(w["model"], p=w["p"], e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"], delta=w["delta"],
+                smoothing=w["smoothing"], refine64_iters=REFINE64, tc_products=TC_PRODUCTS)
+    m = pkg.create_model(dict(base, levels=w["levels"], precision="fp32"), stream=stream.cuda_stream)
     m.sample_level(0, 1, w["seed"] + 1, 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
+    m.sample_level(0, samples, w["seed"], 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m.reset_profile()
+    m.set_profiling(True)
     m.sample_level(0, 1, w["seed"], 0)
+    m.set_profiling(False)
+    prof = m.get_profile()
+    m.close()
+    out = {"N": 64, "n": 8192, "K": 2, "samples": samples, "of_samples": 128, "ms": round(ms, 1),
+           "eigsolves_per_s": samples * 4 / (ms * 1e-3),
+           "precision": f"fp32 reduction, tensor-core trailing update ({TC_PRODUCTS} split-bf16 products), "
+                        f"{REFINE64} fp64 pass",
+           "kernels_ms_per_sample": {k: round(v[0], 2) for k, v in prof.items()}}
+    # executed MMA flops of the trailing update of one n = 8192 matrix (x 4
+    # grid points): tc_products x 16 bw m^2 per panel
+    n, bw = 8192, 16
+    flops = 4 * TC_PRODUCTS * sum(16.0 * bw * (n - k - bw) ** 2 for k in range(0, n - bw, bw))
+    if "k_ts_her2k" in prof and prof["k_ts_her2k"][0] > 0:
+        out["tensor_core_update_tflops"] = flops / (prof["k_ts_her2k"][0] * 1e-3) / 1e12
+    if fp64_check:
+        # eigenvalues of one grid point on both paths (K = 1: the zone centre
+        # of the Monkhorst-Pack grid), same mask
+        w1 = dict(base, levels=[(64, 1)])
+        m32 = pkg.create_model(dict(w1, precision="fp32"), stream=stream.cuda_stream)
+        _, E32 = m32.eval_idos(64, 1, seed=w["seed"], level=0, sample=0, want_eigs=True)
+        m32.close()
+        m64 = pkg.create_model(dict(w1, precision="fp64", refine64_iters=2), stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        _, E64 = m64.eval_idos(64, 1, seed=w["seed"], level=0, sample=0, want_eigs=True)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        m64.close()
+        a32 = np.sort(E32[0][~np.isnan(E32[0])])
+        a64 = np.sort(E64[0][~np.isnan(E64[0])])
+        out["fp32_vs_fp64_gpu"] = {"max_abs_dE_eV": float(np.max(np.abs(a32 - a64))), "n_act": int(a32.size),
+                                   "fp64_seconds_one_solve": t64, "what": "one n = 8192 matrix (sample 0, K = 1)"}
+    return out
+
+
+def fp64_paths(pkg, torch, stream, cfg, levels, M, seed):
+    """The float64 GPU path (the paper's own precision): config 1, plain Monte
+    Carlo, graphene N = 4, 6 x 6 grid, 1000 samples (36 000 eigen-solves), and
+    one step of the MLMC allocation on the float64 path; CUDA events on the
+    model stream."""
+    from synthetic import workload
+    out = {}
+    w1 = workload("graphene_plain_mc")
+    c1 = dict(w1["model"], p=w1["p"], levels=w1["levels"], e_min=w1["e_min"], e_max=w1["e_max"], n_E=w1["n_E"],
+              delta=w1["delta"], smoothing=w1["smoothing"], precision="fp64", refine64_iters=2)
+    m = pkg.create_model(c1, stream=stream.cuda_stream)
+    m.sample_level(0, 8, w1["seed"] + 1, 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    m.sample_level(0, w1["samples"][0], w1["seed"], 0)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     m.close()
-    return {"N": 64, "n": 8192, "K": 2, "samples": 1, "ms": round(ms, 1), "eigsolves_per_s": 4 / (ms * 1e-3),
-            "precision": f"fp32 reduction, tensor-core trailing update ({TC_PRODUCTS} split-bf16 products)"}
+    N, K = w1["levels"][0]
+    solves = w1["samples"][0] * K * K
+    out["config1_plain_mc_fp64"] = {"N": N, "K": K, "samples": w1["samples"][0], "eigsolves": solves, "ms": round(ms, 2),
+                                    "eigsolves_per_s": solves / (ms * 1e-3)}
+    m = pkg.create_model(dict(cfg, precision="fp64", refine64_iters=2, sm_split=-1, graph=-1), stream=stream.cuda_stream)
+    m.sample_levels([1] * len(M), seed + 3, [10 ** 9] * len(M))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    m.sample_levels(M, seed + 3, [0] * len(M))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    m.close()
+    eig = sum(Ml * eigsolves_per_sample(levels, l) for l, Ml in enumerate(M))
+    out["config2_mlmc_fp64_step"] = {"samples_per_level": M, "ms": round(ms, 1), "eigsolves_per_s": eig / (ms * 1e-3),
+                                     "precision": "fp64 reduction, bisection and 2 fp64 passes"}
+    return out
 
 
-def serving(pkg, cfg, levels, seed, rates=(300.0, 1000.0), n_req=120, trace_seed=7):
-    """The request loop under Poisson arrivals of level requests like the ones
-    the adaptive driver emits: level l with probability 0.4, 0.3, 0.2, 0.1,
-    batch log-uniform in [1, B_l] samples (B = 512, 512, 32, 4: fewer samples on
-    costlier levels).  The same trace is served by 4 worker streams
-    (concurrent) and by 1 (one request at a time).  Latency = submission to
-    completion (library clock); throughput = eigen-solves / (last completion -
-    first arrival)."""
+def serving_trace(rng, rate, n_req, bmax, probs):
     import numpy as np
+    gaps = rng.exponential(1.0 / rate, n_req)
+    lv = rng.choice(len(probs), size=n_req, p=probs)
+    nb = [int(round(math.exp(rng.uniform(0.0, math.log(bmax[l]))))) for l in lv]
+    return np.cumsum(gaps), lv, nb
+
+
+def serve_trace(pkg, cfg, arrive, lv, nb, seed, workers):
+    """Replays one arrival trace through the request loop; latency =
+    submission to completion (library clock)."""
+    import numpy as np
+    srv = pkg.Server(dict(cfg, sm_split=0), n_workers=workers)
+    for l in sorted(set(int(x) for x in lv)):            # warm-up: workspaces, first launches
+        srv.wait(srv.submit(l, 1, seed + 5, 0))
+    t0 = time.perf_counter()
+    tickets = []
+    for i in range(len(lv)):
+        dt = t0 + arrive[i] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(int(lv[i]), nb[i], seed, 1_000_000 + 10_000 * i))
+    lat = [srv.wait(t)[2] for t in tickets]
+    elapsed = time.perf_counter() - t0
+    srv.close()
+    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "wall_s": elapsed}, elapsed
+
+
+def serving(pkg, cfg, levels, seed, rates=(10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0), trace_seed=7):
+    """The request loop under Poisson arrivals of level requests like the ones
+    the adaptive driver emits, for both models: graphene levels N = 4 ... 32
+    (probability 0.4, 0.3, 0.2, 0.1; batch log-uniform in [1, 512, 512, 32, 4]
+    samples) and the TMDC-shaped model at N = 4, 8, 16 (n = 176, 704, 2816;
+    0.5, 0.35, 0.15; batch up to 64, 8, 1).  Every trace is served by 4 worker
+    streams (concurrent) and by 1 (one request at a time).  Requests per trace:
+    about 2 s of arrivals, 20 to 120.  Throughput = eigen-solves / (last
+    completion - first arrival)."""
+    import numpy as np
+    from synthetic import workload
     rng = np.random.default_rng(trace_seed)
-    bmax = [512, 512, 32, 4]
+    wt = workload("tmdc_sweep")
+    tm_levels = [(4, wt["K"]), (8, wt["K"]), (16, wt["K"])]
+    tm_cfg = dict(wt["model"], p=wt["p"], levels=tm_levels, e_min=wt["e_min"], e_max=wt["e_max"], n_E=wt["n_E"],
+                  delta=wt["delta"], smoothing=wt["smoothing"], precision="fp32", refine64_iters=REFINE64,
+                  tc_products=TC_PRODUCTS)
+    models = {"graphene": (cfg, levels, [512, 512, 32, 4], [0.4, 0.3, 0.2, 0.1]),
+              "tmdc": (tm_cfg, tm_levels, [64, 8, 1], [0.5, 0.35, 0.15])}
     out = []
-    for rate in rates:
-        gaps = rng.exponential(1.0 / rate, n_req)
-        lv = rng.choice(4, size=n_req, p=[0.4, 0.3, 0.2, 0.1])
-        nb = [int(round(math.exp(rng.uniform(0.0, math.log(bmax[l]))))) for l in lv]
-        arrive = np.cumsum(gaps)
-        eig = sum(n * eigsolves_per_sample(levels, int(l)) for l, n in zip(lv, nb))
-        row = {"rate_per_s": rate, "requests": n_req, "eigsolves": int(eig)}
-        for workers in (4, 1):
-            srv = pkg.Server(dict(cfg, sm_split=0), n_workers=workers)
-            for l in range(4):                      # warm-up: workspaces, first launches
-                srv.wait(srv.submit(l, 1, seed + 5, 0))
-            t0 = time.perf_counter()
-            tickets = []
-            for i in range(n_req):
-                dt = t0 + arrive[i] - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                tickets.append(srv.submit(int(lv[i]), nb[i], seed, 1_000_000 + 10_000 * i))
-            lat = [srv.wait(t)[2] for t in tickets]
-            elapsed = time.perf_counter() - t0
-            srv.close()
-            key = "concurrent_4" if workers == 4 else "one_at_a_time"
-            row[key] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                        "eigsolves_per_s": eig / elapsed, "wall_s": elapsed}
-        out.append(row)
+    for name, (mcfg, mlev, bmax, probs) in models.items():
+        for rate in rates:
+            n_req = int(min(120, max(20, 2 * rate)))
+            arrive, lv, nb = serving_trace(rng, rate, n_req, bmax, probs)
+            eig = sum(n * eigsolves_per_sample(mlev, int(l)) for l, n in zip(lv, nb))
+            row = {"model": name, "rate_per_s": rate, "requests": n_req, "eigsolves": int(eig)}
+            for workers in (4, 1):
+                r, elapsed = serve_trace(pkg, mcfg, arrive, lv, nb, seed, workers)
+                r["eigsolves_per_s"] = eig / elapsed
+                row["concurrent_4" if workers == 4 else "one_at_a_time"] = r
+            out.append(row)
     return out
 
 
@@ -710,6 +807,7 @@ def run_gpu(args):
     sweep = tmdc_sweep(pkg, torch, stream)
     stress_line = stress(pkg, torch, stream)
     serve = serving(pkg, cfg, levels, seed)
+    fp64 = fp64_paths(pkg, torch, stream, cfg, levels, M, seed)
 
     # GPU against the oracle at the bench's settings, outside the timed region
     chk = None
@@ -750,6 +848,7 @@ def run_gpu(args):
             "serving": serve,
             "tmdc_sweep": sweep,
             "stress": stress_line,
+            "fp64_path": fp64,
             "estimate_check": {"Q_at_e_max": float(mean[-1]), "max_std": float(np.sqrt(np.max(var)))},
             "oracle_check": chk,
             "rates": rates,
@@ -796,6 +895,123 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------- profiling helpers --
+# ncu kernel names -> the library profiler's kernel families
+NCU_FAMILY = [("k_small_persistent", "k_small_tridiag"), ("k_small_tridiag", "k_small_tridiag"),
+              ("k_ts_panel", "k_ts_panel"), ("k_ts_w", "k_ts_w"), ("k_ts_wm", "k_ts_z"), ("k_ts_zc", "k_ts_z"),
+              ("k_tc_operands", "k_ts_her2k"), ("k_tc_her2k", "k_ts_her2k"), ("k_ts_her2k", "k_ts_her2k"),
+              ("k_ts_to_band", "k_ts_chase"), ("k_ts_chase", "k_ts_chase"), ("k_bisect", "k_bisect"),
+              ("k_idos", "k_idos"), ("k_level", "k_level_stats"), ("k_fine_masks", "k_masks"),
+              ("k_corner_masks", "k_masks"), ("k_cell_maps", "k_masks"), ("k_lg_assemble", "k_lg_assemble")]
+FAMILY_SOURCE = {"k_small_tridiag": "k_small.cu", "k_ts_panel": "k_large.cu", "k_ts_w": "k_large.cu",
+                 "k_ts_z": "k_large.cu", "k_ts_her2k": "k_tc.cu", "k_ts_chase": "k_chase.cu",
+                 "k_bisect": "k_bisect.cu", "k_idos": "k_idos.cu"}
+
+
+def ncu_family(name):
+    base = name.split("(")[0].split("<")[0].split("::")[-1].strip()
+    for prefix, fam in NCU_FAMILY:
+        if base.startswith(prefix):
+            return fam
+    return None
+
+
+def run_profile_step(args):
+    """One step of the workload for an ncu capture: direct launches on shared
+    SMs, no autotuner, no warm-up, no clock sampler; the allocation scaled by
+    --scale (at least one sample per level).  Writes the step's algorithmic
+    work per kernel family to --work-json."""
+    import numpy as np
+    import torch
+    import paper_1611_09784_gb300 as pkg
+    from synthetic import workload
+    w = workload(WORKLOAD)
+    levels = [tuple(x) for x in w["levels"]]
+    M = [max(1, int(round(Ml * args.scale))) for Ml in load_alloc()["M"]]
+    if args.levels is not None:
+        keep = {int(x) for x in args.levels.split(",")}
+        M = [Ml if l in keep else 0 for l, Ml in enumerate(M)]
+    cfg = dict(w["model"], p=w["p"], levels=levels, e_min=w["e_min"], e_max=w["e_max"], n_E=w["n_E"],
+               delta=w["delta"], smoothing=w["smoothing"], precision="fp32", refine64_iters=REFINE64,
+               tc_products=TC_PRODUCTS, sm_split=0, graph=0)
+    torch.cuda.set_device(0)
+    m = pkg.create_model(cfg)
+    seed = w["seed"]
+    firsts = [0] * len(M)
+    m.sample_levels(M, seed, firsts)
+    torch.cuda.synchronize()
+    work = algorithmic_work(m, levels, M, seed, firsts, n_E=w["n_E"])
+    m.close()
+    if args.work_json:
+        with open(args.work_json, "w") as f:
+            json.dump({"samples_per_level": M, "work": work}, f)
+    print(json.dumps({"profile_step": True, "samples_per_level": M}), flush=True)
+
+
+def traffic_table(csv_path, work_json):
+    """From an ncu CSV of one profile step (--metrics dram__bytes_read.sum,
+    dram__bytes_write.sum, gpu__time_duration.sum) and that step's work file:
+    per kernel family the launches, device time, share and DRAM bytes per
+    algorithmic unit, and the profiles/traffic.txt lines."""
+    import csv
+    with open(work_json) as f:
+        wk = json.load(f)["work"]
+    rows = {}
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for rec in csv.DictReader(lines):
+        fam = ncu_family(rec.get("Kernel Name", ""))
+        if fam is None:
+            continue
+        r = rows.setdefault(fam, {"launch_ids": set(), "ns": 0.0, "dram": 0.0})
+        r["launch_ids"].add(rec["ID"])
+        val = float(rec["Metric Value"].replace(",", "")) if rec.get("Metric Value") else 0.0
+        unit = rec.get("Metric Unit", "")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1, "usecond": 1e3,
+                 "msecond": 1e6}.get(unit, 1)
+        if rec["Metric Name"] == "gpu__time_duration.sum":
+            r["ns"] += val * scale
+        elif rec["Metric Name"].startswith("dram__bytes"):
+            r["dram"] += val * scale
+    total = sum(r["ns"] for r in rows.values()) or 1.0
+    out = []
+    for fam, r in sorted(rows.items(), key=lambda kv: -kv[1]["ns"]):
+        ratio = r["dram"] / wk[fam] if wk.get(fam) else None
+        out.append({"family": fam, "launches": len(r["launch_ids"]), "ms": r["ns"] / 1e6, "share": r["ns"] / total,
+                    "dram_bytes": r["dram"], "algorithmic": wk.get(fam), "dram_per_unit": ratio})
+    print(json.dumps(out, indent=1))
+    for o in out:
+        if o["dram_per_unit"] is not None and o["family"] in FAMILY_SOURCE:
+            src = FAMILY_SOURCE[o["family"]]
+            print(f"{o['family']} {src} {kernel_source_hash(src)} {o['dram_per_unit']:.4e}")
+
+
+def run_case(args):
+    """Single-kernel cases for ncu captures: her2k:N:B (the tensor-core
+    trailing update of B random n = N panels, twice) and eigvalsh:N:B (B random
+    Hermitian matrices through the float32 path at the bench settings, twice)."""
+    import numpy as np
+    import paper_1611_09784_gb300 as pkg
+    from synthetic import matrices as synth
+    kind, N, B = args.case.split(":")
+    N, B = int(N), int(B)
+    rng = np.random.default_rng(5)
+    t0 = time.perf_counter()
+    if kind == "her2k":
+        A = np.stack([synth.hermitian(N, 10 + b, scale=3.0) for b in range(B)])
+        Y = rng.standard_normal((B, 16, N)) + 1j * rng.standard_normal((B, 16, N))
+        Z = rng.standard_normal((B, 16, N)) + 1j * rng.standard_normal((B, 16, N))
+        for _ in range(2):
+            pkg.her2k(A, Y, Z, tc_products=TC_PRODUCTS)
+    elif kind == "eigvalsh":
+        H = np.stack([synth.hermitian(N, 20 + b, scale=3.0) for b in range(B)])
+        for _ in range(2):
+            pkg.eigvalsh(H, precision="fp32", refine64_iters=REFINE64, tc_products=TC_PRODUCTS)
+    else:
+        raise SystemExit(f"unknown case {kind}")
+    print(json.dumps({"case": args.case, "wall_s": time.perf_counter() - t0}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -816,7 +1032,23 @@ def main():
                     help="only the timed steps: no e2e / plain-MC / CPU-baseline measurements")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the GPU-vs-oracle check at the bench settings")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling: run exactly one step (direct launches, shared SMs, no autotuner, no warm-up)")
+    ap.add_argument("--scale", type=float, default=1.0, help="profiling: scale of the allocation in --profile-step")
+    ap.add_argument("--work-json", default=None, help="profiling: where --profile-step writes the step's work")
+    ap.add_argument("--traffic-table", nargs=2, metavar=("NCU_CSV", "WORK_JSON"), default=None,
+                    help="summarise an ncu capture of --profile-step (no GPU needed)")
+    ap.add_argument("--case", default=None, help="profiling: her2k:N:B or eigvalsh:N:B")
     args = ap.parse_args()
+    if args.traffic_table:
+        traffic_table(*args.traffic_table)
+        return
+    if args.case:
+        run_case(args)
+        return
+    if args.profile_step:
+        run_profile_step(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
