@@ -392,8 +392,8 @@ int idos_measure_fma_peak(int precision, int64_t iters, void* cuda_stream, doubl
  * largest n the shared-memory kernel takes before the two-stage path (64, or
  * whatever fits: 160 float32 / 112 float64) and, with the latter, the
  * persistent launch on or off (graphene, IDOS_FP32_REFINE64; on with graph
- * replay, with the two-stage levels below the finest on either partition;
- * off without graph replay), then the winner with graph replay switched (unless
+ * replay in each of the three placements below; off without graph replay),
+ * then the winner with graph replay switched (unless
  * the model gave graphs up), then the two-stage kernel shapes (the W tile
  * and one or two warps per sweep in clustered band chases).  Each candidate
  * runs twice untimed (a direct
@@ -402,7 +402,7 @@ int idos_measure_fma_peak(int precision, int64_t iters, void* cuda_stream, doubl
  * the level statistics are restored afterwards.  Results do not depend on the
  * choice beyond float rounding of the path choice; out: the choice and every
  * candidate's best step time. */
-#define IDOS_TUNE_MAX 32
+#define IDOS_TUNE_MAX 40
 typedef struct idos_tuning {
   int32_t sm_split;      /* chosen SMs reserved for the finest level (0 = shared) */
   int32_t small_max_n;   /* chosen limit of the shared-memory kernel (-1 = what fits) */
@@ -419,9 +419,11 @@ typedef struct idos_tuning {
   int32_t chase_pair;    /* clustered band chases: 1 = two warps per sweep, 0 = one */
   int32_t tried_w_tile[IDOS_TUNE_MAX];
   int32_t tried_chase_pair[IDOS_TUNE_MAX];
-  int32_t large_to_finest; /* persistent route on the partition: 1 = a level below the finest whose
-                              fine cells take the two-stage path runs on the finest level's SMs */
-  int32_t tried_large_to_finest[IDOS_TUNE_MAX];
+  int32_t placement;     /* persistent route on the partition: 0 = every level on its own
+                            partition; 1 = a level below the finest whose fine cells take the
+                            two-stage path runs on the finest level's SMs; 2 = the finest
+                            level's corner cells run on the other levels' SMs */
+  int32_t tried_placement[IDOS_TUNE_MAX];
 } idos_tuning;
 int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
 

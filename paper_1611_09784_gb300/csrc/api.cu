@@ -549,7 +549,8 @@ int apply_partition(Model* m, int split) {
     if (prio > prio_least) prio = prio_least;
     const int which = l == L - 1 ? 0 : 1;
     IDOS_TRY(partition_stream(m->part, which, prio, &m->pstream[l]));
-    IDOS_TRY(partition_stream(m->part, which, prio, &m->pstream2[l]));
+    // placement 2: the finest level's corner solve on the other partition
+    IDOS_TRY(partition_stream(m->part, (l == L - 1 && m->placement == 2) ? 1 : which, prio, &m->pstream2[l]));
     if (l < L - 1) IDOS_TRY(partition_stream(m->part, 0, prio, &m->pstreamF[l]));
     m->lsms[l] = m->part.sms[which];
   }
@@ -889,7 +890,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     lst[l] = streams[l];
     lst2[l] = streams2[l];
     lsm[l] = parted ? m->lsms[l] : 0;
-    if (parted && route_p && m->large_to_finest && l < L - 1 && m->pstreamF[l] &&
+    if (parted && route_p && m->placement == 1 && l < L - 1 && m->pstreamF[l] &&
         !use_small_path(m, orb_per_cell(m->d.kind) * m->d.N[l] * m->d.N[l])) {
       lst[l] = m->pstreamF[l];
       lsm[l] = m->lsms[L - 1];
@@ -912,7 +913,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     std::vector<int64_t> core(n_samples, n_samples + L);
     for (int64_t v : {(int64_t)parted, (int64_t)route_p, (int64_t)m->small_max_n, (int64_t)m->persistent,
                       (int64_t)m->part_gen, (int64_t)m->w_tile, (int64_t)m->chase_pair,
-                      (int64_t)m->large_to_finest})
+                      (int64_t)m->placement})
       core.push_back(v);
     std::vector<int64_t> key = core;
     for (int l = 0; l < L; ++l) key.push_back((int64_t)m->lws[l].gen);
@@ -1459,13 +1460,14 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   // (small-kernel limit, persistent launch): the persistent launch only
   // with the default limit, and only where it applies
   const bool can_persist = m->d.kind == IDOS_GRAPHENE && m->d.precision == IDOS_FP32_REFINE64;
-  // (small-kernel limit, persistent launch, graph replay, two-stage levels on
-  // the finest level's partition)
-  const int variants[][4] = {{-1, 1, 1, 0}, {-1, 1, 1, 1}, {-1, 0, 0, 0}, {64, 0, 0, 0}};
+  // (small-kernel limit, persistent launch, graph replay, placement: 0, or 1 =
+  // two-stage levels below the finest on the finest level's partition, or
+  // 2 = the finest level's corner solve on the other partition)
+  const int variants[][4] = {{-1, 1, 1, 0}, {-1, 1, 1, 2}, {-1, 1, 1, 1}, {-1, 0, 0, 0}, {64, 0, 0, 0}};
   out->n_tried = 0;
   out->best_ms = 1e300;
   int best_split = m->sm_split_now, best_small = m->small_max_n, best_persist = m->persistent, best_graph = m->graph;
-  int best_w = m->w_tile, best_cp = m->chase_pair, best_ltf = m->large_to_finest;
+  int best_w = m->w_tile, best_cp = m->chase_pair, best_ltf = m->placement;
   const int graph_saved = m->graph;
   int64_t first[IDOS_MAX_LEVELS];
   int64_t round = 0;
@@ -1475,7 +1477,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   auto time_config = [&](int sp, int sm, int pers, int gr, int wt, int cp, int ltf) -> int {
     m->small_max_n = sm;
     m->persistent = pers;
-    m->large_to_finest = ltf;
+    m->placement = ltf;
     m->graph = graph_saved ? gr : 0;   // a model that gave up graphs stays without
     m->w_tile = wt;
     m->chase_pair = cp;
@@ -1498,7 +1500,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     out->tried_graph[i] = m->graph;
     out->tried_w_tile[i] = wt;
     out->tried_chase_pair[i] = cp;
-    out->tried_large_to_finest[i] = ltf;
+    out->tried_placement[i] = ltf;
     out->tried_ms[i] = best;
     if (best < out->best_ms) {
       out->best_ms = best;
@@ -1537,7 +1539,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   m->graph = best_graph;
   m->w_tile = best_w;
   m->chase_pair = best_cp;
-  m->large_to_finest = best_ltf;
+  m->placement = best_ltf;
   const int rc2 = apply_partition(m, best_split);
   IDOS_CUDA_TRY(cudaMemcpyAsync(m->acc, acc_saved.data(), sizeof(double) * acc_saved.size(), cudaMemcpyHostToDevice,
                                 m->stream));
@@ -1550,7 +1552,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   out->graph = m->graph;
   out->w_tile = m->w_tile;
   out->chase_pair = m->chase_pair;
-  out->large_to_finest = m->large_to_finest;
+  out->placement = m->placement;
   return rc != IDOS_OK ? rc : rc2;
 }
 

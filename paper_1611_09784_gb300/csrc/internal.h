@@ -120,11 +120,16 @@ struct Model {
   // second stream per level for the corners' solve beside the fine one
   cudaStream_t lstream2[IDOS_MAX_LEVELS] = {}, pstream2[IDOS_MAX_LEVELS] = {};
   // streams of the levels below the finest on the finest level's partition:
-  // with large_to_finest a level whose fine cells take the two-stage path runs
+  // with placement 1 a level whose fine cells take the two-stage path runs
   // there (its latency-bound chain beside the finest level's) instead of
   // waiting for the persistent launch to free the other partition's SMs
   cudaStream_t pstreamF[IDOS_MAX_LEVELS] = {};
-  int large_to_finest = 0;        // off by default (the autotuner may switch it on)
+  // placement of work on the partition: 0 = levels on their own partitions;
+  // 1 = the levels above (pstreamF); 2 = the finest level's corner solve
+  // (many medium matrices, throughput work) on the other partition, leaving
+  // the finest partition to the latency-bound chain of the large matrices.
+  // 0 by default; the autotuner may pick another.
+  int placement = 0;
   cudaEvent_t lfork2[IDOS_MAX_LEVELS] = {}, ljoin2[IDOS_MAX_LEVELS] = {};
   cudaStream_t stream2 = nullptr;                // the same for calls on the model's stream
   cudaEvent_t fork2 = nullptr, join2 = nullptr;
