@@ -394,8 +394,9 @@ int idos_measure_fma_peak(int precision, int64_t iters, void* cuda_stream, doubl
  * persistent launch on or off (graphene, IDOS_FP32_REFINE64; on with graph
  * replay in each of the three placements below; off without graph replay),
  * then the winner with graph replay switched (unless
- * the model gave graphs up), then the two-stage kernel shapes (the W tile
- * and one or two warps per sweep in clustered band chases).  Each candidate
+ * the model gave graphs up), then the two-stage kernel shapes (the W tile,
+ * one or two warps per sweep in clustered band chases, and 1, 2 or 4 CTAs
+ * in the panel QR cluster).  Each candidate
  * runs twice untimed (a direct
  * call, then the graph capture) and `reps` times timed (best kept), on
  * sample indices from 2^40 on;
@@ -424,6 +425,8 @@ typedef struct idos_tuning {
                             two-stage path runs on the finest level's SMs; 2 = the finest
                             level's corner cells run on the other levels' SMs */
   int32_t tried_placement[IDOS_TUNE_MAX];
+  int32_t panel_cluster; /* CTAs of the stage-1 panel QR cluster (0 = the default rule) */
+  int32_t tried_panel_cluster[IDOS_TUNE_MAX];
 } idos_tuning;
 int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
 

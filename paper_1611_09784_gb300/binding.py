@@ -52,7 +52,8 @@ class Tuning(C.Structure):
                 ("tried_persistent", C.c_int32 * TUNE_MAX), ("graph", C.c_int32),
                 ("tried_graph", C.c_int32 * TUNE_MAX), ("w_tile", C.c_int32), ("chase_pair", C.c_int32),
                 ("tried_w_tile", C.c_int32 * TUNE_MAX), ("tried_chase_pair", C.c_int32 * TUNE_MAX),
-                ("placement", C.c_int32), ("tried_placement", C.c_int32 * TUNE_MAX)]
+                ("placement", C.c_int32), ("tried_placement", C.c_int32 * TUNE_MAX),
+                ("panel_cluster", C.c_int32), ("tried_panel_cluster", C.c_int32 * TUNE_MAX)]
 
 
 class Estimate(C.Structure):
@@ -261,10 +262,12 @@ class Model:
         tried = [{"sm_split": t.tried_split[i], "small_max_n": t.tried_small[i],
                   "persistent": t.tried_persistent[i], "graph": t.tried_graph[i], "w_tile": t.tried_w_tile[i],
                   "chase_pair": t.tried_chase_pair[i], "placement": t.tried_placement[i],
+                  "panel_cluster": t.tried_panel_cluster[i],
                   "ms": round(t.tried_ms[i], 3)} for i in range(t.n_tried)]
         return {"sm_split": t.sm_split, "small_max_n": t.small_max_n, "persistent": t.persistent,
                 "graph": t.graph, "w_tile": t.w_tile, "chase_pair": t.chase_pair,
-                "placement": t.placement, "best_ms": round(t.best_ms, 3), "tried": tried}
+                "placement": t.placement, "panel_cluster": t.panel_cluster, "best_ms": round(t.best_ms, 3),
+                "tried": tried}
 
     def graph_info(self):
         """(calls that replayed a graph, captures made, reason graph mode was

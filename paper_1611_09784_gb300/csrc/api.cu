@@ -169,6 +169,7 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.max_cluster = sm_avail ? 8 : 16;
   a.w_tile = M->w_tile;
   a.chase_pair = M->chase_pair;
+  a.panel_cluster = M->panel_cluster;
   if (use_small_path(M, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
   IDOS_TRY(eigs_and_idos(M, cells, Kside, d, e2, eigs, Q, st));
@@ -912,7 +913,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     // from has changed: sample counts, route, settings, partition, arenas
     std::vector<int64_t> core(n_samples, n_samples + L);
     for (int64_t v : {(int64_t)parted, (int64_t)route_p, (int64_t)m->small_max_n, (int64_t)m->persistent,
-                      (int64_t)m->part_gen, (int64_t)m->w_tile, (int64_t)m->chase_pair,
+                      (int64_t)m->part_gen, (int64_t)m->w_tile, (int64_t)m->chase_pair, (int64_t)m->panel_cluster,
                       (int64_t)m->placement})
       core.push_back(v);
     std::vector<int64_t> key = core;
@@ -1467,20 +1468,21 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   out->n_tried = 0;
   out->best_ms = 1e300;
   int best_split = m->sm_split_now, best_small = m->small_max_n, best_persist = m->persistent, best_graph = m->graph;
-  int best_w = m->w_tile, best_cp = m->chase_pair, best_ltf = m->placement;
+  int best_w = m->w_tile, best_cp = m->chase_pair, best_ltf = m->placement, best_pc = m->panel_cluster;
   const int graph_saved = m->graph;
   int64_t first[IDOS_MAX_LEVELS];
   int64_t round = 0;
   int rc = IDOS_OK;
   // two untimed calls per candidate: the first runs directly (and sizes the
   // workspaces), the second captures the graph; the timed calls replay it
-  auto time_config = [&](int sp, int sm, int pers, int gr, int wt, int cp, int ltf) -> int {
+  auto time_config = [&](int sp, int sm, int pers, int gr, int wt, int cp, int ltf, int pc) -> int {
     m->small_max_n = sm;
     m->persistent = pers;
     m->placement = ltf;
     m->graph = graph_saved ? gr : 0;   // a model that gave up graphs stays without
     m->w_tile = wt;
     m->chase_pair = cp;
+    m->panel_cluster = pc;
     int r = apply_partition(m, sp);
     if (r != IDOS_OK) return r;
     if (sp > 0 && m->sm_split_now == 0) return IDOS_OK;   // the driver could not make this split
@@ -1500,6 +1502,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     out->tried_graph[i] = m->graph;
     out->tried_w_tile[i] = wt;
     out->tried_chase_pair[i] = cp;
+    out->tried_panel_cluster[i] = pc;
     out->tried_placement[i] = ltf;
     out->tried_ms[i] = best;
     if (best < out->best_ms) {
@@ -1511,6 +1514,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
       best_w = wt;
       best_cp = cp;
       best_ltf = ltf;
+      best_pc = pc;
     }
     return IDOS_OK;
   };
@@ -1520,7 +1524,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     if (pers == 1 && !can_persist) continue;
     for (int sp : splits) {
       if (sp >= m->sm_count || (sp > 0 && L < 2) || out->n_tried >= IDOS_TUNE_MAX) continue;
-      rc = time_config(sp, sm, pers, gr, 1, 1, ltf);
+      rc = time_config(sp, sm, pers, gr, 1, 1, ltf, 0);
       if (rc != IDOS_OK) break;
     }
     if (rc != IDOS_OK) break;
@@ -1528,11 +1532,15 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   // second stage, at the winner: graph replay switched, then the two-stage
   // kernel shapes (64-row W tiles; one warp per sweep in clustered chases)
   if (rc == IDOS_OK && graph_saved && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
-    rc = time_config(best_split, best_small, best_persist, best_graph ? 0 : 1, best_w, best_cp, best_ltf);
+    rc = time_config(best_split, best_small, best_persist, best_graph ? 0 : 1, best_w, best_cp, best_ltf, best_pc);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
-    rc = time_config(best_split, best_small, best_persist, best_graph, best_w ? 0 : 1, best_cp, best_ltf);
+    rc = time_config(best_split, best_small, best_persist, best_graph, best_w ? 0 : 1, best_cp, best_ltf, best_pc);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
-    rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp ? 0 : 1, best_ltf);
+    rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp ? 0 : 1, best_ltf, best_pc);
+  // the panel QR's cluster size (the default rule picks up to 8 CTAs)
+  for (int pc : {1, 2, 4})
+    if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
+      rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp, best_ltf, pc);
   // install the winner and restore the caller's statistics
   m->small_max_n = best_small;
   m->persistent = best_persist;
@@ -1540,6 +1548,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   m->w_tile = best_w;
   m->chase_pair = best_cp;
   m->placement = best_ltf;
+  m->panel_cluster = best_pc;
   const int rc2 = apply_partition(m, best_split);
   IDOS_CUDA_TRY(cudaMemcpyAsync(m->acc, acc_saved.data(), sizeof(double) * acc_saved.size(), cudaMemcpyHostToDevice,
                                 m->stream));
@@ -1552,6 +1561,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   out->graph = m->graph;
   out->w_tile = m->w_tile;
   out->chase_pair = m->chase_pair;
+  out->panel_cluster = m->panel_cluster;
   out->placement = m->placement;
   return rc != IDOS_OK ? rc : rc2;
 }

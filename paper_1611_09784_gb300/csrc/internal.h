@@ -98,6 +98,9 @@ struct SolveArgs {
   // clustered band chases with two warps per sweep (1) or one (0)
   int w_tile = 1;
   int chase_pair = 1;
+  // CTAs of the stage-1 panel QR cluster (0: the smallest power of two whose
+  // shared memory holds the panel, grown while the batch leaves SMs idle)
+  int panel_cluster = 0;
 };
 
 // Two green contexts splitting the device's SMs (partition.cu): ctx[0] has
@@ -164,6 +167,7 @@ struct Model {
   int small_max_n = -1;           // largest n on the shared-memory kernel (-1: whatever fits)
   int persistent = 1;             // one persistent launch for the levels' shared-memory matrices
   int w_tile = 1, chase_pair = 1;  // two-stage kernel shapes (SolveArgs)
+  int panel_cluster = 0;           // stage-1 panel QR cluster size (SolveArgs)
   double* acc = nullptr;          // device [n_levels][kAccRows][n_E]: sum Y, Y^2, Q_fine, Q_fine^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream

@@ -283,6 +283,16 @@ __device__ __forceinline__ void fence_acq_rel() {
   else asm volatile("fence.acq_rel.cta;" ::: "memory");
 }
 
+// A CTA's band columns are stored diagonal-major with the diagonal stride
+// padded to 2^cwl + kBandPad entries.  Without the pad (a power-of-two stride)
+// the 16 rows of a block, which lie on 16 consecutive diagonals, fall into one
+// shared-memory bank: every block load and store was a 16-way conflict.  With
+// a stride of 3 (mod 16) complex entries the rows of a block below the
+// diagonal (stride +S per row) are conflict-free and the mirrored entries
+// above it (stride 1 - S per row) at most 2-way.
+constexpr int kBandPad = 3;
+__host__ __device__ constexpr int band_stride(int cwl) { return (1 << cwl) + kBandPad; }
+
 // CL = false: the whole band is in this CTA (no distributed addressing).
 template <typename T, bool CL>
 struct DBand {
@@ -291,10 +301,10 @@ struct DBand {
   int rank;
   __device__ __forceinline__ c2<T>* addr(int d, int c) const {
     if constexpr (!CL) {
-      return local + ((size_t)d << cwl) + c;
+      return local + (size_t)d * band_stride(cwl) + c;
     } else {
       const int o = c >> cwl;
-      c2<T>* p = local + ((size_t)d << cwl) + (c & ((1 << cwl) - 1));
+      c2<T>* p = local + (size_t)d * band_stride(cwl) + (c & ((1 << cwl) - 1));
       return o == rank ? p : cg::this_cluster().map_shared_rank(p, o);
     }
   }
@@ -384,7 +394,7 @@ struct LBand {
   c2<T>* local;
   int cwl;
   int lo;
-  __device__ __forceinline__ c2<T>* addr(int d, int c) const { return local + ((size_t)d << cwl) + (c - lo); }
+  __device__ __forceinline__ c2<T>* addr(int d, int c) const { return local + (size_t)d * band_stride(cwl) + (c - lo); }
   __device__ __forceinline__ c2<T> get(int r, int c) const {
     return r >= c ? *addr(r - c, c) : conjg<T>(*addr(c - r, r));
   }
@@ -513,7 +523,7 @@ k_ts_chase_flow(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
   const C* gband = Bd + (size_t)b * ND * nm;
   for (int idx = threadIdx.x; idx < ND * cw; idx += blockDim.x) {
     const int d = idx >> cwl, c = lo + (idx & (cw - 1));
-    local[idx] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
+    local[(size_t)d * band_stride(cwl) + (idx & (cw - 1))] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
   }
   for (int idx = threadIdx.x; idx < NSL; idx += blockDim.x) prog[idx] = 0;
   if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
@@ -740,7 +750,7 @@ k_ts_chase_pair(Batch bt, const c2<T>* __restrict__ Bd, T* __restrict__ d_out, T
   const C* gband = Bd + (size_t)b * ND * nm;
   for (int idx = threadIdx.x; idx < ND * cw; idx += blockDim.x) {
     const int d = idx >> cwl, c = lo + (idx & (cw - 1));
-    local[idx] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
+    local[(size_t)d * band_stride(cwl) + (idx & (cw - 1))] = c < nm ? gband[(size_t)d * nm + c] : mk<T>(T(0), T(0));
   }
   for (int idx = threadIdx.x; idx < NSL; idx += blockDim.x) prog[idx] = 0;
   cg::this_cluster().sync();
@@ -857,7 +867,7 @@ int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p, 
     w = std::min(Chase<T>::WARPS, std::max(2, std::min(active, (1 << cwl) / (2 * BW) + 2)));
     const size_t hb = (sizeof(DScratch<T>) * w + sizeof(Mailbox<T>) * NMB + sizeof(int) * (size_t)chase_ring(1 << cwl) +
                        255) & ~size_t(255);
-    need = hb + sizeof(C) * (size_t)ND * ((size_t)1 << cwl) + 64;
+    need = hb + sizeof(C) * (size_t)ND * band_stride(cwl) + 64;
     return need <= 200 * 1024;
   };
   auto covered = [&](int w, int cwl) { return w >= std::min(active, (1 << cwl) / (2 * BW) + 2); };
@@ -883,7 +893,7 @@ int chase_plan_t(int nm, int64_t batch, int sms, int max_cluster, ChasePlan& p, 
     if (pairs >= cw / (2 * BW) && pairs >= 1) {
       const size_t hb = (sizeof(DScratch<T>) * 2 * pairs + sizeof(Mailbox<T>) * NMB +
                          sizeof(int) * ((size_t)chase_ring(cw) + 16) + 255) & ~size_t(255);
-      const size_t need = hb + sizeof(C) * (size_t)ND * cw + 64;
+      const size_t need = hb + sizeof(C) * (size_t)ND * band_stride(p.ccwl) + 64;
       if (need <= 200 * 1024) {
         p.pair = 1;
         p.cwarps = 2 * pairs;

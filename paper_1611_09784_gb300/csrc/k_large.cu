@@ -785,7 +785,7 @@ int solve_large_t(const SolveArgs& a) {
     const int rows = (nm - BW + q - 1) / q;
     const size_t smem = 2 * sizeof(C) * (size_t)rows * BW;
     if (smem > 200 * 1024) continue;
-    if (pc == 0 || (batch * q <= sms && rows >= 64)) {
+    if (pc == 0 || (a.panel_cluster > 0 ? q <= a.panel_cluster : (batch * q <= sms && rows >= 64))) {
       pc = q;
       pc_rows = rows;
     } else {
