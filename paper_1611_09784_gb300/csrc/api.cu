@@ -729,7 +729,7 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->lprep[l], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->small_done, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&m->small_ctr, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&m->small_ctr, 3 * sizeof(unsigned long long));
   for (int l = 0; l < d->n_levels && e == cudaSuccess; ++l)
     e = cudaEventCreateWithFlags(&m->ljoin[l], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking);

@@ -216,7 +216,7 @@ constexpr int kPersistMaxN = 160;
 // launch of at most `ctas` CTAs (0: one per SM of the device): matrices with
 // n_max > 32 are CTA work items, handed out largest first; the n_max <= 32
 // ones are warp work items taken one at a time by any warp that is free.
-// counters: device [2] uint64 scratch, zeroed here on the stream.
+// counters: device [3] uint64 scratch, zeroed here on the stream.
 int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double eps, unsigned long long* counters,
                            int ctas, cudaStream_t s);
 int solve_large(int precision, const SolveArgs& a);

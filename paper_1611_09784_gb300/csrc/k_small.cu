@@ -426,6 +426,192 @@ __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane
   }
 }
 
+// Register-resident variant for float32 and 32 < n <= 128, one 256-thread
+// CTA per matrix: thread t holds rows [64 h, 64 h + 64) of column c = t & 127
+// (h = t >> 7) in registers.  Same method and step order as the other
+// variants.  Per step: the thread holding row j of column c brings A[j][c] up
+// to date and publishes x_c = conj(A[j][c]) (zero outside (j, n)); after one
+// barrier every thread has sigma, tau and its column's v_c; the pass then
+// applies the pending update to its rows and accumulates its half of
+// p = A22 v, using x itself as v (v and x differ only in row j + 1 by
+// ph sigma, added as one correction term); a second barrier combines the
+// halves and the K reduction.  Packed float32 FMAs as in the warp variant.
+constexpr int kCR = 128, kCRT = 256;
+struct CtaRegSlot {
+  float4 xq[kCR];       // (x.x, x.x, x.y, x.y) of this step (0 outside (j, n))
+  float4 pv[kCR];       // pending (v'.x, v'.y, v'.y, -v'.x)
+  float4 pw[kCR];       // pending (w'.x, w'.y, w'.y, -w'.x)
+  float4 pp[2][kCR];    // p partials of the two row halves (P1, P2)
+  float red_rest[kCRT / 32];
+  float red_kp[kCRT / 32];
+};
+
+__device__ __forceinline__ float block_part_sum(float v, float* red) {
+  // warp sums into red[warp]; the caller synchronises and adds the 8 values
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  return v;
+}
+
+__device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int* __restrict__ n_act_cell,
+                                                      const int* __restrict__ act, const int* __restrict__ inv, int N,
+                                                      int K, int n_max, int64_t mat, double t_hop, double eps,
+                                                      const double2* __restrict__ Hin, float* __restrict__ d_out,
+                                                      float* __restrict__ e2_out) {
+  const int K2 = K * K;
+  const int64_t cell = mat / K2;
+  const int kidx = (int)(mat - cell * K2);
+  const int n = Hin ? n_max : n_act_cell[cell];
+  float* dO = d_out + mat * n_max;
+  float* eO = e2_out + mat * n_max;
+  if (n <= 0) return;   // uniform over the CTA
+  const int t = threadIdx.x, c = t & (kCR - 1), hh = t >> 7, r0 = 64 * hh;
+  float2 a[64];
+  if (Hin) {
+    const double2* src = Hin + mat * (int64_t)n * n;
+#pragma unroll
+    for (int r = 0; r < 64; ++r) {
+      a[r] = f2(0.f, 0.f);
+      if (r0 + r < n && c < n) a[r] = f2((float)src[(size_t)(r0 + r) * n + c].x, (float)src[(size_t)(r0 + r) * n + c].y);
+    }
+  } else {
+    int col[3] = {-1, -1, -1};
+    float2 hv[3] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
+    if (c < n) {
+      const int n_sites = 2 * N * N;
+      int nb[3];
+      bool fromB;
+      graphene_neighbours(N, act[cell * n_sites + c], nb, fromB);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float2 ph = graphene_phase_f(N, K, kidx, b);
+        const float hx = (float)t_hop * ph.x, hy = (float)t_hop * ph.y;
+        col[b] = inv[cell * n_sites + nb[b]] - r0;   // row within this half
+        hv[b] = fromB ? f2(hx, hy) : f2(hx, -hy);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 64; ++r) {
+      float2 s2 = f2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        if (col[b] == r) {
+          s2.x += hv[b].x;
+          s2.y += hv[b].y;
+        }
+      if (r0 + r == c && c < n) s2.x += (float)eps;
+      a[r] = s2;
+    }
+  }
+  float2 nwx = f2(0.f, 0.f), nwy = nwx, nvx = nwx, nvy = nwx;
+  bool pend = false;
+  float2 rowj = a[0];   // A[j][c] on the thread holding row j (row 0: half 0)
+  for (int j = 0; j < n - 1; ++j) {
+    const bool own = (j >> 6) == hh;   // this thread holds row j of its column
+    float rest_part = 0.f;
+    if (own) {
+      if (pend) rowj = pend_update(rowj, sl->pv[j], sl->pw[j], nwx, nwy, nvx, nvy);
+      const bool in = c > j && c < n;
+      const float2 x = in ? f2(rowj.x, -rowj.y) : f2(0.f, 0.f);
+      sl->xq[c] = make_float4(x.x, x.x, x.y, x.y);
+      if (c > j + 1) rest_part = x.x * x.x + x.y * x.y;
+      if (c == j) dO[j] = rowj.x;
+    }
+    block_part_sum(rest_part, sl->red_rest);
+    __syncthreads();   // x, the rest partials
+    float rest = 0.f;
+#pragma unroll
+    for (int w2 = 0; w2 < kCRT / 32; ++w2) rest += sl->red_rest[w2];
+    const float4 xa = sl->xq[j + 1];
+    const float2 alpha = f2(xa.x, xa.z);
+    const float sigma2 = alpha.x * alpha.x + alpha.y * alpha.y + rest;
+    if (t == 0) eO[j] = sigma2;
+    const bool tr = rest > 1e-30f;
+    float tau = 0.f, sigma = 0.f;
+    float2 phs = f2(1.f, 0.f), v = f2(0.f, 0.f);
+    if (tr) {
+      float aa;
+      reflector_scalars<float>(alpha, sigma2, sigma, aa, phs, tau);
+      const float4 xc = sl->xq[c];
+      v = f2(xc.x, xc.z);
+      if (c == j + 1) v = f2(alpha.x + phs.x * sigma, alpha.y + phs.y * sigma);
+    }
+    // pass over this half's 4-row chunks that meet (j, n)
+    float2 p1 = f2(0.f, 0.f), p2 = p1, rown = p1;
+#pragma unroll
+    for (int rb = 0; rb < 16; ++rb) {
+      if (r0 + 4 * rb + 3 > j && r0 + 4 * rb < n) {   // warp-uniform (the half is per warp)
+        const bool has_next = ((j + 1 - r0) >> 2) == rb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = 4 * rb + q, R = r0 + r;
+          float2 ar = a[r];
+          if (pend) ar = pend_update(ar, sl->pv[R], sl->pw[R], nwx, nwy, nvx, nvy);
+          a[r] = ar;
+          if (tr) {
+            const float4 xr = sl->xq[R];
+            p1 = fma2(ar, f2(xr.x, xr.y), p1);
+            p2 = fma2(ar, f2(xr.z, xr.w), p2);
+          }
+          if (has_next && R == j + 1) rown = ar;
+        }
+      }
+    }
+    float kp_part = 0.f;
+    if (tr) {
+      if (((j + 1) >> 6) == hh) {
+        // row j + 1: v - x = ph sigma there
+        const float2 dv = f2(phs.x * sigma, phs.y * sigma);
+        p1 = fma2(rown, f2(dv.x, dv.x), p1);
+        p2 = fma2(rown, f2(dv.y, dv.y), p2);
+      }
+      sl->pp[hh][c] = make_float4(p1.x, p1.y, p2.x, p2.y);
+      // Re(conj(v) p) of this half (linear in p): (P1.x + P2.y, P2.x - P1.y)
+      if (c > j && c < n) kp_part = v.x * (p1.x + p2.y) + v.y * (p2.x - p1.y);
+    }
+    block_part_sum(kp_part, sl->red_kp);
+    __syncthreads();   // p halves, the K partials; every pass is done
+    float2 w = f2(0.f, 0.f);
+    if (tr) {
+      float kp = 0.f;
+#pragma unroll
+      for (int w2 = 0; w2 < kCRT / 32; ++w2) kp += sl->red_kp[w2];
+      const float Kc = 0.5f * tau * tau * kp;
+      const float4 q0 = sl->pp[0][c], q1 = sl->pp[1][c];
+      const float px = tau * ((q0.x + q1.x) + (q0.w + q1.w)), py = tau * ((q0.z + q1.z) - (q0.y + q1.y));
+      if (c > j && c < n) w = f2(px - Kc * v.x, py - Kc * v.y);
+    }
+    if (hh == 0) {
+      sl->pv[c] = make_float4(v.x, v.y, v.y, -v.x);
+      sl->pw[c] = make_float4(w.x, w.y, w.y, -w.x);
+    }
+    nwx = f2(-w.x, -w.x);
+    nwy = f2(-w.y, -w.y);
+    nvx = f2(-v.x, -v.x);
+    nvy = f2(-v.y, -v.y);
+    pend = tr;
+    if (((j + 1) >> 6) == hh) rowj = rown;
+    // the next step reads pv / pw after its first barrier
+  }
+  __syncthreads();
+  if (c == n - 1 && ((n - 1) >> 6) == hh) {
+    float2 dl = rowj;
+    if (pend) dl = pend_update(dl, sl->pv[n - 1], sl->pw[n - 1], nwx, nwy, nvx, nvy);
+    dO[n - 1] = dl.x;
+  }
+}
+
+__global__ void __launch_bounds__(kCRT, 1)
+k_small_tridiag_ctareg(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv,
+                       int N, int K, int n_max, int64_t n_mat, double t_hop, double eps,
+                       const double2* __restrict__ Hin, float* __restrict__ d_out, float* __restrict__ e2_out) {
+  __shared__ CtaRegSlot slot;
+  const int64_t mat = blockIdx.x;
+  if (mat >= n_mat) return;
+  small_tridiag_cta_reg(&slot, n_act_cell, act, inv, N, K, n_max, mat, t_hop, eps, Hin, d_out, e2_out);
+}
+
 constexpr int kRegWarps = 4;   // warps (matrices) per CTA of k_small_tridiag_reg
 
 __global__ void __launch_bounds__(32 * kRegWarps)
@@ -688,9 +874,11 @@ constexpr int kPNC = kPersistMaxN, kPRG = 4, kPThreads = kPNC * kPRG, kPWarps = 
 struct PersistWork {
   SmallSeg seg[kMaxSmallSegs];
   int64_t end[kMaxSmallSegs];   // cumulative matrix counts, per phase
-  int n_cta;                    // segments [0, n_cta): CTA items; [n_cta, n_seg): warp items
+  int n_big;                    // segments [0, n_big): n_max > 128, CTA items of the 640-thread kernel
+  int n_cta;                    // segments [n_big, n_cta): 32 < n_max <= 128, register CTA items;
+                                // [n_cta, n_seg): warp items
   int n_seg;
-  int64_t total_cta, total_warp;
+  int64_t total_big, total_cta, total_warp;
 };
 
 __global__ void __launch_bounds__(kPThreads, 1)
@@ -702,14 +890,35 @@ k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long 
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[0], 1ull);
     __syncthreads();
     const long long it = s_item;
-    if (it >= w.total_cta) break;   // uniform over the CTA
+    if (it >= w.total_big) break;   // uniform over the CTA
     int g = 0;
-    while (g + 1 < w.n_cta && it >= w.end[g]) ++g;
+    while (g + 1 < w.n_big && it >= w.end[g]) ++g;
     const SmallSeg& sg = w.seg[g];
     const int64_t mat = it - (g > 0 ? w.end[g - 1] : 0);
     small_tridiag_rg_cta<float, kPNC, kPRG>(smem_raw, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat,
                                             t_hop, eps, nullptr, sg.d, sg.e2);
     __syncthreads();   // s_item and the shared region are reused
+  }
+}
+
+// The 32 < n <= 128 matrices, one per 256-thread CTA item (register-resident
+// reduction), taken in descending n by whichever CTA is free.
+__global__ void __launch_bounds__(kCRT, 1)
+k_small_persistent_cr(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
+  __shared__ CtaRegSlot slot;
+  __shared__ long long s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[2], 1ull);
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= w.total_cta) break;   // uniform over the CTA
+    int g = w.n_big;
+    while (g + 1 < w.n_cta && it >= w.end[g]) ++g;
+    const SmallSeg& sg = w.seg[g];
+    const int64_t mat = it - (g > w.n_big ? w.end[g - 1] : 0);
+    small_tridiag_cta_reg(&slot, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps, nullptr,
+                          sg.d, sg.e2);
+    __syncthreads();   // s_item and the slot are reused
   }
 }
 
@@ -766,11 +975,16 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
       return IDOS_ERR_INVALID_ARG;
     }
     w.seg[q] = sg;
-    if (sg.n_max > 32) {
+    if (sg.n_max > kCR) {
+      w.total_big += sg.n_mat;
+      w.end[q] = w.total_big;
+      w.n_big = q + 1;
+      w.n_cta = q + 1;
+      smem = std::max(smem, RgLayout<float>::bytes(sg.n_max, kPNC));
+    } else if (sg.n_max > 32) {
       w.total_cta += sg.n_mat;
       w.end[q] = w.total_cta;
       w.n_cta = q + 1;
-      smem = std::max(smem, RgLayout<float>::bytes(sg.n_max, kPNC));
     } else {
       w.total_warp += sg.n_mat;
       w.end[q] = w.total_warp;
@@ -786,9 +1000,15 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
   IDOS_CUDA_TRY(cudaGetDevice(&dev));
   IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int sm_grid = ctas > 0 ? std::min(ctas, sms) : sms;
-  IDOS_CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s));
+  IDOS_CUDA_TRY(cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), s));
   if (w.total_cta > 0) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_grid, w.total_cta));
+    ProfScope ps(KID_SMALL_TRIDIAG, s);
+    k_small_persistent_cr<<<grid, kCRT, 0, s>>>(w, t, eps, counters);
+    IDOS_CHECK_LAUNCH();
+  }
+  if (w.total_big > 0) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_grid, w.total_big));
     IDOS_CUDA_TRY(cudaFuncSetAttribute(k_small_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(KID_SMALL_TRIDIAG, s);
     k_small_persistent<<<grid, kPThreads, smem, s>>>(w, t, eps, counters);
@@ -827,10 +1047,21 @@ int run_small_reg(const SolveArgs& a) {
   return IDOS_OK;
 }
 
+int run_small_ctareg(const SolveArgs& a) {
+  const CellSet* c = a.cells;
+  ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
+  k_small_tridiag_ctareg<<<(unsigned)a.n_mat, kCRT, 0, a.stream>>>(
+      c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside, a.n_max, a.n_mat,
+      a.t, a.eps, a.H, reinterpret_cast<float*>(a.d), reinterpret_cast<float*>(a.e2));
+  IDOS_CHECK_LAUNCH();
+  return IDOS_OK;
+}
+
 template <typename T>
 static int solve_small_t(const SolveArgs& a) {
   if constexpr (sizeof(T) == 4) {
     if (a.n_max <= 32) return run_small_reg(a);
+    if (a.n_max <= kCR) return run_small_ctareg(a);
   }
   if (a.n_max <= 32) {
     // up to 4 matrices per CTA while they fit
