@@ -123,11 +123,11 @@ bool use_small_path(const Model* M, int n) {
 // Eigenvalues of the reduced (d, e^2) of every matrix of `cells` and the IDoS
 // of every cell: Q[count][n_E].
 int eigs_and_idos(Model* M, const CellSet& cells, int Kside, const void* d, const void* e2, double* eigs, double* Q,
-                  cudaStream_t st) {
+                  cudaStream_t st, int* err) {
   const int n_max = cells.n_sites;
   const int K2 = Kside * Kside;
   const int64_t n_mat = cells.count * (int64_t)K2;
-  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st));
+  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st, err));
   if (M->d.overlap_s != 0.0)
     IDOS_TRY(launch_overlap_map(eigs, cells.n_act, K2, n_max, n_mat, M->d.eps_onsite, M->d.overlap_s / M->d.t, st));
   const double area = (double)cells.N * cells.N * cell_area(M->d.a);
@@ -172,7 +172,7 @@ int solve_and_idos(Model* M, const CellSet& cells, int Kside, double* Q, double*
   a.panel_cluster = M->panel_cluster;
   if (use_small_path(M, n_max)) IDOS_TRY(solve_small(M->d.precision, a));
   else IDOS_TRY(solve_large(M->d.precision, a));
-  IDOS_TRY(eigs_and_idos(M, cells, Kside, d, e2, eigs, Q, st));
+  IDOS_TRY(eigs_and_idos(M, cells, Kside, d, e2, eigs, Q, st, err));
   if (eigs_keep) *eigs_keep = eigs;
   return IDOS_OK;
 }
@@ -231,14 +231,24 @@ size_t large_room(const Model* M, int N, int Kside, int64_t count) {
 }
 
 // Reads a device status word once the work that may set it has completed.
-int check_status_word(const int* err) {
-  int h = 0;
-  IDOS_CUDA_TRY(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+// Status word bits: 1 = a bounded device-side wait gave up (band chase or
+// tensor-core pipeline); 2 = a reduced matrix had a non-finite entry.
+int status_from_word(int h) {
+  if (h & 2) {
+    set_error("a reduced matrix has a non-finite entry (the Householder reduction broke down)");
+    return IDOS_ERR_NOT_CONVERGED;
+  }
   if (h) {
-    set_error("band chase: a dependency wait timed out");
+    set_error("a bounded device-side wait timed out (band chase or tensor-core pipeline)");
     return IDOS_ERR_TIMEOUT;
   }
   return IDOS_OK;
+}
+
+int check_status_word(const int* err) {
+  int h = 0;
+  IDOS_CUDA_TRY(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost));
+  return status_from_word(h);
 }
 
 // Samples of one level on stream st with workspace ws.  blocking: wait for
@@ -503,8 +513,8 @@ int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, 
     ws.used = p.mark;
     if (p.fine_small || p.crs_small) {
       if (l != lp) IDOS_CUDA_TRY(cudaStreamWaitEvent(st, m->small_done, 0));
-      if (p.crs_small) IDOS_TRY(eigs_and_idos(m, p.crs, Kc, p.cseg.d, p.cseg.e2, p.ceig, p.Qc, st));
-      if (p.fine_small) IDOS_TRY(eigs_and_idos(m, p.fine, Kf, p.fseg.d, p.fseg.e2, p.feig, p.Qf, st));
+      if (p.crs_small) IDOS_TRY(eigs_and_idos(m, p.crs, Kc, p.cseg.d, p.cseg.e2, p.ceig, p.Qc, st, m->err + l));
+      if (p.fine_small) IDOS_TRY(eigs_and_idos(m, p.fine, Kf, p.fseg.d, p.fseg.e2, p.feig, p.Qf, st, m->err + l));
     }
     IDOS_TRY(launch_level_stats(p.Qf, p.Qc, p.S, n_E, p.Y, m->acc + (size_t)l * kAccRows * n_E, ws, st));
     IDOS_CUDA_TRY(record_timing(m->lev1[l], st));
@@ -610,6 +620,7 @@ int level_run_async(Model* M, int level, int64_t n_samples, uint64_t seed, int64
 }
 size_t level_footprint(const Model* M, int level, int64_t n_samples) { return level_workspace(M, level, n_samples); }
 int read_status_word(const int* err) { return check_status_word(err); }
+int status_of_word(int h) { return status_from_word(h); }
 
 }  // namespace idos
 
@@ -1220,8 +1231,13 @@ int solve_explicit(int precision, int refine64_iters, int tc_products, int n, in
   void* d = ws.take<char>(ts * batch * n);
   void* e2 = ws.take<char>(ts * batch * n);
   double* eigs = ws.take<double>((size_t)batch * n);
+  int* errw = ws.take<int>(1);
   int rc = IDOS_OK;
-  if (!Hd || !d || !e2 || !eigs) { set_error("workspace"); rc = IDOS_ERR_OUT_OF_MEMORY; }
+  if (!Hd || !d || !e2 || !eigs || !errw) { set_error("workspace"); rc = IDOS_ERR_OUT_OF_MEMORY; }
+  if (rc == IDOS_OK) {
+    cudaError_t e = cudaMemsetAsync(errw, 0, sizeof(int), s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = IDOS_ERR_CUDA; }
+  }
   if (rc == IDOS_OK) {
     cudaError_t e = cudaMemcpyAsync(Hd, H, sizeof(double2) * nn * batch, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = IDOS_ERR_CUDA; }
@@ -1239,7 +1255,14 @@ int solve_explicit(int precision, int refine64_iters, int tc_products, int n, in
     a.tc_np = tc_products;
     rc = small ? solve_small(precision, a) : solve_large(precision, a);
   }
-  if (rc == IDOS_OK && eigs_out) rc = launch_bisect(precision, refine64_iters, d, e2, nullptr, 1, n, batch, eigs, s);
+  if (rc == IDOS_OK && eigs_out) rc = launch_bisect(precision, refine64_iters, d, e2, nullptr, 1, n, batch, eigs, s, errw);
+  if (rc == IDOS_OK && eigs_out) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, errw, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = IDOS_ERR_CUDA; }
+    else rc = status_from_word(h);
+  }
   if (rc == IDOS_OK) {
     cudaError_t e = cudaSuccess;
     if (eigs_out) e = cudaMemcpyAsync(eigs_out, eigs, sizeof(double) * batch * n, cudaMemcpyDeviceToHost, s);

@@ -80,7 +80,8 @@ __device__ __forceinline__ T cabs_phase(c2<T> a, c2<T>& ph) {
 }
 // float32: one correctly rounded reciprocal and one hardware reciprocal
 // square root (|ph| = 1 to a few float32 ulp), short on the latency path of
-// the band chase's reflectors.
+// the band chase's reflectors.  A subnormal s is first scaled by 2^64 (exact):
+// its reciprocal would overflow to infinity and the phase become inf * 0.
 template <>
 __device__ __forceinline__ float cabs_phase<float>(float2 a, float2& ph) {
   const float s = fmaxf(fabsf(a.x), fabsf(a.y));
@@ -88,8 +89,9 @@ __device__ __forceinline__ float cabs_phase<float>(float2 a, float2& ph) {
     ph = make_float2(1.f, 0.f);
     return 0.f;
   }
-  const float rs = __frcp_rn(s);
-  const float ax = a.x * rs, ay = a.y * rs;
+  const float up = s < 0x1p-64f ? 0x1p64f : 1.f;
+  const float rs = __frcp_rn(s * up);
+  const float ax = a.x * up * rs, ay = a.y * up * rs;
   const float q = ax * ax + ay * ay;   // in [1, 2]
   const float rq = rsqrtf(q);
   ph = make_float2(ax * rq, ay * rq);

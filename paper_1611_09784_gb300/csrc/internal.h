@@ -224,9 +224,11 @@ int solve_large(int precision, const SolveArgs& a);
 size_t large_path_bytes(int precision, int n_max, int64_t n_mat);
 
 // Sturm-count bisection: eigs[mat][n_max] ascending, NaN beyond n_act.
+// err (nullable, device): status word; bit 2 is set when a matrix's (d, e^2)
+// holds a non-finite entry (the reduction broke down).
 int launch_bisect(int precision, int refine64_iters, const void* d, const void* e2,
                   const int* n_act_cell, int K2, int n_max, int64_t n_mat, double* eigs,
-                  cudaStream_t s);
+                  cudaStream_t s, int* err = nullptr);
 
 // Overlap s != 0 (graphene): eigenvalues l of t B -> generalized eigenvalues
 // (eps + l) / (1 + sigma l), sigma = s / t, kept ascending.
@@ -261,6 +263,8 @@ int level_run_async(Model* M, int level, int64_t n_samples, uint64_t seed, int64
 size_t level_footprint(const Model* M, int level, int64_t n_samples);
 // Reads a status word after the work that sets it completed.
 int read_status_word(const int* err);
+// The idos_status of a status word already on the host (0 = IDOS_OK).
+int status_of_word(int h);
 
 }  // namespace idos
 

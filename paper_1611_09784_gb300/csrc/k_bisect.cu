@@ -218,7 +218,7 @@ __host__ __device__ __forceinline__ size_t bisect_pair_offset(int n_max, int mpb
 template <typename S, int G, int MPB>
 __global__ void __launch_bounds__(G* MPB)
 k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __restrict__ n_act_cell,
-         int K2, int n_max, int64_t n_mat, int chunk, int refine, double* __restrict__ eigs) {
+         int K2, int n_max, int64_t n_mat, int chunk, int refine, double* __restrict__ eigs, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int gid = threadIdx.x / G, tid = threadIdx.x % G;
   const int n_chunks = (n_max + chunk - 1) / chunk;
@@ -249,6 +249,9 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   for (int i = tid; i < n; i += G) {
     const S di = d_in[mat * n_max + i];
     const S ei = (i < n - 1) ? e2_in[mat * n_max + i] : S(0);
+    // a non-finite entry means the reduction broke down: report it (status
+    // bit 2) rather than return eigenvalues of a corrupted matrix
+    if (err && !(isfinite(di) && isfinite(ei))) atomicOr(err, 2);
     if constexpr (sizeof(S) == 4) {
       float* def = reinterpret_cast<float*>(de);
       def[2 * i] = di;
@@ -339,7 +342,7 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
 
 template <typename S, int G, int MPB>
 int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int n_max, int64_t n_mat,
-               int refine, double* eigs, cudaStream_t s, int chunk) {
+               int refine, double* eigs, cudaStream_t s, int chunk, int* err) {
   const size_t smem = sizeof(S) == 4 ? bisect_pair_offset(n_max, MPB) + sizeof(double) * 2 * (size_t)n_max * MPB
                                      : sizeof(S) * 2 * (size_t)n_max * MPB;
   auto kern = k_bisect<S, G, MPB>;
@@ -348,19 +351,19 @@ int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int
   const int64_t blocks = (groups + MPB - 1) / MPB;
   ProfScope ps(KID_BISECT, s);
   kern<<<(unsigned)blocks, G * MPB, smem, s>>>(reinterpret_cast<const S*>(d), reinterpret_cast<const S*>(e2),
-                                               n_act_cell, K2, n_max, n_mat, chunk, refine, eigs);
+                                               n_act_cell, K2, n_max, n_mat, chunk, refine, eigs, err);
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
 }
 
 template <typename S>
 int bisect_t(int refine, const void* d, const void* e2, const int* n_act_cell, int K2, int n_max,
-             int64_t n_mat, double* eigs, cudaStream_t s) {
-  if (n_max <= 32) return run_bisect<S, 32, 8>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max);
-  if (n_max <= 64) return run_bisect<S, 64, 4>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max);
-  if (n_max <= 128) return run_bisect<S, 128, 2>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max);
+             int64_t n_mat, double* eigs, cudaStream_t s, int* err) {
+  if (n_max <= 32) return run_bisect<S, 32, 8>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err);
+  if (n_max <= 64) return run_bisect<S, 64, 4>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err);
+  if (n_max <= 128) return run_bisect<S, 128, 2>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err);
   // larger matrices: 128 eigenvalue indices per CTA, so one matrix spreads over n/128 SMs
-  return run_bisect<S, 128, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, 128);
+  return run_bisect<S, 128, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, 128, err);
 }
 
 }  // namespace
@@ -401,11 +404,11 @@ int launch_overlap_map(double* eigs, const int* n_act_cell, int K2, int n_max, i
 
 int launch_bisect(int precision, int refine64_iters, const void* d, const void* e2,
                   const int* n_act_cell, int K2, int n_max, int64_t n_mat, double* eigs,
-                  cudaStream_t s) {
+                  cudaStream_t s, int* err) {
   if (n_mat == 0) return IDOS_OK;
   if (precision == IDOS_FP64)
-    return bisect_t<double>(0, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s);
-  return bisect_t<float>(refine64_iters, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s);
+    return bisect_t<double>(0, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s, err);
+  return bisect_t<float>(refine64_iters, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s, err);
 }
 
 }  // namespace idos

@@ -88,8 +88,8 @@ void harvest(Server* S, Worker& w) {
     r.status = IDOS_ERR_CUDA;
     r.error = cudaGetErrorString(e);
   } else if (herr) {
-    r.status = IDOS_ERR_TIMEOUT;
-    r.error = "a bounded device-side wait gave up";
+    r.status = status_of_word(herr);
+    r.error = get_error();
   }
   r.device_ms = ms;
   r.latency = std::chrono::duration<double>(Clock::now() - r.t_submit).count();

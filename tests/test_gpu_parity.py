@@ -296,10 +296,10 @@ def _tiny_lead(n, seed, pos, value, band=None):
     return H
 
 
-@pytest.mark.parametrize("mag", [2e-22, 3e-23, 1e-20])
+@pytest.mark.parametrize("mag", [2e-22, 3e-23, 1e-20, 1e-40, 3e-45])
 @pytest.mark.parametrize("n,pos,band,tc", [
     (32, [(0, 1)], None, 6),          # warp path: the first reflector's leading entry is conj(A[0][1])
-    (100, [(0, 1)], None, 6),         # CTA row-group path
+    (100, [(0, 1)], None, 6),         # CTA path (register-resident for n <= 128)
     (300, [(16, 0)], None, 6),        # two-stage: the first panel column's leading entry is A[16][0]
     (300, [(16, 0)], None, 0),
     (300, [(1, 0)], 16, 6),           # a band matrix: stage 1 leaves it, the chase's first sweep starts at A[1][0]
@@ -308,12 +308,19 @@ def test_reflector_with_tiny_leading_entry_fp32(mag, n, pos, band, tc):
     """A reflector whose leading entry alpha is tiny but nonzero (rounding
     noise where the exact value is 0, as the bipartite lattice produces):
     |alpha|^2 is subnormal in float32 for |alpha| below ~1e-19, so its phase
-    must not come from sqrt(|alpha|^2).  Eigenvalues against LAPACK."""
-    value = mag * (0.6 + 0.8j)
+    must not come from sqrt(|alpha|^2); below ~1e-38 alpha itself is
+    subnormal and its reciprocal overflows.  Complex and real alpha (real H at
+    the zone centre).  Eigenvalues against LAPACK."""
+    for value in (mag * (0.6 + 0.8j), complex(mag, 0.0)):
+        _check_tiny_lead(n, pos, band, tc, value)
+
+
+def _check_tiny_lead(n, pos, band, tc, value):
     H = np.stack([_tiny_lead(n, 4000 + b, pos, value, band) for b in range(2)])
     ref = np.linalg.eigvalsh(H)
     got = np.sort(pkg.eigvalsh(H, precision="fp32", refine64_iters=1, tc_products=tc), axis=1)
-    assert np.max(np.abs(got - ref)) < EIG_TOL
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref)) < EIG_TOL, value
 
 
 @pytest.mark.parametrize("n,pos,band", [(32, [(0, 1)], None), (100, [(0, 1)], None), (300, [(16, 0)], None),
@@ -340,4 +347,18 @@ def test_level3_sample_with_noise_level_reflector_entry():
     assert np.max(np.abs(Qf[0] - ref["Q_fine"])) < IDOS_TOL
     for r in range(4):
         assert np.max(np.abs(Qc[0, r] - ref["Q_coarse"][r])) < IDOS_TOL, r
+    assert np.max(np.abs(Y[0] - ref["Y"])) < IDOS_TOL
+
+
+def test_zone_centre_sample_with_subnormal_reflector_entry():
+    """Plain Monte Carlo at N = 32 on the 1 x 1 grid (the zone centre: H is
+    real): sample 29 of key BASE_SEED + 99 meets a reflector whose leading
+    entry is subnormal in float32; before the scaled reciprocal its phase was
+    inf * 0 and the whole reduction NaN.  Y against the oracle at the
+    benchmark's settings."""
+    w, cfg, prm = cfg_and_prm(precision="fp32", refine=1)
+    cfg = dict(cfg, levels=[(32, 1)], tc_products=6)
+    with pkg.create_model(cfg) as m:
+        Y, _, _ = m.sample_level_detail(0, 1, w["seed"] + 99, 29)
+    ref = omlmc.level_sample(prm, [(32, 1)], 0, 29, w["seed"] + 99)
     assert np.max(np.abs(Y[0] - ref["Y"])) < IDOS_TOL
