@@ -507,11 +507,15 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
   float2 nwx = f2(0.f, 0.f), nwy = nwx, nvx = nwx, nvy = nwx;
   bool pend = false;
   float2 rowj = a[0];   // A[j][c] on the thread holding row j (row 0: half 0)
+  // row j of the pending pair (v', w'), computed by every thread itself after
+  // the previous step's second barrier (the shared copies of row j are
+  // written after that barrier, so reading them here would race)
+  float4 pvj = make_float4(0.f, 0.f, 0.f, 0.f), pwj = pvj;
   for (int j = 0; j < n - 1; ++j) {
     const bool own = (j >> 6) == hh;   // this thread holds row j of its column
     float rest_part = 0.f;
     if (own) {
-      if (pend) rowj = pend_update(rowj, sl->pv[j], sl->pw[j], nwx, nwy, nvx, nvy);
+      if (pend) rowj = pend_update(rowj, pvj, pwj, nwx, nwy, nvx, nvy);
       const bool in = c > j && c < n;
       const float2 x = in ? f2(rowj.x, -rowj.y) : f2(0.f, 0.f);
       sl->xq[c] = make_float4(x.x, x.x, x.y, x.y);
@@ -573,6 +577,8 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
     block_part_sum(kp_part, sl->red_kp);
     __syncthreads();   // p halves, the K partials; every pass is done
     float2 w = f2(0.f, 0.f);
+    pvj = make_float4(0.f, 0.f, 0.f, 0.f);
+    pwj = pvj;
     if (tr) {
       float kp = 0.f;
 #pragma unroll
@@ -581,6 +587,13 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
       const float4 q0 = sl->pp[0][c], q1 = sl->pp[1][c];
       const float px = tau * ((q0.x + q1.x) + (q0.w + q1.w)), py = tau * ((q0.z + q1.z) - (q0.y + q1.y));
       if (c > j && c < n) w = f2(px - Kc * v.x, py - Kc * v.y);
+      // row j + 1 of (v, w), the next step's pending entries of its row
+      const float2 vn = f2(alpha.x + phs.x * sigma, alpha.y + phs.y * sigma);
+      const float4 r0q = sl->pp[0][j + 1], r1q = sl->pp[1][j + 1];
+      const float nx = tau * ((r0q.x + r1q.x) + (r0q.w + r1q.w)), ny = tau * ((r0q.z + r1q.z) - (r0q.y + r1q.y));
+      const float2 wn = f2(nx - Kc * vn.x, ny - Kc * vn.y);
+      pvj = make_float4(vn.x, vn.y, vn.y, -vn.x);
+      pwj = make_float4(wn.x, wn.y, wn.y, -wn.x);
     }
     if (hh == 0) {
       sl->pv[c] = make_float4(v.x, v.y, v.y, -v.x);
@@ -594,10 +607,9 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
     if (((j + 1) >> 6) == hh) rowj = rown;
     // the next step reads pv / pw after its first barrier
   }
-  __syncthreads();
   if (c == n - 1 && ((n - 1) >> 6) == hh) {
     float2 dl = rowj;
-    if (pend) dl = pend_update(dl, sl->pv[n - 1], sl->pw[n - 1], nwx, nwy, nvx, nvy);
+    if (pend) dl = pend_update(dl, pvj, pwj, nwx, nwy, nvx, nvy);
     dO[n - 1] = dl.x;
   }
 }

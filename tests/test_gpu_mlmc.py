@@ -54,3 +54,36 @@ def test_one_level_estimate_matches_exhaustive_expectation():
     se = np.sqrt(est["var"])
     assert int(est["M"][0]) >= 64
     assert np.all(np.abs(est["mean"] - exact) <= 4.0 * se + IDOS_TOL)
+
+
+def test_bench_levels_estimate_at_tol_matches_oracle():
+    """The benchmark's estimate: graphene levels N = 4, 8, 16, 32 at TOL = 1e-3
+    (pilot 32, three rounds, float32 with one float64 pass, tensor-core
+    update).  (1) The oracle recomputes eq. (2.6) on the very samples the
+    library drew: means agree within the per-sample tolerance times the
+    levels.  (2) An independent oracle plain Monte Carlo estimate at N = 32
+    (eq. (2.2), samples of another key) agrees with it within four combined
+    standard errors (both estimate E[Q_32])."""
+    import oracle_pool
+    w, cfg, prm = cfg_and_prm(precision="fp32", refine=1)
+    cfg = dict(cfg, tc_products=6)
+    seed = 515
+    with pkg.create_model(cfg) as m:
+        est = m.mlmc_estimate(w["tol"], theta=w["theta"], c_alpha=w["c_alpha"], pilot_samples=32, max_rounds=3,
+                              seed=seed)
+    M = [int(x) for x in est["M"]]
+    levels = [tuple(x) for x in w["levels"]]
+    jobs = [(prm, levels, l, s, seed) for l in reversed(range(len(M))) for s in range(M[l])]
+    n_mc = 48
+    jobs += [(prm, [levels[-1]], 0, s, seed + 1) for s in range(n_mc)]
+    with oracle_pool.pool() as p:
+        res = p.map(oracle_pool.level_y, jobs, chunksize=4)
+    per = [[] for _ in M]
+    mc = []
+    for i, (l, s, Y) in enumerate(res):
+        (mc if i >= len(jobs) - n_mc else per[l]).append(Y)
+    mean = sum(np.mean(np.array(y), axis=0) for y in per)
+    assert np.max(np.abs(est["mean"] - mean)) < len(M) * IDOS_TOL
+    mc_mean, mc_var = omlmc.mc_estimate(np.array(mc))
+    z = np.abs(est["mean"] - mc_mean) / np.sqrt(est["var"] + mc_var + 1e-30)
+    assert np.max(z) < 4.0, float(np.max(z))
