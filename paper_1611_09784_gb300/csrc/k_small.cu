@@ -426,9 +426,9 @@ __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane
   }
 }
 
-// Register-resident variant for float32 and 32 < n <= 128, one 256-thread
-// CTA per matrix: thread t holds rows [64 h, 64 h + 64) of column c = t & 127
-// (h = t >> 7) in registers.  Same method and step order as the other
+// Register-resident variant for float32 and 32 < n <= 128, one CTA of
+// 128 x (128 / RPT) threads per matrix: thread t holds rows [RPT h, RPT h +
+// RPT) of column c = t & 127 (h = t >> 7) in registers.  Same method and step order as the other
 // variants.  Per step: the thread holding row j of column c brings A[j][c] up
 // to date and publishes x_c = conj(A[j][c]) (zero outside (j, n)); after one
 // barrier every thread has sigma, tau and its column's v_c; the pass then
@@ -436,14 +436,16 @@ __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane
 // p = A22 v, using x itself as v (v and x differ only in row j + 1 by
 // ph sigma, added as one correction term); a second barrier combines the
 // halves and the K reduction.  Packed float32 FMAs as in the warp variant.
-constexpr int kCR = 128, kCRT = 256;
+constexpr int kCR = 128;
+template <int RPT>
 struct CtaRegSlot {
-  float4 xq[kCR];       // (x.x, x.x, x.y, x.y) of this step (0 outside (j, n))
-  float4 pv[kCR];       // pending (v'.x, v'.y, v'.y, -v'.x)
-  float4 pw[kCR];       // pending (w'.x, w'.y, w'.y, -w'.x)
-  float4 pp[2][kCR];    // p partials of the two row halves (P1, P2)
-  float red_rest[kCRT / 32];
-  float red_kp[kCRT / 32];
+  static constexpr int kParts = kCR / RPT, kThreads = kCR * kParts;
+  float4 xq[kCR];          // (x.x, x.x, x.y, x.y) of this step (0 outside (j, n))
+  float4 pv[kCR];          // pending (v'.x, v'.y, v'.y, -v'.x)
+  float4 pw[kCR];          // pending (w'.x, w'.y, w'.y, -w'.x)
+  float4 pp[kParts][kCR];  // p partials of the row parts (P1, P2)
+  float red_rest[kThreads / 32];
+  float red_kp[kThreads / 32];
 };
 
 __device__ __forceinline__ float block_part_sum(float v, float* red) {
@@ -454,7 +456,8 @@ __device__ __forceinline__ float block_part_sum(float v, float* red) {
   return v;
 }
 
-__device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int* __restrict__ n_act_cell,
+template <int RPT>
+__device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot<RPT>* sl, const int* __restrict__ n_act_cell,
                                                       const int* __restrict__ act, const int* __restrict__ inv, int N,
                                                       int K, int n_max, int64_t mat, double t_hop, double eps,
                                                       const double2* __restrict__ Hin, float* __restrict__ d_out,
@@ -466,12 +469,13 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
   float* dO = d_out + mat * n_max;
   float* eO = e2_out + mat * n_max;
   if (n <= 0) return;   // uniform over the CTA
-  const int t = threadIdx.x, c = t & (kCR - 1), hh = t >> 7, r0 = 64 * hh;
-  float2 a[64];
+  constexpr int kParts = kCR / RPT, kThreads = kCR * kParts;
+  const int t = threadIdx.x, c = t & (kCR - 1), hh = t >> 7, r0 = RPT * hh;
+  float2 a[RPT];
   if (Hin) {
     const double2* src = Hin + mat * (int64_t)n * n;
 #pragma unroll
-    for (int r = 0; r < 64; ++r) {
+    for (int r = 0; r < RPT; ++r) {
       a[r] = f2(0.f, 0.f);
       if (r0 + r < n && c < n) a[r] = f2((float)src[(size_t)(r0 + r) * n + c].x, (float)src[(size_t)(r0 + r) * n + c].y);
     }
@@ -492,7 +496,7 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
       }
     }
 #pragma unroll
-    for (int r = 0; r < 64; ++r) {
+    for (int r = 0; r < RPT; ++r) {
       float2 s2 = f2(0.f, 0.f);
 #pragma unroll
       for (int b = 0; b < 3; ++b)
@@ -506,13 +510,13 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
   }
   float2 nwx = f2(0.f, 0.f), nwy = nwx, nvx = nwx, nvy = nwx;
   bool pend = false;
-  float2 rowj = a[0];   // A[j][c] on the thread holding row j (row 0: half 0)
+  float2 rowj = a[0];   // A[j][c] on the thread holding row j (row 0: part 0)
   // row j of the pending pair (v', w'), computed by every thread itself after
   // the previous step's second barrier (the shared copies of row j are
   // written after that barrier, so reading them here would race)
   float4 pvj = make_float4(0.f, 0.f, 0.f, 0.f), pwj = pvj;
   for (int j = 0; j < n - 1; ++j) {
-    const bool own = (j >> 6) == hh;   // this thread holds row j of its column
+    const bool own = j / RPT == hh;   // this thread holds row j of its column
     float rest_part = 0.f;
     if (own) {
       if (pend) rowj = pend_update(rowj, pvj, pwj, nwx, nwy, nvx, nvy);
@@ -526,7 +530,7 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
     __syncthreads();   // x, the rest partials
     float rest = 0.f;
 #pragma unroll
-    for (int w2 = 0; w2 < kCRT / 32; ++w2) rest += sl->red_rest[w2];
+    for (int w2 = 0; w2 < kThreads / 32; ++w2) rest += sl->red_rest[w2];
     const float4 xa = sl->xq[j + 1];
     const float2 alpha = f2(xa.x, xa.z);
     const float sigma2 = alpha.x * alpha.x + alpha.y * alpha.y + rest;
@@ -544,8 +548,8 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
     // pass over this half's 4-row chunks that meet (j, n)
     float2 p1 = f2(0.f, 0.f), p2 = p1, rown = p1;
 #pragma unroll
-    for (int rb = 0; rb < 16; ++rb) {
-      if (r0 + 4 * rb + 3 > j && r0 + 4 * rb < n) {   // warp-uniform (the half is per warp)
+    for (int rb = 0; rb < RPT / 4; ++rb) {
+      if (r0 + 4 * rb + 3 > j && r0 + 4 * rb < n) {   // warp-uniform (the row part is per warp)
         const bool has_next = ((j + 1 - r0) >> 2) == rb;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -564,7 +568,7 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
     }
     float kp_part = 0.f;
     if (tr) {
-      if (((j + 1) >> 6) == hh) {
+      if ((j + 1) / RPT == hh) {
         // row j + 1: v - x = ph sigma there
         const float2 dv = f2(phs.x * sigma, phs.y * sigma);
         p1 = fma2(rown, f2(dv.x, dv.x), p1);
@@ -582,15 +586,21 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
     if (tr) {
       float kp = 0.f;
 #pragma unroll
-      for (int w2 = 0; w2 < kCRT / 32; ++w2) kp += sl->red_kp[w2];
-      const float Kc = 0.5f * tau * tau * kp;
-      const float4 q0 = sl->pp[0][c], q1 = sl->pp[1][c];
-      const float px = tau * ((q0.x + q1.x) + (q0.w + q1.w)), py = tau * ((q0.z + q1.z) - (q0.y + q1.y));
+      for (int w2 = 0; w2 < kThreads / 32; ++w2) kp += sl->red_kp[w2];
+      // tau (tau kp): tau reaches ~1e30 for a noise-level column, tau^2 would overflow
+      const float Kc = 0.5f * tau * (tau * kp);
+      float4 q = sl->pp[0][c], qn = sl->pp[0][j + 1];
+#pragma unroll
+      for (int h2 = 1; h2 < kParts; ++h2) {
+        const float4 a1 = sl->pp[h2][c], b1 = sl->pp[h2][j + 1];
+        q = make_float4(q.x + a1.x, q.y + a1.y, q.z + a1.z, q.w + a1.w);
+        qn = make_float4(qn.x + b1.x, qn.y + b1.y, qn.z + b1.z, qn.w + b1.w);
+      }
+      const float px = tau * (q.x + q.w), py = tau * (q.z - q.y);
       if (c > j && c < n) w = f2(px - Kc * v.x, py - Kc * v.y);
       // row j + 1 of (v, w), the next step's pending entries of its row
       const float2 vn = f2(alpha.x + phs.x * sigma, alpha.y + phs.y * sigma);
-      const float4 r0q = sl->pp[0][j + 1], r1q = sl->pp[1][j + 1];
-      const float nx = tau * ((r0q.x + r1q.x) + (r0q.w + r1q.w)), ny = tau * ((r0q.z + r1q.z) - (r0q.y + r1q.y));
+      const float nx = tau * (qn.x + qn.w), ny = tau * (qn.z - qn.y);
       const float2 wn = f2(nx - Kc * vn.x, ny - Kc * vn.y);
       pvj = make_float4(vn.x, vn.y, vn.y, -vn.x);
       pwj = make_float4(wn.x, wn.y, wn.y, -wn.x);
@@ -604,26 +614,28 @@ __device__ __forceinline__ void small_tridiag_cta_reg(CtaRegSlot* sl, const int*
     nvx = f2(-v.x, -v.x);
     nvy = f2(-v.y, -v.y);
     pend = tr;
-    if (((j + 1) >> 6) == hh) rowj = rown;
+    if ((j + 1) / RPT == hh) rowj = rown;
     // the next step reads pv / pw after its first barrier
   }
-  if (c == n - 1 && ((n - 1) >> 6) == hh) {
+  if (c == n - 1 && (n - 1) / RPT == hh) {
     float2 dl = rowj;
     if (pend) dl = pend_update(dl, pvj, pwj, nwx, nwy, nvx, nvy);
     dO[n - 1] = dl.x;
   }
 }
 
-__global__ void __launch_bounds__(kCRT, 1)
+template <int RPT>
+__global__ void __launch_bounds__(CtaRegSlot<RPT>::kThreads, 1)
 k_small_tridiag_ctareg(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv,
                        int N, int K, int n_max, int64_t n_mat, double t_hop, double eps,
                        const double2* __restrict__ Hin, float* __restrict__ d_out, float* __restrict__ e2_out) {
-  __shared__ CtaRegSlot slot;
+  __shared__ CtaRegSlot<RPT> slot;
   const int64_t mat = blockIdx.x;
   if (mat >= n_mat) return;
   small_tridiag_cta_reg(&slot, n_act_cell, act, inv, N, K, n_max, mat, t_hop, eps, Hin, d_out, e2_out);
 }
 
+constexpr int kCtaRpt = 32;   // rows per thread of the register CTA reduction (512 threads)
 constexpr int kRegWarps = 4;   // warps (matrices) per CTA of k_small_tridiag_reg
 
 __global__ void __launch_bounds__(32 * kRegWarps)
@@ -915,9 +927,9 @@ k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long 
 
 // The 32 < n <= 128 matrices, one per 256-thread CTA item (register-resident
 // reduction), taken in descending n by whichever CTA is free.
-__global__ void __launch_bounds__(kCRT, 1)
+__global__ void __launch_bounds__(CtaRegSlot<kCtaRpt>::kThreads, 1)
 k_small_persistent_cr(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
-  __shared__ CtaRegSlot slot;
+  __shared__ CtaRegSlot<kCtaRpt> slot;
   __shared__ long long s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[2], 1ull);
@@ -1016,7 +1028,7 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
   if (w.total_cta > 0) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_grid, w.total_cta));
     ProfScope ps(KID_SMALL_TRIDIAG, s);
-    k_small_persistent_cr<<<grid, kCRT, 0, s>>>(w, t, eps, counters);
+    k_small_persistent_cr<<<grid, CtaRegSlot<kCtaRpt>::kThreads, 0, s>>>(w, t, eps, counters);
     IDOS_CHECK_LAUNCH();
   }
   if (w.total_big > 0) {
@@ -1062,7 +1074,7 @@ int run_small_reg(const SolveArgs& a) {
 int run_small_ctareg(const SolveArgs& a) {
   const CellSet* c = a.cells;
   ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
-  k_small_tridiag_ctareg<<<(unsigned)a.n_mat, kCRT, 0, a.stream>>>(
+  k_small_tridiag_ctareg<kCtaRpt><<<(unsigned)a.n_mat, CtaRegSlot<kCtaRpt>::kThreads, 0, a.stream>>>(
       c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside, a.n_max, a.n_mat,
       a.t, a.eps, a.H, reinterpret_cast<float*>(a.d), reinterpret_cast<float*>(a.e2));
   IDOS_CHECK_LAUNCH();

@@ -362,3 +362,21 @@ def test_zone_centre_sample_with_subnormal_reflector_entry():
         Y, _, _ = m.sample_level_detail(0, 1, w["seed"] + 99, 29)
     ref = omlmc.level_sample(prm, [(32, 1)], 0, 29, w["seed"] + 99)
     assert np.max(np.abs(Y[0] - ref["Y"])) < IDOS_TOL
+
+
+def test_sparse_ragged_matrices_with_isolated_sites():
+    """N = 8 cells at p = 0.6 (about 50 kept sites, many isolated, so many
+    columns are already reduced or hold only rounding noise) on the 3 x 3 grid
+    (index 4 is the zone centre: H real), through the float32 path of the
+    n <= 128 register reduction.  A noise-level column gives tau ~ 1e30;
+    forming tau^2 overflowed before.  Eigenvalues against LAPACK, all finite."""
+    ks = olat.kpoints(8, 3, 2.46)
+    Hs, refs = [], []
+    for s in range(24):
+        mask = ophilox.vacancy_mask(BASE_SEED, 1, 3000 + s, 128, 0.6)
+        keep = np.where(mask == 0)[0]
+        for ki in (2, 4):
+            H = oham.hamiltonian(8, ks[ki], mask, -2.7, 0.0, 2.46, 1e3)[np.ix_(keep, keep)]
+            got = np.sort(pkg.eigvalsh(H, precision="fp32", refine64_iters=1)[0])
+            assert np.all(np.isfinite(got)), (s, ki)
+            assert np.max(np.abs(got - np.linalg.eigvalsh(H))) < EIG_TOL, (s, ki)
