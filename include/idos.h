@@ -308,7 +308,14 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
  * call that launched them synchronises, and accumulated per kernel family.
  * The events add a few microseconds per launch. */
 
-/* enable != 0 turns timing on, 0 off.  Does not clear the totals. */
+/* enable = 1 turns timing on: idos_sample_levels then issues every level's
+ * launches in order on one stream, without the SM partition or a graph, so
+ * that each event pair spans its own kernel alone.  enable = 2 (timeline):
+ * the levels keep their streams and partition, calls are captured and
+ * replayed as a graph as without profiling (the graph then holds the event
+ * record nodes), each pair's span includes any time its kernel waited for
+ * SMs, and idos_sample_levels also keeps a trace of its launches
+ * (idos_get_trace).  0 turns timing off.  Does not clear the totals. */
 int idos_set_profiling(idos_model* m, int enable);
 
 /* Number of kernel families (valid kid values are 0 .. count-1). */
@@ -318,8 +325,22 @@ int idos_profile_count(void);
  * may be NULL), *ms summed event time, *launches. */
 int idos_get_profile(const idos_model* m, int kid, const char** name, double* ms, int64_t* launches);
 
-/* Zero the totals. */
+/* Zero the totals (and the trace). */
 int idos_reset_profile(idos_model* m);
+
+/* One timed scope of the last idos_sample_levels call made in timeline mode. */
+typedef struct idos_trace_entry {
+  int32_t kid;        /* kernel family (idos_get_profile's kid)                */
+  int32_t lane;       /* stream, numbered in order of first use within the call */
+  int32_t launches;   /* kernel launches inside the scope (0: aggregating scope) */
+  int32_t reserved;
+  double t0_ms;       /* start and end, ms after the call was issued (the     */
+  double t1_ms;       /* origin stream's event before the levels fork off)    */
+} idos_trace_entry;
+
+/* Copies up to `capacity` entries of that trace (host array, caller-owned)
+ * and sets *count to the trace's length (which may exceed capacity). */
+int idos_get_trace(const idos_model* m, int64_t capacity, idos_trace_entry* out, int64_t* count);
 
 /* ---- parity / diagnostic entry points (same kernels as the hot path) ---- */
 

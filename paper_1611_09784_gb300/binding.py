@@ -71,6 +71,11 @@ class Rates(C.Structure):
                 ("theta_mc", C.c_double)]
 
 
+class TraceEntry(C.Structure):
+    _fields_ = [("kid", C.c_int32), ("lane", C.c_int32), ("launches", C.c_int32), ("reserved", C.c_int32),
+                ("t0_ms", C.c_double), ("t1_ms", C.c_double)]
+
+
 class IdosError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: {status_string(status)} ({status}): {detail}")
@@ -124,6 +129,7 @@ _SYMBOLS = {
     "idos_get_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]),
     "idos_reset_profile": (C.c_int, [C.c_void_p]),
+    "idos_get_trace": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_int64)]),
     "idos_eval_idos_noalloc": (C.c_int, [C.POINTER(ModelDesc), C.c_int, C.c_int, C.c_void_p, C.c_uint64, C.c_int,
                                          C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -328,8 +334,28 @@ class Model:
         return {"mean": mean, "var": var, "M": M, "V": V, "W": W, "seconds": est.seconds,
                 "rounds": est.rounds, "h2d_bytes": est.h2d_bytes, "d2h_bytes": est.d2h_bytes}
 
-    def set_profiling(self, enable: bool = True):
-        _check(load_library().idos_set_profiling(self._h, 1 if enable else 0), "idos_set_profiling")
+    def set_profiling(self, enable=True):
+        """True / 1: per-family totals, levels serialised on one stream;
+        2: timeline (levels on their own streams and partition, trace kept);
+        False / 0: off."""
+        mode = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+        _check(load_library().idos_set_profiling(self._h, mode), "idos_set_profiling")
+
+    def get_trace(self) -> list:
+        """Timed scopes of the last timeline-mode idos_sample_levels call:
+        [{"kernel", "lane", "launches", "t0_ms", "t1_ms"}] in issue order."""
+        lib = load_library()
+        n = C.c_int64()
+        _check(lib.idos_get_trace(self._h, 0, None, C.byref(n)), "idos_get_trace")
+        buf = (TraceEntry * max(1, n.value))()
+        _check(lib.idos_get_trace(self._h, n.value, C.cast(buf, C.c_void_p), C.byref(n)), "idos_get_trace")
+        out = []
+        for e in buf[:n.value]:
+            name = C.c_char_p()
+            _check(lib.idos_get_profile(self._h, e.kid, C.byref(name), None, None), "idos_get_profile")
+            out.append({"kernel": name.value.decode(), "lane": e.lane, "launches": e.launches,
+                        "t0_ms": e.t0_ms, "t1_ms": e.t1_ms})
+        return out
 
     def reset_profile(self):
         _check(load_library().idos_reset_profile(self._h), "idos_reset_profile")

@@ -886,11 +886,17 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
   IDOS_CUDA_TRY(cudaEventRecord(m->fork0, m->stream));
   IDOS_CUDA_TRY(cudaStreamWaitEvent(origin, m->fork0, 0));
   cudaStream_t ser[IDOS_MAX_LEVELS], ser2[IDOS_MAX_LEVELS] = {};
-  if (m->prof.enabled) {
+  if (m->prof.enabled && !m->prof.timeline) {
     for (int l = 0; l < L; ++l) ser[l] = origin;
     streams = ser;
     streams2 = ser2;
     parted = false;
+  }
+  // timeline mode keeps the levels' streams and partition (kernel spans then
+  // include time spent waiting for SMs) and times every launch from here
+  if (m->prof.enabled && m->prof.timeline && m->prof.mark_origin(origin) != 0) {
+    set_error("profiler: cannot record the trace origin event");
+    return IDOS_ERR_CUDA;
   }
   const bool route_p = persistent_route(m, n_samples);
   // per-level streams and SM counts of this call; with the partition and the
@@ -919,17 +925,21 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     return enqueue_levels(m, origin, n_samples, seed, first_sample, streams, streams2, lsm, route_p, m->dyn_dev);
   };
   bool issued = false;
-  if (m->graph && !m->prof.enabled) {
+  // serialised profiling runs directly; a timeline traces the replayed graph
+  // (its event record nodes time each launch as captured)
+  const int prof_mode = m->prof.enabled ? (m->prof.timeline ? 2 : 1) : 0;
+  if (m->graph && prof_mode != 1) {
     // the graph of the last call is replayed while nothing it was captured
     // from has changed: sample counts, route, settings, partition, arenas
     std::vector<int64_t> core(n_samples, n_samples + L);
     for (int64_t v : {(int64_t)parted, (int64_t)route_p, (int64_t)m->small_max_n, (int64_t)m->persistent,
                       (int64_t)m->part_gen, (int64_t)m->w_tile, (int64_t)m->chase_pair, (int64_t)m->panel_cluster,
-                      (int64_t)m->placement})
+                      (int64_t)m->placement, (int64_t)prof_mode})
       core.push_back(v);
     std::vector<int64_t> key = core;
     for (int l = 0; l < L; ++l) key.push_back((int64_t)m->lws[l].gen);
     if (m->gexec && key == m->gkey) {
+      if (prof_mode == 2) m->prof.restore();
       IDOS_CUDA_TRY(cudaGraphLaunch(m->gexec, origin));
       ++m->graph_replays;
       issued = true;
@@ -958,6 +968,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
         m->gexec = ex;
         m->gkey = key;
         ++m->graph_captures;
+        if (prof_mode == 2) m->prof.snapshot();
         IDOS_CUDA_TRY(cudaGraphLaunch(ex, origin));
         ++m->graph_replays;
         issued = true;
@@ -1313,8 +1324,27 @@ int idos_tridiagonalize(int precision, int tc_products, int n, int64_t batch, co
 }
 
 int idos_set_profiling(idos_model* m, int enable) {
-  if (!m) { set_error("null model"); return IDOS_ERR_INVALID_ARG; }
+  if (!m || enable < 0 || enable > 2) { set_error("null model or enable not 0, 1 or 2"); return IDOS_ERR_INVALID_ARG; }
   m->prof.enabled = enable != 0;
+  m->prof.timeline = enable == 2;
+  return IDOS_OK;
+}
+
+int idos_get_trace(const idos_model* m, int64_t capacity, idos_trace_entry* out, int64_t* count) {
+  if (!m || !count || capacity < 0 || (capacity > 0 && !out)) {
+    set_error("null model or count, negative capacity, or null entries with capacity > 0");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  const auto& t = m->prof.trace;
+  *count = (int64_t)t.size();
+  for (int64_t i = 0; i < capacity && i < (int64_t)t.size(); ++i) {
+    out[i].kid = t[i].kid;
+    out[i].lane = t[i].lane;
+    out[i].launches = t[i].launches;
+    out[i].reserved = 0;
+    out[i].t0_ms = t[i].t0;
+    out[i].t1_ms = t[i].t1;
+  }
   return IDOS_OK;
 }
 

@@ -635,7 +635,7 @@ k_small_tridiag_ctareg(const int* __restrict__ n_act_cell, const int* __restrict
   small_tridiag_cta_reg(&slot, n_act_cell, act, inv, N, K, n_max, mat, t_hop, eps, Hin, d_out, e2_out);
 }
 
-constexpr int kCtaRpt = 32;   // rows per thread of the register CTA reduction (512 threads)
+constexpr int kCtaRpt = 64;   // rows per thread of the register CTA reduction (256 threads; 32 rows per thread was slower)
 constexpr int kRegWarps = 4;   // warps (matrices) per CTA of k_small_tridiag_reg
 
 __global__ void __launch_bounds__(32 * kRegWarps)

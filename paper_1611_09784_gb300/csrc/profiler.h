@@ -1,7 +1,10 @@
 // profiler.h - optional per-kernel timing with CUDA events.  When a model has
 // profiling enabled, every launch site brackets its kernel with an event pair
 // on the launching stream; the pairs are resolved after the API call's final
-// synchronisation and accumulated per kernel family.
+// synchronisation and accumulated per kernel family.  In timeline mode the
+// levels keep their own streams and SM partitions, and every pair is also kept
+// as a trace entry (start and end relative to an origin event recorded when the
+// call was issued, and the stream it ran on).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,15 +20,34 @@ enum KernelId {
 
 const char* kernel_name(int kid);
 
+struct TraceEntry {
+  int kid;        // kernel family
+  int lane;       // index of the stream in order of first use within the call
+  int launches;   // kernel launches inside the pair (0: an aggregating scope)
+  float t0, t1;   // ms after the call's origin event
+};
+
 struct Profiler {
   bool enabled = false;
+  bool timeline = false;            // concurrent streams + trace (else one serial stream)
+  cudaEvent_t origin = nullptr;     // recorded when a traced call is issued
+  bool origin_set = false;
   std::vector<cudaEvent_t> pool;
   std::vector<int> pending_kid;     // kid of pair i (events 2i, 2i+1)
   std::vector<int> pending_n;       // kernel launches inside pair i
+  std::vector<cudaStream_t> pending_stream;
+  std::vector<TraceEntry> trace;    // entries of the last traced call
+  // the pairs a captured graph records (its event nodes use the same pool
+  // events), restored before each replay so that the replay can be resolved
+  std::vector<int> graph_kid, graph_n;
+  std::vector<cudaStream_t> graph_stream;
+  void snapshot() { graph_kid = pending_kid; graph_n = pending_n; graph_stream = pending_stream; }
+  void restore() { pending_kid = graph_kid; pending_n = graph_n; pending_stream = graph_stream; }
   double ms[KID_COUNT] = {};
   long long launches[KID_COUNT] = {};   // kernel launches (not scopes)
   int begin(int kid, cudaStream_t s, int n_launch);   // returns the pair index or -1
   void end(int pair, cudaStream_t s);
+  int mark_origin(cudaStream_t s);   // starts a traced call (clears the trace)
   void resolve();                    // call after the stream has been synchronised
   void clear();
   ~Profiler();
