@@ -178,8 +178,9 @@ def n_act_of(masks, N):
 
 # Kernel families of the library's profiler and what bounds each one:
 # "alu" (float32 FMA issue), "alu64" (float64 FMA issue), "tensor" (bf16 MMA),
-# "hbm" (DRAM bytes).
-FAMILIES = {"k_small_tridiag": "alu", "k_ts_panel": "alu", "k_ts_w": "alu", "k_ts_z": "hbm", "k_ts_her2k": "tensor",
+# "hbm" (DRAM bytes).  W runs on the tensor cores with the tensor-core update
+# (w_tile 2), else on the FP32 pipe.
+FAMILIES = {"k_small_tridiag": "alu", "k_ts_panel": "alu", "k_ts_w": "tensor", "k_ts_z": "hbm", "k_ts_her2k": "tensor",
             "k_ts_chase": "alu", "k_bisect": "alu64", "k_idos": "hbm"}
 
 
@@ -233,29 +234,33 @@ def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16
 AGGREGATE_SCOPES = ("k_lg_band (stage 1, all)",)
 
 
-def roofline(prof, work, steps, pk, pk_kind, fma, tc_products=6):
+def roofline(prof, work, steps, pk, pk_kind, fma, tc_products=6, w_tile=2):
     """Roofline objects of the kernel families; the first is the single kernel
     family (not an aggregate scope) with the largest event time.  fma: the
-    FMA peaks measured in this run (TFLOP/s, float32 and float64)."""
+    FMA peaks measured in this run (TFLOP/s, float32 and float64); w_tile: the
+    W kernel the run used (2 = tensor cores, six products whatever
+    tc_products)."""
     singles = sorted(((k, v) for k, v in prof.items() if k not in AGGREGATE_SCOPES), key=lambda kv: -kv[1][0])
     out = []
     for name, (ms, launches) in singles:
         bound = FAMILIES.get(name)
         if bound is None or not launches or not ms:
             continue
-        if bound == "tensor" and not tc_products:
+        if bound == "tensor" and (not tc_products or (name == "k_ts_w" and w_tile != 2)):
             bound = "alu"
         per_launch_s = ms * 1e-3 / launches
         units_per_launch = work[name] * steps / launches
         executed = units_per_launch
         if bound == "tensor":
-            # the trailing update runs on the tensor cores: tc_products bf16 MMA
-            # flops per algorithmic flop, against the measured bf16 GEMM rate
-            # (sustained: the kernels are timed inside a long replay)
-            executed = units_per_launch * tc_products
+            # the trailing update and W run on the tensor cores: split-bf16 MMA
+            # flops per algorithmic flop (tc_products for the update, six for
+            # W), against the measured bf16 GEMM rate (sustained: the kernels
+            # are timed inside a long replay)
+            nprod = 6 if name == "k_ts_w" else tc_products
+            executed = units_per_launch * nprod
             achieved, unit = executed / per_launch_s / 1e12, "TFLOP/s"
             peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
-            src = f"{pk_kind} bf16 GEMM, sustained; achieved counts the {tc_products} split-bf16 products per algorithmic flop"
+            src = f"{pk_kind} bf16 GEMM, sustained; achieved counts the {nprod} split-bf16 products per algorithmic flop"
         elif bound == "hbm":
             achieved, unit = units_per_launch / per_launch_s / 1e9, "GB/s"
             peak = pk.get("hbm_gbs", 6800.0)
@@ -728,7 +733,8 @@ def run_gpu(args):
             work[k2] = work.get(k2, 0.0) + wk[k2] / args.steps
     pk, pk_kind = peaks()
     fma = measure_fma_peaks(pkg, stream.cuda_stream, local)
-    roof, roofs = roofline(prof, work, args.steps, pk, pk_kind, fma, tc_products=TC_PRODUCTS)
+    w_tile = tuning.get("w_tile", 2) if isinstance(tuning, dict) else 2
+    roof, roofs = roofline(prof, work, args.steps, pk, pk_kind, fma, tc_products=TC_PRODUCTS, w_tile=w_tile)
 
     # rates W, S, D, C (Sec. 2.1-2.2, fitted as Sec. 4.4 does) from the timed
     # steps' level accumulators; cost per sample: each level alone on the
@@ -898,12 +904,12 @@ def run_reference(args):
 # ---------------------------------------------------- profiling helpers --
 # ncu kernel names -> the library profiler's kernel families
 NCU_FAMILY = [("k_small_persistent", "k_small_tridiag"), ("k_small_tridiag", "k_small_tridiag"),
-              ("k_ts_panel", "k_ts_panel"), ("k_ts_w", "k_ts_w"), ("k_ts_wm", "k_ts_z"), ("k_ts_zc", "k_ts_z"),
-              ("k_tc_operands", "k_ts_her2k"), ("k_tc_her2k", "k_ts_her2k"), ("k_ts_her2k", "k_ts_her2k"),
+              ("k_ts_panel", "k_ts_panel"), ("k_ts_wm", "k_ts_z"), ("k_ts_zc", "k_ts_z"), ("k_ts_w", "k_ts_w"),
+              ("k_tc_w", "k_ts_w"), ("k_tc_operands", "k_ts_her2k"), ("k_tc_her2k", "k_ts_her2k"), ("k_ts_her2k", "k_ts_her2k"),
               ("k_ts_to_band", "k_ts_chase"), ("k_ts_chase", "k_ts_chase"), ("k_bisect", "k_bisect"),
               ("k_idos", "k_idos"), ("k_level", "k_level_stats"), ("k_fine_masks", "k_masks"),
               ("k_corner_masks", "k_masks"), ("k_cell_maps", "k_masks"), ("k_lg_assemble", "k_lg_assemble")]
-FAMILY_SOURCE = {"k_small_tridiag": "k_small.cu", "k_ts_panel": "k_large.cu", "k_ts_w": "k_large.cu",
+FAMILY_SOURCE = {"k_small_tridiag": "k_small.cu", "k_ts_panel": "k_large.cu", "k_ts_w": "k_tc.cu",
                  "k_ts_z": "k_large.cu", "k_ts_her2k": "k_tc.cu", "k_ts_chase": "k_chase.cu",
                  "k_bisect": "k_bisect.cu", "k_idos": "k_idos.cu"}
 

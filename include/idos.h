@@ -390,6 +390,20 @@ int idos_tridiagonalize(int precision, int tc_products, int n, int64_t batch, co
 int idos_her2k(int tc_products, int n, int64_t batch, const double* A, const double* Y, const double* Z,
                double* A_out);
 
+/* The product W = A22 V of one stage-1 panel (the first factor of the
+ * compact-WY two-sided update, Sec. 4.2's dense eigensolver in two-stage
+ * form): A22 = rows and columns k + 16 .. n-1 of A (m = n - k - 16, k a
+ * multiple of 16 with 0 <= k < n - 16), V = columns 0..m-1 of YT.  mode =
+ * the kernel the large path runs: 2 = tensor cores (six split-bfloat16
+ * products, n even), 1 = FP32 pipe with 128-row register tiles (n even), 0 =
+ * FP32 pipe with 64-row tiles; the partial sums of the kernel's K splits are
+ * added in split order on the host.  A: host complex128 float64[batch * 2 n^2]
+ * row-major; YT: host float64[batch * 2 * 16 n], column c of matrix b at
+ * YT[b][c][0..n); W_out: host float64[batch * 2 * 16 n] in the same layout,
+ * entries m..n-1 of each column zero.  Inputs are rounded to float32.
+ * Allocates and frees its own device buffers; blocking. */
+int idos_stage1_w(int mode, int n, int64_t batch, int k, const double* A, const double* YT, double* W_out);
+
 /* Density of states from an IDoS on the uniform energy grid (host float64
  * Q[n_E], n_E >= 2) by numerical differentiation, as the paper suggests for
  * the expected IDoS: central differences (Q[j+1] - Q[j-1]) / (2h) inside,
@@ -437,7 +451,8 @@ typedef struct idos_tuning {
   int32_t tried_persistent[IDOS_TUNE_MAX];
   int32_t graph;         /* chosen graph setting (idos_model_desc.graph) */
   int32_t tried_graph[IDOS_TUNE_MAX];
-  int32_t w_tile;        /* stage-1 W kernel: 1 = 128-row register tiles, 0 = 64-row tiles */
+  int32_t w_tile;        /* stage-1 W kernel: 2 = tensor cores (with tc_products > 0), 1 = 128-row
+                            register tiles, 0 = 64-row tiles */
   int32_t chase_pair;    /* clustered band chases: 1 = two warps per sweep, 0 = one */
   int32_t tried_w_tile[IDOS_TUNE_MAX];
   int32_t tried_chase_pair[IDOS_TUNE_MAX];

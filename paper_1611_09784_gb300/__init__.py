@@ -9,5 +9,5 @@ library has not been built: there is no CPU fallback.
 from .binding import (  # noqa: F401
     FP32_REFINE64, FP64, GRAPHENE, SMOOTH_GAUSS, SMOOTH_POLY, TMDC, IdosError, Model, Server, combine_level_stats,
     create_model, dos_from_idos, eigvalsh, fit_rates, her2k, lib_path, load_library, measure_fma_peak,
-    status_string, tridiagonalize,
+    stage1_w, status_string, tridiagonalize,
 )

@@ -110,6 +110,7 @@ _SYMBOLS = {
     "idos_tridiagonalize": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
     "idos_her2k": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "idos_stage1_w": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "idos_get_partition": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_char_p)]),
     "idos_get_graph_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_char_p)]),
@@ -512,6 +513,21 @@ def tridiagonalize(H, precision="fp32", stream: int | None = None, tc_products: 
     _check(load_library().idos_tridiagonalize(_PRECISION[precision], tc, n, batch, _ptr(H), _ptr(d), _ptr(e2),
                                               C.c_void_p(stream or 0)), "idos_tridiagonalize")
     return d, e2
+
+
+def stage1_w(A, YT, k: int = 0, mode: int = 2):
+    """W = A22 (Y T) of one stage-1 panel through the large path's W kernel
+    (float32 storage; mode 2 = tensor cores, 1 / 0 = FP32 pipe tiles).
+    A: (batch, n, n) complex; YT: (batch, 16, n) complex; A22 = A[k+16:, k+16:]
+    and V = YT[:, :, :m]; returns (batch, 16, n), entries m.. zero."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    YT = np.ascontiguousarray(YT, dtype=np.complex128)
+    batch, n, _ = A.shape
+    if YT.shape != (batch, 16, n):
+        raise ValueError("YT must have shape (batch, 16, n)")
+    out = np.empty_like(YT)
+    _check(load_library().idos_stage1_w(int(mode), n, batch, int(k), _ptr(A), _ptr(YT), _ptr(out)), "idos_stage1_w")
+    return out
 
 
 def her2k(A, Y, Z, tc_products: int = DEFAULT_TC_PRODUCTS):

@@ -854,13 +854,24 @@ int solve_large_t(const SolveArgs& a) {
                                                                                               use_smem);
           }
         }
-        // float32 with an even n_max: the register-tiled W (16-byte pairs)
+        // float32 with an even n_max: W on the tensor cores (w_tile 2, with
+        // the tensor-core update) or the register-tiled W (16-byte pairs)
+        const bool wtc = use_tc && a.w_tile == 2;
         const bool w4 = sizeof(T) == 4 && (nm % 2) == 0 && a.w_tile != 0;
-        const int wr = w4 ? W4R : Tiles<T>::WR;
+        const int wr = wtc ? 128 : (w4 ? W4R : Tiles<T>::WR);
         const int rt = (m + wr - 1) / wr;
-        const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (2 * sms + rt * nb_mat - 1) / (rt * nb_mat)));
+        // K splits: about one CTA per SM for the tensor-core W (one resident
+        // per SM), two per SM for the register-tiled kernels
+        const int nsplit =
+            wtc ? (int)std::max<int64_t>(1, std::min<int64_t>(std::min(kMaxSplit, (m + 31) / 32),
+                                                              (sms + rt * nb_mat - 1) / (rt * nb_mat)))
+                : (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (2 * sms + rt * nb_mat - 1) / (rt * nb_mat)));
         {
-          {
+          if (wtc) {
+            ProfScope p2(KID_LG_W, a.stream, 2);
+            IDOS_TRY(tc_w(tcp, bt, k, reinterpret_cast<const c2<float>*>(YT), reinterpret_cast<c2<float>*>(Wp), nsplit,
+                          d_err, a.stream));
+          } else {
             ProfScope p2(KID_LG_W, a.stream);
             if constexpr (sizeof(T) == 4) {
               if (w4)
@@ -992,5 +1003,86 @@ extern "C" int idos_her2k(int tc_products, int n, int64_t batch, const double* A
   }
   IDOS_CUDA_TRY(cudaMemcpy(hA.data(), dA.p, sizeof(float) * 2 * na, cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < 2 * na; ++i) A_out[i] = (double)hA[i];
+  return IDOS_OK;
+}
+
+extern "C" int idos_stage1_w(int mode, int n, int64_t batch, int k, const double* A, const double* YT,
+                             double* W_out) {
+  using namespace idos;
+  using namespace idos::lg;
+  if (!A || !YT || !W_out) {
+    set_error("null argument");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  if (mode < 0 || mode > 2 || n < BW + 1 || n > 8192 || batch < 1 || batch > 65535 || k < 0 || k % BW != 0 ||
+      k + BW >= n || (mode != 0 && n % 2 != 0)) {
+    set_error("mode (0..2), n (17..8192, even for modes 1 and 2), batch (1..65535) or k (multiple of 16 below n - 16) "
+              "out of range");
+    return IDOS_ERR_INVALID_ARG;
+  }
+  int sms = 0;
+  IDOS_TRY(check_device(sms));
+  const int m = n - k - BW;
+  const size_t na = (size_t)batch * n * n, ny = (size_t)batch * BW * n;
+  std::vector<float> hA(2 * na), hV(2 * ny);
+  for (size_t i = 0; i < 2 * na; ++i) hA[i] = (float)A[i];
+  for (size_t i = 0; i < 2 * ny; ++i) hV[i] = (float)YT[i];
+  DevBuf dA, dV, dW, dErr, dOp;
+  IDOS_CUDA_TRY(cudaMalloc(&dA.p, sizeof(float) * 2 * na));
+  IDOS_CUDA_TRY(cudaMalloc(&dV.p, sizeof(float) * 2 * ny));
+  IDOS_CUDA_TRY(cudaMalloc(&dW.p, sizeof(float) * 2 * ny * kMaxSplit));
+  IDOS_CUDA_TRY(cudaMalloc(&dErr.p, sizeof(int)));
+  IDOS_CUDA_TRY(cudaMemcpy(dA.p, hA.data(), sizeof(float) * 2 * na, cudaMemcpyHostToDevice));
+  IDOS_CUDA_TRY(cudaMemcpy(dV.p, hV.data(), sizeof(float) * 2 * ny, cudaMemcpyHostToDevice));
+  IDOS_CUDA_TRY(cudaMemset(dErr.p, 0, sizeof(int)));
+  const Batch bt{n, (int)batch, 1, 0, nullptr};
+  auto* cA = reinterpret_cast<c2<float>*>(dA.p);
+  auto* cV = reinterpret_cast<c2<float>*>(dV.p);
+  auto* cW = reinterpret_cast<c2<float>*>(dW.p);
+  // the split rule of the solver's loop
+  const int wr = mode == 2 ? 128 : (mode == 1 ? W4R : Tiles<float>::WR);
+  const int rt = (m + wr - 1) / wr;
+  const int nsplit =
+      mode == 2 ? (int)std::max<int64_t>(1, std::min<int64_t>(std::min(kMaxSplit, (m + 31) / 32),
+                                                              (sms + rt * batch - 1) / (rt * batch)))
+                : (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSplit, (2 * sms + rt * batch - 1) / (rt * batch)));
+  if (mode == 2) {
+    const size_t a_bytes = ((size_t)batch * n * 6 * 4 * BW * 2 + 255) & ~size_t(255);
+    IDOS_CUDA_TRY(cudaMalloc(&dOp.p, a_bytes * 3));
+    TcPlan p;
+    IDOS_TRY(tc_plan(p, n, batch, 6, dOp.p, static_cast<char*>(dOp.p) + a_bytes, dA.p));
+    IDOS_TRY(tc_w(p, bt, k, cV, cW, nsplit, static_cast<int*>(dErr.p), 0));
+  } else if (mode == 1) {
+    k_ts_w4<<<dim3(rt, 1, (unsigned)(batch * nsplit)), 256>>>(bt, k, reinterpret_cast<const float2*>(cA),
+                                                              reinterpret_cast<const float2*>(cV),
+                                                              reinterpret_cast<float2*>(cW), nsplit);
+    IDOS_CHECK_LAUNCH();
+  } else {
+    k_ts_w<float><<<dim3(rt, 1, (unsigned)(batch * nsplit)), 256>>>(bt, k, cA, cV, cW, nsplit);
+    IDOS_CHECK_LAUNCH();
+  }
+  IDOS_CUDA_TRY(cudaDeviceSynchronize());
+  int herr = 0;
+  IDOS_CUDA_TRY(cudaMemcpy(&herr, dErr.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) {
+    set_error("tensor-core W: a bounded wait timed out");
+    return IDOS_ERR_TIMEOUT;
+  }
+  std::vector<float> hW(2 * ny * nsplit);
+  IDOS_CUDA_TRY(cudaMemcpy(hW.data(), dW.p, sizeof(float) * hW.size(), cudaMemcpyDeviceToHost));
+  for (int64_t b = 0; b < batch; ++b)
+    for (int c = 0; c < BW; ++c)
+      for (int r = 0; r < n; ++r) {
+        float re = 0.f, im = 0.f;
+        if (r < m)
+          for (int sp = 0; sp < nsplit; ++sp) {
+            const size_t o = (((size_t)b * nsplit + sp) * BW + c) * n + r;
+            re += hW[2 * o];
+            im += hW[2 * o + 1];
+          }
+        const size_t q = ((size_t)b * BW + c) * n + r;
+        W_out[2 * q] = re;
+        W_out[2 * q + 1] = im;
+      }
   return IDOS_OK;
 }

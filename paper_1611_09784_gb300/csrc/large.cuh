@@ -68,6 +68,10 @@ int chase_run(const ChasePlan& p, const Batch& bt, const c2<T>* A, c2<T>* Bd, T*
 // and their TMA descriptors.
 struct TcPlan {
   CUtensorMap mapA, mapB, mapC;
+  CUtensorMap mapB2, mapCm;   // the lower-triangle update: B boxes of 256 rows, 16-row reduce-add boxes
+  CUtensorMap mapWB;          // W's operand B' (in Bop's memory)
+  int kw = 0;                 // its row length (bfloat16)
+  int lower = 1;              // 1: lower-triangle tiles with mirrored blocks, 0: the full tile grid
   int np = 6;
   int n_max = 0;
   void* Aop = nullptr;
@@ -86,6 +90,13 @@ int tc_plan(TcPlan& p, int n_max, int64_t batch, int np, void* Aop, void* Bop, v
 // trailing block starts at row and column k + BW; k = -BW updates the whole
 // matrix).  Y, Z: [B][BW][n_max] complex float32; A is the plan's batch.
 int tc_her2k(const TcPlan& p, const Batch& bt, int k, const c2<float>* Y, const c2<float>* Z, int* err, cudaStream_t s);
+
+// W = A22 (Y T) on the tensor cores (six split-bfloat16 products) for every
+// matrix of the plan's batch at panel offset k >= 0: partial sums over nsplit
+// ranges of A22's columns into Wp[b][split][BW][n_max] (complex float32),
+// each range's slice written in full.  YT: [B][BW][n_max].
+int tc_w(const TcPlan& p, const Batch& bt, int k, const c2<float>* YT, c2<float>* Wp, int nsplit, int* err,
+         cudaStream_t s);
 
 }  // namespace lg
 }  // namespace idos

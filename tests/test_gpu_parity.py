@@ -250,7 +250,8 @@ def test_autotune_picks_the_fastest_and_restores_statistics():
         s1 = ref.get_level_stats(l)[1]
         assert np.max(np.abs(tuned[l] - s1)) <= counts[l] * 2 * IDOS_TOL
     assert {"w_tile", "chase_pair", "persistent", "graph"} <= set(tune)
-    assert any(t["w_tile"] == 0 for t in tune["tried"]) and any(t["chase_pair"] == 0 for t in tune["tried"])
+    # both W kernels (tensor cores, FP32 pipe) and both chase shapes were timed
+    assert {1, 2} <= {t["w_tile"] for t in tune["tried"]} and any(t["chase_pair"] == 0 for t in tune["tried"])
     ref.close()
 
 

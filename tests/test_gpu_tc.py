@@ -109,3 +109,46 @@ def test_fp32_tensor_path_against_fp64_path_full_size_graphene():
     assert np.array_equal(keep, ~np.isnan(e32[0]))
     assert np.max(np.abs(np.sort(e32[0][keep]) - np.sort(e64[0][keep]))) < 1e-4
     assert np.max(np.abs(q32 - q64)) < 1e-5
+
+
+def _w_case(n, batch, k, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((batch, n, n)) + 1j * rng.standard_normal((batch, n, n))
+    A = (A + np.conj(np.swapaxes(A, 1, 2))) / 2
+    YT = rng.standard_normal((batch, 16, n)) + 1j * rng.standard_normal((batch, 16, n))
+    m = n - k - 16
+    A22 = A[:, k + 16:, k + 16:]
+    V = np.swapaxes(YT[:, :, :m], 1, 2)           # (batch, m, 16)
+    ref = np.zeros_like(YT)
+    ref[:, :, :m] = np.swapaxes(A22 @ V, 1, 2)
+    # per entry, sum_x |A22[r][x]| |V[x][c]|: the scale of a dot product's
+    # rounding error
+    bound = np.ones(YT.shape)
+    bound[:, :, :m] = np.swapaxes(np.abs(A22) @ np.abs(V), 1, 2)
+    return A, YT, ref, bound, m
+
+
+@pytest.mark.parametrize("mode", [2, 1, 0])
+@pytest.mark.parametrize("n,batch,k", [(48, 1, 0), (300, 2, 16), (514, 1, 0), (1030, 2, 496), (2048, 1, 0)])
+def test_stage1_w_matches_float64(mode, n, batch, k):
+    # W = A22 (Y T): the tensor-core kernel (six split-bfloat16 products,
+    # float32 accumulation, the hi*hi and the smaller products in separate
+    # accumulators) and the FP32-pipe kernels against float64.  Each entry's
+    # error is measured against sum |A22| |V|: rounding the inputs to float32
+    # alone gives about 2^-24 of it, the float32 sums a few more units.
+    import paper_1611_09784_gb300 as pkg
+    A, YT, ref, bound, m = _w_case(n, batch, k, 100 + n + k)
+    got = pkg.stage1_w(A, YT, k=k, mode=mode)
+    assert np.all(got[:, :, m:] == 0)
+    err = np.max(np.abs(got - ref) / bound)
+    assert err < 5e-7, f"mode={mode} n={n} k={k}: error {err:.3e} of sum |A22| |V|"
+
+
+def test_stage1_w_tensor_cores_track_fp32_pipe():
+    # the tensor-core W is float32-class: within a small factor of the FP32
+    # pipe's own error against float64
+    import paper_1611_09784_gb300 as pkg
+    A, YT, ref, bound, m = _w_case(640, 2, 32, 5)
+    e2 = np.max(np.abs(pkg.stage1_w(A, YT, k=32, mode=2) - ref) / bound)
+    e1 = np.max(np.abs(pkg.stage1_w(A, YT, k=32, mode=1) - ref) / bound)
+    assert e2 <= 8 * e1 + 1e-9, (e2, e1)
