@@ -311,11 +311,12 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
 /* enable = 1 turns timing on: idos_sample_levels then issues every level's
  * launches in order on one stream, without the SM partition or a graph, so
  * that each event pair spans its own kernel alone.  enable = 2 (timeline):
- * the levels keep their streams and partition, calls are captured and
- * replayed as a graph as without profiling (the graph then holds the event
- * record nodes), each pair's span includes any time its kernel waited for
- * SMs, and idos_sample_levels also keeps a trace of its launches
- * (idos_get_trace).  0 turns timing off.  Does not clear the totals. */
+ * the levels keep their streams and partition but run without a graph
+ * (launches issued directly, levels in the library's issue order, so a
+ * level's first kernel can start only once the host has issued it), each
+ * pair's span includes any time its kernel waited for SMs, and
+ * idos_sample_levels also keeps a trace of its launches (idos_get_trace).
+ * 0 turns timing off.  Does not clear the totals. */
 int idos_set_profiling(idos_model* m, int enable);
 
 /* Number of kernel families (valid kid values are 0 .. count-1). */
@@ -465,6 +466,16 @@ typedef struct idos_tuning {
   int32_t tried_panel_cluster[IDOS_TUNE_MAX];
 } idos_tuning;
 int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
+
+/* Installs the configuration fields of `t` (sm_split, small_max_n,
+ * persistent, graph, w_tile, chase_pair, placement, panel_cluster; the timing
+ * and tried_* fields are ignored), e.g. a choice an earlier idos_autotune
+ * returned, without timing anything.  sm_split 0 shares all SMs; a split the
+ * driver cannot make leaves every level on all SMs (idos_autotune's rule).
+ * Results do not depend on the configuration beyond float rounding of the
+ * path choice (small_max_n, w_tile).  Invalid values: IDOS_ERR_INVALID_ARG,
+ * nothing changed. */
+int idos_set_tuning(idos_model* m, const idos_tuning* t);
 
 /* ---- serving ----
  * A request loop over the level sampler (a scheduler thread inside the

@@ -131,6 +131,7 @@ _SYMBOLS = {
                                    C.POINTER(C.c_int64)]),
     "idos_reset_profile": (C.c_int, [C.c_void_p]),
     "idos_get_trace": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_int64)]),
+    "idos_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(Tuning)]),
     "idos_eval_idos_noalloc": (C.c_int, [C.POINTER(ModelDesc), C.c_int, C.c_int, C.c_void_p, C.c_uint64, C.c_int,
                                          C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -275,6 +276,16 @@ class Model:
                 "graph": t.graph, "w_tile": t.w_tile, "chase_pair": t.chase_pair,
                 "placement": t.placement, "panel_cluster": t.panel_cluster, "best_ms": round(t.best_ms, 3),
                 "tried": tried}
+
+    def set_tuning(self, tuning: dict):
+        """idos_set_tuning: install a configuration (e.g. autotune()'s result;
+        keys sm_split, small_max_n, persistent, graph, w_tile, chase_pair,
+        placement, panel_cluster) without timing anything."""
+        t = Tuning()
+        for key in ("sm_split", "small_max_n", "persistent", "graph", "w_tile", "chase_pair", "placement",
+                    "panel_cluster"):
+            setattr(t, key, int(tuning[key]))
+        _check(load_library().idos_set_tuning(self._h, C.byref(t)), "idos_set_tuning")
 
     def graph_info(self):
         """(calls that replayed a graph, captures made, reason graph mode was

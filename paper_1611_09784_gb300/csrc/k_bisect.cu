@@ -324,7 +324,9 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   // counts bracket it (a binary search that keeps count(lo) <= k < count(hi)
   // for whatever counts it reads), saving about log2(G + 1) - 1 bisection
   // steps per eigenvalue for one count per thread.
-  const auto x_ms = [&](int t) { return (float)(glo + (double)(t + 1) * (ghi - glo) / (double)(G + 1)); };
+  // (float32 points from one float64 step: no float64 division per point)
+  const float ms_lo = (float)glo, ms_step = (float)((ghi - glo) / (double)(G + 1));
+  const auto x_ms = [&](int t) { return fmaf((float)(t + 1), ms_step, ms_lo); };
   {
     int c;
     if constexpr (sizeof(S) == 4) c = sturm_count_pairs(de, n, x_ms(tid), piv32);

@@ -37,12 +37,6 @@ struct Profiler {
   std::vector<int> pending_n;       // kernel launches inside pair i
   std::vector<cudaStream_t> pending_stream;
   std::vector<TraceEntry> trace;    // entries of the last traced call
-  // the pairs a captured graph records (its event nodes use the same pool
-  // events), restored before each replay so that the replay can be resolved
-  std::vector<int> graph_kid, graph_n;
-  std::vector<cudaStream_t> graph_stream;
-  void snapshot() { graph_kid = pending_kid; graph_n = pending_n; graph_stream = pending_stream; }
-  void restore() { pending_kid = graph_kid; pending_n = graph_n; pending_stream = graph_stream; }
   double ms[KID_COUNT] = {};
   long long launches[KID_COUNT] = {};   // kernel launches (not scopes)
   int begin(int kid, cudaStream_t s, int n_launch);   // returns the pair index or -1
