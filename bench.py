@@ -178,8 +178,8 @@ def n_act_of(masks, N):
 
 # Kernel families of the library's profiler and what bounds each one:
 # "alu" (float32 FMA issue), "alu64" (float64 FMA issue), "tensor" (bf16 MMA),
-# "hbm" (DRAM bytes).  W runs on the tensor cores with the tensor-core update
-# (w_tile 2), else on the FP32 pipe.
+# "hbm" (DRAM bytes).  W runs on the FP32 pipe unless the autotuner picked the
+# tensor-core W (w_tile 2).
 FAMILIES = {"k_small_tridiag": "alu", "k_ts_panel": "alu", "k_ts_w": "tensor", "k_ts_z": "hbm", "k_ts_her2k": "tensor",
             "k_ts_chase": "alu", "k_bisect": "alu64", "k_idos": "hbm"}
 
@@ -234,7 +234,7 @@ def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16
 AGGREGATE_SCOPES = ("k_lg_band (stage 1, all)",)
 
 
-def roofline(prof, work, steps, pk, pk_kind, fma, tc_products=6, w_tile=2):
+def roofline(prof, work, steps, pk, pk_kind, fma, tc_products=6, w_tile=1):
     """Roofline objects of the kernel families; the first is the single kernel
     family (not an aggregate scope) with the largest event time.  fma: the
     FMA peaks measured in this run (TFLOP/s, float32 and float64); w_tile: the
@@ -733,7 +733,7 @@ def run_gpu(args):
             work[k2] = work.get(k2, 0.0) + wk[k2] / args.steps
     pk, pk_kind = peaks()
     fma = measure_fma_peaks(pkg, stream.cuda_stream, local)
-    w_tile = tuning.get("w_tile", 2) if isinstance(tuning, dict) else 2
+    w_tile = tuning.get("w_tile", 1) if isinstance(tuning, dict) else 1
     roof, roofs = roofline(prof, work, args.steps, pk, pk_kind, fma, tc_products=TC_PRODUCTS, w_tile=w_tile)
 
     # rates W, S, D, C (Sec. 2.1-2.2, fitted as Sec. 4.4 does) from the timed
@@ -909,7 +909,7 @@ NCU_FAMILY = [("k_small_persistent", "k_small_tridiag"), ("k_small_tridiag", "k_
               ("k_ts_to_band", "k_ts_chase"), ("k_ts_chase", "k_ts_chase"), ("k_bisect", "k_bisect"),
               ("k_idos", "k_idos"), ("k_level", "k_level_stats"), ("k_fine_masks", "k_masks"),
               ("k_corner_masks", "k_masks"), ("k_cell_maps", "k_masks"), ("k_lg_assemble", "k_lg_assemble")]
-FAMILY_SOURCE = {"k_small_tridiag": "k_small.cu", "k_ts_panel": "k_large.cu", "k_ts_w": "k_tc.cu",
+FAMILY_SOURCE = {"k_small_tridiag": "k_small.cu", "k_ts_panel": "k_large.cu", "k_ts_w": "k_large.cu",
                  "k_ts_z": "k_large.cu", "k_ts_her2k": "k_tc.cu", "k_ts_chase": "k_chase.cu",
                  "k_bisect": "k_bisect.cu", "k_idos": "k_idos.cu"}
 

@@ -452,8 +452,8 @@ typedef struct idos_tuning {
   int32_t tried_persistent[IDOS_TUNE_MAX];
   int32_t graph;         /* chosen graph setting (idos_model_desc.graph) */
   int32_t tried_graph[IDOS_TUNE_MAX];
-  int32_t w_tile;        /* stage-1 W kernel: 2 = tensor cores (with tc_products > 0), 1 = 128-row
-                            register tiles, 0 = 64-row tiles */
+  int32_t w_tile;        /* stage-1 W kernel: 1 = 128-row register tiles (default), 0 = 64-row
+                            tiles, 2 = tensor cores (with tc_products > 0) */
   int32_t chase_pair;    /* clustered band chases: 1 = two warps per sweep, 0 = one */
   int32_t tried_w_tile[IDOS_TUNE_MAX];
   int32_t tried_chase_pair[IDOS_TUNE_MAX];

@@ -1596,13 +1596,13 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     if (pers == 1 && !can_persist) continue;
     for (int sp : splits) {
       if (sp >= m->sm_count || (sp > 0 && L < 2) || out->n_tried >= IDOS_TUNE_MAX) continue;
-      rc = time_config(sp, sm, pers, gr, 2, 1, ltf, 0);
+      rc = time_config(sp, sm, pers, gr, 1, 1, ltf, 0);
       if (rc != IDOS_OK) break;
     }
     if (rc != IDOS_OK) break;
   }
   // second stage, at the winner: graph replay switched, then the two-stage
-  // kernel shapes (W on the FP32 pipe; one warp per sweep in clustered chases)
+  // kernel shapes (W on the tensor cores; one warp per sweep in clustered chases)
   if (rc == IDOS_OK && graph_saved && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
     rc = time_config(best_split, best_small, best_persist, best_graph ? 0 : 1, best_w, best_cp, best_ltf, best_pc);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)

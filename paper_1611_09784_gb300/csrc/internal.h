@@ -94,10 +94,10 @@ struct SolveArgs {
   int sm_avail = 0;
   int max_cluster = 16;
   // kernel shapes of the two-stage path (set by the autotuner): the float32
-  // W = A22 (Y T) on the tensor cores (2, with the tensor-core trailing
-  // update; else as 1), with 128-row register tiles (1) or 64-row tiles (0);
+  // W = A22 (Y T) with 128-row register tiles (1), 64-row tiles (0) or on the
+  // tensor cores (2, with the tensor-core trailing update; else as 1);
   // clustered band chases with two warps per sweep (1) or one (0)
-  int w_tile = 2;
+  int w_tile = 1;
   int chase_pair = 1;
   // CTAs of the stage-1 panel QR cluster (0: the smallest power of two whose
   // shared memory holds the panel, grown while the batch leaves SMs idle)
@@ -167,7 +167,7 @@ struct Model {
   int sm_split_now = 0;           // SMs reserved for the finest level now (0: no partition)
   int small_max_n = -1;           // largest n on the shared-memory kernel (-1: whatever fits)
   int persistent = 1;             // one persistent launch for the levels' shared-memory matrices
-  int w_tile = 2, chase_pair = 1;  // two-stage kernel shapes (SolveArgs)
+  int w_tile = 1, chase_pair = 1;  // two-stage kernel shapes (SolveArgs)
   int panel_cluster = 0;           // stage-1 panel QR cluster size (SolveArgs)
   double* acc = nullptr;          // device [n_levels][kAccRows][n_E]: sum Y, Y^2, Q_fine, Q_fine^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)

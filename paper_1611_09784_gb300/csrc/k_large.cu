@@ -854,8 +854,9 @@ int solve_large_t(const SolveArgs& a) {
                                                                                               use_smem);
           }
         }
-        // float32 with an even n_max: W on the tensor cores (w_tile 2, with
-        // the tensor-core update) or the register-tiled W (16-byte pairs)
+        // float32 with an even n_max: the register-tiled W (16-byte pairs) or,
+        // when the autotuner picked it (w_tile 2, with the tensor-core
+        // update), W on the tensor cores
         const bool wtc = use_tc && a.w_tile == 2;
         const bool w4 = sizeof(T) == 4 && (nm % 2) == 0 && a.w_tile != 0;
         const int wr = wtc ? 128 : (w4 ? W4R : Tiles<T>::WR);

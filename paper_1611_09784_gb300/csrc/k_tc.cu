@@ -335,6 +335,7 @@ constexpr uint32_t TL_STAGE_BYTES = (TC_M + TL_N) * TC_KC * 2;   // A and B box 
 constexpr uint32_t TL_GROUP_BYTES = 2 * TC_M * 128;              // direct (128 rows) + mirror (16 x 256 floats) group
 constexpr int TL_GROUPS_PER_BATCH = (int)(TL_STAGES * TL_STAGE_BYTES / TL_GROUP_BYTES);
 static_assert(TL_GROUPS_PER_BATCH >= 1, "epilogue staging fits the operand ring");
+constexpr int TL_THREADS = 256;   // two warps per TMEM lane quarter share the epilogue's column groups
 
 __device__ __forceinline__ void tile_of(int t, int& I, int& J) {
   int i = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -345,7 +346,7 @@ __device__ __forceinline__ void tile_of(int t, int& I, int& J) {
 }
 
 template <int NP>
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(TL_THREADS, 2)
 k_tc_her2k_lt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmCm, Batch bt, int k,
               int* __restrict__ err) {
@@ -416,15 +417,16 @@ k_tc_her2k_lt(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   tc_fence_after();
   // block-uniform: every thread takes part in the staging barriers below
   const bool ok = __syncthreads_and(ready && !*(volatile int*)err) != 0;
-  const int row = warp * 32 + lane;   // tile row = TMEM lane
+  const int q4 = warp & 3, half = warp >> 2;   // TMEM lane quarter; which groups of a batch
+  const int row = q4 * 32 + lane;               // tile row = TMEM lane
   if (ok) {
     for (int g0 = 0; g0 < TL_N / 32; g0 += TL_GROUPS_PER_BATCH) {
       const int g1 = min(TL_N / 32, g0 + TL_GROUPS_PER_BATCH);
-      for (int g = g0; g < g1; ++g) {
+      for (int g = g0 + half; g < g1; g += 2) {
         // complex columns 16 g .. 16 g + 15 of the tile
         float acc[32];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * 32), acc);
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * 32 + 16), acc + 16);
+        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * 32), acc);
+        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * 32 + 16), acc + 16);
         const uint32_t dbase = base + (uint32_t)(g - g0) * TL_GROUP_BYTES;
         const uint32_t rbase = dbase + (uint32_t)row * 128;
 #pragma unroll
@@ -875,13 +877,13 @@ int tc_her2k(const TcPlan& p, const Batch& bt, int k, const c2<float>* Y, const 
   if (p.np == 3) {
     k_tc_operands<3><<<og, 256, 0, s>>>(bt, k, Y, Z, ab, bb, m_max);
     if (p.lower)
-      k_tc_her2k_lt<3><<<tl, TC_THREADS, tl_smem_bytes(), s>>>(p.mapA, p.mapB2, p.mapC, p.mapCm, bt, k, err);
+      k_tc_her2k_lt<3><<<tl, TL_THREADS, tl_smem_bytes(), s>>>(p.mapA, p.mapB2, p.mapC, p.mapCm, bt, k, err);
     else
       k_tc_her2k<3><<<tg, TC_THREADS, tc_smem_bytes(), s>>>(p.mapA, p.mapB, p.mapC, bt, k, err);
   } else {
     k_tc_operands<6><<<og, 256, 0, s>>>(bt, k, Y, Z, ab, bb, m_max);
     if (p.lower)
-      k_tc_her2k_lt<6><<<tl, TC_THREADS, tl_smem_bytes(), s>>>(p.mapA, p.mapB2, p.mapC, p.mapCm, bt, k, err);
+      k_tc_her2k_lt<6><<<tl, TL_THREADS, tl_smem_bytes(), s>>>(p.mapA, p.mapB2, p.mapC, p.mapCm, bt, k, err);
     else
       k_tc_her2k<6><<<tg, TC_THREADS, tc_smem_bytes(), s>>>(p.mapA, p.mapB, p.mapC, bt, k, err);
   }
