@@ -42,7 +42,7 @@ class MlmcOpts(C.Structure):
                 ("seed", C.c_uint64)]
 
 
-TUNE_MAX = 40
+TUNE_MAX = 48
 
 
 class Tuning(C.Structure):
@@ -53,7 +53,8 @@ class Tuning(C.Structure):
                 ("tried_graph", C.c_int32 * TUNE_MAX), ("w_tile", C.c_int32), ("chase_pair", C.c_int32),
                 ("tried_w_tile", C.c_int32 * TUNE_MAX), ("tried_chase_pair", C.c_int32 * TUNE_MAX),
                 ("placement", C.c_int32), ("tried_placement", C.c_int32 * TUNE_MAX),
-                ("panel_cluster", C.c_int32), ("tried_panel_cluster", C.c_int32 * TUNE_MAX)]
+                ("panel_cluster", C.c_int32), ("tried_panel_cluster", C.c_int32 * TUNE_MAX),
+                ("her2k_lower", C.c_int32), ("tried_her2k_lower", C.c_int32 * TUNE_MAX)]
 
 
 class Estimate(C.Structure):
@@ -270,11 +271,12 @@ class Model:
         tried = [{"sm_split": t.tried_split[i], "small_max_n": t.tried_small[i],
                   "persistent": t.tried_persistent[i], "graph": t.tried_graph[i], "w_tile": t.tried_w_tile[i],
                   "chase_pair": t.tried_chase_pair[i], "placement": t.tried_placement[i],
-                  "panel_cluster": t.tried_panel_cluster[i],
+                  "panel_cluster": t.tried_panel_cluster[i], "her2k_lower": t.tried_her2k_lower[i],
                   "ms": round(t.tried_ms[i], 3)} for i in range(t.n_tried)]
         return {"sm_split": t.sm_split, "small_max_n": t.small_max_n, "persistent": t.persistent,
                 "graph": t.graph, "w_tile": t.w_tile, "chase_pair": t.chase_pair,
-                "placement": t.placement, "panel_cluster": t.panel_cluster, "best_ms": round(t.best_ms, 3),
+                "placement": t.placement, "panel_cluster": t.panel_cluster, "her2k_lower": t.her2k_lower,
+                "best_ms": round(t.best_ms, 3),
                 "tried": tried}
 
     def set_tuning(self, tuning: dict):
@@ -285,6 +287,7 @@ class Model:
         for key in ("sm_split", "small_max_n", "persistent", "graph", "w_tile", "chase_pair", "placement",
                     "panel_cluster"):
             setattr(t, key, int(tuning[key]))
+        t.her2k_lower = int(tuning.get("her2k_lower", 1))
         _check(load_library().idos_set_tuning(self._h, C.byref(t)), "idos_set_tuning")
 
     def graph_info(self):

@@ -102,6 +102,9 @@ struct SolveArgs {
   // CTAs of the stage-1 panel QR cluster (0: the smallest power of two whose
   // shared memory holds the panel, grown while the batch leaves SMs idle)
   int panel_cluster = 0;
+  // tensor-core trailing update on lower-triangle tiles with mirrored blocks
+  // (1) or on the full tile grid (0)
+  int her2k_lower = 1;
 };
 
 // Two green contexts splitting the device's SMs (partition.cu): ctx[0] has
@@ -169,6 +172,7 @@ struct Model {
   int persistent = 1;             // one persistent launch for the levels' shared-memory matrices
   int w_tile = 1, chase_pair = 1;  // two-stage kernel shapes (SolveArgs)
   int panel_cluster = 0;           // stage-1 panel QR cluster size (SolveArgs)
+  int her2k_lower = 1;             // trailing update on lower-triangle tiles (SolveArgs)
   double* acc = nullptr;          // device [n_levels][kAccRows][n_E]: sum Y, Y^2, Q_fine, Q_fine^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream

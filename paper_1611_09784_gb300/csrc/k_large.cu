@@ -766,6 +766,7 @@ int solve_large_t(const SolveArgs& a) {
       return IDOS_ERR_OUT_OF_MEMORY;
     }
     IDOS_TRY(tc_plan(tcp, nm, batch, a.tc_np, Aop, Bop, A));
+    tcp.lower = a.her2k_lower;
   }
   // panel QR in shared memory when the (n - BW) x BW panel fits
   const size_t panel_smem = sizeof(C) * (size_t)(nm - BW) * BW;
