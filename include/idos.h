@@ -439,7 +439,7 @@ int idos_measure_fma_peak(int precision, int64_t iters, void* cuda_stream, doubl
  * the level statistics are restored afterwards.  Results do not depend on the
  * choice beyond float rounding of the path choice; out: the choice and every
  * candidate's best step time. */
-#define IDOS_TUNE_MAX 48
+#define IDOS_TUNE_MAX 56
 typedef struct idos_tuning {
   int32_t sm_split;      /* chosen SMs reserved for the finest level (0 = shared) */
   int32_t small_max_n;   /* chosen limit of the shared-memory kernel (-1 = what fits) */
@@ -467,12 +467,15 @@ typedef struct idos_tuning {
   int32_t her2k_lower;   /* tensor-core trailing update: 1 = lower-triangle tiles with mirrored
                             blocks (default), 0 = the full tile grid */
   int32_t tried_her2k_lower[IDOS_TUNE_MAX];
+  int32_t persist_reserve; /* SMs of its partition the persistent small-matrix launch leaves free
+                              for the two-stage chains beside it (0 = none) */
+  int32_t tried_persist_reserve[IDOS_TUNE_MAX];
 } idos_tuning;
 int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning* out);
 
 /* Installs the configuration fields of `t` (sm_split, small_max_n,
  * persistent, graph, w_tile, chase_pair, placement, panel_cluster,
- * her2k_lower; the timing
+ * her2k_lower, persist_reserve; the timing
  * and tried_* fields are ignored), e.g. a choice an earlier idos_autotune
  * returned, without timing anything.  sm_split 0 shares all SMs; a split the
  * driver cannot make leaves every level on all SMs (idos_autotune's rule).

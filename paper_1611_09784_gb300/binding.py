@@ -42,7 +42,7 @@ class MlmcOpts(C.Structure):
                 ("seed", C.c_uint64)]
 
 
-TUNE_MAX = 48
+TUNE_MAX = 56
 
 
 class Tuning(C.Structure):
@@ -54,7 +54,8 @@ class Tuning(C.Structure):
                 ("tried_w_tile", C.c_int32 * TUNE_MAX), ("tried_chase_pair", C.c_int32 * TUNE_MAX),
                 ("placement", C.c_int32), ("tried_placement", C.c_int32 * TUNE_MAX),
                 ("panel_cluster", C.c_int32), ("tried_panel_cluster", C.c_int32 * TUNE_MAX),
-                ("her2k_lower", C.c_int32), ("tried_her2k_lower", C.c_int32 * TUNE_MAX)]
+                ("her2k_lower", C.c_int32), ("tried_her2k_lower", C.c_int32 * TUNE_MAX),
+                ("persist_reserve", C.c_int32), ("tried_persist_reserve", C.c_int32 * TUNE_MAX)]
 
 
 class Estimate(C.Structure):
@@ -272,10 +273,12 @@ class Model:
                   "persistent": t.tried_persistent[i], "graph": t.tried_graph[i], "w_tile": t.tried_w_tile[i],
                   "chase_pair": t.tried_chase_pair[i], "placement": t.tried_placement[i],
                   "panel_cluster": t.tried_panel_cluster[i], "her2k_lower": t.tried_her2k_lower[i],
+                  "persist_reserve": t.tried_persist_reserve[i],
                   "ms": round(t.tried_ms[i], 3)} for i in range(t.n_tried)]
         return {"sm_split": t.sm_split, "small_max_n": t.small_max_n, "persistent": t.persistent,
                 "graph": t.graph, "w_tile": t.w_tile, "chase_pair": t.chase_pair,
                 "placement": t.placement, "panel_cluster": t.panel_cluster, "her2k_lower": t.her2k_lower,
+                "persist_reserve": t.persist_reserve,
                 "best_ms": round(t.best_ms, 3),
                 "tried": tried}
 
@@ -288,6 +291,7 @@ class Model:
                     "panel_cluster"):
             setattr(t, key, int(tuning[key]))
         t.her2k_lower = int(tuning.get("her2k_lower", 1))
+        t.persist_reserve = int(tuning.get("persist_reserve", 0))
         _check(load_library().idos_set_tuning(self._h, C.byref(t)), "idos_set_tuning")
 
     def graph_info(self):

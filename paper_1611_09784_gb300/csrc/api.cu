@@ -477,7 +477,7 @@ int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, 
     for (int l = lp + 1; l < L; ++l)
       if (P[l].S > 0 && (P[l].fine_small || P[l].crs_small)) IDOS_CUDA_TRY(cudaStreamWaitEvent(ps, m->lprep[l], 0));
     const double eps = d.overlap_s != 0.0 ? 0.0 : d.eps_onsite;
-    IDOS_TRY(solve_small_persistent(segs, n_seg, d.t, eps, m->small_ctr, lsms[lp], ps));
+    IDOS_TRY(solve_small_persistent(segs, n_seg, d.t, eps, m->small_ctr, lsms[lp], m->persist_reserve, ps));
     IDOS_CUDA_TRY(cudaEventRecord(m->small_done, ps));
   }
   // (C) large sets, then the rest of every level, finest first
@@ -936,7 +936,7 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     std::vector<int64_t> core(n_samples, n_samples + L);
     for (int64_t v : {(int64_t)parted, (int64_t)route_p, (int64_t)m->small_max_n, (int64_t)m->persistent,
                       (int64_t)m->part_gen, (int64_t)m->w_tile, (int64_t)m->chase_pair, (int64_t)m->panel_cluster,
-                      (int64_t)m->her2k_lower,
+                      (int64_t)m->her2k_lower, (int64_t)m->persist_reserve,
                       (int64_t)m->placement})
       core.push_back(v);
     std::vector<int64_t> key = core;
@@ -1494,9 +1494,10 @@ int idos_set_tuning(idos_model* m, const idos_tuning* t) {
   if (t->sm_split < 0 || t->sm_split >= m->sm_count || t->small_max_n < -1 || t->small_max_n > 1024 ||
       t->persistent < 0 || t->persistent > 1 || t->graph < 0 || t->graph > 1 || t->w_tile < 0 || t->w_tile > 2 ||
       t->chase_pair < 0 || t->chase_pair > 1 || t->placement < 0 || t->placement > 2 || t->panel_cluster < 0 ||
-      t->panel_cluster > 8 || t->her2k_lower < 0 || t->her2k_lower > 1) {
+      t->panel_cluster > 8 || t->her2k_lower < 0 || t->her2k_lower > 1 || t->persist_reserve < 0 ||
+      t->persist_reserve >= m->sm_count) {
     set_error("tuning field out of range (sm_split 0..SMs-1, small_max_n -1..1024, persistent/graph/chase_pair 0..1, "
-              "w_tile 0..2, placement 0..2, panel_cluster 0..8, her2k_lower 0..1)");
+              "w_tile 0..2, placement 0..2, panel_cluster 0..8, her2k_lower 0..1, persist_reserve 0..SMs-1)");
     return IDOS_ERR_INVALID_ARG;
   }
   m->small_max_n = t->small_max_n;
@@ -1507,6 +1508,7 @@ int idos_set_tuning(idos_model* m, const idos_tuning* t) {
   m->placement = t->placement;
   m->panel_cluster = t->panel_cluster;
   m->her2k_lower = t->her2k_lower;
+  m->persist_reserve = t->persist_reserve;
   return apply_partition(m, t->sm_split);
 }
 
@@ -1544,15 +1546,17 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   out->best_ms = 1e300;
   int best_split = m->sm_split_now, best_small = m->small_max_n, best_persist = m->persistent, best_graph = m->graph;
   int best_w = m->w_tile, best_cp = m->chase_pair, best_ltf = m->placement, best_pc = m->panel_cluster;
-  int best_hl = m->her2k_lower;
+  int best_hl = m->her2k_lower, best_pr = m->persist_reserve;
   const int graph_saved = m->graph;
   int64_t first[IDOS_MAX_LEVELS];
   int64_t round = 0;
   int rc = IDOS_OK;
   // two untimed calls per candidate: the first runs directly (and sizes the
   // workspaces), the second captures the graph; the timed calls replay it
-  auto time_config = [&](int sp, int sm, int pers, int gr, int wt, int cp, int ltf, int pc, int hl) -> int {
+  auto time_config = [&](int sp, int sm, int pers, int gr, int wt, int cp, int ltf, int pc, int hl,
+                         int pr) -> int {
     m->her2k_lower = hl;
+    m->persist_reserve = pr;
     m->small_max_n = sm;
     m->persistent = pers;
     m->placement = ltf;
@@ -1582,6 +1586,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     out->tried_panel_cluster[i] = pc;
     out->tried_placement[i] = ltf;
     out->tried_her2k_lower[i] = hl;
+    out->tried_persist_reserve[i] = pr;
     out->tried_ms[i] = best;
     if (best < out->best_ms) {
       out->best_ms = best;
@@ -1594,6 +1599,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
       best_ltf = ltf;
       best_pc = pc;
       best_hl = hl;
+      best_pr = pr;
     }
     return IDOS_OK;
   };
@@ -1603,7 +1609,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     if (pers == 1 && !can_persist) continue;
     for (int sp : splits) {
       if (sp >= m->sm_count || (sp > 0 && L < 2) || out->n_tried >= IDOS_TUNE_MAX) continue;
-      rc = time_config(sp, sm, pers, gr, 1, 1, ltf, 0, best_hl);
+      rc = time_config(sp, sm, pers, gr, 1, 1, ltf, 0, best_hl, best_pr);
       if (rc != IDOS_OK) break;
     }
     if (rc != IDOS_OK) break;
@@ -1613,20 +1619,27 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   // chases; the trailing update on the full tile grid)
   if (rc == IDOS_OK && graph_saved && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
     rc = time_config(best_split, best_small, best_persist, best_graph ? 0 : 1, best_w, best_cp, best_ltf, best_pc,
-                     best_hl);
+                     best_hl, best_pr);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
     rc = time_config(best_split, best_small, best_persist, best_graph, best_w == 2 ? 1 : 2, best_cp, best_ltf, best_pc,
-                     best_hl);
+                     best_hl, best_pr);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
     rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp ? 0 : 1, best_ltf, best_pc,
-                     best_hl);
+                     best_hl, best_pr);
   if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
     rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp, best_ltf, best_pc,
-                     best_hl ? 0 : 1);
+                     best_hl ? 0 : 1, best_pr);
+  // SMs the persistent small-matrix launch leaves free for the two-stage
+  // chains beside it (with the persistent route only)
+  for (int pr : {8, 16, 32})
+    if (rc == IDOS_OK && best_persist && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
+      rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp, best_ltf, best_pc, best_hl,
+                       pr);
   // the panel QR's cluster size (the default rule picks up to 8 CTAs)
   for (int pc : {1, 2, 4})
     if (rc == IDOS_OK && out->n_tried > 0 && out->n_tried < IDOS_TUNE_MAX)
-      rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp, best_ltf, pc, best_hl);
+      rc = time_config(best_split, best_small, best_persist, best_graph, best_w, best_cp, best_ltf, pc, best_hl,
+                       best_pr);
   // install the winner and restore the caller's statistics
   m->small_max_n = best_small;
   m->persistent = best_persist;
@@ -1636,6 +1649,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   m->placement = best_ltf;
   m->panel_cluster = best_pc;
   m->her2k_lower = best_hl;
+  m->persist_reserve = best_pr;
   const int rc2 = apply_partition(m, best_split);
   IDOS_CUDA_TRY(cudaMemcpyAsync(m->acc, acc_saved.data(), sizeof(double) * acc_saved.size(), cudaMemcpyHostToDevice,
                                 m->stream));
@@ -1650,6 +1664,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
   out->chase_pair = m->chase_pair;
   out->panel_cluster = m->panel_cluster;
   out->her2k_lower = m->her2k_lower;
+  out->persist_reserve = m->persist_reserve;
   out->placement = m->placement;
   return rc != IDOS_OK ? rc : rc2;
 }

@@ -173,6 +173,7 @@ struct Model {
   int w_tile = 1, chase_pair = 1;  // two-stage kernel shapes (SolveArgs)
   int panel_cluster = 0;           // stage-1 panel QR cluster size (SolveArgs)
   int her2k_lower = 1;             // trailing update on lower-triangle tiles (SolveArgs)
+  int persist_reserve = 0;         // SMs of its partition the persistent launch leaves free
   double* acc = nullptr;          // device [n_levels][kAccRows][n_E]: sum Y, Y^2, Q_fine, Q_fine^2
   double* tmdc_p = nullptr;       // device parameter table of the TMDC-shaped model (null for graphene)
   int* err = nullptr;             // device [IDOS_MAX_LEVELS + 1] status words: level streams, then the model stream
@@ -217,13 +218,15 @@ struct SmallSeg {
 };
 // Largest n_max the persistent launch takes (float32).
 constexpr int kPersistMaxN = 160;
-// Reduces the matrices of all segments (n_max <= kPersistMaxN each) in one
-// launch of at most `ctas` CTAs (0: one per SM of the device): matrices with
-// n_max > 32 are CTA work items, handed out largest first; the n_max <= 32
-// ones are warp work items taken one at a time by any warp that is free.
-// counters: device [3] uint64 scratch, zeroed here on the stream.
+// Reduces the matrices of all segments (n_max <= kPersistMaxN each) by
+// persistent launches of at most `ctas` - `reserve` CTAs (ctas 0: one per SM
+// of the device), each CTA filling one SM, so that `reserve` SMs stay free
+// for other streams' kernels: matrices with n_max > 32 are CTA work items,
+// handed out largest first; the n_max <= 32 ones are warp work items taken
+// one at a time by any warp that is free.  counters: device [3] uint64
+// scratch, zeroed here on the stream.
 int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double eps, unsigned long long* counters,
-                           int ctas, cudaStream_t s);
+                           int ctas, int reserve, cudaStream_t s);
 int solve_large(int precision, const SolveArgs& a);
 // Workspace the large-matrix path needs to hold n_mat matrices in one batch.
 size_t large_path_bytes(int precision, int n_max, int64_t n_mat);

@@ -950,7 +950,7 @@ k_small_persistent_cr(const PersistWork w, double t_hop, double eps, unsigned lo
 // whichever warp is free (a second persistent launch after the CTA items:
 // the register-resident reduction needs more registers per thread than the
 // 640-thread CTA items leave).
-constexpr int kPWarpCta = 4;   // warps per CTA of the warp-item launch
+constexpr int kPWarpCta = 16;   // warps per CTA of the warp-item launch (one CTA fills an SM's registers)
 
 __global__ void __launch_bounds__(32 * kPWarpCta)
 k_small_persistent_warps(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
@@ -974,7 +974,7 @@ k_small_persistent_warps(const PersistWork w, double t_hop, double eps, unsigned
 }  // namespace
 
 int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double eps, unsigned long long* counters,
-                           int ctas, cudaStream_t s) {
+                           int ctas, int reserve, cudaStream_t s) {
   if (n_segs <= 0) return IDOS_OK;
   if (n_segs > kMaxSmallSegs || !counters) {
     set_error("persistent launch: too many segments or no counters");
@@ -1023,7 +1023,7 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
   int dev = 0, sms = 0;
   IDOS_CUDA_TRY(cudaGetDevice(&dev));
   IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int sm_grid = ctas > 0 ? std::min(ctas, sms) : sms;
+  const int sm_grid = std::max(1, (ctas > 0 ? std::min(ctas, sms) : sms) - std::max(0, reserve));
   IDOS_CUDA_TRY(cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), s));
   if (w.total_cta > 0) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_grid, w.total_cta));
@@ -1039,9 +1039,9 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
     IDOS_CHECK_LAUNCH();
   }
   if (w.total_warp > 0) {
-    // four 4-warp CTAs per SM (the register-resident reduction's occupancy)
+    // one 16-warp CTA per SM (the register-resident reduction's occupancy)
     const int64_t ctas_w = (w.total_warp + kPWarpCta - 1) / kPWarpCta;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_grid * 4, ctas_w));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_grid, ctas_w));
     ProfScope ps(KID_SMALL_TRIDIAG, s);
     k_small_persistent_warps<<<grid, 32 * kPWarpCta, 0, s>>>(w, t, eps, counters);
     IDOS_CHECK_LAUNCH();
