@@ -127,7 +127,14 @@ int eigs_and_idos(Model* M, const CellSet& cells, int Kside, const void* d, cons
   const int n_max = cells.n_sites;
   const int K2 = Kside * Kside;
   const int64_t n_mat = cells.count * (int64_t)K2;
-  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st, err));
+  // graphene: H(k) = (on-site) I + a hopping matrix between the two
+  // sublattices (vacancies remove sites, not the bipartition), so every
+  // spectrum is symmetric about the on-site energy (0 for the overlap form's
+  // t B): only the upper half is bisected, the lower half mirrored
+  const bool sym = M->d.kind == IDOS_GRAPHENE;
+  const double center = M->d.overlap_s != 0.0 ? 0.0 : M->d.eps_onsite;
+  IDOS_TRY(launch_bisect(M->d.precision, M->d.refine64_iters, d, e2, cells.n_act, K2, n_max, n_mat, eigs, st, err,
+                         sym ? 1 : 0, center));
   if (M->d.overlap_s != 0.0)
     IDOS_TRY(launch_overlap_map(eigs, cells.n_act, K2, n_max, n_mat, M->d.eps_onsite, M->d.overlap_s / M->d.t, st));
   const double area = (double)cells.N * cells.N * cell_area(M->d.a);

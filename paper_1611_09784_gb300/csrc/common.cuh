@@ -133,11 +133,14 @@ constexpr uint64_t kStreamVacancy = 1;
 constexpr uint64_t kStreamParams = 2;
 
 // ---------------------------------------------------------------- groups ---
-// A "group" is NT consecutive threads (NT a multiple of 32) working on one
-// matrix; MPB groups share a CTA.  Groups synchronise with a named barrier.
+// A "group" is NT consecutive threads (NT a multiple of 32, or 16: half a
+// warp) working on one matrix; MPB groups share a CTA.  Groups synchronise
+// with a named barrier (warp or half-warp groups: __syncwarp over their lanes).
 template <int NT, int MPB>
 __device__ __forceinline__ void group_sync(int gid) {
-  if constexpr (NT == 32) {
+  if constexpr (NT == 16) {
+    __syncwarp(0xFFFFu << (16 * (gid & 1)));
+  } else if constexpr (NT == 32) {
     __syncwarp();
   } else if constexpr (MPB == 1) {
     __syncthreads();

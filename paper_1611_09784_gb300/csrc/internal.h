@@ -233,10 +233,12 @@ size_t large_path_bytes(int precision, int n_max, int64_t n_mat);
 
 // Sturm-count bisection: eigs[mat][n_max] ascending, NaN beyond n_act.
 // err (nullable, device): status word; bit 2 is set when a matrix's (d, e^2)
-// holds a non-finite entry (the reduction broke down).
+// holds a non-finite entry (the reduction broke down).  sym != 0: every
+// spectrum is symmetric about `center`; only indices >= n/2 are bisected and
+// the rest mirrored.
 int launch_bisect(int precision, int refine64_iters, const void* d, const void* e2,
                   const int* n_act_cell, int K2, int n_max, int64_t n_mat, double* eigs,
-                  cudaStream_t s, int* err = nullptr);
+                  cudaStream_t s, int* err = nullptr, int sym = 0, double center = 0.0);
 
 // Overlap s != 0 (graphene): eigenvalues l of t B -> generalized eigenvalues
 // (eps + l) / (1 + sigma l), sigma = s / t, kept ascending.

@@ -215,10 +215,14 @@ __host__ __device__ __forceinline__ size_t bisect_pair_offset(int n_max, int mpb
 // One group of G threads per (matrix, chunk of `chunk` eigenvalue indices),
 // MPB groups per CTA; every group holds its matrix's whole (d, e^2) in shared
 // memory.  S = storage type of (d, e^2).
+// sym != 0: the spectrum is symmetric about `center` (a bipartite hopping
+// matrix plus center I: chiral symmetry), so only the indices k >= n / 2 are
+// bisected and lambda_{n-1-k} = 2 center - lambda_k is written beside them.
 template <typename S, int G, int MPB>
 __global__ void __launch_bounds__(G* MPB)
 k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __restrict__ n_act_cell,
-         int K2, int n_max, int64_t n_mat, int chunk, int refine, double* __restrict__ eigs, int* __restrict__ err) {
+         int K2, int n_max, int64_t n_mat, int chunk, int refine, double* __restrict__ eigs, int* __restrict__ err,
+         int sym, double center) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int gid = threadIdx.x / G, tid = threadIdx.x % G;
   const int n_chunks = (n_max + chunk - 1) / chunk;
@@ -236,14 +240,18 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   double2* dde = reinterpret_cast<double2*>(smem_raw + bisect_pair_offset(n_max, MPB)) + (size_t)gid * n_max;
   double* dd = reinterpret_cast<double*>(d);   // float64 path: the same arrays
   double* ee = dd + n_max;
-  __shared__ double red_lo[MPB][G / 32], red_hi[MPB][G / 32], red_e[MPB][G / 32];
+  constexpr int NW = G >= 32 ? G / 32 : 1;
+  __shared__ double red_lo[MPB][NW], red_hi[MPB][NW], red_e[MPB][NW];
+  // the lanes of this group (half-warp groups shuffle within their half)
+  const unsigned gmask = G >= 32 ? 0xffffffffu : (0xFFFFu << (16 * (gid & 1)));
   __shared__ int ms_cnt[MPB][G];
   const int n = n_act_cell ? n_act_cell[mat / K2] : n_max;
   double* out = eigs + mat * n_max;
   for (int i = c_lo + tid; i < c_hi; i += G) {
     if (i >= n) out[i] = __longlong_as_double(0x7ff8000000000000ll);   // NaN padding
   }
-  if (n <= 0 || c_lo >= n) return;
+  const int h0 = sym ? n / 2 : 0;   // first bisected index
+  if (n <= 0 || c_lo >= n || c_hi <= h0) return;
   // Gershgorin bounds and the largest e^2 in the storage precision (widened
   // below by far more than their rounding)
   S glo_s = S(1e30), ghi_s = S(-1e30), emax_s = S(0);
@@ -269,10 +277,10 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
     emax_s = fmax(emax_s, ei);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    glo_s = fmin(glo_s, __shfl_xor_sync(0xffffffffu, glo_s, o));
-    ghi_s = fmax(ghi_s, __shfl_xor_sync(0xffffffffu, ghi_s, o));
-    emax_s = fmax(emax_s, __shfl_xor_sync(0xffffffffu, emax_s, o));
+  for (int o = G >= 32 ? 16 : G / 2; o > 0; o >>= 1) {
+    glo_s = fmin(glo_s, __shfl_xor_sync(gmask, glo_s, o));
+    ghi_s = fmax(ghi_s, __shfl_xor_sync(gmask, ghi_s, o));
+    emax_s = fmax(emax_s, __shfl_xor_sync(gmask, emax_s, o));
   }
   double glo = (double)glo_s, ghi = (double)ghi_s, emax = (double)emax_s;
   if constexpr (G > 32) {
@@ -344,7 +352,8 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
     lo = L < 0 ? (float)glo : x_ms(L);
     hi = H >= G ? (float)ghi : x_ms(H);
   };
-  for (int k = c_lo + tid; k < min(n, c_hi); k += G) {
+  for (int k = max(c_lo, h0) + tid; k < min(n, c_hi); k += G) {
+    double lam;
     if constexpr (sizeof(S) == 8) {
       // float32 bracket on the rounded tridiagonal (float64 data read and
       // rounded on the fly), widened, checked in float64, then polished
@@ -357,21 +366,23 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
       if (sturm_newton64(dd, ee, n, lo, st) > k) lo = glo;      // bracket lost: fall back
       if (sturm_newton64(dd, ee, n, hi, st) < k + 1) hi = ghi;
       const auto pass = [&](double x, double& step) { return sturm_newton64(dd, ee, n, x, step); };
-      out[k] = isc * newton_polish(pass, k, lo, hi, 60);
+      lam = isc * newton_polish(pass, k, lo, hi, 60);
     } else {
       float lo, hi;
       ms_bracket(k, lo, hi);
       bisect_index_pairs(de, n, k, piv32, lo, hi, 100, atol32);
       const auto pass = [&](double x, double& step) { return sturm_newton_mixed_pairs(dde, de, n, x, step); };
-      out[k] = isc * (refine > 0 ? newton_polish(pass, k, (double)lo, (double)hi, refine)
-                                 : 0.5 * ((double)lo + (double)hi));
+      lam = isc * (refine > 0 ? newton_polish(pass, k, (double)lo, (double)hi, refine)
+                              : 0.5 * ((double)lo + (double)hi));
     }
+    out[k] = lam;
+    if (sym && n - 1 - k != k) out[n - 1 - k] = 2.0 * center - lam;
   }
 }
 
 template <typename S, int G, int MPB>
 int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int n_max, int64_t n_mat,
-               int refine, double* eigs, cudaStream_t s, int chunk, int* err) {
+               int refine, double* eigs, cudaStream_t s, int chunk, int* err, int sym, double center) {
   const size_t smem = sizeof(S) == 4 ? bisect_pair_offset(n_max, MPB) + sizeof(double) * 2 * (size_t)n_max * MPB
                                      : sizeof(S) * 2 * (size_t)n_max * MPB;
   auto kern = k_bisect<S, G, MPB>;
@@ -380,19 +391,32 @@ int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int
   const int64_t blocks = (groups + MPB - 1) / MPB;
   ProfScope ps(KID_BISECT, s);
   kern<<<(unsigned)blocks, G * MPB, smem, s>>>(reinterpret_cast<const S*>(d), reinterpret_cast<const S*>(e2),
-                                               n_act_cell, K2, n_max, n_mat, chunk, refine, eigs, err);
+                                               n_act_cell, K2, n_max, n_mat, chunk, refine, eigs, err, sym, center);
   IDOS_CHECK_LAUNCH();
   return IDOS_OK;
 }
 
 template <typename S>
 int bisect_t(int refine, const void* d, const void* e2, const int* n_act_cell, int K2, int n_max,
-             int64_t n_mat, double* eigs, cudaStream_t s, int* err) {
-  if (n_max <= 32) return run_bisect<S, 32, 8>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err);
-  if (n_max <= 64) return run_bisect<S, 64, 4>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err);
-  if (n_max <= 128) return run_bisect<S, 128, 2>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err);
+             int64_t n_mat, double* eigs, cudaStream_t s, int* err, int sym, double center) {
+  if (sym) {
+    // half the indices per matrix: groups of half the size
+    if (n_max <= 32)
+      return run_bisect<S, 16, 16>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err, 1, center);
+    if (n_max <= 64)
+      return run_bisect<S, 32, 8>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err, 1, center);
+    if (n_max <= 128)
+      return run_bisect<S, 64, 4>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err, 1, center);
+    if (n_max <= 256)
+      return run_bisect<S, 128, 2>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err, 1, center);
+    // chunks of 128 indices; the chunks below n / 2 return at once
+    return run_bisect<S, 128, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, 128, err, 1, center);
+  }
+  if (n_max <= 32) return run_bisect<S, 32, 8>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err, 0, 0.0);
+  if (n_max <= 64) return run_bisect<S, 64, 4>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err, 0, 0.0);
+  if (n_max <= 128) return run_bisect<S, 128, 2>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, n_max, err, 0, 0.0);
   // larger matrices: 128 eigenvalue indices per CTA, so one matrix spreads over n/128 SMs
-  return run_bisect<S, 128, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, 128, err);
+  return run_bisect<S, 128, 1>(d, e2, n_act_cell, K2, n_max, n_mat, refine, eigs, s, 128, err, 0, 0.0);
 }
 
 }  // namespace
@@ -433,11 +457,11 @@ int launch_overlap_map(double* eigs, const int* n_act_cell, int K2, int n_max, i
 
 int launch_bisect(int precision, int refine64_iters, const void* d, const void* e2,
                   const int* n_act_cell, int K2, int n_max, int64_t n_mat, double* eigs,
-                  cudaStream_t s, int* err) {
+                  cudaStream_t s, int* err, int sym, double center) {
   if (n_mat == 0) return IDOS_OK;
   if (precision == IDOS_FP64)
-    return bisect_t<double>(0, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s, err);
-  return bisect_t<float>(refine64_iters, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s, err);
+    return bisect_t<double>(0, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s, err, sym, center);
+  return bisect_t<float>(refine64_iters, d, e2, n_act_cell, K2, n_max, n_mat, eigs, s, err, sym, center);
 }
 
 }  // namespace idos

@@ -381,3 +381,28 @@ def test_sparse_ragged_matrices_with_isolated_sites():
             got = np.sort(pkg.eigvalsh(H, precision="fp32", refine64_iters=1)[0])
             assert np.all(np.isfinite(got)), (s, ki)
             assert np.max(np.abs(got - np.linalg.eigvalsh(H))) < EIG_TOL, (s, ki)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("N,K,level", [(4, 3, 0), (8, 2, 1), (16, 1, 2)])
+def test_onsite_energy_mirrored_spectrum(precision, N, K, level):
+    # Graphene spectra are symmetric about the on-site energy (bipartite
+    # hopping plus eps I), and the bisection computes only the upper half;
+    # a nonzero eps moves the mirror point.  Eigenvalues and IDoS against the
+    # oracle, including odd kept-site counts (a middle eigenvalue at eps).
+    import paper_1611_09784_gb300 as pkg
+    w, cfg, prm = cfg_and_prm(precision=precision)
+    cfg["eps_onsite"] = 0.37
+    prm["eps_onsite"] = 0.37
+    m = pkg.create_model(cfg)
+    n_odd = 0
+    for sample in range(4):
+        Q, E = m.eval_idos(N, K, seed=w["seed"] + 17, level=level, sample=sample, want_eigs=True)
+        mask = ophilox.vacancy_mask(w["seed"] + 17, level, sample, 2 * N * N, prm["p"])
+        Eo = oidos.band_energies(N, K, mask, prm)
+        for g, r in zip(sorted_active(E), Eo):
+            assert g.shape == r.shape
+            n_odd += g.shape[0] % 2
+            assert np.max(np.abs(g - r)) < EIG_TOL
+        assert np.max(np.abs(Q - oidos.sample_idos(N, K, mask, prm))) < IDOS_TOL
+    m.close()
