@@ -375,6 +375,10 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
       lam = isc * (refine > 0 ? newton_polish(pass, k, (double)lo, (double)hi, refine)
                               : 0.5 * ((double)lo + (double)hi));
     }
+    // an upper-half eigenvalue of a symmetric spectrum is >= center; a
+    // rounding-level value below it (a zero mode) is raised to it, so that
+    // the mirrored sequence stays ascending across the middle
+    if (sym) lam = fmax(lam, center);
     out[k] = lam;
     if (sym && n - 1 - k != k) out[n - 1 - k] = 2.0 * center - lam;
   }
