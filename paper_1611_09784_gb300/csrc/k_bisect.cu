@@ -209,7 +209,7 @@ __device__ __forceinline__ void bisect_index_pairs(const float2* de, int n, int 
 
 // Byte offset of the float64 pair copies in the float32 layout (16-byte aligned).
 __host__ __device__ __forceinline__ size_t bisect_pair_offset(int n_max, int mpb) {
-  return (sizeof(float) * 2 * (size_t)n_max * mpb + 15) & ~size_t(15);
+  return (sizeof(float) * 2 * (size_t)(n_max + 1) * mpb + 15) & ~size_t(15);
 }
 
 // One group of G threads per (matrix, chunk of `chunk` eigenvalue indices),
@@ -234,10 +234,13 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   // float64 storage: d[n_max], e2[n_max] per group.  float32 storage: the
   // same bytes hold de[n_max] = (d_i, e^2_{i-1}) pairs, then (16-byte
   // aligned) their float64 copies dde[n_max].
-  S* d = reinterpret_cast<S*>(smem_raw) + (size_t)gid * 2 * n_max;
+  // per-group arrays padded by one element: two half-warp groups reading
+  // the same row index then hit different banks
+  const int gs = n_max + 1;
+  S* d = reinterpret_cast<S*>(smem_raw) + (size_t)gid * 2 * gs;
   S* e2 = d + n_max;
-  float2* de = reinterpret_cast<float2*>(smem_raw) + (size_t)gid * n_max;
-  double2* dde = reinterpret_cast<double2*>(smem_raw + bisect_pair_offset(n_max, MPB)) + (size_t)gid * n_max;
+  float2* de = reinterpret_cast<float2*>(smem_raw) + (size_t)gid * gs;
+  double2* dde = reinterpret_cast<double2*>(smem_raw + bisect_pair_offset(n_max, MPB)) + (size_t)gid * gs;
   double* dd = reinterpret_cast<double*>(d);   // float64 path: the same arrays
   double* ee = dd + n_max;
   constexpr int NW = G >= 32 ? G / 32 : 1;
@@ -387,8 +390,8 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
 template <typename S, int G, int MPB>
 int run_bisect(const void* d, const void* e2, const int* n_act_cell, int K2, int n_max, int64_t n_mat,
                int refine, double* eigs, cudaStream_t s, int chunk, int* err, int sym, double center) {
-  const size_t smem = sizeof(S) == 4 ? bisect_pair_offset(n_max, MPB) + sizeof(double) * 2 * (size_t)n_max * MPB
-                                     : sizeof(S) * 2 * (size_t)n_max * MPB;
+  const size_t smem = sizeof(S) == 4 ? bisect_pair_offset(n_max, MPB) + sizeof(double) * 2 * (size_t)(n_max + 1) * MPB
+                                     : sizeof(S) * 2 * (size_t)(n_max + 1) * MPB;
   auto kern = k_bisect<S, G, MPB>;
   IDOS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t groups = n_mat * ((n_max + chunk - 1) / chunk);
