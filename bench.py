@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import multiprocessing as mp
 import os
@@ -276,7 +277,8 @@ def roofline(prof, work, steps, pk, pk_kind, fma, tc_products=6, w_tile=1):
         out.append({"kernel": name, "bound": "alu" if bound == "alu64" else bound,
                     "pipe": {"alu": "fp32", "alu64": "fp64", "tensor": "bf16 mma", "hbm": "dram"}[bound],
                     "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                    "traffic": ncu_traffic(name, units_per_launch),
+                    # (the committed capture is of the FP32-pipe W)
+                    "traffic": None if (name == "k_ts_w" and bound == "tensor") else ncu_traffic(name, units_per_launch),
                     "algorithmic_per_launch": units_per_launch, "executed_per_launch": executed,
                     "launches": launches, "avg_launch_ms": per_launch_s * 1e3, "peak_source": src})
     dominant = singles[0][0] if singles else None
@@ -915,7 +917,10 @@ FAMILY_SOURCE = {"k_small_tridiag": "k_small.cu", "k_ts_panel": "k_large.cu", "k
 
 
 def ncu_family(name):
-    base = name.split("(")[0].split("<")[0].split("::")[-1].strip()
+    # the first identifier of the library's kernel naming (k_...), whatever
+    # return type, namespaces or template arguments ncu prints around it
+    m = re.search(r"\b(k_[A-Za-z0-9_]+)", name)
+    base = m.group(1) if m else ""
     for prefix, fam in NCU_FAMILY:
         if base.startswith(prefix):
             return fam
