@@ -778,11 +778,14 @@ int solve_large_t(const SolveArgs& a) {
   IDOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // (launch shapes follow the device's SM count even inside an SM partition,
   // so that results do not depend on how the SMs are shared)
-  // cluster panel QR: the smallest cluster (<= 8 CTAs) whose shared memory
+  // cluster panel QR: the smallest cluster (<= 16 CTAs, more than 8 only
+  // where the level is not confined to an SM partition) whose shared memory
   // holds the first panel, grown while the batch leaves SMs idle and each CTA
-  // keeps at least 64 rows; pc = 0 keeps the one-CTA kernel above
+  // keeps at least 64 rows; pc = 0 keeps the one-CTA kernel above (the panel
+  // in global memory: n = 8192 needs 16 CTAs)
   int pc = 0, pc_rows = 0;
-  for (int q = 1; q <= std::min(8, a.max_cluster); q *= 2) {
+  for (int q = 1; q <= std::min(16, a.max_cluster); q *= 2) {
+    if (q > 8 && pc != 0) break;   // 16 CTAs only when 8 cannot hold the panel
     const int rows = (nm - BW + q - 1) / q;
     const size_t smem = 2 * sizeof(C) * (size_t)rows * BW;
     if (smem > 200 * 1024) continue;
@@ -798,6 +801,8 @@ int solve_large_t(const SolveArgs& a) {
     IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel_cl<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
   } else if (pc > 1) {
     IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel_cl<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+    if (pc > 8)
+      IDOS_CUDA_TRY(cudaFuncSetAttribute(k_ts_panel_cl<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   }
   ChasePlan cp;
   IDOS_TRY(chase_plan<T>(nm, batch, sms, a.max_cluster, cp, a.chase_pair != 0));
