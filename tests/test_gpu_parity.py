@@ -406,3 +406,21 @@ def test_onsite_energy_mirrored_spectrum(precision, N, K, level):
             assert np.max(np.abs(g - r)) < EIG_TOL
         assert np.max(np.abs(Q - oidos.sample_idos(N, K, mask, prm))) < IDOS_TOL
     m.close()
+
+
+def test_n8192_float32_path_tracks_float64_path():
+    # N = 64 (n = 8192, the large-level stress size): the stage-1 panel no
+    # longer fits 8 CTAs of shared memory and runs on a 16-CTA cluster.  The
+    # float32 path (tensor-core update) against the float64 GPU path on one
+    # sample at the zone centre, within the eigenvalue tolerance.
+    import paper_1611_09784_gb300 as pkg
+    res = {}
+    for precision in ("fp32", "fp64"):
+        w, cfg, prm = cfg_and_prm(precision=precision)
+        m = pkg.create_model(cfg)
+        Q, E = m.eval_idos(64, 1, seed=w["seed"], level=0, sample=0, want_eigs=True)
+        res[precision] = (Q, sorted_active(E)[0])
+        m.close()
+    assert res["fp32"][1].shape == res["fp64"][1].shape
+    assert np.max(np.abs(res["fp32"][1] - res["fp64"][1])) < EIG_TOL
+    assert np.max(np.abs(res["fp32"][0] - res["fp64"][0])) < IDOS_TOL
