@@ -46,7 +46,7 @@ enum idos_status {
   IDOS_ERR_CUDA = -3,          /* a CUDA runtime call or kernel launch failed   */
   IDOS_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up            */
   IDOS_ERR_NOT_CONVERGED = -5, /* an iteration hit its limit, or a reduced matrix came out non-finite */
-  IDOS_ERR_UNSUPPORTED = -6,   /* valid request this build does not implement   */
+  IDOS_ERR_UNSUPPORTED = -6,   /* valid request the library does not implement  */
   IDOS_ERR_NO_DEVICE = -7      /* no CUDA device of compute capability 10.3     */
 };
 
