@@ -271,7 +271,9 @@ typedef struct idos_mlmc_opts {
   double tol;            /* TOL of Sec. 2 (states / Angstrom^2)                  */
   double theta;          /* statistical share of TOL (0 < theta < 1)             */
   double c_alpha;        /* confidence quantile (1.96)                           */
-  int64_t pilot_samples; /* pilot samples on level 0 (>= 2); level l takes
+  int64_t pilot_samples; /* pilot samples on level 0 (>= 2); with three or more
+                            levels also on every level below the finest; the
+                            finest (every level l > 0 with fewer levels) takes
                             max(4, ceil(pilot_samples sqrt(W_0/W_l))), W = flop model */
   int32_t work_model;    /* 0: W_l from the flop model sum n^3; 1: measured time */
   int32_t max_rounds;    /* extra allocation rounds after the pilot (>= 1)       */
@@ -286,20 +288,23 @@ typedef struct idos_estimate {
   double* V;       /* float64[n_levels]: max over eps of the level variance  */
   double* W;       /* float64[n_levels]: work per sample used in eq. (2.7)   */
   double seconds;  /* wall time of the call                                  */
-  int32_t rounds;  /* allocation rounds performed after the pilot            */
+  int32_t rounds;  /* eq. (2.7) rounds with every level's pilot in           */
   int64_t h2d_bytes; /* bytes copied host -> device during the call          */
   int64_t d2h_bytes; /* bytes copied device -> host during the call          */
 } idos_estimate;
 
 /* Adaptive MLMC (Sec. 2.2): pilot round (see pilot_samples), V_l and
  * W_l, M_l from eq. (2.7) with target variance (theta tol / c_alpha)^2, extra
- * samples, combine by eq. (2.6).  With three or more levels the pilots of
- * all but the finest level run first, and the finest level's pilot runs in
- * one concurrent call with a provisional top-up of the other levels sized by
- * eq. (2.7) with the finest level's term estimated from the variance decay
- * of the two levels below it (half of it counted); the rounds then top up
- * every level to eq. (2.7) with all pilots.  Starts from zeroed
- * accumulators.  Sample indices continue from 0 on every level. */
+ * samples, combine by eq. (2.6).  With three or more levels the finest
+ * level's pilot is issued first, on its own SM partition, and the other
+ * levels run beside it: their pilots, then up to max_rounds provisional
+ * rounds sized by eq. (2.7) with the finest level's term estimated from the
+ * variance decay of the two levels below it (half of it counted); once the
+ * finest pilot is in, the rounds top up every level to eq. (2.7) with all
+ * pilots.  With profiling on the same calls run one after the other: with
+ * work_model 0 the sample counts depend on the seed and the options only,
+ * neither on timing nor on profiling.  Starts from zeroed accumulators.  Sample indices
+ * continue from 0 on every level. */
 int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* out);
 
 /* ---- kernel timing (tracing) ----

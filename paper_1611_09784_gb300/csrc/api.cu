@@ -484,7 +484,11 @@ int sample_levels_persistent(Model* m, const int64_t* n_samples, uint64_t seed, 
     for (int l = lp + 1; l < L; ++l)
       if (P[l].S > 0 && (P[l].fine_small || P[l].crs_small)) IDOS_CUDA_TRY(cudaStreamWaitEvent(ps, m->lprep[l], 0));
     const double eps = d.overlap_s != 0.0 ? 0.0 : d.eps_onsite;
-    IDOS_TRY(solve_small_persistent(segs, n_seg, d.t, eps, m->small_ctr, lsms[lp], m->persist_reserve, ps));
+    // the counter block of level lp: calls in flight together (the adaptive
+    // estimator's finest pilot beside the other levels' calls) have
+    // different lowest levels, so no launch resets another's counters
+    IDOS_TRY(solve_small_persistent(segs, n_seg, d.t, eps, m->small_ctr + 3 * lp, lsms[lp], m->persist_reserve,
+                                    ps));
     IDOS_CUDA_TRY(cudaEventRecord(m->small_done, ps));
   }
   // (C) large sets, then the rest of every level, finest first
@@ -748,7 +752,7 @@ int idos_create_model(const idos_model_desc* d, void* cuda_stream, idos_model** 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->lprep[l], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->small_done, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&m->small_ctr, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&m->small_ctr, 3 * IDOS_MAX_LEVELS * sizeof(unsigned long long));
   for (int l = 0; l < d->n_levels && e == cudaSuccess; ++l)
     e = cudaEventCreateWithFlags(&m->ljoin[l], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking);
@@ -839,9 +843,29 @@ int idos_sample_level(idos_model* m, int level, int64_t n_samples, uint64_t seed
 // Issues every level of one idos_sample_levels call: the level streams fork
 // from the model's stream and join it again at the end (so the call can be
 // captured as one graph from that stream).
+// Streams and SM counts of one call's levels: the SM partition's with
+// `parted`, the shared-SM ones otherwise; with the partition and the
+// persistent route, placement 1 moves a level below the finest whose fine
+// cells take the two-stage path onto the finest level's partition.
+static void call_streams(Model* m, bool parted, bool route_p, cudaStream_t* lst, cudaStream_t* lst2, int* lsm) {
+  const int L = m->d.n_levels;
+  const cudaStream_t* streams = parted ? m->pstream : m->lstream;
+  const cudaStream_t* streams2 = parted ? m->pstream2 : m->lstream2;
+  for (int l = 0; l < L; ++l) {
+    lst[l] = streams[l];
+    lst2[l] = streams2[l];
+    lsm[l] = parted ? m->lsms[l] : 0;
+    if (parted && route_p && m->placement == 1 && l < L - 1 && m->pstreamF[l] &&
+        !use_small_path(m, orb_per_cell(m->d.kind) * m->d.N[l] * m->d.N[l])) {
+      lst[l] = m->pstreamF[l];
+      lsm[l] = m->lsms[L - 1];
+    }
+  }
+}
+
 int enqueue_levels(Model* m, cudaStream_t origin, const int64_t* n_samples, uint64_t seed,
                    const int64_t* first_sample, cudaStream_t* streams, cudaStream_t* streams2, const int* lsms,
-                   bool route_p, const uint64_t* dyn) {
+                   bool route_p, const uint64_t* dyn, bool join_origin = true) {
   const int L = m->d.n_levels;
   IDOS_CUDA_TRY(cudaEventRecord(m->fork, origin));
   for (int l = 0; l < L; ++l)
@@ -860,9 +884,38 @@ int enqueue_levels(Model* m, cudaStream_t origin, const int64_t* n_samples, uint
   for (int l = 0; l < L; ++l) {
     if (n_samples[l] == 0) continue;
     IDOS_CUDA_TRY(cudaEventRecord(m->ljoin[l], streams[l]));
-    IDOS_CUDA_TRY(cudaStreamWaitEvent(origin, m->ljoin[l], 0));
+    if (join_origin) IDOS_CUDA_TRY(cudaStreamWaitEvent(origin, m->ljoin[l], 0));
   }
   return IDOS_OK;
+}
+
+// Issues n_samples[l] samples of every level (first index m->M[l]) on the
+// levels' streams, on the SM partition when there is one, after the work
+// queued on the model's stream, and returns without waiting: complete_level
+// then waits for a level and counts its samples.  Launches are direct (the
+// call's seed and first indices travel as kernel arguments), so that calls
+// issued while earlier ones run share no per-call device buffer.
+static int issue_levels(Model* m, const int64_t* n_samples, uint64_t seed) {
+  const int L = m->d.n_levels;
+  const bool route_p = persistent_route(m, n_samples);
+  cudaStream_t lst[IDOS_MAX_LEVELS], lst2[IDOS_MAX_LEVELS];
+  int lsm[IDOS_MAX_LEVELS];
+  call_streams(m, m->pstream[L - 1] != nullptr, route_p, lst, lst2, lsm);
+  int64_t first[IDOS_MAX_LEVELS] = {};
+  for (int l = 0; l < L; ++l) first[l] = m->M[l];
+  return enqueue_levels(m, m->stream, n_samples, seed, first, lst, lst2, lsm, route_p, nullptr, false);
+}
+
+// Waits for the samples issue_levels put on `level` and adds their count and
+// time to the level's accumulators.
+static int complete_level(Model* m, int level, int64_t n_samples) {
+  if (n_samples == 0) return IDOS_OK;
+  IDOS_CUDA_TRY(cudaEventSynchronize(m->ljoin[level]));
+  float ms = 0.f;
+  IDOS_CUDA_TRY(cudaEventElapsedTime(&ms, m->lev0[level], m->lev1[level]));
+  m->M[level] += n_samples;
+  m->seconds[level] += ms * 1e-3;
+  return check_status_word(m->err + level);
 }
 
 int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, const int64_t* first_sample) {
@@ -882,8 +935,6 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
   double w_fin = 0.0, w_rest = 0.0;
   for (int l = 0; l < L; ++l) (l == L - 1 ? w_fin : w_rest) += (double)n_samples[l] * flop_model(m->d, l);
   bool parted = m->pstream[L - 1] != nullptr && w_fin > 0.0 && w_rest >= 0.5 * w_fin;
-  cudaStream_t* streams = parted ? m->pstream : m->lstream;
-  cudaStream_t* streams2 = parted ? m->pstream2 : m->lstream2;
   // A profiled call issues the same launches in order on the model's stream,
   // so that each kernel's event span is its own (on concurrent streams it
   // would include time spent waiting for SMs held by other levels).
@@ -893,13 +944,8 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
   cudaStream_t origin = m->gstream;
   IDOS_CUDA_TRY(cudaEventRecord(m->fork0, m->stream));
   IDOS_CUDA_TRY(cudaStreamWaitEvent(origin, m->fork0, 0));
-  cudaStream_t ser[IDOS_MAX_LEVELS], ser2[IDOS_MAX_LEVELS] = {};
-  if (m->prof.enabled && !m->prof.timeline) {
-    for (int l = 0; l < L; ++l) ser[l] = origin;
-    streams = ser;
-    streams2 = ser2;
-    parted = false;
-  }
+  const bool serial = m->prof.enabled && !m->prof.timeline;
+  if (serial) parted = false;
   // timeline mode keeps the levels' streams and partition (kernel spans then
   // include time spent waiting for SMs) and times every launch from here
   if (m->prof.enabled && m->prof.timeline && m->prof.mark_origin(origin) != 0) {
@@ -907,23 +953,16 @@ int idos_sample_levels(idos_model* m, const int64_t* n_samples, uint64_t seed, c
     return IDOS_ERR_CUDA;
   }
   const bool route_p = persistent_route(m, n_samples);
-  // per-level streams and SM counts of this call; with the partition and the
-  // persistent route, a level below the finest whose fine cells take the
-  // two-stage path may run on the finest level's partition
   cudaStream_t lst[IDOS_MAX_LEVELS], lst2[IDOS_MAX_LEVELS];
   int lsm[IDOS_MAX_LEVELS];
-  for (int l = 0; l < L; ++l) {
-    lst[l] = streams[l];
-    lst2[l] = streams2[l];
-    lsm[l] = parted ? m->lsms[l] : 0;
-    if (parted && route_p && m->placement == 1 && l < L - 1 && m->pstreamF[l] &&
-        !use_small_path(m, orb_per_cell(m->d.kind) * m->d.N[l] * m->d.N[l])) {
-      lst[l] = m->pstreamF[l];
-      lsm[l] = m->lsms[L - 1];
+  call_streams(m, parted, route_p, lst, lst2, lsm);
+  if (serial)
+    for (int l = 0; l < L; ++l) {
+      lst[l] = origin;
+      lst2[l] = nullptr;
     }
-  }
-  streams = lst;
-  streams2 = lst2;
+  cudaStream_t* streams = lst;
+  cudaStream_t* streams2 = lst2;
   // per-call values of the mask kernels (a replayed graph reads them here)
   m->dyn_host[0] = seed;
   for (int l = 0; l < L; ++l) m->dyn_host[1 + l] = (uint64_t)(first_sample ? first_sample[l] : m->M[l]);
@@ -1384,11 +1423,18 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
   IDOS_TRY(idos_reset_level_stats(m, -1));
   std::vector<double> sum(2 * (size_t)n_E);
   std::vector<double> V(L), W(L);
-  // pilot: pilot_samples on level 0, fewer on costlier levels
+  // pilot: pilot_samples on level 0; with three or more levels the same on
+  // every level below the finest (they run beside the finest level's pilot,
+  // and a level variance from 4 samples is good to about +-70 %: measured on
+  // the N = 4..32 graphene levels at TOL = 1e-3, a 32-sample pilot there cut
+  // the median estimate from 59.6 to 52.1 ms over 16 seeds, 24, 48 and 64
+  // were no better); fewer on costlier levels otherwise, at least 4
   std::vector<int64_t> target(L);
   for (int l = 0; l < L; ++l)
-    target[l] = std::max<int64_t>(4, (int64_t)std::ceil(o->pilot_samples *
-                                                        std::sqrt(flop_model(m->d, 0) / flop_model(m->d, l))));
+    target[l] = (L >= 3 && l < L - 1)
+                    ? o->pilot_samples
+                    : std::max<int64_t>(4, (int64_t)std::ceil(o->pilot_samples *
+                                                              std::sqrt(flop_model(m->d, 0) / flop_model(m->d, l))));
   int64_t d2h = 0, h2d = 0;
   int rounds = 0;
   // V_l (max over the grid of the unbiased sample variance) and W_l of level l
@@ -1409,26 +1455,73 @@ int idos_mlmc_estimate(idos_model* m, const idos_mlmc_opts* o, idos_estimate* ou
     return idos_sample_levels(m, extra, o->seed, first);
   };
   if (L >= 3) {
-    // The finest level's pilot is the longest part of the pilot round, so it
-    // runs beside a provisional top-up of the other levels: their pilots come
-    // first, then eq. (2.7) with the finest level's term estimated from the
-    // rate at which the variance decays over the two levels below it
-    // (V_{L-1} ~ V_{L-2}^2 / V_{L-3}, W_{L-1} from the flop model relative to
-    // W_{L-2}), counted at half its size so that the provisional targets stay
-    // below the final ones; round 0 below issues both at once.
+    // The finest level's pilot is the longest part of the estimate, so the
+    // other levels' work runs beside it.  Their pilots come first; then
+    // eq. (2.7) gives their targets with the finest level's term estimated
+    // from the variance decay over the two levels below it (V_{L-1} ~
+    // V_{L-2}^2 / V_{L-3}, W_{L-1} from the flop model relative to W_{L-2}),
+    // counted at half its size so that these provisional targets stay below
+    // the final ones.  The finest pilot is issued first, on its own
+    // partition, and the other levels take up to max_rounds provisional
+    // rounds beside it (pilot, top-up, re-estimate, ...); the rounds below
+    // then top up every level to eq. (2.7) with all pilots.  A profiled call
+    // makes the same calls one after the other, so with the flop-model W the
+    // sample counts depend neither on timing nor on profiling.
+    const bool overlap = !m->prof.enabled;
+    int64_t fin[IDOS_MAX_LEVELS] = {};
+    fin[L - 1] = target[L - 1];
+    if (overlap) {
+      h2d += (int64_t)sizeof(uint64_t) * (1 + L);
+      IDOS_TRY(issue_levels(m, fin, o->seed));
+    } else {
+      IDOS_TRY(sample(fin));
+    }
+    // an early return still waits for the finest pilot (and counts it)
+    struct Drain {
+      Model* m;
+      int64_t n;
+      ~Drain() {
+        if (n) (void)complete_level(m, m->d.n_levels - 1, n);
+      }
+    } drain{m, overlap ? fin[L - 1] : 0};
+    auto coarse = [&](const int64_t* extra) -> int {
+      if (!overlap) return sample(extra);
+      h2d += (int64_t)sizeof(uint64_t) * (1 + L);
+      IDOS_TRY(issue_levels(m, extra, o->seed));
+      for (int l = 0; l + 1 < L; ++l) IDOS_TRY(complete_level(m, l, extra[l]));
+      return IDOS_OK;
+    };
+    auto provisional = [&]() -> int {
+      double s0 = 0.0;
+      for (int l = 0; l + 1 < L; ++l) {
+        IDOS_TRY(estimate_vw(l));
+        s0 += std::sqrt(W[l] * V[l]);
+      }
+      const double v_fin = V[L - 2] * std::min(1.0, V[L - 2] / V[L - 3]);
+      const double w_fin = W[L - 2] * flop_model(m->d, L - 1) / flop_model(m->d, L - 2);
+      s0 += 0.5 * std::sqrt(w_fin * v_fin);
+      for (int l = 0; l + 1 < L; ++l)
+        target[l] = std::max(target[l], std::max<int64_t>(2, (int64_t)std::ceil(f * std::sqrt(V[l] / W[l]) * s0)));
+      return IDOS_OK;
+    };
     int64_t extra[IDOS_MAX_LEVELS] = {};
     for (int l = 0; l + 1 < L; ++l) extra[l] = target[l];
-    IDOS_TRY(sample(extra));
-    double s0 = 0.0;
-    for (int l = 0; l + 1 < L; ++l) {
-      IDOS_TRY(estimate_vw(l));
-      s0 += std::sqrt(W[l] * V[l]);
+    IDOS_TRY(coarse(extra));
+    IDOS_TRY(provisional());
+    for (int r = 0; r < o->max_rounds; ++r) {
+      bool any = false;
+      for (int l = 0; l + 1 < L; ++l) {
+        extra[l] = std::max<int64_t>(0, target[l] - m->M[l]);
+        any = any || extra[l] > 0;
+      }
+      if (!any) break;
+      IDOS_TRY(coarse(extra));
+      IDOS_TRY(provisional());
     }
-    const double v_fin = V[L - 2] * std::min(1.0, V[L - 2] / V[L - 3]);
-    const double w_fin = W[L - 2] * flop_model(m->d, L - 1) / flop_model(m->d, L - 2);
-    s0 += 0.5 * std::sqrt(w_fin * v_fin);
-    for (int l = 0; l + 1 < L; ++l)
-      target[l] = std::max(target[l], std::max<int64_t>(2, (int64_t)std::ceil(f * std::sqrt(V[l] / W[l]) * s0)));
+    if (overlap) {
+      drain.n = 0;
+      IDOS_TRY(complete_level(m, L - 1, fin[L - 1]));
+    }
   }
   for (int round = 0; round <= o->max_rounds; ++round) {
     // every level's extra samples in one concurrent call (level streams)

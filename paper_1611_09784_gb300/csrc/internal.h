@@ -144,7 +144,8 @@ struct Model {
   cudaEvent_t lev0[IDOS_MAX_LEVELS] = {}, lev1[IDOS_MAX_LEVELS] = {};
   cudaEvent_t fork = nullptr;
   // persistent launch over the levels' shared-memory matrices: per-level
-  // "inputs ready" events, the launch's completion, its work counters
+  // "inputs ready" events, the launch's completion, its work counters (three
+  // per level: a launch uses those of the lowest level it serves)
   cudaEvent_t lprep[IDOS_MAX_LEVELS] = {};
   cudaEvent_t small_done = nullptr;
   unsigned long long* small_ctr = nullptr;

@@ -1,7 +1,7 @@
 """The adaptive MLMC estimator (idos_mlmc_estimate, eq. (2.6)-(2.7)) against
 the oracle: the same estimator recomputed by the oracle on the same samples,
-and a one-level estimate against the exact expectation over every vacancy
-outcome of a 2 x 2 cell."""
+a one-level estimate against the exact expectation over every vacancy
+outcome of a 2 x 2 cell, and sample counts that depend on the seed alone."""
 import numpy as np
 import pytest
 
@@ -87,3 +87,29 @@ def test_bench_levels_estimate_at_tol_matches_oracle():
     mc_mean, mc_var = omlmc.mc_estimate(np.array(mc))
     z = np.abs(est["mean"] - mc_mean) / np.sqrt(est["var"] + mc_var + 1e-30)
     assert np.max(z) < 4.0, float(np.max(z))
+
+
+def test_sample_counts_depend_on_seed_only():
+    """Three levels: the finest level's pilot runs beside the other levels'
+    pilots and provisional rounds of eq. (2.7); with profiling on the same
+    calls run one after the other.  With the flop-model W_l, the same seed
+    gives the same samples per level whatever the timing (two unprofiled
+    calls) and with profiling on, hence the same eq. (2.6) mean up to the
+    summation order of the level sums."""
+    levels = [(2, 4), (4, 3), (8, 2)]
+    w, cfg, prm = cfg_and_prm(precision="fp32", p=0.1)
+    cfg = dict(cfg, levels=levels)
+    kw = dict(theta=0.5, c_alpha=1.96, pilot_samples=8, max_rounds=3, seed=2024)
+    with pkg.create_model(cfg) as m:
+        a = m.mlmc_estimate(8e-3, **kw)
+        b = m.mlmc_estimate(8e-3, **kw)
+        m.set_profiling(1)
+        c = m.mlmc_estimate(8e-3, **kw)
+        m.set_profiling(0)
+    for e in (b, c):
+        assert list(e["M"]) == list(a["M"])
+        assert e["rounds"] == a["rounds"]
+        np.testing.assert_allclose(e["mean"], a["mean"], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(e["var"], a["var"], rtol=1e-9, atol=1e-15)
+    # every level below the finest took at least the pilot
+    assert all(int(x) >= 8 for x in a["M"][:-1]) and int(a["M"][-1]) >= 4
