@@ -163,19 +163,37 @@ def ncu_traffic(kernel, algorithmic_per_launch):
 
 
 # --------------------------------------------------------- algorithmic work --
-def n_act_of(masks, N):
+def n_act_of(masks, N, sublattice=False):
     """Kept-site counts of the fine cells and of their 4 corners (site index
-    m = 2(i + N j) + s, corner r = ri + 2 rj)."""
+    m = 2(i + N j) + s, corner r = ri + 2 rj); with `sublattice`, the counts
+    per sublattice s (last axis of 2)."""
     import numpy as np
     S = masks.shape[0]
     keep = 1 - masks.reshape(S, N, N, 2)
-    fine = keep.reshape(S, -1).sum(1)
+    fine = keep.reshape(S, -1, 2).sum(1) if sublattice else keep.reshape(S, -1).sum(1)
     h = N // 2
     corners = []
     for r in range(4):
         ri, rj = r % 2, r // 2
-        corners.append(keep[:, rj * h:(rj + 1) * h, ri * h:(ri + 1) * h, :].reshape(S, -1).sum(1))
+        blk = keep[:, rj * h:(rj + 1) * h, ri * h:(ri + 1) * h, :]
+        corners.append(blk.reshape(S, -1, 2).sum(1) if sublattice else blk.reshape(S, -1).sum(1))
     return fine, np.stack(corners, 1)
+
+
+def gk_flops(nAB):
+    """Real flops of the Golub-Kahan bidiagonalisation of graphene's q x p
+    sublattice block (p = min(n_A, n_B), q = max) as the warp kernel does it:
+    per left reflector j the dot and the update over rows j .. q-1 of columns
+    j+1 .. p-1, per right reflector the row products and the update over rows
+    j+1 .. q-1 of the same columns, 8 flops per complex multiply-add."""
+    import numpy as np
+    nAB = np.asarray(nAB).reshape(-1, 2)
+    total = 0.0
+    pairs, counts = np.unique(np.sort(nAB, axis=1), axis=0, return_counts=True)
+    for (p, q), c in zip(pairs, counts):
+        j = np.arange(int(p), dtype=np.float64)
+        total += c * float(np.sum(16.0 * ((q - j) * (p - 1 - j) + (q - 1 - j) * (p - 1 - j))))
+    return total
 
 
 # Kernel families of the library's profiler and what bounds each one:
@@ -189,7 +207,9 @@ FAMILIES = {"k_small_tridiag": "alu", "k_ts_panel": "alu", "k_ts_w": "tensor", "
 def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16):
     """Exact algorithmic work of one step from the samples' kept-site counts,
     per kernel family (flops, or bytes for the HBM-bound families):
-    - k_small_tridiag: Householder reduction, 16/3 n^3 real flops per matrix;
+    - k_small_tridiag: graphene n <= 32: the Golub-Kahan bidiagonalisation of
+      the sublattice block (gk_flops); larger n: Householder tridiagonal
+      reduction, 16/3 n^3 real flops per matrix;
     - per stage-1 panel of bw columns with m rows below it (float32 complex,
       8 bytes per entry): panel QR 8 m bw^2 flops, W = A22 (Y T) 8 m^2 bw
       flops, Z = W - 1/2 Y (T^H M) 4 bw m x 8 bytes (W and Y twice read, Z
@@ -204,12 +224,16 @@ def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16
     import numpy as np
     work = {k: 0.0 for k in FAMILIES}
 
-    def add(n_arr, K2, big):
+    def add(n_ab, K2, big, n_sites):
+        n_arr = n_ab.sum(-1)
         n = n_arr.astype(np.float64)
         work["k_bisect"] += K2 * float(np.sum(4.0 * refine * n ** 2))
         work["k_idos"] += float(np.sum(8.0 * K2 * n + 8.0 * n_E))
         if not big:
-            work["k_small_tridiag"] += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
+            if n_sites <= 32:
+                work["k_small_tridiag"] += K2 * gk_flops(n_ab)
+            else:
+                work["k_small_tridiag"] += K2 * float(np.sum(16.0 / 3.0 * n ** 3))
             return
         for nn in n_arr:
             nn = int(nn)
@@ -225,11 +249,11 @@ def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16
         if not M[l]:
             continue
         masks = m.vacancy_masks(N, l, seed, firsts[l], M[l])
-        fine, corners = n_act_of(masks, N)
-        add(fine, K * K, 2 * N * N > 160)
+        fine, corners = n_act_of(masks, N, sublattice=True)
+        add(fine, K * K, 2 * N * N > 160, 2 * N * N)
         if l > 0:
             Kc = levels[l - 1][1]
-            add(corners.reshape(-1), Kc * Kc, 2 * (N // 2) ** 2 > 160)
+            add(corners.reshape(-1, 2), Kc * Kc, 2 * (N // 2) ** 2 > 160, 2 * (N // 2) ** 2)
     return work
 
 

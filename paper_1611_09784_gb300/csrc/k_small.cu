@@ -289,6 +289,210 @@ __device__ __forceinline__ float2 pend_update(float2 a, float4 pv, float4 pw, fl
   return a;
 }
 
+// ------------------------------------------ graphene: bidiagonal form --
+// Graphene's H(k) in the basis (A sites, B sites) is eps I + [[0, T], [T^H,
+// 0]]: the nearest-neighbour hopping of Sec. 3.1 couples only the two
+// sublattices, and vacancies remove sites without breaking that.  Its
+// eigenvalues are eps +- sigma_i(T) and, when the sublattices keep different
+// numbers of sites, |n_A - n_B| more at eps.  The q x p block M between them
+// (p = min(n_A, n_B) columns, q = max(n_A, n_B) rows, M[r][c] = H[row site
+// r][column site c]) is reduced to upper bidiagonal form (diagonal a_j,
+// superdiagonal b_j) by Householder reflectors applied from the left (column
+// j) and from the right (row j) in turn (Golub-Kahan).  The tridiagonal with
+// diagonal eps and off-diagonals |a_0|, |b_0|, |a_1|, ..., |a_{p-1}|, followed
+// by q - p decoupled rows at eps, has exactly the eigenvalues of H(k): the
+// output is its (d, e^2).  The reflectors' backward error is float32 eps |M|,
+// as for the full reduction, for about a quarter of its flops.  One half-warp
+// per matrix (n <= 32, so p, q <= 16): lane c holds column c of M in
+// registers; a left reflector's vector lives in one lane and is broadcast,
+// a right reflector's row products are summed by a reduce-scatter over the
+// 16 lanes and gathered back.
+// Every operation below is an explicitly rounded intrinsic: the function is
+// inlined into two kernels (per cell set and persistent), and free FMA
+// contraction could round them differently; pinned, both routes give the
+// same bits.
+__device__ __forceinline__ float2 cmul_f(float2 a, float2 b) {
+  return f2(__fmaf_rn(a.x, b.x, __fmul_rn(-a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 cjmul_f(float2 a, float2 b) {   // conj(a) b
+  return f2(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(-a.y, b.x)));
+}
+__device__ __forceinline__ float2 cadd_f(float2 a, float2 b) { return f2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 csub_f(float2 a, float2 b) { return f2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+__device__ __forceinline__ float cabs2_f(float2 a, float acc) { return __fmaf_rn(a.x, a.x, __fmaf_rn(a.y, a.y, acc)); }
+// Householder scalars for x = (alpha, rest): sigma = |x| (sigma2 = |x|^2),
+// phs = alpha / |alpha| (1 for alpha = 0), tau = 1 / (sigma (sigma + |alpha|));
+// v = x + phs sigma e_1 maps x to -phs sigma e_1.
+__device__ __forceinline__ void gk_reflector(float2 al, float sigma2, float& sigma, float2& phs, float& tau) {
+  const float s = fmaxf(fabsf(al.x), fabsf(al.y));
+  float aa = 0.f;
+  phs = f2(1.f, 0.f);
+  if (s > 0.f) {
+    const float up = s < 0x1p-64f ? 0x1p64f : 1.f;
+    const float rs = __frcp_rn(__fmul_rn(s, up));
+    const float ax = __fmul_rn(__fmul_rn(al.x, up), rs), ay = __fmul_rn(__fmul_rn(al.y, up), rs);
+    const float q = __fmaf_rn(ax, ax, __fmul_rn(ay, ay));
+    const float rq = rsqrtf(q);
+    phs = f2(__fmul_rn(ax, rq), __fmul_rn(ay, rq));
+    aa = __fmul_rn(s, __fmul_rn(q, rq));
+  }
+  sigma = __fmul_rn(sigma2, rsqrtf(sigma2));
+  tau = __fdividef(1.f, __fmul_rn(sigma, __fadd_rn(sigma, aa)));
+}
+
+__device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase, const int* __restrict__ n_act_cell,
+                                              const int* __restrict__ act, const int* __restrict__ inv, int N, int K,
+                                              int n_max, int64_t mat, double t_hop, double eps,
+                                              float* __restrict__ d_out, float* __restrict__ e2_out) {
+  const int K2 = K * K;
+  const int64_t cell = mat / K2;
+  const int kidx = (int)(mat - cell * K2);
+  const int n = n_act_cell[cell];
+  float* dO = d_out + mat * n_max;
+  float* eO = e2_out + mat * n_max;
+  if (n <= 0) return;
+  const int n_sites = 2 * N * N;
+  const int* ac = act + cell * n_sites;
+  const int* iv = inv + cell * n_sites;
+  // sublattice masks over the active indices (site parity 0: A, 1: B)
+  const bool isA0 = hl < n && (ac[hl] & 1) == 0;
+  const bool isA1 = hl + 16 < n && (ac[hl + 16] & 1) == 0;
+  const unsigned lo = (__ballot_sync(hmask, isA0) >> hbase) & 0xFFFFu;
+  const unsigned hi = (__ballot_sync(hmask, isA1) >> hbase) & 0xFFFFu;
+  const unsigned live = n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  const unsigned maskA = lo | (hi << 16), maskB = live & ~maskA;
+  const int nA = __popc(maskA), nB = n - nA;
+  const unsigned colm = nA >= nB ? maskB : maskA, rowm = live & ~colm;
+  const int p = min(nA, nB), q = n - p;
+  // column hl of M from the three bonds of its site (a bond to a removed
+  // site is dropped; bonds to the same site add up)
+  float2 m[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) m[r] = f2(0.f, 0.f);
+  if (hl < p) {
+    unsigned mm = colm;
+    for (int t = 0; t < hl; ++t) mm &= mm - 1u;
+    const int ic = __ffs(mm) - 1;
+    int nb[3];
+    bool fromB;
+    graphene_neighbours(N, ac[ic], nb, fromB);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int ai = iv[nb[b]];
+      if (ai >= 0 && ((rowm >> ai) & 1u)) {
+        const int rw = __popc(rowm & ((1u << ai) - 1u));
+        const float2 ph = graphene_phase_f(N, K, kidx, b);
+        const float hx = __fmul_rn((float)t_hop, ph.x), hy = __fmul_rn((float)t_hop, ph.y);
+        const float2 hv = fromB ? f2(hx, hy) : f2(hx, -hy);   // H[row site][column site]
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          if (r == rw) m[r] = cadd_f(m[r], hv);
+      }
+    }
+  }
+  for (int j = 0; j < p; ++j) {
+    // left reflector from column j (lane j), rows j .. q-1
+    float rest = 0.f;
+    float2 al = f2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      if (r == j) al = m[r];
+      if (r > j && r < q) rest = cabs2_f(m[r], rest);
+    }
+    rest = __shfl_sync(hmask, rest, hbase + j);
+    al.x = __shfl_sync(hmask, al.x, hbase + j);
+    al.y = __shfl_sync(hmask, al.y, hbase + j);
+    const float sa = cabs2_f(al, rest);
+    if (hl == 0) eO[2 * j] = sa;
+    if (rest > 1e-30f) {
+      float sigma, tau;
+      float2 phs;
+      gk_reflector(al, sa, sigma, phs, tau);
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const float vx = __shfl_sync(hmask, m[r].x, hbase + j), vy = __shfl_sync(hmask, m[r].y, hbase + j);
+        v[r] = r == j ? f2(__fmaf_rn(phs.x, sigma, al.x), __fmaf_rn(phs.y, sigma, al.y))
+                      : (r > j && r < q ? f2(vx, vy) : f2(0.f, 0.f));
+      }
+      if (hl > j && hl < p) {
+        float2 s0 = f2(0.f, 0.f), s1 = s0;
+#pragma unroll
+        for (int r = 0; r < 16; r += 2) {
+          s0 = cadd_f(s0, cjmul_f(v[r], m[r]));
+          s1 = cadd_f(s1, cjmul_f(v[r + 1], m[r + 1]));
+        }
+        const float2 sm = cadd_f(s0, s1);
+        const float2 s = f2(__fmul_rn(sm.x, tau), __fmul_rn(sm.y, tau));
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          m[r] = csub_f(m[r], cmul_f(v[r], s));
+        }
+      }
+    }
+    if (j + 1 >= p) break;
+    // right reflector from row j, columns j+1 .. p-1 (lane c holds M[j][c]):
+    // z = conj(row), H z = beta e_{j+1}, then M <- M H on rows j+1 .. q-1
+    float2 mj = f2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+      if (r == j) mj = m[r];
+    const float2 z = (hl > j && hl < p) ? f2(mj.x, -mj.y) : f2(0.f, 0.f);
+    float rz = hl > j + 1 ? cabs2_f(z, 0.f) : 0.f;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) rz = __fadd_rn(rz, __shfl_xor_sync(hmask, rz, o));
+    float2 az;
+    az.x = __shfl_sync(hmask, z.x, hbase + j + 1);
+    az.y = __shfl_sync(hmask, z.y, hbase + j + 1);
+    const float sb = cabs2_f(az, rz);
+    if (hl == 0) eO[2 * j + 1] = sb;
+    if (rz > 1e-30f) {
+      float sigma, tau;
+      float2 phs;
+      gk_reflector(az, sb, sigma, phs, tau);
+      const float2 u = hl == j + 1 ? f2(__fmaf_rn(phs.x, sigma, az.x), __fmaf_rn(phs.y, sigma, az.y)) : z;
+      // x_r = sum_c M[r][c] u_c: reduce-scatter (lane hl ends with row hl)
+      float2 k8[8];
+      const bool b3 = (hl & 8) != 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float2 plo = (t > j && t < q) ? cmul_f(m[t], u) : f2(0.f, 0.f);
+        const float2 phi = (t + 8 > j && t + 8 < q) ? cmul_f(m[t + 8], u) : f2(0.f, 0.f);
+        const float2 snd = b3 ? plo : phi, kp = b3 ? phi : plo;
+        k8[t] = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 8), __shfl_xor_sync(hmask, snd.y, 8)));
+      }
+      float2 k4[4];
+      const bool b2 = (hl & 4) != 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float2 snd = b2 ? k8[t] : k8[t + 4], kp = b2 ? k8[t + 4] : k8[t];
+        k4[t] = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 4), __shfl_xor_sync(hmask, snd.y, 4)));
+      }
+      float2 k2[2];
+      const bool b1 = (hl & 2) != 0;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const float2 snd = b1 ? k4[t] : k4[t + 2], kp = b1 ? k4[t + 2] : k4[t];
+        k2[t] = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 2), __shfl_xor_sync(hmask, snd.y, 2)));
+      }
+      const bool b0 = (hl & 1) != 0;
+      const float2 snd = b0 ? k2[0] : k2[1], kp = b0 ? k2[1] : k2[0];
+      const float2 X = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 1), __shfl_xor_sync(hmask, snd.y, 1)));
+      const float2 tu = f2(__fmul_rn(tau, u.x), __fmul_rn(-tau, u.y));   // tau conj(u_c)
+      const bool col = hl > j && hl < p;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const float2 x = f2(__shfl_sync(hmask, X.x, hbase + r), __shfl_sync(hmask, X.y, hbase + r));
+        if (col && r > j && r < q) {
+          m[r] = csub_f(m[r], cmul_f(x, tu));
+        }
+      }
+    }
+  }
+  for (int r = hl; r < n; r += 16) dO[r] = (float)eps;
+  for (int r = max(0, 2 * p - 1) + hl; r < n - 1; r += 16) eO[r] = 0.f;
+}
+
 __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane, const int* __restrict__ n_act_cell,
                                                        const int* __restrict__ act, const int* __restrict__ inv,
                                                        int N, int K, int n_max, int64_t mat, double t_hop,
@@ -644,6 +848,15 @@ k_small_tridiag_reg(const int* __restrict__ n_act_cell, const int* __restrict__ 
                     float* __restrict__ d_out, float* __restrict__ e2_out) {
   __shared__ WarpRegSlot slots[kRegWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!Hin) {
+    // graphene cells: one matrix per half-warp, bidiagonal form
+    const int half = lane >> 4;
+    const int64_t mat = ((int64_t)blockIdx.x * kRegWarps + warp) * 2 + half;
+    if (mat >= n_mat) return;   // the half-warp leaves together
+    small_gk_half(lane & 15, 0xFFFFu << (16 * half), 16 * half, n_act_cell, act, inv, N, K, n_max, mat, t_hop, eps,
+                  d_out, e2_out);
+    return;
+  }
   const int64_t mat = (int64_t)blockIdx.x * kRegWarps + warp;
   if (mat >= n_mat) return;   // whole warp leaves together
   small_tridiag_warp_reg(&slots[warp], lane, n_act_cell, act, inv, N, K, n_max, mat, t_hop, eps, Hin, d_out, e2_out);
@@ -954,20 +1167,21 @@ constexpr int kPWarpCta = 16;   // warps per CTA of the warp-item launch (one CT
 
 __global__ void __launch_bounds__(32 * kPWarpCta)
 k_small_persistent_warps(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
-  __shared__ WarpRegSlot slots[kPWarpCta];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // each half-warp takes matrices from the list on its own (bidiagonal form)
+  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const unsigned hmask = 0xFFFFu << (16 * half);
   for (;;) {
     long long it = 0;
-    if (lane == 0) it = (long long)atomicAdd(&ctr[1], 1ull);
-    it = __shfl_sync(0xffffffffu, it, 0);
+    if (hl == 0) it = (long long)atomicAdd(&ctr[1], 1ull);
+    it = __shfl_sync(hmask, it, 16 * half);
     if (it >= w.total_warp) break;
     int g = w.n_cta;
     while (g + 1 < w.n_seg && it >= w.end[g]) ++g;
     const SmallSeg& sg = w.seg[g];
     const int64_t mat = it - (g > w.n_cta ? w.end[g - 1] : 0);
-    small_tridiag_warp_reg(&slots[warp], lane, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps,
-                           nullptr, sg.d, sg.e2);
-    __syncwarp();
+    small_gk_half(hl, hmask, 16 * half, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps, sg.d,
+                  sg.e2);
+    __syncwarp(hmask);
   }
 }
 
@@ -1040,7 +1254,7 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
   }
   if (w.total_warp > 0) {
     // one 16-warp CTA per SM (the register-resident reduction's occupancy)
-    const int64_t ctas_w = (w.total_warp + kPWarpCta - 1) / kPWarpCta;
+    const int64_t ctas_w = (w.total_warp + 2 * kPWarpCta - 1) / (2 * kPWarpCta);   // two matrices per warp
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_grid, ctas_w));
     ProfScope ps(KID_SMALL_TRIDIAG, s);
     k_small_persistent_warps<<<grid, 32 * kPWarpCta, 0, s>>>(w, t, eps, counters);
@@ -1062,7 +1276,8 @@ bool small_path_fits(int precision, int n_max) {
 
 int run_small_reg(const SolveArgs& a) {
   const CellSet* c = a.cells;
-  const int64_t blocks = (a.n_mat + kRegWarps - 1) / kRegWarps;
+  const int per = a.H ? kRegWarps : 2 * kRegWarps;   // cell sets: one matrix per half-warp
+  const int64_t blocks = (a.n_mat + per - 1) / per;
   ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
   k_small_tridiag_reg<<<(unsigned)blocks, 32 * kRegWarps, 0, a.stream>>>(
       c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside, a.n_max, a.n_mat,
