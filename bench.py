@@ -182,7 +182,7 @@ def n_act_of(masks, N, sublattice=False):
 
 def gk_flops(nAB):
     """Real flops of the Golub-Kahan bidiagonalisation of graphene's q x p
-    sublattice block (p = min(n_A, n_B), q = max) as the warp kernel does it:
+    sublattice block (p = min(n_A, n_B), q = max) as the kernels do it:
     per left reflector j the dot and the update over rows j .. q-1 of columns
     j+1 .. p-1, per right reflector the row products and the update over rows
     j+1 .. q-1 of the same columns, 8 flops per complex multiply-add."""
@@ -207,9 +207,9 @@ FAMILIES = {"k_small_tridiag": "alu", "k_ts_panel": "alu", "k_ts_w": "tensor", "
 def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16):
     """Exact algorithmic work of one step from the samples' kept-site counts,
     per kernel family (flops, or bytes for the HBM-bound families):
-    - k_small_tridiag: graphene n <= 32: the Golub-Kahan bidiagonalisation of
-      the sublattice block (gk_flops); larger n: Householder tridiagonal
-      reduction, 16/3 n^3 real flops per matrix;
+    - k_small_tridiag: graphene n <= 128: the Golub-Kahan bidiagonalisation
+      of the sublattice block (gk_flops); otherwise the Householder
+      tridiagonal reduction, 16/3 n^3 real flops per matrix;
     - per stage-1 panel of bw columns with m rows below it (float32 complex,
       8 bytes per entry): panel QR 8 m bw^2 flops, W = A22 (Y T) 8 m^2 bw
       flops, Z = W - 1/2 Y (T^H M) 4 bw m x 8 bytes (W and Y twice read, Z
@@ -230,7 +230,7 @@ def algorithmic_work(m, levels, M, seed, firsts, refine=REFINE64, n_E=201, bw=16
         work["k_bisect"] += K2 * float(np.sum(4.0 * refine * n ** 2))
         work["k_idos"] += float(np.sum(8.0 * K2 * n + 8.0 * n_E))
         if not big:
-            if n_sites <= 32:
+            if n_sites <= 128:
                 work["k_small_tridiag"] += K2 * gk_flops(n_ab)
             else:
                 work["k_small_tridiag"] += K2 * float(np.sum(16.0 / 3.0 * n ** 3))

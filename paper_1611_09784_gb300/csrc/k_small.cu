@@ -493,6 +493,231 @@ __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase,
   for (int r = max(0, 2 * p - 1) + hl; r < n - 1; r += 16) eO[r] = 0.f;
 }
 
+// The same Golub-Kahan reduction for 32 < n <= 128 (graphene N = 5 .. 8, so
+// p, q <= 64): 64 threads per matrix, thread c holding column c of M (64
+// complex registers).  Per j: the owner of column j publishes its entries as
+// the left reflector's vector (shared, double-buffered by the parity of j;
+// one barrier), every later column takes its dot and update against it; the
+// right reflector's norm is two warp reductions combined in shared memory,
+// its row products are summed over each warp by a reduce-scatter (rows in
+// two halves of 32, lane l ending with row 32 h + l) and the two warps' sums
+// added when read back (two more barriers).  Rows outside (j, q) are skipped
+// in 4-row chunks by branches uniform over the CTA.  About 170 registers per
+// thread, so several matrices share an SM (the tridiagonal register CTA holds
+// one 128 x 128 matrix per SM).
+constexpr int kGkT = 64;           // threads per matrix of the CTA variant
+constexpr int kGkCtasPerSm = 5;    // resident CTAs per SM it is compiled for (at most 204 registers)
+struct GkCtaSlot {
+  float2 v[2][64];    // left reflector's vector, by the parity of j
+  float2 xw[2][64];   // right reflector: per-warp row sums
+  float2 al[2];       // left: alpha, by parity
+  float rest[2];      // left: |rows below alpha|^2, by parity
+  float red[2];       // right: per-warp partial norms
+  float2 az;          // right: alpha
+  unsigned words[4];  // sublattice A bits of the active indices
+};
+
+__device__ __forceinline__ float2 rs_level(float2 lo, float2 hi, bool bit, int off) {
+  const float2 snd = bit ? lo : hi, kp = bit ? hi : lo;
+  return cadd_f(kp, f2(__shfl_xor_sync(0xffffffffu, snd.x, off), __shfl_xor_sync(0xffffffffu, snd.y, off)));
+}
+
+__device__ __forceinline__ void small_gk_cta(GkCtaSlot* sl, const int* __restrict__ n_act_cell,
+                                             const int* __restrict__ act, const int* __restrict__ inv, int N, int K,
+                                             int n_max, int64_t mat, double t_hop, double eps,
+                                             float* __restrict__ d_out, float* __restrict__ e2_out) {
+  const int c = threadIdx.x, warp = c >> 5, lane = c & 31;
+  const int K2 = K * K;
+  const int64_t cell = mat / K2;
+  const int kidx = (int)(mat - cell * K2);
+  const int n = n_act_cell[cell];
+  float* dO = d_out + mat * n_max;
+  float* eO = e2_out + mat * n_max;
+  if (n <= 0) return;   // uniform over the CTA
+  const int n_sites = 2 * N * N;
+  const int* ac = act + cell * n_sites;
+  const int* iv = inv + cell * n_sites;
+  // sublattice words: thread c covers active indices c and c + 64
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int idx = c + 64 * k;
+    const unsigned b = __ballot_sync(0xffffffffu, idx < n && (ac[min(idx, n_sites - 1)] & 1) == 0);
+    if (lane == 0) sl->words[2 * k + warp] = b;
+  }
+  __syncthreads();
+  unsigned colm[4], rowm[4];
+  int nA = 0;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) nA += __popc(sl->words[w]);
+  const int nB = n - nA;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const int cnt = min(32, max(0, n - 32 * w));
+    const unsigned live = cnt >= 32 ? 0xFFFFFFFFu : ((1u << cnt) - 1u);
+    const unsigned mA = sl->words[w];
+    colm[w] = nA >= nB ? (live & ~mA) : mA;
+    rowm[w] = live & ~colm[w];
+  }
+  const int p = min(nA, nB), q = n - p;
+  float2 m[64];
+#pragma unroll
+  for (int r = 0; r < 64; ++r) m[r] = f2(0.f, 0.f);
+  if (c < p) {
+    int ic = -1, cum = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int pc = __popc(colm[w]);
+      if (ic < 0 && c < cum + pc) {
+        unsigned mm = colm[w];
+        for (int t = 0; t < c - cum; ++t) mm &= mm - 1u;
+        ic = 32 * w + __ffs(mm) - 1;
+      }
+      cum += pc;
+    }
+    int nb[3];
+    bool fromB;
+    graphene_neighbours(N, ac[ic], nb, fromB);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int ai = iv[nb[b]];
+      if (ai >= 0 && ((rowm[ai >> 5] >> (ai & 31)) & 1u)) {
+        int rw = __popc(rowm[ai >> 5] & ((1u << (ai & 31)) - 1u));
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+          if (w < (ai >> 5)) rw += __popc(rowm[w]);
+        const float2 ph = graphene_phase_f(N, K, kidx, b);
+        const float hx = __fmul_rn((float)t_hop, ph.x), hy = __fmul_rn((float)t_hop, ph.y);
+        const float2 hv = fromB ? f2(hx, hy) : f2(hx, -hy);
+#pragma unroll
+        for (int r = 0; r < 64; ++r)
+          if (r == rw) m[r] = cadd_f(m[r], hv);
+      }
+    }
+  }
+  for (int j = 0; j < p; ++j) {
+    const int bf = j & 1;
+    // left reflector from column j (thread j), rows j .. q-1
+    if (c == j) {
+      float rest = 0.f;
+      float2 al = f2(0.f, 0.f);
+#pragma unroll
+      for (int rb = 0; rb < 16; ++rb) {
+        if (4 * rb + 3 < j || 4 * rb >= q) continue;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = 4 * rb + t;
+          if (r == j) al = m[r];
+          if (r > j && r < q) {
+            rest = cabs2_f(m[r], rest);
+            sl->v[bf][r] = m[r];
+          }
+        }
+      }
+      sl->al[bf] = al;
+      sl->rest[bf] = rest;
+    }
+    __syncthreads();
+    const float2 al = sl->al[bf];
+    const float rest = sl->rest[bf];
+    const float sa = cabs2_f(al, rest);
+    if (c == 0) eO[2 * j] = sa;
+    if (rest > 1e-30f) {
+      float sigma, tau;
+      float2 phs;
+      gk_reflector(al, sa, sigma, phs, tau);
+      const float2 vj = f2(__fmaf_rn(phs.x, sigma, al.x), __fmaf_rn(phs.y, sigma, al.y));
+      if (c > j && c < p) {
+        float2 s0 = f2(0.f, 0.f), s1 = s0;
+#pragma unroll
+        for (int rb = 0; rb < 16; ++rb) {
+          if (4 * rb + 3 < j || 4 * rb >= q) continue;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int r = 4 * rb + t;
+            if (r == j) s0 = cadd_f(s0, cjmul_f(vj, m[r]));
+            else if (r > j && r < q) {
+              if (t & 1) s1 = cadd_f(s1, cjmul_f(sl->v[bf][r], m[r]));
+              else s0 = cadd_f(s0, cjmul_f(sl->v[bf][r], m[r]));
+            }
+          }
+        }
+        const float2 sm = cadd_f(s0, s1);
+        const float2 s = f2(__fmul_rn(sm.x, tau), __fmul_rn(sm.y, tau));
+#pragma unroll
+        for (int rb = 0; rb < 16; ++rb) {
+          if (4 * rb + 3 < j || 4 * rb >= q) continue;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int r = 4 * rb + t;
+            if (r == j) m[r] = csub_f(m[r], cmul_f(vj, s));
+            else if (r > j && r < q) m[r] = csub_f(m[r], cmul_f(sl->v[bf][r], s));
+          }
+        }
+      }
+    }
+    if (j + 1 >= p) break;
+    // right reflector from row j, columns j+1 .. p-1, applied to rows j+1 .. q-1
+    float2 mj = f2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 64; ++r)
+      if (r == j) mj = m[r];
+    const float2 z = (c > j && c < p) ? f2(mj.x, -mj.y) : f2(0.f, 0.f);
+    float rz = (c > j + 1 && c < p) ? cabs2_f(z, 0.f) : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rz = __fadd_rn(rz, __shfl_xor_sync(0xffffffffu, rz, o));
+    if (lane == 0) sl->red[warp] = rz;
+    if (c == j + 1) sl->az = z;
+    __syncthreads();
+    const float rzt = __fadd_rn(sl->red[0], sl->red[1]);
+    const float2 az = sl->az;
+    const float sb = cabs2_f(az, rzt);
+    if (c == 0) eO[2 * j + 1] = sb;
+    if (rzt > 1e-30f) {
+      float sigma, tau;
+      float2 phs;
+      gk_reflector(az, sb, sigma, phs, tau);
+      const float2 u = c == j + 1 ? f2(__fmaf_rn(phs.x, sigma, az.x), __fmaf_rn(phs.y, sigma, az.y)) : z;
+#pragma unroll
+      for (int H = 0; H < 2; ++H) {
+        if (32 * H + 31 <= j || 32 * H >= q) continue;
+        float2 k16[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int rl = 32 * H + t, rh = rl + 16;
+          const float2 plo = (rl > j && rl < q) ? cmul_f(m[rl], u) : f2(0.f, 0.f);
+          const float2 phi = (rh > j && rh < q) ? cmul_f(m[rh], u) : f2(0.f, 0.f);
+          k16[t] = rs_level(plo, phi, (lane & 16) != 0, 16);
+        }
+        float2 k8[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) k8[t] = rs_level(k16[t], k16[t + 8], (lane & 8) != 0, 8);
+        float2 k4[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) k4[t] = rs_level(k8[t], k8[t + 4], (lane & 4) != 0, 4);
+        float2 k2[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) k2[t] = rs_level(k4[t], k4[t + 2], (lane & 2) != 0, 2);
+        sl->xw[warp][32 * H + lane] = rs_level(k2[0], k2[1], (lane & 1) != 0, 1);
+      }
+      __syncthreads();
+      if (c > j && c < p) {
+        const float2 tu = f2(__fmul_rn(tau, u.x), __fmul_rn(-tau, u.y));   // tau conj(u_c)
+#pragma unroll
+        for (int rb = 0; rb < 16; ++rb) {
+          if (4 * rb + 3 <= j || 4 * rb >= q) continue;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int r = 4 * rb + t;
+            if (r > j && r < q) m[r] = csub_f(m[r], cmul_f(cadd_f(sl->xw[0][r], sl->xw[1][r]), tu));
+          }
+        }
+      }
+    }
+  }
+  for (int r = c; r < n; r += kGkT) dO[r] = (float)eps;
+  for (int r = max(0, 2 * p - 1) + c; r < n - 1; r += kGkT) eO[r] = 0.f;
+}
+
 __device__ __forceinline__ void small_tridiag_warp_reg(WarpRegSlot* sl, int lane, const int* __restrict__ n_act_cell,
                                                        const int* __restrict__ act, const int* __restrict__ inv,
                                                        int N, int K, int n_max, int64_t mat, double t_hop,
@@ -840,6 +1065,14 @@ k_small_tridiag_ctareg(const int* __restrict__ n_act_cell, const int* __restrict
 }
 
 constexpr int kCtaRpt = 64;   // rows per thread of the register CTA reduction (256 threads; 32 rows per thread was slower)
+
+// graphene cell sets with 32 < n <= 128: one matrix per 64-thread CTA
+__global__ void __launch_bounds__(kGkT, kGkCtasPerSm)
+k_small_gk_cta(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv, int N,
+               int K, int n_max, double t_hop, double eps, float* __restrict__ d_out, float* __restrict__ e2_out) {
+  __shared__ GkCtaSlot slot;
+  small_gk_cta(&slot, n_act_cell, act, inv, N, K, n_max, blockIdx.x, t_hop, eps, d_out, e2_out);
+}
 constexpr int kRegWarps = 4;   // warps (matrices) per CTA of k_small_tridiag_reg
 
 __global__ void __launch_bounds__(32 * kRegWarps)
@@ -1138,11 +1371,11 @@ k_small_persistent(const PersistWork w, double t_hop, double eps, unsigned long 
   }
 }
 
-// The 32 < n <= 128 matrices, one per 256-thread CTA item (register-resident
-// reduction), taken in descending n by whichever CTA is free.
-__global__ void __launch_bounds__(CtaRegSlot<kCtaRpt>::kThreads, 1)
+// The 32 < n <= 128 matrices, one per 64-thread CTA item (bidiagonal form),
+// taken in descending n by whichever CTA is free.
+__global__ void __launch_bounds__(kGkT, kGkCtasPerSm)
 k_small_persistent_cr(const PersistWork w, double t_hop, double eps, unsigned long long* __restrict__ ctr) {
-  __shared__ CtaRegSlot<kCtaRpt> slot;
+  __shared__ GkCtaSlot slot;
   __shared__ long long s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr[2], 1ull);
@@ -1153,8 +1386,7 @@ k_small_persistent_cr(const PersistWork w, double t_hop, double eps, unsigned lo
     while (g + 1 < w.n_cta && it >= w.end[g]) ++g;
     const SmallSeg& sg = w.seg[g];
     const int64_t mat = it - (g > w.n_big ? w.end[g - 1] : 0);
-    small_tridiag_cta_reg(&slot, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps, nullptr,
-                          sg.d, sg.e2);
+    small_gk_cta(&slot, sg.n_act, sg.act, sg.inv, sg.N, sg.Kside, sg.n_max, mat, t_hop, eps, sg.d, sg.e2);
     __syncthreads();   // s_item and the slot are reused
   }
 }
@@ -1240,9 +1472,9 @@ int solve_small_persistent(const SmallSeg* segs, int n_segs, double t, double ep
   const int sm_grid = std::max(1, (ctas > 0 ? std::min(ctas, sms) : sms) - std::max(0, reserve));
   IDOS_CUDA_TRY(cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), s));
   if (w.total_cta > 0) {
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_grid, w.total_cta));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_grid * kGkCtasPerSm, w.total_cta));
     ProfScope ps(KID_SMALL_TRIDIAG, s);
-    k_small_persistent_cr<<<grid, CtaRegSlot<kCtaRpt>::kThreads, 0, s>>>(w, t, eps, counters);
+    k_small_persistent_cr<<<grid, kGkT, 0, s>>>(w, t, eps, counters);
     IDOS_CHECK_LAUNCH();
   }
   if (w.total_big > 0) {
@@ -1289,6 +1521,14 @@ int run_small_reg(const SolveArgs& a) {
 int run_small_ctareg(const SolveArgs& a) {
   const CellSet* c = a.cells;
   ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
+  if (!a.H && c) {
+    // graphene cells: bidiagonal form, 64 threads per matrix
+    k_small_gk_cta<<<(unsigned)a.n_mat, kGkT, 0, a.stream>>>(c->n_act, c->act, c->inv, c->N, a.Kside, a.n_max,
+                                                              a.t, a.eps, reinterpret_cast<float*>(a.d),
+                                                              reinterpret_cast<float*>(a.e2));
+    IDOS_CHECK_LAUNCH();
+    return IDOS_OK;
+  }
   k_small_tridiag_ctareg<kCtaRpt><<<(unsigned)a.n_mat, CtaRegSlot<kCtaRpt>::kThreads, 0, a.stream>>>(
       c ? c->n_act : nullptr, c ? c->act : nullptr, c ? c->inv : nullptr, c ? c->N : 0, a.Kside, a.n_max, a.n_mat,
       a.t, a.eps, a.H, reinterpret_cast<float*>(a.d), reinterpret_cast<float*>(a.e2));
