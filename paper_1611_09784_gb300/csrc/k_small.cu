@@ -495,32 +495,29 @@ __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase,
 
 // The same Golub-Kahan reduction for 32 < n <= 128 (graphene N = 5 .. 8, so
 // p, q <= 64): 64 threads per matrix, thread c holding column c of M (64
-// complex registers).  Per j: the owner of column j publishes its entries as
-// the left reflector's vector (shared, double-buffered by the parity of j;
-// one barrier), every later column takes its dot and update against it; the
-// right reflector's norm is two warp reductions combined in shared memory,
-// its row products are summed over each warp by a reduce-scatter (rows in
-// two halves of 32, lane l ending with row 32 h + l) and the two warps' sums
-// added when read back (two more barriers).  Rows outside (j, q) are skipped
-// in 4-row chunks by branches uniform over the CTA.  About 170 registers per
-// thread, so several matrices share an SM (the tridiagonal register CTA holds
-// one 128 x 128 matrix per SM).
+// complex registers).  Per j: the owner of column j publishes the left
+// reflector's vector in shared memory (double-buffered by the parity of j;
+// one barrier) and every later column takes its dot and update against it
+// (four float32 FMAs per row each);
+// the right reflector's norm is two warp reductions combined in shared
+// memory; its row products are written to a 64 x 65 shared array (column c
+// writes its rows, thread r then sums row r over the live columns) and read
+// back per row (three more barriers).  Rows outside (j, q) are skipped in
+// 4-row chunks by branches uniform over the CTA.  About 170 registers and 36
+// KB of shared memory per matrix: six matrices share an SM (the tridiagonal
+// register CTA holds one 128 x 128 matrix per SM).
 constexpr int kGkT = 64;           // threads per matrix of the CTA variant
-constexpr int kGkCtasPerSm = 5;    // resident CTAs per SM it is compiled for (at most 204 registers)
+constexpr int kGkCtasPerSm = 6;    // resident CTAs per SM it is compiled for (at most 170 registers)
 struct GkCtaSlot {
   float2 v[2][64];    // left reflector's vector, by the parity of j
-  float2 xw[2][64];   // right reflector: per-warp row sums
+  float2 P[64][65];   // right reflector: row products P[r][c] (padded against bank conflicts)
+  float2 X[64];       // right reflector: row sums
   float2 al[2];       // left: alpha, by parity
   float rest[2];      // left: |rows below alpha|^2, by parity
   float red[2];       // right: per-warp partial norms
   float2 az;          // right: alpha
   unsigned words[4];  // sublattice A bits of the active indices
 };
-
-__device__ __forceinline__ float2 rs_level(float2 lo, float2 hi, bool bit, int off) {
-  const float2 snd = bit ? lo : hi, kp = bit ? hi : lo;
-  return cadd_f(kp, f2(__shfl_xor_sync(0xffffffffu, snd.x, off), __shfl_xor_sync(0xffffffffu, snd.y, off)));
-}
 
 __device__ __forceinline__ void small_gk_cta(GkCtaSlot* sl, const int* __restrict__ n_act_cell,
                                              const int* __restrict__ act, const int* __restrict__ inv, int N, int K,
@@ -627,30 +624,34 @@ __device__ __forceinline__ void small_gk_cta(GkCtaSlot* sl, const int* __restric
       gk_reflector(al, sa, sigma, phs, tau);
       const float2 vj = f2(__fmaf_rn(phs.x, sigma, al.x), __fmaf_rn(phs.y, sigma, al.y));
       if (c > j && c < p) {
-        float2 s0 = f2(0.f, 0.f), s1 = s0;
+        // conj(v)^T m = (A.x + B.y, A.y - B.x) with A = sum v.x m, B = sum v.y m
+        float2 A = f2(0.f, 0.f), B = A;
 #pragma unroll
         for (int rb = 0; rb < 16; ++rb) {
           if (4 * rb + 3 < j || 4 * rb >= q) continue;
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             const int r = 4 * rb + t;
-            if (r == j) s0 = cadd_f(s0, cjmul_f(vj, m[r]));
-            else if (r > j && r < q) {
-              if (t & 1) s1 = cadd_f(s1, cjmul_f(sl->v[bf][r], m[r]));
-              else s0 = cadd_f(s0, cjmul_f(sl->v[bf][r], m[r]));
+            if (r >= j && r < q) {
+              const float2 vr = r == j ? vj : sl->v[bf][r];
+              A = f2(__fmaf_rn(vr.x, m[r].x, A.x), __fmaf_rn(vr.x, m[r].y, A.y));
+              B = f2(__fmaf_rn(vr.y, m[r].x, B.x), __fmaf_rn(vr.y, m[r].y, B.y));
             }
           }
         }
-        const float2 sm = cadd_f(s0, s1);
-        const float2 s = f2(__fmul_rn(sm.x, tau), __fmul_rn(sm.y, tau));
+        const float2 s = f2(__fmul_rn(__fadd_rn(A.x, B.y), tau), __fmul_rn(__fsub_rn(A.y, B.x), tau));
+        // m <- m - v s: re -= v.x s.x - v.y s.y, im -= v.x s.y + v.y s.x
 #pragma unroll
         for (int rb = 0; rb < 16; ++rb) {
           if (4 * rb + 3 < j || 4 * rb >= q) continue;
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             const int r = 4 * rb + t;
-            if (r == j) m[r] = csub_f(m[r], cmul_f(vj, s));
-            else if (r > j && r < q) m[r] = csub_f(m[r], cmul_f(sl->v[bf][r], s));
+            if (r >= j && r < q) {
+              const float2 vr = r == j ? vj : sl->v[bf][r];
+              m[r] = f2(__fmaf_rn(vr.y, s.y, __fmaf_rn(-vr.x, s.x, m[r].x)),
+                        __fmaf_rn(-vr.y, s.x, __fmaf_rn(-vr.x, s.y, m[r].y)));
+            }
           }
         }
       }
@@ -677,38 +678,39 @@ __device__ __forceinline__ void small_gk_cta(GkCtaSlot* sl, const int* __restric
       float2 phs;
       gk_reflector(az, sb, sigma, phs, tau);
       const float2 u = c == j + 1 ? f2(__fmaf_rn(phs.x, sigma, az.x), __fmaf_rn(phs.y, sigma, az.y)) : z;
-#pragma unroll
-      for (int H = 0; H < 2; ++H) {
-        if (32 * H + 31 <= j || 32 * H >= q) continue;
-        float2 k16[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int rl = 32 * H + t, rh = rl + 16;
-          const float2 plo = (rl > j && rl < q) ? cmul_f(m[rl], u) : f2(0.f, 0.f);
-          const float2 phi = (rh > j && rh < q) ? cmul_f(m[rh], u) : f2(0.f, 0.f);
-          k16[t] = rs_level(plo, phi, (lane & 16) != 0, 16);
-        }
-        float2 k8[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) k8[t] = rs_level(k16[t], k16[t + 8], (lane & 8) != 0, 8);
-        float2 k4[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) k4[t] = rs_level(k8[t], k8[t + 4], (lane & 4) != 0, 4);
-        float2 k2[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) k2[t] = rs_level(k4[t], k4[t + 2], (lane & 2) != 0, 2);
-        sl->xw[warp][32 * H + lane] = rs_level(k2[0], k2[1], (lane & 1) != 0, 1);
-      }
-      __syncthreads();
+      // row products m[r] u of the live columns
       if (c > j && c < p) {
-        const float2 tu = f2(__fmul_rn(tau, u.x), __fmul_rn(-tau, u.y));   // tau conj(u_c)
 #pragma unroll
         for (int rb = 0; rb < 16; ++rb) {
           if (4 * rb + 3 <= j || 4 * rb >= q) continue;
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             const int r = 4 * rb + t;
-            if (r > j && r < q) m[r] = csub_f(m[r], cmul_f(cadd_f(sl->xw[0][r], sl->xw[1][r]), tu));
+            if (r > j && r < q) sl->P[r][c] = cmul_f(m[r], u);
+          }
+        }
+      }
+      __syncthreads();
+      if (c > j && c < q) {
+        float2 x = f2(0.f, 0.f);
+        for (int cc = j + 1; cc < p; ++cc) x = cadd_f(x, sl->P[c][cc]);
+        sl->X[c] = x;
+      }
+      __syncthreads();
+      if (c > j && c < p) {
+        // m <- m - x w with w = tau conj(u_c)
+        const float2 wv = f2(__fmul_rn(tau, u.x), __fmul_rn(-tau, u.y));
+#pragma unroll
+        for (int rb = 0; rb < 16; ++rb) {
+          if (4 * rb + 3 <= j || 4 * rb >= q) continue;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int r = 4 * rb + t;
+            if (r > j && r < q) {
+              const float2 x = sl->X[r];
+              m[r] = f2(__fmaf_rn(x.y, wv.y, __fmaf_rn(-x.x, wv.x, m[r].x)),
+                        __fmaf_rn(-x.y, wv.x, __fmaf_rn(-x.x, wv.y, m[r].y)));
+            }
           }
         }
       }
