@@ -434,7 +434,8 @@ int idos_measure_fma_peak(int precision, int64_t iters, void* cuda_stream, doubl
  * whatever fits: 160 float32 / 112 float64) and, with the latter, the
  * persistent launch on or off (graphene, IDOS_FP32_REFINE64; on with graph
  * replay in each of the three placements below; off without graph replay),
- * then the winner with graph replay switched (unless
+ * then the winner's split +- 4 SMs where the partition alignment gives a size
+ * not yet timed, then the winner with graph replay switched (unless
  * the model gave graphs up), then the two-stage kernel shapes (the W tile,
  * one or two warps per sweep in clustered band chases, and 1, 2 or 4 CTAs
  * in the panel QR cluster).  Each candidate
@@ -446,7 +447,8 @@ int idos_measure_fma_peak(int precision, int64_t iters, void* cuda_stream, doubl
  * candidate's best step time. */
 #define IDOS_TUNE_MAX 56
 typedef struct idos_tuning {
-  int32_t sm_split;      /* chosen SMs reserved for the finest level (0 = shared) */
+  int32_t sm_split;      /* chosen SMs reserved for the finest level (0 = shared; the partition's
+                            actual size) */
   int32_t small_max_n;   /* chosen limit of the shared-memory kernel (-1 = what fits) */
   double best_ms;        /* step time of the chosen configuration */
   int32_t n_tried;

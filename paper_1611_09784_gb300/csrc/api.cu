@@ -1690,7 +1690,7 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
     out->tried_ms[i] = best;
     if (best < out->best_ms) {
       out->best_ms = best;
-      best_split = sp;
+      best_split = m->sm_split_now;
       best_small = sm;
       best_persist = pers;
       best_graph = m->graph;
@@ -1713,6 +1713,15 @@ int idos_autotune(idos_model* m, const int64_t* n_samples, int reps, idos_tuning
       if (rc != IDOS_OK) break;
     }
     if (rc != IDOS_OK) break;
+  }
+  // the split refined halfway between the grid's points, where the
+  // partition's alignment gives a size the grid has not timed
+  for (int d : {-4, 4}) {
+    if (rc != IDOS_OK || best_split <= 0 || out->n_tried >= IDOS_TUNE_MAX) break;
+    const int sp = best_split + d, got = partition_rounded(sp);
+    if (sp <= 0 || got >= m->sm_count || std::find(std::begin(splits), std::end(splits), got) != std::end(splits))
+      continue;
+    rc = time_config(sp, best_small, best_persist, best_graph, best_w, best_cp, best_ltf, best_pc, best_hl, best_pr);
   }
   // second stage, at the winner: graph replay switched, then the two-stage
   // kernel shapes (W on the tensor cores; one warp per sweep in clustered

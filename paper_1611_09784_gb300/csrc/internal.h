@@ -115,6 +115,7 @@ struct SmPartition {
   bool shared = false;   // owned by the process-wide cache (never destroyed by a model)
 };
 int partition_create(int big_sms, SmPartition& p);
+int partition_rounded(int big_sms);   // the SM count a request of big_sms rounds up to
 int partition_stream(const SmPartition& p, int which, int priority, cudaStream_t* out);
 void partition_destroy(SmPartition& p);
 

@@ -108,6 +108,22 @@ int partition_create_new(int big_sms, SmPartition& p) {
   return IDOS_OK;
 }
 
+// The SM count a partition of `big_sms` SMs rounds up to on this device (the
+// driver's co-scheduling alignment and minimum partition size); big_sms when
+// green contexts are not available.
+int partition_rounded(int big_sms) {
+  const GreenApi& g = api();
+  if (!g.ok || big_sms <= 0) return big_sms;
+  int ordinal = 0;
+  if (cudaGetDevice(&ordinal) != cudaSuccess) return big_sms;
+  CUdevice dev;
+  CUdevResource all;
+  if (g.device_get(&dev, ordinal) != CUDA_SUCCESS || g.get_resource(dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS)
+    return big_sms;
+  const int align = (int)std::max(1u, all.sm.smCoscheduledAlignment);
+  return std::max<int>((big_sms + align - 1) / align * align, (int)all.sm.minSmPartitionSize);
+}
+
 // One partition per (device, reserved SM count), created on first use and
 // kept for the life of the process: kernels are loaded into a context on
 // their first launch there, so models created later reuse warm contexts.
