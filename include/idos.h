@@ -73,7 +73,11 @@ enum idos_kind { IDOS_GRAPHENE = 0, IDOS_TMDC = 1 };
  * IDOS_FP32_REFINE64: reduction and Sturm bisection in float32, then
  *   refine64_iters float64 passes (Sturm count + Newton step each) on the
  *   float32 tridiagonal; the smoothing argument and every sum are float64,
- *   erfc is evaluated in float32. */
+ *   erfc is evaluated in float32.  Graphene matrices up to n = 128 are
+ *   reduced in the bidiagonal form of the block between the two sublattices
+ *   (H(k) = eps I + [[0, T], [T^H, 0]]): the tridiagonal handed to the
+ *   bisection has diagonal eps and off-diagonals the bidiagonal's entries,
+ *   with exactly the eigenvalues eps +- sigma_i(T) and |n_A - n_B| at eps. */
 enum idos_precision { IDOS_FP64 = 0, IDOS_FP32_REFINE64 = 1 };
 
 /* Smoothed step g of eq. (4.2).
