@@ -58,15 +58,18 @@ __device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20)
 // One float64 pass over (d, e^2) held in float64: count of eigenvalues below
 // x and the Newton step -p_n(x)/p_n'(x) of the characteristic polynomial.
 // Five float64 operations per row: t = d_i - x, p' = t p - b p_prev and
-// q' = t q - (b q_prev + p) as two fused pairs.
+// q' = t q - (b q_prev + p) as two fused pairs (four with CD: every d_i equal
+// to d_0 bit for bit, t formed once with the same value).
+template <bool CD>
 __device__ __forceinline__ int sturm_newton64(const double* __restrict__ d, const double* __restrict__ e2, int n,
                                               double x, double& step) {
-  double p0 = 1.0, p1 = d[0] - x;               // p_{i-1}, p_i
+  const double t0 = d[0] - x;
+  double p0 = 1.0, p1 = t0;                     // p_{i-1}, p_i
   double q0 = 0.0, q1 = -1.0;                   // derivatives
   if (dzero(p1)) p1 = -0x1p-1000;              // exact zero pivot counts as negative
   int cnt = dneg(p1);
   for (int i = 1; i < n; ++i) {
-    const double t = d[i] - x, b = e2[i - 1];
+    const double t = CD ? t0 : d[i] - x, b = e2[i - 1];
     double p2 = fma(t, p1, -(b * p0));
     const double q2 = fma(t, q1, -fma(b, q0, p1));
     if (dzero(p2)) p2 = -copysign(fmax(fabs(p1) * 0x1p-52, 0x1p-1000), p1);   // zero pivot -> negative
@@ -270,6 +273,7 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
   for (int i = tid; i < n; i += G) {
     const S di = d_in[mat * n_max + i];
     if constexpr (sizeof(S) == 4) cdiag = cdiag && __float_as_int(di) == __float_as_int(d_first);
+    else cdiag = cdiag && __double_as_longlong(di) == __double_as_longlong(d_first);
     const S ei = (i < n - 1) ? e2_in[mat * n_max + i] : S(0);
     // a non-finite entry means the reduction broke down: report it (status
     // bit 2) rather than return eigenvalues of a corrupted matrix
@@ -378,9 +382,11 @@ k_bisect(const S* __restrict__ d_in, const S* __restrict__ e2_in, const int* __r
       const double w = 64.0 * (double)FLT_EPSILON * fmax(fabs(glo), fabs(ghi)) + 1e-12;
       double lo = fmax(glo, (double)lo32 - w), hi = fmin(ghi, (double)hi32 + w);
       double st;
-      if (sturm_newton64(dd, ee, n, lo, st) > k) lo = glo;      // bracket lost: fall back
-      if (sturm_newton64(dd, ee, n, hi, st) < k + 1) hi = ghi;
-      const auto pass = [&](double x, double& step) { return sturm_newton64(dd, ee, n, x, step); };
+      const auto pass = [&](double x, double& step) {
+        return cdiag ? sturm_newton64<true>(dd, ee, n, x, step) : sturm_newton64<false>(dd, ee, n, x, step);
+      };
+      if (pass(lo, st) > k) lo = glo;      // bracket lost: fall back
+      if (pass(hi, st) < k + 1) hi = ghi;
       lam = isc * newton_polish(pass, k, lo, hi, 60);
     } else {
       float lo, hi;

@@ -320,6 +320,20 @@ __device__ __forceinline__ float2 cjmul_f(float2 a, float2 b) {   // conj(a) b
 __device__ __forceinline__ float2 cadd_f(float2 a, float2 b) { return f2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
 __device__ __forceinline__ float2 csub_f(float2 a, float2 b) { return f2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
 __device__ __forceinline__ float cabs2_f(float2 a, float acc) { return __fmaf_rn(a.x, a.x, __fmaf_rn(a.y, a.y, acc)); }
+// the same in float64 (the float64 path's bidiagonal form)
+__device__ __forceinline__ double2 cmul_f(double2 a, double2 b) {
+  return make_double2(__fma_rn(a.x, b.x, __dmul_rn(-a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ double2 cjmul_f(double2 a, double2 b) {
+  return make_double2(__fma_rn(a.x, b.x, __dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(-a.y, b.x)));
+}
+__device__ __forceinline__ double2 cadd_f(double2 a, double2 b) {
+  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 csub_f(double2 a, double2 b) {
+  return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ double cabs2_f(double2 a, double acc) { return __fma_rn(a.x, a.x, __fma_rn(a.y, a.y, acc)); }
 // Householder scalars for x = (alpha, rest): sigma = |x| (sigma2 = |x|^2),
 // phs = alpha / |alpha| (1 for alpha = 0), tau = 1 / (sigma (sigma + |alpha|));
 // v = x + phs sigma e_1 maps x to -phs sigma e_1.
@@ -339,17 +353,40 @@ __device__ __forceinline__ void gk_reflector(float2 al, float sigma2, float& sig
   sigma = __fmul_rn(sigma2, rsqrtf(sigma2));
   tau = __fdividef(1.f, __fmul_rn(sigma, __fadd_rn(sigma, aa)));
 }
+__device__ __forceinline__ void gk_reflector(double2 al, double sigma2, double& sigma, double2& phs, double& tau) {
+  const double s = fmax(fabs(al.x), fabs(al.y));
+  double aa = 0.0;
+  phs = make_double2(1.0, 0.0);
+  if (s > 0.0) {
+    const double ax = __ddiv_rn(al.x, s), ay = __ddiv_rn(al.y, s);
+    const double r = __dsqrt_rn(__fma_rn(ax, ax, __dmul_rn(ay, ay)));
+    phs = make_double2(__ddiv_rn(ax, r), __ddiv_rn(ay, r));
+    aa = __dmul_rn(s, r);
+  }
+  sigma = __dsqrt_rn(sigma2);
+  tau = __ddiv_rn(1.0, __dmul_rn(sigma, __dadd_rn(sigma, aa)));
+}
 
+__device__ __forceinline__ float gk_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double gk_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float gk_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double gk_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float gk_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double gk_add(double a, double b) { return __dadd_rn(a, b); }
+
+template <typename T>
 __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase, const int* __restrict__ n_act_cell,
                                               const int* __restrict__ act, const int* __restrict__ inv, int N, int K,
                                               int n_max, int64_t mat, double t_hop, double eps,
-                                              float* __restrict__ d_out, float* __restrict__ e2_out) {
+                                              T* __restrict__ d_out, T* __restrict__ e2_out) {
+  using C = c2<T>;
+  const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-300);
   const int K2 = K * K;
   const int64_t cell = mat / K2;
   const int kidx = (int)(mat - cell * K2);
   const int n = n_act_cell[cell];
-  float* dO = d_out + mat * n_max;
-  float* eO = e2_out + mat * n_max;
+  T* dO = d_out + mat * n_max;
+  T* eO = e2_out + mat * n_max;
   if (n <= 0) return;
   const int n_sites = 2 * N * N;
   const int* ac = act + cell * n_sites;
@@ -366,9 +403,9 @@ __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase,
   const int p = min(nA, nB), q = n - p;
   // column hl of M from the three bonds of its site (a bond to a removed
   // site is dropped; bonds to the same site add up)
-  float2 m[16];
+  C m[16];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) m[r] = f2(0.f, 0.f);
+  for (int r = 0; r < 16; ++r) m[r] = mk<T>(T(0), T(0));
   if (hl < p) {
     unsigned mm = colm;
     for (int t = 0; t < hl; ++t) mm &= mm - 1u;
@@ -381,9 +418,17 @@ __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase,
       const int ai = iv[nb[b]];
       if (ai >= 0 && ((rowm >> ai) & 1u)) {
         const int rw = __popc(rowm & ((1u << ai) - 1u));
-        const float2 ph = graphene_phase_f(N, K, kidx, b);
-        const float hx = __fmul_rn((float)t_hop, ph.x), hy = __fmul_rn((float)t_hop, ph.y);
-        const float2 hv = fromB ? f2(hx, hy) : f2(hx, -hy);   // H[row site][column site]
+        T hx, hy;
+        if constexpr (sizeof(T) == 4) {
+          const float2 ph = graphene_phase_f(N, K, kidx, b);
+          hx = gk_mul((float)t_hop, ph.x);
+          hy = gk_mul((float)t_hop, ph.y);
+        } else {
+          const double2 ph = graphene_phase(N, K, kidx, b);
+          hx = __dmul_rn(t_hop, ph.x);
+          hy = __dmul_rn(t_hop, ph.y);
+        }
+        const C hv = fromB ? mk<T>(hx, hy) : mk<T>(hx, -hy);   // H[row site][column site]
 #pragma unroll
         for (int r = 0; r < 16; ++r)
           if (r == rw) m[r] = cadd_f(m[r], hv);
@@ -392,8 +437,8 @@ __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase,
   }
   for (int j = 0; j < p; ++j) {
     // left reflector from column j (lane j), rows j .. q-1
-    float rest = 0.f;
-    float2 al = f2(0.f, 0.f);
+    T rest = T(0);
+    C al = mk<T>(T(0), T(0));
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       if (r == j) al = m[r];
@@ -402,28 +447,28 @@ __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase,
     rest = __shfl_sync(hmask, rest, hbase + j);
     al.x = __shfl_sync(hmask, al.x, hbase + j);
     al.y = __shfl_sync(hmask, al.y, hbase + j);
-    const float sa = cabs2_f(al, rest);
+    const T sa = cabs2_f(al, rest);
     if (hl == 0) eO[2 * j] = sa;
-    if (rest > 1e-30f) {
-      float sigma, tau;
-      float2 phs;
+    if (rest > tiny) {
+      T sigma, tau;
+      C phs;
       gk_reflector(al, sa, sigma, phs, tau);
-      float2 v[16];
+      C v[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
-        const float vx = __shfl_sync(hmask, m[r].x, hbase + j), vy = __shfl_sync(hmask, m[r].y, hbase + j);
-        v[r] = r == j ? f2(__fmaf_rn(phs.x, sigma, al.x), __fmaf_rn(phs.y, sigma, al.y))
-                      : (r > j && r < q ? f2(vx, vy) : f2(0.f, 0.f));
+        const T vx = __shfl_sync(hmask, m[r].x, hbase + j), vy = __shfl_sync(hmask, m[r].y, hbase + j);
+        v[r] = r == j ? mk<T>(gk_fma(phs.x, sigma, al.x), gk_fma(phs.y, sigma, al.y))
+                      : (r > j && r < q ? mk<T>(vx, vy) : mk<T>(T(0), T(0)));
       }
       if (hl > j && hl < p) {
-        float2 s0 = f2(0.f, 0.f), s1 = s0;
+        C s0 = mk<T>(T(0), T(0)), s1 = s0;
 #pragma unroll
         for (int r = 0; r < 16; r += 2) {
           s0 = cadd_f(s0, cjmul_f(v[r], m[r]));
           s1 = cadd_f(s1, cjmul_f(v[r + 1], m[r + 1]));
         }
-        const float2 sm = cadd_f(s0, s1);
-        const float2 s = f2(__fmul_rn(sm.x, tau), __fmul_rn(sm.y, tau));
+        const C sm = cadd_f(s0, s1);
+        const C s = mk<T>(gk_mul(sm.x, tau), gk_mul(sm.y, tau));
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
           m[r] = csub_f(m[r], cmul_f(v[r], s));
@@ -433,64 +478,64 @@ __device__ __forceinline__ void small_gk_half(int hl, unsigned hmask, int hbase,
     if (j + 1 >= p) break;
     // right reflector from row j, columns j+1 .. p-1 (lane c holds M[j][c]):
     // z = conj(row), H z = beta e_{j+1}, then M <- M H on rows j+1 .. q-1
-    float2 mj = f2(0.f, 0.f);
+    C mj = mk<T>(T(0), T(0));
 #pragma unroll
     for (int r = 0; r < 16; ++r)
       if (r == j) mj = m[r];
-    const float2 z = (hl > j && hl < p) ? f2(mj.x, -mj.y) : f2(0.f, 0.f);
-    float rz = hl > j + 1 ? cabs2_f(z, 0.f) : 0.f;
+    const C z = (hl > j && hl < p) ? mk<T>(mj.x, -mj.y) : mk<T>(T(0), T(0));
+    T rz = hl > j + 1 ? cabs2_f(z, T(0)) : T(0);
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) rz = __fadd_rn(rz, __shfl_xor_sync(hmask, rz, o));
-    float2 az;
+    for (int o = 8; o > 0; o >>= 1) rz = gk_add(rz, __shfl_xor_sync(hmask, rz, o));
+    C az;
     az.x = __shfl_sync(hmask, z.x, hbase + j + 1);
     az.y = __shfl_sync(hmask, z.y, hbase + j + 1);
-    const float sb = cabs2_f(az, rz);
+    const T sb = cabs2_f(az, rz);
     if (hl == 0) eO[2 * j + 1] = sb;
-    if (rz > 1e-30f) {
-      float sigma, tau;
-      float2 phs;
+    if (rz > tiny) {
+      T sigma, tau;
+      C phs;
       gk_reflector(az, sb, sigma, phs, tau);
-      const float2 u = hl == j + 1 ? f2(__fmaf_rn(phs.x, sigma, az.x), __fmaf_rn(phs.y, sigma, az.y)) : z;
+      const C u = hl == j + 1 ? mk<T>(gk_fma(phs.x, sigma, az.x), gk_fma(phs.y, sigma, az.y)) : z;
       // x_r = sum_c M[r][c] u_c: reduce-scatter (lane hl ends with row hl)
-      float2 k8[8];
+      C k8[8];
       const bool b3 = (hl & 8) != 0;
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        const float2 plo = (t > j && t < q) ? cmul_f(m[t], u) : f2(0.f, 0.f);
-        const float2 phi = (t + 8 > j && t + 8 < q) ? cmul_f(m[t + 8], u) : f2(0.f, 0.f);
-        const float2 snd = b3 ? plo : phi, kp = b3 ? phi : plo;
-        k8[t] = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 8), __shfl_xor_sync(hmask, snd.y, 8)));
+        const C plo = (t > j && t < q) ? cmul_f(m[t], u) : mk<T>(T(0), T(0));
+        const C phi = (t + 8 > j && t + 8 < q) ? cmul_f(m[t + 8], u) : mk<T>(T(0), T(0));
+        const C snd = b3 ? plo : phi, kp = b3 ? phi : plo;
+        k8[t] = cadd_f(kp, mk<T>(__shfl_xor_sync(hmask, snd.x, 8), __shfl_xor_sync(hmask, snd.y, 8)));
       }
-      float2 k4[4];
+      C k4[4];
       const bool b2 = (hl & 4) != 0;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const float2 snd = b2 ? k8[t] : k8[t + 4], kp = b2 ? k8[t + 4] : k8[t];
-        k4[t] = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 4), __shfl_xor_sync(hmask, snd.y, 4)));
+        const C snd = b2 ? k8[t] : k8[t + 4], kp = b2 ? k8[t + 4] : k8[t];
+        k4[t] = cadd_f(kp, mk<T>(__shfl_xor_sync(hmask, snd.x, 4), __shfl_xor_sync(hmask, snd.y, 4)));
       }
-      float2 k2[2];
+      C k2[2];
       const bool b1 = (hl & 2) != 0;
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const float2 snd = b1 ? k4[t] : k4[t + 2], kp = b1 ? k4[t + 2] : k4[t];
-        k2[t] = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 2), __shfl_xor_sync(hmask, snd.y, 2)));
+        const C snd = b1 ? k4[t] : k4[t + 2], kp = b1 ? k4[t + 2] : k4[t];
+        k2[t] = cadd_f(kp, mk<T>(__shfl_xor_sync(hmask, snd.x, 2), __shfl_xor_sync(hmask, snd.y, 2)));
       }
       const bool b0 = (hl & 1) != 0;
-      const float2 snd = b0 ? k2[0] : k2[1], kp = b0 ? k2[1] : k2[0];
-      const float2 X = cadd_f(kp, f2(__shfl_xor_sync(hmask, snd.x, 1), __shfl_xor_sync(hmask, snd.y, 1)));
-      const float2 tu = f2(__fmul_rn(tau, u.x), __fmul_rn(-tau, u.y));   // tau conj(u_c)
+      const C snd = b0 ? k2[0] : k2[1], kp = b0 ? k2[1] : k2[0];
+      const C X = cadd_f(kp, mk<T>(__shfl_xor_sync(hmask, snd.x, 1), __shfl_xor_sync(hmask, snd.y, 1)));
+      const C tu = mk<T>(gk_mul(tau, u.x), gk_mul(-tau, u.y));   // tau conj(u_c)
       const bool col = hl > j && hl < p;
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
-        const float2 x = f2(__shfl_sync(hmask, X.x, hbase + r), __shfl_sync(hmask, X.y, hbase + r));
+        const C x = mk<T>(__shfl_sync(hmask, X.x, hbase + r), __shfl_sync(hmask, X.y, hbase + r));
         if (col && r > j && r < q) {
           m[r] = csub_f(m[r], cmul_f(x, tu));
         }
       }
     }
   }
-  for (int r = hl; r < n; r += 16) dO[r] = (float)eps;
-  for (int r = max(0, 2 * p - 1) + hl; r < n - 1; r += 16) eO[r] = 0.f;
+  for (int r = hl; r < n; r += 16) dO[r] = (T)eps;
+  for (int r = max(0, 2 * p - 1) + hl; r < n - 1; r += 16) eO[r] = T(0);
 }
 
 // The same Golub-Kahan reduction for 32 < n <= 128 (graphene N = 5 .. 8, so
@@ -1538,11 +1583,35 @@ int run_small_ctareg(const SolveArgs& a) {
   return IDOS_OK;
 }
 
+// float64 graphene cell sets with n <= 32: the bidiagonal form, one matrix per
+// half-warp (the float32 cell sets take it inside k_small_tridiag_reg)
+__global__ void __launch_bounds__(32 * kRegWarps)
+k_small_gk_half64(const int* __restrict__ n_act_cell, const int* __restrict__ act, const int* __restrict__ inv, int N,
+                  int K, int n_max, int64_t n_mat, double t_hop, double eps, double* __restrict__ d_out,
+                  double* __restrict__ e2_out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4;
+  const int64_t mat = ((int64_t)blockIdx.x * kRegWarps + warp) * 2 + half;
+  if (mat >= n_mat) return;   // the half-warp leaves together
+  small_gk_half<double>(lane & 15, 0xFFFFu << (16 * half), 16 * half, n_act_cell, act, inv, N, K, n_max, mat, t_hop,
+                        eps, d_out, e2_out);
+}
+
 template <typename T>
 static int solve_small_t(const SolveArgs& a) {
   if constexpr (sizeof(T) == 4) {
     if (a.n_max <= 32) return run_small_reg(a);
     if (a.n_max <= kCR) return run_small_ctareg(a);
+  } else {
+    if (a.n_max <= 32 && !a.H && a.cells) {
+      const CellSet* c = a.cells;
+      const int64_t blocks = (a.n_mat + 2 * kRegWarps - 1) / (2 * kRegWarps);
+      ProfScope ps(KID_SMALL_TRIDIAG, a.stream);
+      k_small_gk_half64<<<(unsigned)blocks, 32 * kRegWarps, 0, a.stream>>>(
+          c->n_act, c->act, c->inv, c->N, a.Kside, a.n_max, a.n_mat, a.t, a.eps, reinterpret_cast<double*>(a.d),
+          reinterpret_cast<double*>(a.e2));
+      IDOS_CHECK_LAUNCH();
+      return IDOS_OK;
+    }
   }
   if (a.n_max <= 32) {
     // up to 4 matrices per CTA while they fit

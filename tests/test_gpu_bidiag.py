@@ -1,7 +1,8 @@
 """Graphene's matrices up to n = 128 in the bidiagonal form (eigenvalues eps
 +- the singular values of the block between the sublattices, |n_A - n_B| more
 at eps): its degenerate cases against the oracle's dense eigenvalues of H(k)
-and its IDoS, on both kernels (half-warp for n <= 32, 64-thread CTA above)."""
+and its IDoS, on both float32 kernels (half-warp for n <= 32, 64-thread CTA
+above) and the float64 half-warp kernel."""
 import numpy as np
 import pytest
 
@@ -35,10 +36,13 @@ def crafted_masks(N, rng):
     return out
 
 
+CASES = [("fp32", N) for N in (1, 2, 4, 5, 8)] + [("fp64", N) for N in (1, 2, 4)]
+
+
 @pytest.mark.parametrize("eps", [0.0, 0.37])
-@pytest.mark.parametrize("N", [1, 2, 4, 5, 8])
-def test_bidiagonal_degenerate_cells(N, eps):
-    w, cfg, prm = cfg_and_prm(precision="fp32", refine=1)
+@pytest.mark.parametrize("precision,N", CASES)
+def test_bidiagonal_degenerate_cells(precision, N, eps):
+    w, cfg, prm = cfg_and_prm(precision=precision, refine=1)
     cfg.update(eps_onsite=eps, tc_products=6)
     prm["eps_onsite"] = eps
     K = 2
