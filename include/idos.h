@@ -280,7 +280,9 @@ typedef struct idos_mlmc_opts {
                             finest (every level l > 0 with fewer levels) takes
                             max(4, ceil(pilot_samples sqrt(W_0/W_l))), W = flop model */
   int32_t work_model;    /* 0: W_l from the flop model sum n^3; 1: measured time */
-  int32_t max_rounds;    /* extra allocation rounds after the pilot (>= 1)       */
+  int32_t max_rounds;    /* eq. (2.7) rounds after the pilots (>= 1); with three or
+                            more levels also the most provisional rounds of the
+                            levels below the finest beside its pilot          */
   uint64_t seed;         /* generator key                                        */
 } idos_mlmc_opts;
 
